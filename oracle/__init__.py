@@ -1,0 +1,42 @@
+"""FP64 CPU oracle for the preconditioned primal-dual method (PDRQS1, Alg. 4) of
+"TV-regularized CT Reconstruction and Metal Artifact Reduction Using Inequality
+Constraints with Preconditioning" (C. Schiffer, 2018).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with
+the CUDA library (``paper_1810_03275_gb300``): the Radon pair is plain C
+(``radon_ref.c``), everything else is plain numpy in FP64, written step by step
+from the thesis.
+
+Parity status of each function is stated in its docstring; all are pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+"""
+from .radon import Geometry, rh_forward, rh_adjoint, rh_forward_entries, rh_adjoint_entries, build_oracle, num_threads
+from .pdrq_ref import (
+    grad,
+    div,
+    tv_norm,
+    lap_symbol,
+    freq_norm,
+    precond_symbol,
+    precond_apply,
+    prox_dual,
+    tv_project,
+    conj_data_term,
+    make_descriptors,
+    power_beta,
+    power_c,
+    power_start,
+    PDRQState,
+    pdrq_solve,
+    cp_solve,
+    diagnostics,
+)
+
+__all__ = [
+    "Geometry", "rh_forward", "rh_adjoint", "rh_forward_entries", "rh_adjoint_entries",
+    "build_oracle", "num_threads", "grad", "div", "tv_norm", "lap_symbol", "freq_norm",
+    "precond_symbol", "precond_apply", "prox_dual", "tv_project", "conj_data_term",
+    "make_descriptors", "power_beta", "power_c", "power_start", "PDRQState", "pdrq_solve", "cp_solve",
+    "diagnostics",
+]

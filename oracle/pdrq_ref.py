@@ -1,0 +1,343 @@
+"""FP64 numpy oracle for everything around R_h: the discrete gradient and
+divergence, the pointwise resolvents, the inverse-norm Fourier preconditioner,
+the power iterations, Alg. 4 (PDRQS1) and Alg. 1 (Chambolle-Pock).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows
+the thesis step by step, with library primitives (numpy FFT) as single steps;
+no fusion, no reordering.  Readings of passages where the thesis is silent,
+ambiguous or garbled are stated where they are used.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from .radon import Geometry, rh_adjoint, rh_forward
+
+
+# ----------------------------------------------------------------------------
+# Sec. 3.1: discrete gradient (forward differences, Neumann) and divergence
+# (backward differences, Dirichlet), div_h = -grad_h^*.
+# ----------------------------------------------------------------------------
+def grad(u: np.ndarray, h: float = 1.0):
+    """grad_h u = (d_x u, d_y u): (u[i+1,j]-u[i,j])/h for i < n-1, else 0; the
+    same along j.  Sec. 3.1."""
+    u = np.asarray(u, dtype=np.float64)
+    px = np.zeros_like(u)
+    py = np.zeros_like(u)
+    px[:-1, :] = (u[1:, :] - u[:-1, :]) / h
+    py[:, :-1] = (u[:, 1:] - u[:, :-1]) / h
+    return px, py
+
+
+def div(px: np.ndarray, py: np.ndarray, h: float = 1.0) -> np.ndarray:
+    """div_h p = (d_1(p) + d_2(p))/h with d_1 = p_1 at the first row, p_i - p_{i-1}
+    inside, -p_{n-1} at the last row (0-based: px[0], px[i]-px[i-1], -px[n-2]);
+    d_2 the same along j.  Sec. 3.1.  For n = 1 the gradient is the zero map and
+    so is its adjoint."""
+    px = np.asarray(px, dtype=np.float64)
+    py = np.asarray(py, dtype=np.float64)
+    n = px.shape[0]
+    d1 = np.zeros_like(px)
+    d2 = np.zeros_like(py)
+    if n >= 2:
+        d1[0, :] = px[0, :]
+        d1[1:n - 1, :] = px[1:n - 1, :] - px[0:n - 2, :]
+        d1[n - 1, :] = -px[n - 2, :]
+        d2[:, 0] = py[:, 0]
+        d2[:, 1:n - 1] = py[:, 1:n - 1] - py[:, 0:n - 2]
+        d2[:, n - 1] = -py[:, n - 2]
+    return (d1 + d2) / h
+
+
+def tv_norm(u: np.ndarray, h: float = 1.0) -> float:
+    """Isotropic ||grad_h u||_1 = sum sqrt(q1^2 + q2^2), Sec. 3.1."""
+    px, py = grad(u, h)
+    return float(np.sum(np.sqrt(px * px + py * py)))
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4.3 / 4.3.1 / 4.4: inverse-norm preconditioner
+#   M^{-1} y = F^{-1}( F(y) * ||xi||_eps / (sigma^2 c + (sigma tau)^2 F(kappa_Delta) ||xi||_eps) )
+# Readings: F(kappa_Delta)_{ij} = 4 sin^2(pi i/n) + 4 sin^2(pi j/n) (the printed
+# formula repeats i; the closed form of the periodic 5-point stencil has j);
+# ||xi|| is the norm of the wrapped signed angular frequency 2 pi (i~, j~)/n,
+# i~ in (-n/2, n/2]; eps > 0 is kept in the algorithm (Alg. 4 prints it without
+# eps, which would zero the mean mode).
+# ----------------------------------------------------------------------------
+def lap_symbol(n: int) -> np.ndarray:
+    """DFT of the periodic Laplacian stencil kappa_Delta, Sec. 4.3."""
+    s = np.sin(np.pi * np.arange(n) / n) ** 2
+    return 4.0 * s[:, None] + 4.0 * s[None, :]
+
+
+def freq_norm(n: int, eps: float) -> np.ndarray:
+    """||xi||_eps = sqrt(|xi|^2 + eps^2) on the DFT grid, Sec. 4.3.1."""
+    xi = 2.0 * np.pi * np.fft.fftfreq(n)
+    return np.sqrt(xi[:, None] ** 2 + xi[None, :] ** 2 + eps * eps)
+
+
+def precond_symbol(n: int, sigma: float, tau: float, c: float, eps: float) -> np.ndarray:
+    """Fourier multiplier of M^{-1} in Alg. 4."""
+    nrm = freq_norm(n, eps)
+    L = lap_symbol(n)
+    return nrm / (sigma * sigma * c + (sigma * tau) ** 2 * L * nrm)
+
+
+def precond_apply(y: np.ndarray, symbol: np.ndarray) -> np.ndarray:
+    """x = F^{-1}(F(y) * symbol) with the 2-D DFT (numpy FFT as one step)."""
+    return np.real(np.fft.ifft2(np.fft.fft2(np.asarray(y, dtype=np.float64)) * symbol))
+
+
+# ----------------------------------------------------------------------------
+# Sec. 3.3 / 3.5: pointwise resolvents.
+# Per-bin data term g_r(z) = (w_r/2)(z - a_r)^2 + I_[lo_r, hi_r](z).  By
+# Lemma lem_loc the resolvent of sigma*G1^* acts per bin, and by the Moreau
+# identity (Sec. 1.3) it is v - sigma * prox_{g_r/sigma}(v/sigma), where the
+# prox of a 1-D quadratic plus a box is the clipped unconstrained minimiser:
+#     (id + sigma d g_r^*)^{-1}(v) = v - sigma * clip((v + w a)/(sigma + w), lo, hi).
+# Special cases reproduce every resolvent printed in Sec. 3.3-3.5 (tested).
+# ----------------------------------------------------------------------------
+def prox_dual(v, sigma, w, a, lo, hi):
+    """Resolvent of sigma * g^* for the box-quadratic data term above."""
+    v = np.asarray(v, dtype=np.float64)
+    z = (v + w * a) / (sigma + w)
+    return v - sigma * np.clip(z, lo, hi)
+
+
+def tv_project(zx, zy, lam: float, tau: float):
+    """Projection onto the pointwise isotropic ball of radius lam/tau:
+    z / max(1, tau |z| / lam)  (Alg. 4; Sec. 3.3 for the unscaled ball)."""
+    zx = np.asarray(zx, dtype=np.float64)
+    zy = np.asarray(zy, dtype=np.float64)
+    if lam <= 0.0:
+        return np.zeros_like(zx), np.zeros_like(zy)
+    den = np.maximum(1.0, tau * np.sqrt(zx * zx + zy * zy) / lam)
+    return zx / den, zy / den
+
+
+def conj_data_term(t, w, a, lo, hi):
+    """g_r^*(t) = sup_{lo <= z <= hi} t z - (w/2)(z - a)^2 per bin (Lemma
+    lem_f_ast1 and its variants).  +inf where the supremum is unbounded."""
+    t = np.asarray(t, dtype=np.float64)
+    w = np.broadcast_to(np.asarray(w, dtype=np.float64), t.shape)
+    a = np.broadcast_to(np.asarray(a, dtype=np.float64), t.shape)
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), t.shape)
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), t.shape)
+    out = np.empty_like(t)
+    pos = w > 0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        zq = np.clip(a + t / np.where(pos, w, 1.0), lo, hi)
+        vq = t * zq - 0.5 * w * (zq - a) ** 2
+        zl = np.where(t > 0, hi, np.where(t < 0, lo, 0.0))
+        vl = np.where(t == 0, 0.0, t * zl)
+    out[pos] = vq[pos]
+    out[~pos] = vl[~pos]
+    return out
+
+
+def make_descriptors(f, metal_mask, delta: float, trace_ratio: float = 0.8):
+    """Per-bin data term (w, a, lo, hi) of problem (C_h) with the data tolerance:
+    off the metal trace  w = 1, a = f, [lo, hi] = [f - delta, f + delta]
+    (delta < 0: no box, the thesis's plain quadratic fit);
+    on the metal trace   w = 0, lo = C = trace_ratio * f, hi = +inf
+    (the inequality constraint R_h u >= C of Sec. 2.2 / 3.2 with the pointwise
+    threshold C = 0.8 f of Sec. 5.2)."""
+    f = np.asarray(f, dtype=np.float64)
+    m = np.asarray(metal_mask).astype(bool) if metal_mask is not None else np.zeros(f.shape, bool)
+    w = np.where(m, 0.0, 1.0)
+    a = np.where(m, 0.0, f)
+    if delta >= 0:
+        lo = np.where(m, trace_ratio * f, f - delta)
+        hi = np.where(m, np.inf, f + delta)
+    else:
+        lo = np.where(m, trace_ratio * f, -np.inf)
+        hi = np.full(f.shape, np.inf)
+    return w, a, lo, hi
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4.3 / 5.1: power iterations.
+# beta ~ ||R_h|| (the problem is solved with R_h/beta, f/beta, lambda/beta^2,
+# Sec. 5.1); c ~ 1.05 lambda_max(Mt^{-1} Rt^* Rt) with Mt = F^{-1}(1/||xi||_eps) F
+# (Sec. 4.3.1), iterated in the symmetric form Mt^{-1/2} Rt^* Rt Mt^{-1/2}.
+# Both run a fixed count from the same deterministic start: the R2
+# low-discrepancy pattern x_ij = frac(1/2 + i/g + j/g^2) - 1/2 (g the plastic
+# number), normalised.  (The all-ones image is orthogonal to the symmetric-broken
+# top eigenvectors of these operators and stalls below lambda_max.)
+# ----------------------------------------------------------------------------
+PLASTIC = 1.32471795724474602596
+
+
+def power_start(n: int) -> np.ndarray:
+    i = np.arange(n, dtype=np.float64)
+    x = np.mod(0.5 + i[:, None] / PLASTIC + i[None, :] / (PLASTIC * PLASTIC), 1.0) - 0.5
+    nx = np.linalg.norm(x)
+    return x / nx if nx > 0 else x
+
+
+def power_beta(geo: Geometry, iters: int = 50) -> float:
+    n = geo.n
+    x = power_start(n)
+    lam = 0.0
+    for _ in range(iters):
+        y = rh_adjoint(rh_forward(x, geo), geo)
+        lam = float(np.sum(x * y))
+        ny = float(np.linalg.norm(y))
+        if ny == 0.0:
+            return 0.0
+        x = y / ny
+    return float(np.sqrt(max(lam, 0.0)))
+
+
+def power_c(geo: Geometry, beta: float, eps: float, iters: int = 50, margin: float = 1.05) -> float:
+    n = geo.n
+    half = np.sqrt(freq_norm(n, eps))
+
+    def mhalf(x):
+        return np.real(np.fft.ifft2(np.fft.fft2(x) * half))
+
+    z = power_start(n)
+    lam = 0.0
+    for _ in range(iters):
+        x = mhalf(z)
+        y = mhalf(rh_adjoint(rh_forward(x, geo), geo) / (beta * beta))
+        lam = float(np.sum(z * y))
+        ny = float(np.linalg.norm(y))
+        if ny == 0.0:
+            return 0.0
+        z = y / ny
+    return margin * lam
+
+
+# ----------------------------------------------------------------------------
+# Alg. 4 (PDRQS1) for problem (C_h), with K = [R; tau grad] on the scaled problem.
+# ----------------------------------------------------------------------------
+@dataclass
+class PDRQState:
+    u: np.ndarray       # primal iterate (original scale of u; u is not rescaled)
+    Ru: np.ndarray      # cached Rt u = R_h u / beta (Sec. 4.4: R_h u is saved)
+    v1b: np.ndarray     # bar v_1 (sinogram)
+    v2bx: np.ndarray    # bar v_2 (two image planes)
+    v2by: np.ndarray
+    t1: Optional[np.ndarray] = None   # last resolvent outputs (dual certificates)
+    t2x: Optional[np.ndarray] = None
+    t2y: Optional[np.ndarray] = None
+    k: int = 0
+
+    @staticmethod
+    def zeros(geo: Geometry) -> "PDRQState":
+        n = geo.n
+        return PDRQState(np.zeros((n, n)), np.zeros(geo.sino_shape), np.zeros(geo.sino_shape),
+                         np.zeros((n, n)), np.zeros((n, n)))
+
+    def copy(self) -> "PDRQState":
+        c = lambda a: None if a is None else a.copy()
+        return PDRQState(self.u.copy(), self.Ru.copy(), self.v1b.copy(), self.v2bx.copy(),
+                         self.v2by.copy(), c(self.t1), c(self.t2x), c(self.t2y), self.k)
+
+
+def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, tau: float,
+               eps: float, beta: float, c: float, state: Optional[PDRQState] = None,
+               callback=None) -> PDRQState:
+    """Run ``iters`` iterations of Alg. 4 on the problem scaled by beta (Sec. 5.1).
+
+    desc = (w, a, lo, hi) per bin in the original scale (see make_descriptors).
+    One iteration, in the order of Alg. 4:
+        u_tmp = -sigma ( Rt^*(v1b + sigma Rt u) - tau div(v2b + sigma tau grad u) )
+        u_new = u + F^{-1}( F(u_tmp) * m )
+        v1 = v1b + sigma Rt u_new ;  v2 = v2b + sigma tau grad u_new
+        t1 = (id + sigma d G1^*)^{-1}(2 v1 - v1b) ;  v1b += t1 - v1
+        t2 = P_{lambda/tau}(2 v2 - v2b)           ;  v2b += t2 - v2
+        u  = u_new
+    with Rt = R_h/beta, lambda = alpha/beta^2 and the bounds of G1 divided by beta.
+    """
+    h = geo.h
+    w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
+    at, lot, hit = a / beta, lo / beta, hi / beta
+    lam = alpha / (beta * beta)
+    m = precond_symbol(geo.n, sigma, tau, c, eps)
+    st = PDRQState.zeros(geo) if state is None else state.copy()
+    for _ in range(iters):
+        y1 = st.v1b + sigma * st.Ru
+        gx, gy = grad(st.u, h)
+        y2x = st.v2bx + sigma * tau * gx
+        y2y = st.v2by + sigma * tau * gy
+        u_tmp = -sigma * (rh_adjoint(y1, geo) / beta - tau * div(y2x, y2y, h))
+        u_new = st.u + precond_apply(u_tmp, m)
+        Ru_new = rh_forward(u_new, geo) / beta
+        v1 = st.v1b + sigma * Ru_new
+        gx, gy = grad(u_new, h)
+        v2x = st.v2bx + sigma * tau * gx
+        v2y = st.v2by + sigma * tau * gy
+        t1 = prox_dual(2.0 * v1 - st.v1b, sigma, w, at, lot, hit)
+        st.v1b = st.v1b + t1 - v1
+        t2x, t2y = tv_project(2.0 * v2x - st.v2bx, 2.0 * v2y - st.v2by, lam, tau)
+        st.v2bx = st.v2bx + t2x - v2x
+        st.v2by = st.v2by + t2y - v2y
+        st.u, st.Ru = u_new, Ru_new
+        st.t1, st.t2x, st.t2y = t1, t2x, t2y
+        st.k += 1
+        if callback is not None:
+            callback(st)
+    return st
+
+
+def cp_solve(geo: Geometry, desc, alpha: float, iters: int, *, beta: float,
+             sigma: Optional[float] = None, tau: Optional[float] = None,
+             u0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Alg. 1 (Chambolle-Pock) for problem (C_h) on the same beta-scaled problem,
+    used only as an independent minimiser: (C_h) has a unique solution when R_h
+    is injective (Sec. 3.2), so Alg. 1 and Alg. 4 must agree there.  Notation of
+    Alg. 1: tau is the dual and sigma the primal step, sigma tau (||Rt||^2 + 8/h^2) < 1."""
+    h = geo.h
+    w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
+    at, lot, hit = a / beta, lo / beta, hi / beta
+    lam = alpha / (beta * beta)
+    L2 = 1.0 + 8.0 / (h * h)   # ||Rt|| = 1 up to the power-iteration estimate
+    if sigma is None or tau is None:
+        sigma = tau = 0.99 / np.sqrt(L2 * 1.02)
+    n = geo.n
+    u = np.zeros((n, n)) if u0 is None else np.array(u0, dtype=np.float64)
+    ub = u.copy()
+    v = np.zeros(geo.sino_shape)
+    wx = np.zeros((n, n))
+    wy = np.zeros((n, n))
+    for _ in range(iters):
+        gx, gy = grad(ub, h)
+        wbx, wby = wx + tau * gx, wy + tau * gy
+        vb = v + tau * rh_forward(ub, geo) / beta
+        wx, wy = tv_project(wbx, wby, lam, 1.0)
+        v = prox_dual(vb, tau, w, at, lot, hit)
+        u_new = u + sigma * div(wx, wy, h) - sigma * rh_adjoint(v, geo) / beta
+        ub = 2.0 * u_new - u
+        u = u_new
+    return u
+
+
+def diagnostics(geo: Geometry, desc, alpha: float, u: np.ndarray, *, beta: float = 1.0,
+                tau: float = 1.0, t1=None, t2x=None, t2y=None) -> dict:
+    """Objective of (C_h) in the original scale, its parts, the constraint
+    violation, and -- given dual certificates t = (t1, t2) of the beta-scaled
+    saddle problem -- the Fenchel-Young gap G(Ku) + G^*(t) - <Ku, t> (box
+    indicators left out; they are reported as the violation) and ||K^* t||."""
+    w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
+    Ru = rh_forward(u, geo)
+    data = 0.5 * float(np.sum(w * (Ru - a) ** 2))
+    tv = tv_norm(u, geo.h)
+    viol = float(max(0.0, np.max(lo - Ru, initial=0.0), np.max(Ru - hi, initial=0.0)))
+    out = {"objective": data + alpha * tv, "data_fit": data, "tv": tv, "violation": viol}
+    if t1 is not None:
+        lam = alpha / (beta * beta)
+        z = Ru / beta
+        at, lot, hit = a / beta, lo / beta, hi / beta
+        gz = 0.5 * w * (z - at) ** 2
+        g1 = float(np.sum(gz + conj_data_term(t1, w, at, lot, hit) - z * t1))
+        gx, gy = grad(u, geo.h)
+        g2 = float(np.sum(lam * np.sqrt(gx * gx + gy * gy) - tau * (gx * t2x + gy * t2y)))
+        kt = rh_adjoint(t1, geo) / beta - tau * div(t2x, t2y, geo.h)
+        out["gap"] = g1 + g2
+        out["dual_residual"] = float(np.linalg.norm(kt))
+    return out
