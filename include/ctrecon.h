@@ -1,0 +1,171 @@
+/*
+ * ctrecon -- GB300-native (sm_103a) preconditioned primal-dual TV-CT reconstruction
+ * with inequality constraints.
+ *
+ * C ABI of libctrecon.so.  Plain pointers and sizes only.  Every device pointer is
+ * owned by the caller and must hold the plan's element type (float for CTR_F32,
+ * double for CTR_F64) unless stated otherwise; images are row-major u[i*n + j]
+ * (first index i <-> x, second j <-> y), sinograms row-major g[l*M + k] (angle l,
+ * detector bin k).  All calls are asynchronous on `stream` (a cudaStream_t, NULL =
+ * the legacy default stream) except where a host output is returned, which
+ * synchronises that stream.  No call throws, aborts or traps: every error is a
+ * negative ctr_status with a message from ctr_last_error() (thread-local).
+ * A plan is not thread-safe: calls on one plan must not overlap.
+ *
+ * The method: "TV-regularized CT Reconstruction and Metal Artifact Reduction
+ * Using Inequality Constraints with Preconditioning" (C. Schiffer, 2018).
+ * Section/equation/algorithm numbers below refer to it.
+ */
+#ifndef CTRECON_H
+#define CTRECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CTR_OK = 0,
+    CTR_EINVAL = -1,        /* bad argument (null pointer, size, non-finite parameter) */
+    CTR_ENOMEM = -2,        /* device or host allocation failed (only in ctr_plan_create) */
+    CTR_ECUDA = -3,         /* a CUDA runtime call failed; message has the CUDA error string */
+    CTR_ETIMEOUT = -4,      /* a bounded device wait ran out (reported through a status word) */
+    CTR_ENUMERIC = -5,      /* NaN/Inf detected in diagnostics */
+    CTR_EUNSUPPORTED = -6   /* geometry/dtype outside the implemented range */
+} ctr_status;
+
+typedef enum { CTR_F32 = 0, CTR_F64 = 1, CTR_BF16 = 2 } ctr_dtype;
+
+/* Parallel-beam geometry of Sec. 3.1: n x n pixels of side h centred on the
+ * rotation axis (x_i = h (i - (n-1)/2)); n_angles angles theta_l (radians, any
+ * values); n_bins detector bins of width ds centred at s_k = (k - (n_bins-1)/2) ds.
+ * angles_host is copied by ctr_plan_create. */
+typedef struct {
+    int n;
+    int n_angles;
+    int n_bins;
+    double h;
+    double ds;
+    const double *angles_host;
+} ctr_geometry;
+
+typedef struct ctr_plan ctr_plan;   /* opaque: geometry tables + all device workspace */
+
+/* Solver parameters of Alg. 4 (PDRQS1).  ctr_default_params fills the defaults. */
+typedef struct {
+    double sigma;        /* step sigma > 0 (default 1) */
+    double tau;          /* gradient scaling tau > 0 (default 1/sqrt(8)) */
+    double eps;          /* ||xi||_eps regulariser of the inverse-norm preconditioner (default pi/n) */
+    double c;            /* preconditioner constant; <= 0: 1.05 x power iteration (Sec. 4.3.1) */
+    double beta;         /* problem scaling ~ ||R_h||; <= 0: power iteration (Sec. 5.1) */
+    int power_iters;     /* power-iteration steps for beta and c (default 50) */
+    double c_margin;     /* c = c_margin * lambda_max estimate (default 1.05) */
+    double trace_ratio;  /* metal-trace threshold C = trace_ratio * f (default 0.8, Sec. 5.2) */
+    int check_every;     /* diagnostics cadence; 0 = only after the last iteration */
+    int graph_block;     /* iterations per captured CUDA graph; 0 = plain launches (default 25) */
+} ctr_params;
+
+/* Diagnostics after the solve (original, unscaled problem unless noted). */
+typedef struct {
+    double beta;           /* scaling used */
+    double c;              /* preconditioner constant used */
+    double objective;      /* sum_r w_r/2 (R u - a)_r^2 + alpha TV(u) */
+    double data_fit;
+    double tv;             /* ||grad_h u||_1, isotropic */
+    double violation;      /* max_r max(lo_r - (R u)_r, (R u)_r - hi_r, 0) */
+    double gap;            /* Fenchel-Young gap G(Ku)+G*(t)-<Ku,t> of the beta-scaled problem (boxes excluded) */
+    double dual_residual;  /* ||K^* t||_2 of the beta-scaled problem */
+    double rel_change;     /* ||u_k - u_{k-1}|| / ||u_k|| */
+    int iters_done;
+} ctr_diag;
+
+/* Iterate state of Alg. 4 for warm start / checkpoint-resume; device buffers of the
+ * plan's dtype: u (n*n), Ru = R_h u / beta (N*M), v1b (N*M), v2b (2*n*n: x plane then
+ * y plane). */
+typedef struct {
+    void *u;
+    void *Ru;
+    void *v1b;
+    void *v2b;
+} ctr_state;
+
+/* Create a plan for `geo` computing in `dtype` (CTR_F32 or CTR_F64; CTR_BF16 stores
+ * sinogram and image operands of R_h/R_h^* in bfloat16 with FP32 accumulation).
+ * Allocates all device workspace on the current device; nothing is allocated later.
+ * Returns CTR_EINVAL for n < 1, n_angles < 1, n_bins < 1, h or ds <= 0 or a null
+ * angles_host; CTR_EUNSUPPORTED for n > 4096 or an FFT length with a prime factor
+ * other than 2 or 3, or ds/h > 2.5; CTR_ENOMEM if allocation fails. */
+ctr_status ctr_plan_create(const ctr_geometry *geo, ctr_dtype dtype, ctr_plan **out);
+void ctr_plan_destroy(ctr_plan *plan);
+void ctr_default_params(ctr_params *p);
+const char *ctr_last_error(void);
+/* Bytes of device memory the plan holds. */
+size_t ctr_plan_device_bytes(const ctr_plan *plan);
+/* Number of this library's kernels the plan has launched so far (kernels replayed
+ * inside CUDA graphs included). */
+unsigned long long ctr_plan_launch_count(const ctr_plan *plan);
+
+/* g = R_h u, the discrete Radon transform of Sec. 3.1 (the adjoint of linear
+ * backprojection): bin k of angle l gets sum_ij u_ij Lambda(p_ijl - k) with
+ * p = (x_i cos theta_l + y_j sin theta_l)/ds + (M-1)/2 and the hat
+ * Lambda(t) = max(0, 1 - |t|).  u_dev: n*n, g_dev: N*M (overwritten).
+ * Ray-driven gather (no atomics); exact transpose of rh_adjoint. */
+ctr_status rh_forward(ctr_plan *plan, const void *u_dev, void *g_dev, void *stream);
+
+/* rh_forward for a caller that also holds the transposed image uT_dev[j*n + i] =
+ * u[i*n + j] (the layout the solver keeps): one kernel launch, no workspace use.
+ * Angles with |cos| >= |sin| read uT, the others read u. */
+ctr_status rh_forward_t(ctr_plan *plan, const void *u_dev, const void *uT_dev, void *g_dev, void *stream);
+
+/* u = R_h^* g, linear backprojection (Sec. 3.1, definition of R_h^*): pixel (i,j)
+ * gets sum_l of g linearly interpolated at p_ijl.  g_dev: N*M, u_dev: n*n
+ * (overwritten).  Pixel-driven gather. */
+ctr_status rh_adjoint(ctr_plan *plan, const void *g_dev, void *u_dev, void *stream);
+
+/* x = M^{-1} y, the inverse-norm Fourier preconditioner of Alg. 4 (Sec. 4.3.1, 4.4):
+ * x = F^{-1}( F(y) ||xi||_eps / (sigma^2 c + (sigma tau)^2 L ||xi||_eps) ),
+ * L_ij = 4 sin^2(pi i/n) + 4 sin^2(pi j/n), xi = 2 pi (i~, j~)/n wrapped.
+ * Uses params->sigma, tau, eps, c (c must be > 0).  y_dev, x_dev: n*n (may alias). */
+ctr_status precond_apply(ctr_plan *plan, const ctr_params *params, const void *y_dev,
+                         void *x_dev, void *stream);
+
+/* Solve problem (C_h) (Sec. 3.2, with the data tolerance) by `iters` iterations of
+ * Alg. 4 (PDRQS1) from u = 0:
+ *   min_u  sum_{r off trace} 1/2 ((R_h u)_r - f_r)^2 + alpha ||grad_h u||_1
+ *   s.t.   |(R_h u)_r - f_r| <= delta off the metal trace (delta < 0: no bound),
+ *          (R_h u)_r >= trace_ratio * f_r on the trace (metal_mask_dev[r] != 0).
+ * f_dev: N*M data; metal_mask_dev: N*M bytes or NULL (no trace); u_out_dev: n*n.
+ * beta and c come from power iterations unless given in params (NULL = defaults).
+ * diag_out (host, may be NULL) is filled after an internal sync of `stream`. */
+ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_mask_dev,
+                       double alpha, double delta, int iters, const ctr_params *params,
+                       void *u_out_dev, ctr_diag *diag_out, void *stream);
+
+/* General form: per-bin data term g_r(z) = w_r/2 (z - a_r)^2 + I_[lo_r, hi_r](z) given
+ * by four device arrays of N*M (original scale, +-inf allowed in lo/hi), which covers
+ * every resolvent variant of Sec. 3.3-3.5.  `state` (may be NULL) holds the start on
+ * entry (NULL: zeros) and the final iterate on exit; u_out_dev (may be NULL if state
+ * is given) receives u.  Iterations are counted from the state given. */
+ctr_status tv_pd_run(ctr_plan *plan, const void *w_dev, const void *a_dev, const void *lo_dev,
+                     const void *hi_dev, double alpha, int iters, const ctr_params *params,
+                     ctr_state *state, void *u_out_dev, ctr_diag *diag_out, void *stream);
+
+/* Power iterations of Sec. 4.3 / 5.1 from the fixed R2 start pattern
+ * x_ij = frac(1/2 + i/g + j/g^2) - 1/2 (g the plastic number): beta ~ ||R_h||
+ * (iters steps on R_h^* R_h) and lambda_max(Mt^{-1} Rt^* Rt) with Rt = R_h/beta,
+ * Mt = F^{-1}(1/||xi||_eps) F.  Host outputs; synchronises `stream`. */
+ctr_status ctr_power_beta(ctr_plan *plan, int iters, double *beta_out, void *stream);
+ctr_status ctr_power_lambda(ctr_plan *plan, double beta, double eps, int iters,
+                            double *lambda_out, void *stream);
+
+/* grad_h (forward differences, Neumann; Sec. 3.1): u (n*n) -> p (2*n*n, x then y). */
+ctr_status ctr_grad(ctr_plan *plan, const void *u_dev, void *p_dev, void *stream);
+/* div_h = -grad_h^* (backward differences, Dirichlet; Sec. 3.1): p (2*n*n) -> d (n*n). */
+ctr_status ctr_div(ctr_plan *plan, const void *p_dev, void *d_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTRECON_H */

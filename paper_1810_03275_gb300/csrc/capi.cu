@@ -1,0 +1,508 @@
+// The C ABI of libctrecon (declared in include/ctrecon.h): argument checking,
+// plan construction (fixed-point geometry tables, FFT plan, device workspace),
+// dtype dispatch and stream handling.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctr_internal.cuh"
+
+namespace ctr {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+ctr_status fail(ctr_status st, const std::string &msg)
+{
+    set_error(msg);
+    return st;
+}
+
+ctr_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return CTR_ECUDA;
+}
+
+// implemented in solver.cu
+template <typename T> ctr_status dot2(ctr_plan *, const T *, const T *, size_t, double *, cudaStream_t);
+template <typename T> ctr_status op_grad(ctr_plan *, const T *, T *, cudaStream_t);
+template <typename T> ctr_status op_div(ctr_plan *, const T *, T *, cudaStream_t);
+template <typename T> ctr_status op_forward(ctr_plan *, const T *, const T *, T *, double, cudaStream_t);
+template <typename T> ctr_status op_adjoint(ctr_plan *, const T *, T *, double, cudaStream_t);
+template <typename T> ctr_status power_beta(ctr_plan *, int, double *, cudaStream_t);
+template <typename T> ctr_status power_lambda(ctr_plan *, double, double, int, double *, cudaStream_t);
+template <typename T>
+ctr_status pdrq_loop(ctr_plan *, double, int, const ctr_params &, double, double, ctr_diag *, cudaStream_t);
+template <typename T>
+ctr_status build_desc_from_data(ctr_plan *, const T *, const uint8_t *, double, double, double, cudaStream_t);
+template <typename T>
+ctr_status build_desc_from_arrays(ctr_plan *, const T *, const T *, const T *, const T *, double, cudaStream_t);
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+ctr_status alloc(ctr_plan *p, void **ptr, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(CTR_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    p->allocations.push_back(*ptr);
+    p->bytes += bytes;
+    return CTR_OK;
+}
+
+long long floor_div2(__int128 v)
+{
+    __int128 q = v / 2;
+    if (q * 2 > v) --q;
+    return (long long)q;
+}
+
+ctr_status build_tables(ctr_plan *p)
+{
+    const int n = p->n, N = p->N, M = p->M;
+    std::vector<AngleGeom> geo(N);
+    std::vector<AngleMarch> mar(N);
+    const double ratio = p->h / p->ds;
+    const long long one = 1ll << p->F;
+    long long wmax = 0;
+    int ncand = 1;
+    for (int l = 0; l < N; ++l) {
+        const double th = p->theta[l];
+        const long long C = llround(ldexp(ratio * cos(th), p->F));
+        const long long S = llround(ldexp(ratio * sin(th), p->F));
+        // O: P(i, j) = i C + j S + O with p = (x_i cos + y_j sin)/ds + (M-1)/2, x_i = h(i - (n-1)/2)
+        const __int128 num = ((__int128)(M - 1) << p->F) - (__int128)(n - 1) * ((__int128)C + (__int128)S);
+        const long long O = floor_div2(num);
+        geo[l] = AngleGeom{C, S, O};
+        const long long aC = C < 0 ? -C : C, aS = S < 0 ? -S : S;
+        if (aC == 0 && aS == 0) return fail(CTR_EINVAL, "degenerate geometry (h/ds too small)");
+        const long long w = ((31 * aC + 31 * aS) >> p->F) + 2;
+        if (w > wmax) wmax = w;
+        AngleMarch am{};
+        if (aC >= aS) {
+            am.layout = 0;   // pick along i (x), march along j
+            if (C > 0) { am.A = C; am.Op = O; am.flip = 0; }
+            else { am.A = -C; am.Op = O + (long long)(n - 1) * C; am.flip = 1; }
+            am.B = S;
+        } else {
+            am.layout = 1;   // pick along j (y), march along i
+            if (S > 0) { am.A = S; am.Op = O; am.flip = 0; }
+            else { am.A = -S; am.Op = O + (long long)(n - 1) * S; am.flip = 1; }
+            am.B = C;
+        }
+        am.kA = (double)one / (double)am.A;
+        am.oA = (double)am.Op / (double)am.A;
+        am.bA = (double)am.B / (double)am.A;
+        mar[l] = am;
+        const long long nc = (one + am.A - 1) / am.A;
+        if (nc > ncand) ncand = (int)nc;
+    }
+    if (ncand > 4) return fail(CTR_EUNSUPPORTED, "ds/h too large for the ray-driven projector (more than 4 pixels per bin and row)");
+    p->ncand = ncand;
+    p->wstride = (int)wmax;
+    CTR_CUDA(cudaMemcpy(p->d_geom, geo.data(), sizeof(AngleGeom) * N, cudaMemcpyHostToDevice));
+    CTR_CUDA(cudaMemcpy(p->d_march, mar.data(), sizeof(AngleMarch) * N, cudaMemcpyHostToDevice));
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status build_twiddles(ctr_plan *p)
+{
+    const int n = p->n;
+    std::vector<T> tw(2 * (size_t)n);
+    const double pi = 3.14159265358979323846;
+    for (int t = 0; t < n; ++t) {
+        tw[2 * t] = (T)cos(2.0 * pi * t / n);
+        tw[2 * t + 1] = (T)(-sin(2.0 * pi * t / n));
+    }
+    CTR_CUDA(cudaMemcpy(p->d_twiddle, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice));
+    return CTR_OK;
+}
+
+void destroy(ctr_plan *p)
+{
+    if (!p) return;
+    for (void *a : p->allocations) cudaFree(a);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+    delete p;
+}
+
+ctr_status check_params(const ctr_params &q)
+{
+    if (!(q.sigma > 0) || !(q.tau > 0) || !std::isfinite(q.sigma) || !std::isfinite(q.tau))
+        return fail(CTR_EINVAL, "sigma and tau must be finite and > 0");
+    if (!(q.eps > 0) || !std::isfinite(q.eps)) return fail(CTR_EINVAL, "eps must be finite and > 0");
+    if (!std::isfinite(q.c) || !std::isfinite(q.beta)) return fail(CTR_EINVAL, "c and beta must be finite");
+    if (q.power_iters < 1) return fail(CTR_EINVAL, "power_iters must be >= 1");
+    if (!(q.c_margin >= 1.0)) return fail(CTR_EINVAL, "c_margin must be >= 1");
+    if (!std::isfinite(q.trace_ratio)) return fail(CTR_EINVAL, "trace_ratio must be finite");
+    if (q.graph_block < 0 || q.check_every < 0) return fail(CTR_EINVAL, "graph_block and check_every must be >= 0");
+    return CTR_OK;
+}
+
+ctr_params resolve(const ctr_plan *p, const ctr_params *prm)
+{
+    ctr_params q;
+    ctr_default_params(&q);
+    if (prm) q = *prm;
+    if (!(q.eps > 0)) q.eps = 3.14159265358979323846 / p->n;
+    return q;
+}
+
+// Join the caller's stream to the plan's internal stream and back.
+struct StreamJoin {
+    ctr_plan *p;
+    cudaStream_t user;
+    bool joined = false;
+    StreamJoin(ctr_plan *pp, void *s) : p(pp), user((cudaStream_t)s) {}
+    ctr_status begin()
+    {
+        CTR_CUDA(cudaEventRecord(p->ev_in, user));
+        CTR_CUDA(cudaStreamWaitEvent(p->stream, p->ev_in, 0));
+        joined = true;
+        return CTR_OK;
+    }
+    ~StreamJoin()
+    {
+        if (joined) {
+            cudaEventRecord(p->ev_out, p->stream);
+            cudaStreamWaitEvent(user, p->ev_out, 0);
+        }
+    }
+};
+
+template <typename T>
+ctr_status solve_impl(ctr_plan *p, const void *f, const uint8_t *mask, const void *w, const void *a, const void *lo,
+                      const void *hi, double alpha, double delta, int iters, const ctr_params &q, ctr_state *state,
+                      void *u_out, ctr_diag *diag, void *stream)
+{
+    StreamJoin sj(p, stream);
+    ctr_status st = sj.begin();
+    if (st != CTR_OK) return st;
+    cudaStream_t s = p->stream;
+    double beta = q.beta;
+    if (!(beta > 0)) {
+        if ((st = power_beta<T>(p, q.power_iters, &beta, s)) != CTR_OK) return st;
+        if (!(beta > 0)) return fail(CTR_ENUMERIC, "power iteration gave ||R_h|| = 0");
+    }
+    double c = q.c;
+    if (!(c > 0)) {
+        double lam = 0;
+        if ((st = power_lambda<T>(p, beta, q.eps, q.power_iters, &lam, s)) != CTR_OK) return st;
+        c = q.c_margin * lam;
+        if (!(c > 0)) return fail(CTR_ENUMERIC, "power iteration gave c <= 0");
+    }
+    if (f) st = build_desc_from_data<T>(p, (const T *)f, mask, delta, q.trace_ratio, beta, s);
+    else st = build_desc_from_arrays<T>(p, (const T *)w, (const T *)a, (const T *)lo, (const T *)hi, beta, s);
+    if (st != CTR_OK) return st;
+    const size_t nn = (size_t)p->n * p->n, nm = (size_t)p->N * p->M;
+    if (state) {
+        CTR_CUDA(cudaMemcpyAsync(p->u, state->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->Ru, state->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->v1b, state->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->v2b, state->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    } else {
+        CTR_CUDA(cudaMemsetAsync(p->u, 0, nn * sizeof(T), s));
+        CTR_CUDA(cudaMemsetAsync(p->Ru, 0, nm * sizeof(T), s));
+        CTR_CUDA(cudaMemsetAsync(p->v1b, 0, nm * sizeof(T), s));
+        CTR_CUDA(cudaMemsetAsync(p->v2b, 0, 2 * nn * sizeof(T), s));
+    }
+    ctr_diag local{};
+    if ((st = pdrq_loop<T>(p, alpha, iters, q, beta, c, diag ? &local : nullptr, s)) != CTR_OK) return st;
+    if (state) {
+        CTR_CUDA(cudaMemcpyAsync(state->u, p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(state->Ru, p->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(state->v1b, p->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(state->v2b, p->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    if (u_out) CTR_CUDA(cudaMemcpyAsync(u_out, p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (diag) {
+        *diag = local;
+        diag->beta = beta;
+        diag->c = c;
+    }
+    return CTR_OK;
+}
+
+}  // namespace
+}  // namespace ctr
+
+using namespace ctr;
+
+extern "C" {
+
+const char *ctr_last_error(void) { return g_last_error.c_str(); }
+
+void ctr_default_params(ctr_params *q)
+{
+    if (!q) return;
+    q->sigma = 1.0;
+    q->tau = 1.0 / std::sqrt(8.0);
+    q->eps = 0.0;          // resolved to pi/n
+    q->c = 0.0;
+    q->beta = 0.0;
+    q->power_iters = 50;
+    q->c_margin = 1.05;
+    q->trace_ratio = 0.8;
+    q->check_every = 0;
+    q->graph_block = 25;
+}
+
+size_t ctr_plan_device_bytes(const ctr_plan *p) { return p ? p->bytes : 0; }
+
+ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **out)
+{
+    if (!out) return fail(CTR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(CTR_EINVAL, "geometry is NULL");
+    if (g->n < 1 || g->n_angles < 1 || g->n_bins < 1) return fail(CTR_EINVAL, "n, n_angles and n_bins must be >= 1");
+    if (!(g->h > 0) || !(g->ds > 0) || !std::isfinite(g->h) || !std::isfinite(g->ds))
+        return fail(CTR_EINVAL, "h and ds must be finite and > 0");
+    if (!g->angles_host) return fail(CTR_EINVAL, "angles_host is NULL");
+    if (g->n > 4096) return fail(CTR_EUNSUPPORTED, "n > 4096");
+    if (g->n_angles > 65535) return fail(CTR_EUNSUPPORTED, "more than 65535 angles");
+    if (g->ds / g->h > 2.5) return fail(CTR_EUNSUPPORTED, "ds/h > 2.5");
+    if (dtype != CTR_F32 && dtype != CTR_F64) return fail(CTR_EUNSUPPORTED, "dtype not supported by this build");
+    for (int l = 0; l < g->n_angles; ++l)
+        if (!std::isfinite(g->angles_host[l])) return fail(CTR_EINVAL, "non-finite angle");
+    const double pmax = g->n_bins + 4.0 + 2.0 * g->n * (g->h / g->ds);
+    ctr_plan *p = new (std::nothrow) ctr_plan();
+    if (!p) return fail(CTR_ENOMEM, "host allocation failed");
+    p->n = g->n;
+    p->N = g->n_angles;
+    p->M = g->n_bins;
+    p->h = g->h;
+    p->ds = g->ds;
+    p->dtype = dtype;
+    p->theta.assign(g->angles_host, g->angles_host + g->n_angles);
+    if (dtype == CTR_F64) {
+        int F = 62 - (int)std::ceil(std::log2(pmax));
+        p->F = F > 48 ? 48 : F;
+        p->esize = 8;
+    } else {
+        p->F = 32;
+        p->esize = 4;
+        if (pmax > (double)(1 << 28)) { destroy(p); return fail(CTR_EUNSUPPORTED, "geometry too large"); }
+    }
+    ctr_status st = fft_radices(p->n, p->radices);
+    p->fft_ok = (st == CTR_OK);
+    if (!p->fft_ok) p->radices.clear();
+    st = CTR_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { destroy(p); return fail(CTR_ECUDA, "no CUDA device"); }
+    const size_t nn = (size_t)p->n * p->n, nm = (size_t)p->N * p->M, es = p->esize;
+    p->red_blocks = 1024;
+#define ALLOC(ptr, bytes)                                          \
+    do {                                                           \
+        void *tmp_ = nullptr;                                      \
+        if ((st = alloc(p, &tmp_, (bytes))) != CTR_OK) {           \
+            destroy(p);                                            \
+            return st;                                             \
+        }                                                          \
+        ptr = (decltype(ptr))tmp_;                                 \
+    } while (0)
+    ALLOC(p->d_geom, sizeof(AngleGeom) * p->N);
+    ALLOC(p->d_march, sizeof(AngleMarch) * p->N);
+    ALLOC(p->d_twiddle, 2 * es * p->n);
+    ALLOC(p->uT, es * nn);
+    ALLOC(p->cbuf, 2 * es * nn);
+    ALLOC(p->sym, es * nn);
+    ALLOC(p->symh, es * nn);
+    ALLOC(p->u, es * nn);
+    ALLOC(p->du, es * nn);
+    ALLOC(p->x, es * nn);
+    ALLOC(p->xt, es * nn);
+    ALLOC(p->y2, 2 * es * nn);
+    ALLOC(p->v2b, 2 * es * nn);
+    ALLOC(p->t2, 2 * es * nn);
+    ALLOC(p->y1, es * nm);
+    ALLOC(p->Ru, es * nm);
+    ALLOC(p->v1b, es * nm);
+    ALLOC(p->t1, es * nm);
+    ALLOC(p->gs, es * nm);
+    ALLOC(p->desc, 4 * es * nm);
+    ALLOC(p->d_red, sizeof(double) * 8 * p->red_blocks);
+    ALLOC(p->d_scal, sizeof(double) * 64);
+#undef ALLOC
+    if ((st = build_tables(p)) != CTR_OK) { destroy(p); return st; }
+    st = (dtype == CTR_F64) ? build_twiddles<double>(p) : build_twiddles<float>(p);
+    if (st != CTR_OK) { destroy(p); return st; }
+    st = (dtype == CTR_F64) ? configure_radon<double>(p) : configure_radon<float>(p);
+    if (st == CTR_OK) st = (dtype == CTR_F64) ? configure_fft<double>(p) : configure_fft<float>(p);
+    if (st != CTR_OK) { destroy(p); return st; }
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        destroy(p);
+        return fail(CTR_ECUDA, "stream/event creation failed");
+    }
+    *out = p;
+    return CTR_OK;
+}
+
+void ctr_plan_destroy(ctr_plan *p)
+{
+    if (!p) return;
+    DeviceGuard dg(p->device);
+    cudaDeviceSynchronize();
+    destroy(p);
+}
+
+#define CTR_DISPATCH(p, call_f32, call_f64) ((p)->dtype == CTR_F64 ? (call_f64) : (call_f32))
+#define CTR_GUARD(p)                                                                  \
+    if (!(p)) return fail(CTR_EINVAL, "plan is NULL");                                \
+    DeviceGuard dg_((p)->device);                                                     \
+    if (!dg_.ok) return fail(CTR_ECUDA, "cannot select the plan's device");
+
+ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
+{
+    CTR_GUARD(p);
+    if (!u || !g) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctr_status st;
+    if (p->dtype == CTR_F64) {
+        if ((st = launch_transpose<double>(p, (const double *)u, (double *)p->uT, s)) != CTR_OK) return st;
+        return op_forward<double>(p, (const double *)u, (const double *)p->uT, (double *)g, 1.0, s);
+    }
+    if ((st = launch_transpose<float>(p, (const float *)u, (float *)p->uT, s)) != CTR_OK) return st;
+    return op_forward<float>(p, (const float *)u, (const float *)p->uT, (float *)g, 1.0, s);
+}
+
+ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, void *stream)
+{
+    CTR_GUARD(p);
+    if (!u || !uT || !g) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, op_forward<float>(p, (const float *)u, (const float *)uT, (float *)g, 1.0, s),
+                        op_forward<double>(p, (const double *)u, (const double *)uT, (double *)g, 1.0, s));
+}
+
+unsigned long long ctr_plan_launch_count(const ctr_plan *p) { return p ? p->launches : 0ull; }
+
+ctr_status rh_adjoint(ctr_plan *p, const void *g, void *u, void *stream)
+{
+    CTR_GUARD(p);
+    if (!u || !g) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, op_adjoint<float>(p, (const float *)g, (float *)u, 1.0, s),
+                        op_adjoint<double>(p, (const double *)g, (double *)u, 1.0, s));
+}
+
+ctr_status precond_apply(ctr_plan *p, const ctr_params *prm, const void *y, void *x, void *stream)
+{
+    CTR_GUARD(p);
+    if (!prm || !y || !x) return fail(CTR_EINVAL, "null argument");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = check_params(q);
+    if (st != CTR_OK) return st;
+    if (!(q.c > 0)) return fail(CTR_EINVAL, "precond_apply needs c > 0");
+    if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->dtype == CTR_F64) {
+        if ((st = launch_symbols<double>(p, q.sigma, q.tau, q.c, q.eps, s)) != CTR_OK) return st;
+        return launch_circulant<double>(p, (const double *)y, false, (const double *)p->sym, (double *)x, 0, nullptr, nullptr, s);
+    }
+    if ((st = launch_symbols<float>(p, q.sigma, q.tau, q.c, q.eps, s)) != CTR_OK) return st;
+    return launch_circulant<float>(p, (const float *)y, false, (const float *)p->sym, (float *)x, 0, nullptr, nullptr, s);
+}
+
+static ctr_status validate_solve(ctr_plan *p, double alpha, int iters, const ctr_params &q)
+{
+    if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
+    if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(CTR_EINVAL, "alpha must be finite and >= 0");
+    if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
+    (void)p;
+    return check_params(q);
+}
+
+ctr_status tv_pd_solve(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,
+                       const ctr_params *prm, void *u_out, ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
+    if (std::isnan(delta)) return fail(CTR_EINVAL, "delta is NaN");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, iters, q);
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p,
+                        solve_impl<float>(p, f, mask, nullptr, nullptr, nullptr, nullptr, alpha, delta, iters, q, nullptr, u_out, diag, stream),
+                        solve_impl<double>(p, f, mask, nullptr, nullptr, nullptr, nullptr, alpha, delta, iters, q, nullptr, u_out, diag, stream));
+}
+
+ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, const void *hi, double alpha, int iters,
+                     const ctr_params *prm, ctr_state *state, void *u_out, ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!w || !a || !lo || !hi) return fail(CTR_EINVAL, "data-term arrays must not be NULL");
+    if (!state && !u_out) return fail(CTR_EINVAL, "state and u_out are both NULL");
+    if (state && (!state->u || !state->Ru || !state->v1b || !state->v2b)) return fail(CTR_EINVAL, "state has a NULL buffer");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, iters, q);
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p,
+                        solve_impl<float>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream),
+                        solve_impl<double>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream));
+}
+
+ctr_status ctr_power_beta(ctr_plan *p, int iters, double *beta_out, void *stream)
+{
+    CTR_GUARD(p);
+    if (!beta_out || iters < 1) return fail(CTR_EINVAL, "beta_out NULL or iters < 1");
+    StreamJoin sj(p, stream);
+    ctr_status st = sj.begin();
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p, power_beta<float>(p, iters, beta_out, p->stream), power_beta<double>(p, iters, beta_out, p->stream));
+}
+
+ctr_status ctr_power_lambda(ctr_plan *p, double beta, double eps, int iters, double *lam, void *stream)
+{
+    CTR_GUARD(p);
+    if (!lam || iters < 1 || !(beta > 0) || !(eps > 0)) return fail(CTR_EINVAL, "bad argument");
+    if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
+    StreamJoin sj(p, stream);
+    ctr_status st = sj.begin();
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p, power_lambda<float>(p, beta, eps, iters, lam, p->stream),
+                        power_lambda<double>(p, beta, eps, iters, lam, p->stream));
+}
+
+ctr_status ctr_grad(ctr_plan *p, const void *u, void *px, void *stream)
+{
+    CTR_GUARD(p);
+    if (!u || !px) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, op_grad<float>(p, (const float *)u, (float *)px, s), op_grad<double>(p, (const double *)u, (double *)px, s));
+}
+
+ctr_status ctr_div(ctr_plan *p, const void *px, void *d, void *stream)
+{
+    CTR_GUARD(p);
+    if (!px || !d) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, op_div<float>(p, (const float *)px, (float *)d, s), op_div<double>(p, (const double *)px, (double *)d, s));
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal declarations shared by the CUDA translation units of libctrecon.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ctrecon.h"
+
+namespace ctr {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message, returned through ctr_last_error()).
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+ctr_status fail(ctr_status st, const std::string &msg);
+ctr_status cuda_fail(cudaError_t e, const char *what);
+
+#define CTR_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return ::ctr::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define CTR_CHECK_LAUNCH(what)                                      \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return ::ctr::cuda_fail(e_, what);   \
+    } while (0)
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// ---------------------------------------------------------------------------
+// Fixed-point detector geometry.
+// The detector coordinate of pixel (i, j) at angle l, in bin units,
+//     p = (x_i cos theta_l + y_j sin theta_l)/ds + (M-1)/2,
+// is represented exactly as the integer P = i*C + j*S + O in units of 2^-F bins,
+// with C = round(2^F h cos/ds), S = round(2^F h sin/ds) and O chosen so that the
+// grid is centred.  floor(p) = P >> F and frac(p) = (P mod 2^F) 2^-F.  Both
+// projectors derive every interpolation weight from the same integer P, so the
+// ray-driven R_h is the exact transpose of the pixel-driven R_h^*.
+// F = 32 for FP32/BF16 (weight = top 23 fraction bits), F = 48 or less for FP64.
+// ---------------------------------------------------------------------------
+struct AngleGeom {
+    long long C, S, O;
+};
+
+// Ray-driven march of one angle: pixels are addressed by a "pick" index q along
+// the axis where p changes fastest and a "march" index m along the other, with
+// P(q, m) = q*A + m*B + Op, A > 0 and |B| <= A.  layout 0: q = i, m = j, values read
+// from the transposed image uT[j][i]; layout 1: q = j, m = i, read from u[i][j].
+// flip: the physical pick index is n-1-q.
+struct AngleMarch {
+    long long A, B, Op;
+    int layout, flip;
+    double kA;   // 2^F / A
+    double oA;   // Op / A
+    double bA;   // B / A
+};
+
+// Kernel-side parameter blocks ------------------------------------------------
+template <typename T>
+struct BackprojEpi {
+    T *out;            // real output (n*n) or complex output (n*n pairs) when complex_out
+    int complex_out;
+    T scale;           // multiplies the backprojection sum
+    const T *px;       // optional vector field (x plane, y plane = px + n*n) for -tau div
+    T divtau;          // coefficient of div p (value = scale*R^*g - divtau*div p)
+    T outscale;        // final multiplier
+    T inv_h;
+};
+
+template <typename T>
+struct ForwardEpi {
+    int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4)
+    T *g;              // mode 0 output
+    T scale;
+    // mode 1
+    T sigma;
+    T *Ru;             // out: Rt u_new
+    T *v1b;            // in/out: bar v1
+    T *y1;             // out: bar v1_new + sigma Rt u_new
+    T *t1;             // optional out: resolvent output (dual certificate)
+    const T *dw, *da, *dlo, *dhi;   // per-bin data term, beta-scaled
+};
+
+}  // namespace ctr
+
+// ---------------------------------------------------------------------------
+// The plan.
+// ---------------------------------------------------------------------------
+struct ctr_plan {
+    int n = 0, N = 0, M = 0;
+    double h = 1.0, ds = 1.0;
+    ctr_dtype dtype = CTR_F32;
+    int F = 32;
+    int device = 0;
+    int wstride = 48;       // adjoint footprint stride (bins per staged angle)
+    int ncand = 2;          // forward candidates per (ray, row)
+    std::vector<double> theta;
+    std::vector<int> radices;    // FFT radices, product n
+    bool fft_ok = false;         // n = 2^a 3^b (needed by the preconditioner only)
+    size_t bytes = 0;
+    std::vector<void *> allocations;
+    mutable unsigned long long launches = 0;   // kernels launched (graph replays included)
+
+    ctr::AngleGeom *d_geom = nullptr;
+    ctr::AngleMarch *d_march = nullptr;
+    void *d_twiddle = nullptr;  // n complex exp(-2 pi i t/n)
+
+    // workspace, element type T (sizeof(T) = esize)
+    size_t esize = 4;
+    void *uT = nullptr;        // n*n
+    void *cbuf = nullptr;      // n*n complex
+    void *sym = nullptr;       // n*n preconditioner symbol (incl. 1/n^2)
+    void *symh = nullptr;      // n*n sqrt(||xi||_eps)/n^2 for the power iteration
+    void *u = nullptr;         // n*n primal iterate
+    void *du = nullptr;        // n*n last increment / scratch
+    void *x = nullptr;         // n*n power-iteration vector
+    void *xt = nullptr;        // n*n scratch
+    void *y2 = nullptr;        // 2*n*n
+    void *v2b = nullptr;       // 2*n*n
+    void *t2 = nullptr;        // 2*n*n
+    void *y1 = nullptr;        // N*M
+    void *Ru = nullptr;        // N*M
+    void *v1b = nullptr;       // N*M
+    void *t1 = nullptr;        // N*M
+    void *gs = nullptr;        // N*M scratch sinogram
+    void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
+    double *d_red = nullptr;   // reduction partials
+    double *d_scal = nullptr;  // device scalars
+    int red_blocks = 0;
+    cudaStream_t stream = nullptr;       // internal stream (graph capture)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace ctr {
+
+// Launch helpers implemented in the .cu files ------------------------------------
+template <typename T>
+ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s);
+template <typename T>
+ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s);
+template <typename T>
+ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t s);
+
+// FFT-based circulant operators: out = F^{-1}(sym * F(in)) (sym includes 1/n^2).
+// mode 0: out = result; mode 1: out += result (accumulate, solver update).
+// outT (optional) receives the transpose of the final out; dout (optional) the
+// result before accumulation.
+template <typename T>
+ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf, const T *sym, T *out,
+                            int mode, T *outT, T *dout, cudaStream_t s);
+template <typename T>
+ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s);
+
+template <typename T> ctr_status configure_radon(const ctr_plan *p);   // smem attributes, at plan creation
+template <typename T> ctr_status configure_fft(const ctr_plan *p);
+ctr_status fft_radices(int n, std::vector<int> &out);
+size_t fft_smem_bytes(const ctr_plan *p, int which);
+
+}  // namespace ctr

@@ -1,0 +1,373 @@
+// The discrete Radon transform R_h and its adjoint R_h^* (linear backprojection)
+// of Sec. 3.1, as an exact transpose pair of gather kernels for sm_103a.
+//
+//  * R_h^* (pixel-driven): a CTA owns a tile of pixels; per chunk of angles it
+//    stages, for every angle, the tile's detector footprint into shared memory as
+//    interpolation-ready pairs, then each thread walks its pixels' exact
+//    fixed-point detector coordinate P and accumulates one shared-memory load and
+//    one FMA per (pixel, angle).  No atomics.
+//  * R_h (ray-driven): one lane per detector interval [k, k+1) of one angle
+//    marches across the image rows, tracking exactly (integer arithmetic) the
+//    first pixel whose coordinate falls in its interval; it accumulates
+//    sum u and sum frac*u over the pixels of its interval, and the two neighbouring
+//    intervals' sums are combined with one warp shuffle:
+//        g_k = sum_{floor p = k} (1 - frac) u  +  sum_{floor p = k-1} frac u.
+//    No atomics; each output bin is written once.
+// Both kernels derive each weight from the same integer P (see ctr_internal.cuh),
+// so they are transposes of one matrix, bit for bit in the weights.
+#include "ctr_internal.cuh"
+
+namespace ctr {
+
+namespace {
+
+constexpr int BP_TJ = 32;    // tile width along j (one warp)
+constexpr int BP_ACH = 32;   // angles per staged chunk
+
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// 1 + frac(p) in [1, 2) from the low 32 bits of P (F = 32): the top 23 fraction
+// bits become the mantissa of a float, so the weight is exact and identical in
+// both projectors.
+__device__ __forceinline__ float one_plus_frac32(long long P)
+{
+    return __uint_as_float((((unsigned)(unsigned long long)P) >> 9) | 0x3F800000u);
+}
+
+__device__ __forceinline__ float2 make_stage(float g0, float g1)
+{
+    const float d = g1 - g0;
+    return make_float2(g0 - d, d);     // value = (g0 - d) + (1 + frac) d
+}
+__device__ __forceinline__ double2 make_stage(double g0, double g1)
+{
+    return make_double2(g0, g1 - g0);  // value = g0 + frac d
+}
+
+__device__ __forceinline__ float interp(float acc, float2 pr, long long P, int, double)
+{
+    return fmaf(one_plus_frac32(P), pr.y, acc + pr.x);
+}
+__device__ __forceinline__ double interp(double acc, double2 pr, long long P, int F, double inv2F)
+{
+    const unsigned long long mask = (1ull << F) - 1ull;
+    const double a = (double)((unsigned long long)P & mask) * inv2F;
+    return acc + fma(a, pr.y, pr.x);
+}
+
+template <typename T>
+__device__ __forceinline__ T div_at(const T *__restrict__ px, int n, int i, int j, T inv_h)
+{
+    // div_h p = (d1 + d2)/h, backward differences with Dirichlet ends (Sec. 3.1)
+    if (n < 2) return T(0);
+    const T *py = px + (size_t)n * n;
+    T d1, d2;
+    if (i == 0) d1 = px[j];
+    else if (i == n - 1) d1 = -px[(size_t)(n - 2) * n + j];
+    else d1 = px[(size_t)i * n + j] - px[(size_t)(i - 1) * n + j];
+    const size_t row = (size_t)i * n;
+    if (j == 0) d2 = py[row];
+    else if (j == n - 1) d2 = -py[row + n - 2];
+    else d2 = py[row + j] - py[row + j - 1];
+    return (d1 + d2) * inv_h;
+}
+
+template <typename T, int TY, int R>
+__global__ void __launch_bounds__(32 * TY)
+k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride,
+              const AngleGeom *__restrict__ geom, BackprojEpi<T> epi)
+{
+    using T2 = typename Pair<T>::type;
+    constexpr int NT = 32 * TY;
+    constexpr int TI = TY * R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *stage = reinterpret_cast<T2 *>(smem_raw);
+    long long *sPb = reinterpret_cast<long long *>(stage + BP_ACH * wstride);
+    long long *sC = sPb + BP_ACH;
+    long long *sS = sC + BP_ACH;
+    int *sK = reinterpret_cast<int *>(sS + BP_ACH);
+
+    const int tx = threadIdx.x & 31;
+    const int ty = threadIdx.x >> 5;
+    const int i0 = blockIdx.y * TI;
+    const int j0 = blockIdx.x * BP_TJ;
+    const double inv2F = ldexp(1.0, -F);
+
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+
+    for (int l0 = 0; l0 < N; l0 += BP_ACH) {
+        const int na = min(BP_ACH, N - l0);
+        __syncthreads();
+        if (threadIdx.x < na) {
+            const AngleGeom ag = geom[l0 + threadIdx.x];
+            const long long P00 = (long long)i0 * ag.C + (long long)j0 * ag.S + ag.O;
+            const long long P10 = P00 + (long long)(TI - 1) * ag.C;
+            const long long P01 = P00 + (long long)(BP_TJ - 1) * ag.S;
+            const long long P11 = P10 + (long long)(BP_TJ - 1) * ag.S;
+            const long long pmin = min(min(P00, P10), min(P01, P11));
+            const long long kmin = pmin >> F;   // arithmetic shift: floor
+            sK[threadIdx.x] = (int)kmin;
+            sPb[threadIdx.x] = P00 - (kmin << F);
+            sC[threadIdx.x] = ag.C;
+            sS[threadIdx.x] = ag.S;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < na * wstride; e += NT) {
+            const int a = e / wstride;
+            const int k = sK[a] + (e - a * wstride);
+            const T *row = g + (size_t)(l0 + a) * M;
+            const T g0 = (k >= 0 && k < M) ? row[k] : T(0);
+            const T g1 = (k + 1 >= 0 && k + 1 < M) ? row[k + 1] : T(0);
+            stage[e] = make_stage(g0, g1);
+        }
+        __syncthreads();
+        for (int a = 0; a < na; ++a) {
+            const long long C = sC[a];
+            long long P = sPb[a] + (long long)ty * C + (long long)tx * sS[a];
+            const long long D = C * TY;
+            const T2 *row = stage + a * wstride;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int idx = (int)(P >> F);
+                acc[r] = interp(acc[r], row[idx], P, F, inv2F);
+                P += D;
+            }
+        }
+    }
+
+    const int j = j0 + tx;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = i0 + ty + TY * r;
+        if (i < n && j < n) {
+            T v = acc[r] * epi.scale;
+            if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
+            v *= epi.outscale;
+            const size_t o = (size_t)i * n + j;
+            if (epi.complex_out) {
+                epi.out[2 * o] = v;
+                epi.out[2 * o + 1] = T(0);
+            } else {
+                epi.out[o] = v;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b)
+{
+    // b > 0
+    long long q = a / b;
+    if (q * b < a) ++q;
+    return q;
+}
+
+__device__ __forceinline__ void acc_sample(float &Su, float &Sf, float v, long long P)
+{
+    Su += v;
+    Sf = fmaf(one_plus_frac32(P), v, Sf);     // sum (1 + frac) u
+}
+__device__ __forceinline__ void acc_sample(double &Su, double &Sf, double v, long long P, int F, double inv2F)
+{
+    const unsigned long long mask = (1ull << F) - 1ull;
+    Su += v;
+    Sf = fma((double)((unsigned long long)P & mask) * inv2F, v, Sf);   // sum frac u
+}
+
+template <typename T>
+__device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_t r, T val)
+{
+    if (epi.mode == 0) {
+        epi.g[r] = val * epi.scale;
+        return;
+    }
+    // Alg. 4: v1 = v1b + sigma Rt u_new; t = (id + sigma dG1^*)^{-1}(2 v1 - v1b);
+    // v1b <- v1b + t - v1; and the next iteration's y1 = v1b + sigma Rt u_new.
+    const T sigma = epi.sigma;
+    const T Ru = val * epi.scale;
+    const T vb = epi.v1b[r];
+    const T v1 = vb + sigma * Ru;
+    const T z = T(2) * v1 - vb;
+    const T w = epi.dw[r];
+    T zz = (z + w * epi.da[r]) / (sigma + w);
+    zz = fmin(fmax(zz, epi.dlo[r]), epi.dhi[r]);
+    const T t = z - sigma * zz;
+    const T vbn = vb + t - v1;
+    epi.Ru[r] = Ru;
+    epi.v1b[r] = vbn;
+    epi.y1[r] = vbn + sigma * Ru;
+    if (epi.t1) epi.t1[r] = t;
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(128)
+k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F,
+          const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
+{
+    const int l = blockIdx.y;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int kb = (blockIdx.x * 4 + warp) * 31;     // first output bin of this warp
+    if (kb >= M) return;                              // warp-uniform
+    const AngleMarch am = march[l];
+    const int k = kb + lane - 1;                      // this lane's interval [k, k+1)
+    const T *__restrict__ src = am.layout ? u : uT;
+    const double inv2F = ldexp(1.0, -F);
+
+    // Rows m where the lane's pixel run may be inside [0, n): q*(m) = Q0 - m b.
+    int mlo = n, mhi = -1;
+    {
+        const double Q0 = (double)k * am.kA - am.oA;
+        const double b = am.bA;
+        const double lo_q = -(double)NC - 1.0, hi_q = (double)n + 1.0;
+        if (fabs(b) > 1e-9) {
+            const double m1 = (Q0 - hi_q) / b, m2 = (Q0 - lo_q) / b;
+            const double a0 = fmax(0.0, floor(fmin(m1, m2)));
+            const double a1 = fmin((double)(n - 1), ceil(fmax(m1, m2)));
+            if (a0 <= a1) {
+                mlo = (int)a0;
+                mhi = (int)a1;
+            }
+        } else if (Q0 > lo_q && Q0 < hi_q) {
+            mlo = 0;
+            mhi = n - 1;
+        }
+    }
+    const int mlo_w = __reduce_min_sync(0xffffffffu, mlo);
+    const int mhi_w = __reduce_max_sync(0xffffffffu, mhi);
+
+    T Su = T(0), Sf = T(0);
+    if (mlo_w <= mhi_w) {
+        const long long K = (long long)k << F;
+        const long long A = am.A, B = am.B;
+        long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
+        long long Pa = qa * A + (long long)mlo_w * B + am.Op;   // in [K, K + A)
+        int q = (int)qa;
+        for (int m = mlo_w; m <= mhi_w; ++m) {
+            const T *rowp = src + (size_t)m * n;
+            long long P = Pa;
+            int qq = q;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if ((P >> F) == (long long)k && (unsigned)qq < (unsigned)n) {
+                    const int qp = am.flip ? (n - 1 - qq) : qq;
+                    if constexpr (sizeof(T) == 4) acc_sample(Su, Sf, rowp[qp], P);
+                    else acc_sample(Su, Sf, rowp[qp], P, F, inv2F);
+                }
+                P += A;
+                ++qq;
+            }
+            // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
+            Pa += B;
+            if (B >= 0) {
+                if (Pa - A >= K) { Pa -= A; --q; }
+            } else {
+                if (Pa < K) { Pa += A; ++q; }
+            }
+        }
+    }
+    T Bk, Ak;
+    if constexpr (sizeof(T) == 4) { Bk = Sf - Su; Ak = Su - Bk; }
+    else { Bk = Sf; Ak = Su - Sf; }
+    const T Bprev = __shfl_up_sync(0xffffffffu, Bk, 1);
+    if (lane >= 1 && k < M) forward_epilogue(epi, (size_t)l * M + k, Ak + Bprev);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *__restrict__ out, int n)
+{
+    __shared__ T tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = by + r, j = bx + threadIdx.x;
+        if (i < n && j < n) tile[r][threadIdx.x] = in[(size_t)i * n + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = bx + r, j = by + threadIdx.x;
+        if (i < n && j < n) out[(size_t)i * n + j] = tile[threadIdx.x][r];
+    }
+}
+
+template <typename T, int TY, int R>
+ctr_status launch_bp_cfg(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+{
+    using T2 = typename Pair<T>::type;
+    const size_t smem = sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
+    auto kern = k_backproject<T, TY, R>;
+    dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + TY * R - 1) / (TY * R));
+    p->launches++;
+    kern<<<grid, 32 * TY, smem, s>>>(g, p->n, p->N, p->M, p->F, p->wstride, p->d_geom, epi);
+    CTR_CHECK_LAUNCH("k_backproject");
+    return CTR_OK;
+}
+
+template <typename T, int TY, int R>
+ctr_status configure_bp_cfg(const ctr_plan *p)
+{
+    using T2 = typename Pair<T>::type;
+    const size_t smem = sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
+    if (smem > 48 * 1024)
+        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T, TY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return CTR_OK;
+}
+
+}  // namespace
+
+template <typename T>
+ctr_status configure_radon(const ctr_plan *p)
+{
+    ctr_status st = configure_bp_cfg<T, 8, 4>(p);
+    if (st != CTR_OK) return st;
+    return configure_bp_cfg<T, 4, 4>(p);
+}
+
+template <typename T>
+ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+{
+    // 16 x 32 tiles (4 warps, 4 rows each) keep enough CTAs in flight at n <= 1024;
+    // 32 x 32 tiles (8 warps) above.
+    if (p->n > 1024) return launch_bp_cfg<T, 8, 4>(p, g, epi, s);
+    return launch_bp_cfg<T, 4, 4>(p, g, epi, s);
+}
+
+template <typename T>
+ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+{
+    dim3 grid((p->M + 4 * 31 - 1) / (4 * 31), p->N);
+    p->launches++;
+    switch (p->ncand) {
+    case 1: k_forward<T, 1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
+    case 2: k_forward<T, 2><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
+    case 3: k_forward<T, 3><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
+    case 4: k_forward<T, 4><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
+    default: return fail(CTR_EUNSUPPORTED, "forward projector: too many pixels per detector interval");
+    }
+    CTR_CHECK_LAUNCH("k_forward");
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t s)
+{
+    dim3 grid((p->n + 31) / 32, (p->n + 31) / 32);
+    p->launches++;
+    k_transpose<T><<<grid, dim3(32, 8), 0, s>>>(in, out, p->n);
+    CTR_CHECK_LAUNCH("k_transpose");
+    return CTR_OK;
+}
+
+template ctr_status launch_backproject<float>(const ctr_plan *, const float *, const BackprojEpi<float> &, cudaStream_t);
+template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &, cudaStream_t);
+template ctr_status launch_forward<float>(const ctr_plan *, const float *, const float *, const ForwardEpi<float> &, cudaStream_t);
+template ctr_status launch_forward<double>(const ctr_plan *, const double *, const double *, const ForwardEpi<double> &, cudaStream_t);
+template ctr_status configure_radon<float>(const ctr_plan *);
+template ctr_status configure_radon<double>(const ctr_plan *);
+template ctr_status launch_transpose<float>(const ctr_plan *, const float *, float *, cudaStream_t);
+template ctr_status launch_transpose<double>(const ctr_plan *, const double *, double *, cudaStream_t);
+
+}  // namespace ctr

@@ -1,0 +1,632 @@
+// Alg. 4 (PDRQS1) on the GPU: the fused pointwise kernels around the projectors,
+// deterministic FP64 reductions, the power iterations, the diagnostics and the
+// iteration driver (optionally captured as CUDA graphs).
+//
+// One iteration is four stream-ordered steps, all in this library's kernels:
+//   A  u_tmp = -sigma ( Rt^* y1 - tau div y2 )        backprojection + div epilogue
+//   B  u    += F^{-1}( F(u_tmp) m ),  uT = u^T          three FFT passes
+//   C  Rt u, v1 = v1b + sigma Rt u, t1 = prox(2 v1 - v1b), v1b += t1 - v1,
+//      y1 = v1b + sigma Rt u                            ray-driven projection + epilogue
+//   D  g = grad u, v2 = v2b + sigma tau g, t2 = P(2 v2 - v2b), v2b += t2 - v2,
+//      y2 = v2b + sigma tau g                           stencil kernel
+// y1, y2 carry Alg. 4's "v1b + sigma R u" and "v2b + sigma tau grad u" into the
+// next iteration, so R_h u is computed once per iteration (Sec. 4.4).
+#include <cmath>
+
+#include "ctr_internal.cuh"
+
+namespace ctr {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+
+// ------------------------------------------------------------------------------
+// elementwise kernels
+// ------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_make_desc(const T *__restrict__ f, const uint8_t *__restrict__ mask, size_t len, double delta,
+                            double trace_ratio, double inv_beta, T *w, T *a, T *lo, T *hi)
+{
+    // problem (C_h) with the data tolerance: off the metal trace w = 1, a = f,
+    // [f - delta, f + delta] (delta < 0: unbounded); on the trace w = 0,
+    // [trace_ratio f, +inf).  All values divided by beta (Sec. 5.1 scaling).
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x) {
+        const double fv = (double)f[r];
+        const bool tr = mask && mask[r];
+        if (tr) {
+            w[r] = T(0);
+            a[r] = T(0);
+            lo[r] = (T)(trace_ratio * fv * inv_beta);
+            hi[r] = (T)inf;
+        } else {
+            w[r] = T(1);
+            a[r] = (T)(fv * inv_beta);
+            lo[r] = (T)(delta >= 0 ? (fv - delta) * inv_beta : -inf);
+            hi[r] = (T)(delta >= 0 ? (fv + delta) * inv_beta : inf);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_scale_desc(const T *__restrict__ wi, const T *__restrict__ ai, const T *__restrict__ loi,
+                             const T *__restrict__ hii, size_t len, double inv_beta, T *w, T *a, T *lo, T *hi)
+{
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x) {
+        w[r] = wi[r];
+        a[r] = (T)((double)ai[r] * inv_beta);
+        lo[r] = (T)((double)loi[r] * inv_beta);
+        hi[r] = (T)((double)hii[r] * inv_beta);
+    }
+}
+
+// y = a + s * b
+template <typename T>
+__global__ void k_axpy(const T *__restrict__ a, const T *__restrict__ b, T s, size_t len, T *y)
+{
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
+        y[r] = a[r] + s * b[r];
+}
+
+template <typename T>
+__device__ __forceinline__ void grad_at(const T *__restrict__ u, int n, int i, int j, T inv_h, T &gx, T &gy)
+{
+    // forward differences with Neumann boundary (Sec. 3.1)
+    const size_t e = (size_t)i * n + j;
+    const T c = u[e];
+    gx = (i < n - 1) ? (u[e + n] - c) * inv_h : T(0);
+    gy = (j < n - 1) ? (u[e + 1] - c) * inv_h : T(0);
+}
+
+template <typename T>
+__global__ void k_grad(const T *__restrict__ u, int n, T inv_h, T *px)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T gx, gy;
+        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        px[e] = gx;
+        px[e + nn] = gy;
+    }
+}
+
+template <typename T>
+__global__ void k_div(const T *__restrict__ px, int n, T inv_h, T *d)
+{
+    const size_t nn = (size_t)n * n;
+    const T *py = px + nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        T d1 = T(0), d2 = T(0);
+        if (n >= 2) {
+            d1 = (i == 0) ? px[e] : (i == n - 1 ? -px[e - n] : px[e] - px[e - n]);
+            d2 = (j == 0) ? py[e] : (j == n - 1 ? -py[e - 1] : py[e] - py[e - 1]);
+        }
+        d[e] = (d1 + d2) * inv_h;
+    }
+}
+
+// y2 = v2b + sigma tau grad u   (start of the iteration from a given state)
+template <typename T>
+__global__ void k_init_y2(const T *__restrict__ u, const T *__restrict__ v2b, int n, T st, T inv_h, T *y2)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T gx, gy;
+        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        y2[e] = v2b[e] + st * gx;
+        y2[e + nn] = v2b[e + nn] + st * gy;
+    }
+}
+
+// Step D of Alg. 4: TV dual update with the projection onto the ball of radius lam/tau.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b, T *y2, T *t2)
+{
+    const size_t nn = (size_t)n * n;
+    const T st = sigma * tau;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T gx, gy;
+        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        const T bx = v2b[e], by = v2b[e + nn];
+        const T vx = bx + st * gx, vy = by + st * gy;
+        const T zx = T(2) * vx - bx, zy = T(2) * vy - by;
+        T tx = T(0), ty = T(0);
+        if (lam > T(0)) {
+            const T den = fmax(T(1), tau * sqrt(zx * zx + zy * zy) / lam);
+            tx = zx / den;
+            ty = zy / den;
+        }
+        const T nbx = bx + tx - vx, nby = by + ty - vy;
+        v2b[e] = nbx;
+        v2b[e + nn] = nby;
+        y2[e] = nbx + st * gx;
+        y2[e + nn] = nby + st * gy;
+        if (t2) {
+            t2[e] = tx;
+            t2[e + nn] = ty;
+        }
+    }
+}
+
+// Power-iteration start pattern x_ij = frac(1/2 + i/g + j/g^2) - 1/2, g the plastic number.
+template <typename T>
+__global__ void k_start_pattern(T *x, int n)
+{
+    const double g = 1.32471795724474602596;
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const double i = (double)(e / n), j = (double)(e % n);
+        const double v = 0.5 + i / g + j / (g * g);
+        x[e] = (T)(v - floor(v) - 0.5);
+    }
+}
+
+// x = y / sqrt(scal[idx])   (scal holds a squared norm)
+template <typename T>
+__global__ void k_normalize(const T *__restrict__ y, size_t len, const double *__restrict__ scal, int idx, T *x)
+{
+    const double s = scal[idx];
+    const T inv = s > 0 ? (T)(1.0 / sqrt(s)) : T(0);
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
+        x[r] = y[r] * inv;
+}
+
+// ------------------------------------------------------------------------------
+// deterministic reductions: each block writes NV partials; one block combines them
+// ------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], unsigned maxmask, double *out)
+{
+    __shared__ double sh[NV][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = ((maxmask >> q) & 1u) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) sh[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double x = sh[q][0];
+            for (int w = 1; w < RED_THREADS / 32; ++w) x = ((maxmask >> q) & 1u) ? fmax(x, sh[q][w]) : x + sh[q][w];
+            out[q] = x;
+        }
+    }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS) k_finalize(const double *__restrict__ part, int nblk, unsigned maxmask, double *out)
+{
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = ((maxmask >> q) & 1u) ? -INFINITY : 0.0;
+    for (int b = threadIdx.x; b < nblk; b += RED_THREADS)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const double x = part[(size_t)b * NV + q];
+            v[q] = ((maxmask >> q) & 1u) ? fmax(v[q], x) : v[q] + x;
+        }
+    block_reduce<NV>(v, maxmask, out);
+}
+
+// (sum a*b, sum b*b)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_dot2(const T *__restrict__ a, const T *__restrict__ b, size_t len, double *part)
+{
+    double v[2] = {0.0, 0.0};
+    for (size_t r = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; r < len; r += (size_t)gridDim.x * RED_THREADS) {
+        const double x = (double)a[r], y = (double)b[r];
+        v[0] += x * y;
+        v[1] += y * y;
+    }
+    block_reduce<2>(v, 0u, part + (size_t)blockIdx.x * 2);
+}
+
+// conjugate of the per-bin data term (beta-scaled values)
+__device__ __forceinline__ double conj_term(double t, double w, double a, double lo, double hi)
+{
+    if (w > 0) {
+        const double z = fmin(fmax(a + t / w, lo), hi);
+        return t * z - 0.5 * w * (z - a) * (z - a);
+    }
+    if (t > 0) return t * hi;
+    if (t < 0) return t * lo;
+    return 0.0;
+}
+
+// sinogram diagnostics: sum 1/2 w (Ru - a)^2, max violation, sum of the data part of the gap
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_diag_sino(const T *__restrict__ Ru, const T *__restrict__ dw, const T *__restrict__ da, const T *__restrict__ dlo,
+            const T *__restrict__ dhi, const T *__restrict__ t1, size_t len, double *part)
+{
+    double v[3] = {0.0, 0.0, 0.0};
+    for (size_t r = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; r < len; r += (size_t)gridDim.x * RED_THREADS) {
+        const double z = Ru[r], w = dw[r], a = da[r], lo = dlo[r], hi = dhi[r];
+        const double q = 0.5 * w * (z - a) * (z - a);
+        v[0] += q;
+        v[1] = fmax(v[1], fmax(lo - z, z - hi));
+        if (t1) {
+            const double t = t1[r];
+            v[2] += q + conj_term(t, w, a, lo, hi) - z * t;
+        }
+    }
+    block_reduce<3>(v, 2u, part + (size_t)blockIdx.x * 3);
+}
+
+// image diagnostics: TV(u), TV part of the gap, ||du||^2, ||u||^2
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_diag_img(const T *__restrict__ u, const T *__restrict__ du, const T *__restrict__ t2, int n, double inv_h,
+           double lam, double tau, double *part)
+{
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; e < nn; e += (size_t)gridDim.x * RED_THREADS) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double c = u[e];
+        const double gx = (i < n - 1) ? ((double)u[e + n] - c) * inv_h : 0.0;
+        const double gy = (j < n - 1) ? ((double)u[e + 1] - c) * inv_h : 0.0;
+        const double mag = sqrt(gx * gx + gy * gy);
+        v[0] += mag;
+        if (t2) v[1] += lam * mag - tau * (gx * (double)t2[e] + gy * (double)t2[e + nn]);
+        if (du) v[2] += (double)du[e] * (double)du[e];
+        v[3] += c * c;
+    }
+    block_reduce<4>(v, 0u, part + (size_t)blockIdx.x * 4);
+}
+
+inline int grid_for(size_t len, int threads = 256, int cap = 2048)
+{
+    size_t b = (len + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (size_t)cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------
+// host-side building blocks
+// ------------------------------------------------------------------------------
+template <typename T>
+ctr_status dot2(ctr_plan *p, const T *a, const T *b, size_t len, double *out_dev, cudaStream_t s)
+{
+    const int nb = grid_for(len, RED_THREADS, p->red_blocks);
+    p->launches++;
+    k_dot2<T><<<nb, RED_THREADS, 0, s>>>(a, b, len, p->d_red);
+    p->launches++;
+    k_finalize<2><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 0u, out_dev);
+    CTR_CHECK_LAUNCH("k_dot2");
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status op_grad(ctr_plan *p, const T *u, T *px, cudaStream_t s)
+{
+    const size_t nn = (size_t)p->n * p->n;
+    p->launches++;
+    k_grad<T><<<grid_for(nn), 256, 0, s>>>(u, p->n, (T)(1.0 / p->h), px);
+    CTR_CHECK_LAUNCH("k_grad");
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status op_div(ctr_plan *p, const T *px, T *d, cudaStream_t s)
+{
+    const size_t nn = (size_t)p->n * p->n;
+    p->launches++;
+    k_div<T><<<grid_for(nn), 256, 0, s>>>(px, p->n, (T)(1.0 / p->h), d);
+    CTR_CHECK_LAUNCH("k_div");
+    return CTR_OK;
+}
+
+// g = scale * R_h x  (x, xT both given)
+template <typename T>
+ctr_status op_forward(ctr_plan *p, const T *x, const T *xT, T *g, double scale, cudaStream_t s)
+{
+    ForwardEpi<T> e{};
+    e.mode = 0;
+    e.g = g;
+    e.scale = (T)scale;
+    return launch_forward<T>(p, x, xT, e, s);
+}
+
+// u = scale * R_h^* g
+template <typename T>
+ctr_status op_adjoint(ctr_plan *p, const T *g, T *u, double scale, cudaStream_t s)
+{
+    BackprojEpi<T> e{};
+    e.out = u;
+    e.complex_out = 0;
+    e.scale = (T)scale;
+    e.px = nullptr;
+    e.divtau = T(0);
+    e.outscale = T(1);
+    e.inv_h = (T)(1.0 / p->h);
+    return launch_backproject<T>(p, g, e, s);
+}
+
+// Power iteration for beta ~ ||R_h||: x <- R^*R x / ||R^*R x|| from the R2 start.
+template <typename T>
+ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
+{
+    const size_t nn = (size_t)p->n * p->n;
+    T *x = (T *)p->x, *xt = (T *)p->xt, *y = (T *)p->du, *g = (T *)p->gs;
+    p->launches++;
+    k_start_pattern<T><<<grid_for(nn), 256, 0, s>>>(x, p->n);
+    ctr_status st;
+    if ((st = dot2<T>(p, x, x, nn, p->d_scal, s)) != CTR_OK) return st;
+    p->launches++;
+    k_normalize<T><<<grid_for(nn), 256, 0, s>>>(x, nn, p->d_scal, 1, x);
+    CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
+    for (int it = 0; it < iters; ++it) {
+        if ((st = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return st;
+        if ((st = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return st;
+        if ((st = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return st;
+        if ((st = dot2<T>(p, x, y, nn, p->d_scal, s)) != CTR_OK) return st;
+        p->launches++;
+        k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, x);
+    }
+    CTR_CHECK_LAUNCH("power_beta");
+    double h[2];
+    CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CTR_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(h[0])) return fail(CTR_ENUMERIC, "power iteration for beta produced a non-finite value");
+    *beta = std::sqrt(h[0] > 0 ? h[0] : 0.0);
+    return CTR_OK;
+}
+
+// Power iteration for lambda_max(Mt^{-1} Rt^* Rt) in the symmetric form
+// Mt^{-1/2} Rt^* Rt Mt^{-1/2}, Mt^{-1/2} = F^{-1} sqrt(||xi||_eps) F.
+template <typename T>
+ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double *lam, cudaStream_t s)
+{
+    const size_t nn = (size_t)p->n * p->n;
+    T *z = (T *)p->x, *x = (T *)p->u, *xt = (T *)p->xt, *yp = (T *)p->du, *y = (T *)p->t2, *g = (T *)p->gs;
+    ctr_status st;
+    if ((st = launch_symbols<T>(p, 1.0, 1.0, 1.0, eps, s)) != CTR_OK) return st;   // symh only matters here
+    p->launches++;
+    k_start_pattern<T><<<grid_for(nn), 256, 0, s>>>(z, p->n);
+    if ((st = dot2<T>(p, z, z, nn, p->d_scal, s)) != CTR_OK) return st;
+    p->launches++;
+    k_normalize<T><<<grid_for(nn), 256, 0, s>>>(z, nn, p->d_scal, 1, z);
+    CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
+    const double ib = 1.0 / beta;
+    for (int it = 0; it < iters; ++it) {
+        if ((st = launch_circulant<T>(p, z, false, (const T *)p->symh, x, 0, xt, nullptr, s)) != CTR_OK) return st;
+        if ((st = op_forward<T>(p, x, xt, g, ib, s)) != CTR_OK) return st;
+        if ((st = op_adjoint<T>(p, g, yp, ib, s)) != CTR_OK) return st;
+        if ((st = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s)) != CTR_OK) return st;
+        if ((st = dot2<T>(p, z, y, nn, p->d_scal, s)) != CTR_OK) return st;
+        p->launches++;
+        k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, z);
+    }
+    CTR_CHECK_LAUNCH("power_lambda");
+    double h[2];
+    CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CTR_CUDA(cudaStreamSynchronize(s));
+    if (!std::isfinite(h[0])) return fail(CTR_ENUMERIC, "power iteration for c produced a non-finite value");
+    *lam = h[0];
+    return CTR_OK;
+}
+
+template <typename T>
+struct IterArgs {
+    T sigma, tau, lam, inv_beta, inv_h;
+};
+
+// One iteration of Alg. 4 (steps A-D).  diag: also keep du, t1, t2 for diagnostics.
+template <typename T>
+ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nm = (size_t)p->N * p->M;
+    ctr_status st;
+    // A: u_tmp = -sigma (Rt^* y1 - tau div y2) into the complex FFT buffer
+    BackprojEpi<T> ea{};
+    ea.out = (T *)p->cbuf;
+    ea.complex_out = 1;
+    ea.scale = a.inv_beta;
+    ea.px = (const T *)p->y2;
+    ea.divtau = a.tau;
+    ea.outscale = -a.sigma;
+    ea.inv_h = a.inv_h;
+    if ((st = launch_backproject<T>(p, (const T *)p->y1, ea, s)) != CTR_OK) return st;
+    // B: u += F^{-1}(F(u_tmp) m), and uT
+    if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, (T *)p->uT,
+                                  diag ? (T *)p->du : nullptr, s)) != CTR_OK)
+        return st;
+    // C: ray-driven Rt u with the data-dual step
+    ForwardEpi<T> ec{};
+    ec.mode = 1;
+    ec.scale = a.inv_beta;
+    ec.sigma = a.sigma;
+    ec.Ru = (T *)p->Ru;
+    ec.v1b = (T *)p->v1b;
+    ec.y1 = (T *)p->y1;
+    ec.t1 = diag ? (T *)p->t1 : nullptr;
+    const T *d = (const T *)p->desc;
+    ec.dw = d;
+    ec.da = d + nm;
+    ec.dlo = d + 2 * nm;
+    ec.dhi = d + 3 * nm;
+    if ((st = launch_forward<T>(p, (const T *)p->u, (const T *)p->uT, ec, s)) != CTR_OK) return st;
+    // D: TV dual step
+    const size_t nn = (size_t)n * n;
+    p->launches++;
+    k_tv_dual<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, n, a.sigma, a.tau, a.lam, a.inv_h,
+                                                        (T *)p->v2b, (T *)p->y2, diag ? (T *)p->t2 : nullptr);
+    CTR_CHECK_LAUNCH("k_tv_dual");
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, double c, int iters_done,
+                        ctr_diag *out, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nm = (size_t)p->N * p->M, nn = (size_t)n * n;
+    const T *d = (const T *)p->desc;
+    const double lam = alpha / (beta * beta);
+    double *sc = p->d_scal;
+    int nb = grid_for(nm, RED_THREADS, p->red_blocks);
+    p->launches++;
+    k_diag_sino<T><<<nb, RED_THREADS, 0, s>>>((const T *)p->Ru, d, d + nm, d + 2 * nm, d + 3 * nm, (const T *)p->t1, nm, p->d_red);
+    p->launches++;
+    k_finalize<3><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 2u, sc + 4);
+    nb = grid_for(nn, RED_THREADS, p->red_blocks);
+    p->launches++;
+    k_diag_img<T><<<nb, RED_THREADS, 0, s>>>((const T *)p->u, (const T *)p->du, (const T *)p->t2, n, 1.0 / p->h, lam, tau, p->d_red);
+    p->launches++;
+    k_finalize<4><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 0u, sc + 8);
+    CTR_CHECK_LAUNCH("diagnostics");
+    // dual residual K^* t = Rt^* t1 - tau div t2
+    BackprojEpi<T> e{};
+    e.out = (T *)p->x;
+    e.complex_out = 0;
+    e.scale = (T)(1.0 / beta);
+    e.px = (const T *)p->t2;
+    e.divtau = (T)tau;
+    e.outscale = T(1);
+    e.inv_h = (T)(1.0 / p->h);
+    ctr_status st;
+    if ((st = launch_backproject<T>(p, (const T *)p->t1, e, s)) != CTR_OK) return st;
+    if ((st = dot2<T>(p, (const T *)p->x, (const T *)p->x, nn, sc + 12, s)) != CTR_OK) return st;
+    double h[16];
+    CTR_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CTR_CUDA(cudaStreamSynchronize(s));
+    out->beta = beta;
+    out->c = c;
+    out->data_fit = h[4] * beta * beta;
+    out->violation = h[5] > 0 ? h[5] * beta : 0.0;
+    out->tv = h[8];
+    out->objective = out->data_fit + alpha * out->tv;
+    out->gap = h[6] + h[9];
+    out->dual_residual = std::sqrt(h[13]);
+    out->rel_change = h[11] > 0 ? std::sqrt(h[10] / h[11]) : 0.0;
+    out->iters_done = iters_done;
+    if (!std::isfinite(out->objective) || !std::isfinite(out->tv))
+        return fail(CTR_ENUMERIC, "non-finite objective after the solve");
+    return CTR_OK;
+}
+
+// Full solve on the plan's internal stream.  desc must already hold the
+// beta-scaled data term; u, Ru, v1b, v2b hold the start state.
+template <typename T>
+ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm, double beta, double c,
+                     ctr_diag *diag, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    IterArgs<T> a;
+    a.sigma = (T)prm.sigma;
+    a.tau = (T)prm.tau;
+    a.lam = (T)(alpha / (beta * beta));
+    a.inv_beta = (T)(1.0 / beta);
+    a.inv_h = (T)(1.0 / p->h);
+    ctr_status st;
+    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s)) != CTR_OK) return st;
+    // y1 = v1b + sigma Ru ; y2 = v2b + sigma tau grad u
+    p->launches++;
+    k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->v1b, (const T *)p->Ru, a.sigma, nm, (T *)p->y1);
+    p->launches++;
+    k_init_y2<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, (const T *)p->v2b, n, a.sigma * a.tau, a.inv_h, (T *)p->y2);
+    CTR_CHECK_LAUNCH("pdrq init");
+    if (iters <= 0) {
+        CTR_CUDA(cudaMemsetAsync(p->du, 0, nn * sizeof(T), s));
+        CTR_CUDA(cudaMemsetAsync(p->t1, 0, nm * sizeof(T), s));
+        CTR_CUDA(cudaMemsetAsync(p->t2, 0, 2 * nn * sizeof(T), s));
+        if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, 0, diag, s);
+        return CTR_OK;
+    }
+    const int body = iters - 1;     // the last iteration also keeps du, t1, t2
+    const int blk = prm.graph_block > 0 ? prm.graph_block : 0;
+    int done = 0;
+    if (blk > 0 && body >= blk) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long before = p->launches;
+        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < blk; ++k) {
+            st = pdrq_iteration<T>(p, a, false, s);
+            if (st != CTR_OK) break;
+        }
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
+        p->launches = before;
+        if (st != CTR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        for (; done + blk <= body; done += blk) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(ce, "cudaGraphLaunch");
+            }
+            p->launches += per_graph;
+        }
+        cudaGraphExecDestroy(exec);
+    }
+    for (; done < body; ++done)
+        if ((st = pdrq_iteration<T>(p, a, false, s)) != CTR_OK) return st;
+    if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
+    if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, iters, diag, s);
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status build_desc_from_data(ctr_plan *p, const T *f, const uint8_t *mask, double delta, double ratio, double beta,
+                                cudaStream_t s)
+{
+    const size_t nm = (size_t)p->N * p->M;
+    T *d = (T *)p->desc;
+    p->launches++;
+    k_make_desc<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(f, mask, nm, delta, ratio, 1.0 / beta, d, d + nm, d + 2 * nm, d + 3 * nm);
+    CTR_CHECK_LAUNCH("k_make_desc");
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status build_desc_from_arrays(ctr_plan *p, const T *w, const T *a, const T *lo, const T *hi, double beta, cudaStream_t s)
+{
+    const size_t nm = (size_t)p->N * p->M;
+    T *d = (T *)p->desc;
+    p->launches++;
+    k_scale_desc<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(w, a, lo, hi, nm, 1.0 / beta, d, d + nm, d + 2 * nm, d + 3 * nm);
+    CTR_CHECK_LAUNCH("k_scale_desc");
+    return CTR_OK;
+}
+
+#define CTR_INST(T)                                                                                                   \
+    template ctr_status dot2<T>(ctr_plan *, const T *, const T *, size_t, double *, cudaStream_t);                  \
+    template ctr_status op_grad<T>(ctr_plan *, const T *, T *, cudaStream_t);                                         \
+    template ctr_status op_div<T>(ctr_plan *, const T *, T *, cudaStream_t);                                          \
+    template ctr_status op_forward<T>(ctr_plan *, const T *, const T *, T *, double, cudaStream_t);                   \
+    template ctr_status op_adjoint<T>(ctr_plan *, const T *, T *, double, cudaStream_t);                              \
+    template ctr_status power_beta<T>(ctr_plan *, int, double *, cudaStream_t);                                       \
+    template ctr_status power_lambda<T>(ctr_plan *, double, double, int, double *, cudaStream_t);                     \
+    template ctr_status pdrq_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, ctr_diag *,         \
+                                     cudaStream_t);                                                                   \
+    template ctr_status build_desc_from_data<T>(ctr_plan *, const T *, const uint8_t *, double, double, double,       \
+                                                cudaStream_t);                                                        \
+    template ctr_status build_desc_from_arrays<T>(ctr_plan *, const T *, const T *, const T *, const T *, double,     \
+                                                  cudaStream_t);
+CTR_INST(float)
+CTR_INST(double)
+#undef CTR_INST
+
+}  // namespace ctr

@@ -1,0 +1,279 @@
+"""Thin Python binding of libctrecon (include/ctrecon.h): argument marshalling only.
+
+Every operation runs in the library's CUDA kernels; tensors are PyTorch CUDA
+tensors used as device buffers, and the current torch stream is passed through.
+Loading fails loudly if the library has not been built (run
+``python -c "import __graft_entry__ as g; g.build()"``) -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctrecon.so")
+_lock = threading.Lock()
+_lib = None
+
+CTR_OK = 0
+CTR_F32, CTR_F64, CTR_BF16 = 0, 1, 2
+_STATUS = {0: "CTR_OK", -1: "CTR_EINVAL", -2: "CTR_ENOMEM", -3: "CTR_ECUDA", -4: "CTR_ETIMEOUT",
+           -5: "CTR_ENUMERIC", -6: "CTR_EUNSUPPORTED"}
+
+
+class CtrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("h", ctypes.c_double), ("ds", ctypes.c_double),
+                ("angles_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("eps", ctypes.c_double),
+                ("c", ctypes.c_double), ("beta", ctypes.c_double), ("power_iters", ctypes.c_int),
+                ("c_margin", ctypes.c_double), ("trace_ratio", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("c", ctypes.c_double), ("objective", ctypes.c_double),
+                ("data_fit", ctypes.c_double), ("tv", ctypes.c_double), ("violation", ctypes.c_double),
+                ("gap", ctypes.c_double), ("dual_residual", ctypes.c_double),
+                ("rel_change", ctypes.c_double), ("iters_done", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class State(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("Ru", ctypes.c_void_p), ("v1b", ctypes.c_void_p), ("v2b", ctypes.c_void_p)]
+
+
+EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_last_error", "ctr_plan_device_bytes",
+           "ctr_plan_launch_count", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
+           "ctr_power_lambda", "ctr_grad", "ctr_div"]
+
+
+def load(path: str = LIB_PATH):
+    """Load libctrecon.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libctrecon.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, P = ctypes.c_void_p, ctypes.POINTER
+        lib.ctr_plan_create.argtypes = [P(Geometry), ctypes.c_int, P(vp)]
+        lib.ctr_plan_destroy.argtypes = [vp]
+        lib.ctr_plan_destroy.restype = None
+        lib.ctr_default_params.argtypes = [P(Params)]
+        lib.ctr_default_params.restype = None
+        lib.ctr_last_error.restype = ctypes.c_char_p
+        lib.ctr_plan_device_bytes.argtypes = [vp]
+        lib.ctr_plan_device_bytes.restype = ctypes.c_size_t
+        lib.rh_forward.argtypes = [vp, vp, vp, vp]
+        lib.rh_adjoint.argtypes = [vp, vp, vp, vp]
+        lib.rh_forward_t.argtypes = [vp, vp, vp, vp, vp]
+        lib.rh_forward_t.restype = ctypes.c_int
+        lib.ctr_plan_launch_count.argtypes = [vp]
+        lib.ctr_plan_launch_count.restype = ctypes.c_ulonglong
+        lib.precond_apply.argtypes = [vp, P(Params), vp, vp, vp]
+        lib.tv_pd_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(Params), vp,
+                                    P(Diag), vp]
+        lib.tv_pd_run.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, P(Params), P(State), vp,
+                                  P(Diag), vp]
+        lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
+        lib.ctr_power_lambda.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(ctypes.c_double), vp]
+        lib.ctr_grad.argtypes = [vp, vp, vp, vp]
+        lib.ctr_div.argtypes = [vp, vp, vp, vp]
+        for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
+                     "ctr_power_beta", "ctr_power_lambda", "ctr_grad", "ctr_div"]:
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != CTR_OK:
+        raise CtrError(st, load().ctr_last_error().decode(errors="replace"))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().ctr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A ctr_plan: geometry tables and device workspace for one (n, angles, bins, dtype)."""
+
+    def __init__(self, n: int, n_angles: int, n_bins: int, angles=None, h: float = 1.0, ds: float = 1.0,
+                 dtype: str = "f32"):
+        import torch
+        lib = load()
+        if angles is None:
+            angles = np.arange(n_angles, dtype=np.float64) * (np.pi / n_angles)
+        self.angles = np.ascontiguousarray(angles, dtype=np.float64)
+        self.n, self.n_angles, self.n_bins, self.h, self.ds = n, n_angles, n_bins, h, ds
+        self.dtype = dtype
+        self.torch_dtype = {"f32": torch.float32, "f64": torch.float64}[dtype]
+        code = {"f32": CTR_F32, "f64": CTR_F64, "bf16": CTR_BF16}[dtype]
+        geo = Geometry(n, n_angles, n_bins, h, ds, self.angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        handle = ctypes.c_void_p()
+        _check(lib.ctr_plan_create(ctypes.byref(geo), code, ctypes.byref(handle)))
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ctr_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------------
+    @property
+    def device_bytes(self) -> int:
+        return int(load().ctr_plan_device_bytes(self._h))
+
+    def _t(self, x, shape, name):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if x.dtype != self.torch_dtype:
+            raise TypeError(f"{name} must be {self.torch_dtype}, got {x.dtype}")
+        if tuple(x.shape) != tuple(shape) or not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {shape}, got {tuple(x.shape)}")
+        return ctypes.c_void_p(x.data_ptr())
+
+    def empty_image(self, planes: int = 1):
+        import torch
+        shape = (self.n, self.n) if planes == 1 else (planes, self.n, self.n)
+        return torch.empty(shape, dtype=self.torch_dtype, device="cuda")
+
+    def empty_sino(self):
+        import torch
+        return torch.empty((self.n_angles, self.n_bins), dtype=self.torch_dtype, device="cuda")
+
+    # -- the C ABI -------------------------------------------------------------
+    def rh_forward(self, u, g=None, stream=None):
+        g = self.empty_sino() if g is None else g
+        _check(load().rh_forward(self._h, self._t(u, (self.n, self.n), "u"),
+                                 self._t(g, (self.n_angles, self.n_bins), "g"), _stream(stream)))
+        return g
+
+    def rh_forward_t(self, u, uT, g=None, stream=None):
+        g = self.empty_sino() if g is None else g
+        _check(load().rh_forward_t(self._h, self._t(u, (self.n, self.n), "u"), self._t(uT, (self.n, self.n), "uT"),
+                                   self._t(g, (self.n_angles, self.n_bins), "g"), _stream(stream)))
+        return g
+
+    @property
+    def launch_count(self) -> int:
+        return int(load().ctr_plan_launch_count(self._h))
+
+    def rh_adjoint(self, g, u=None, stream=None):
+        u = self.empty_image() if u is None else u
+        _check(load().rh_adjoint(self._h, self._t(g, (self.n_angles, self.n_bins), "g"),
+                                 self._t(u, (self.n, self.n), "u"), _stream(stream)))
+        return u
+
+    def precond_apply(self, y, params: Params, x=None, stream=None):
+        x = self.empty_image() if x is None else x
+        _check(load().precond_apply(self._h, ctypes.byref(params), self._t(y, (self.n, self.n), "y"),
+                                    self._t(x, (self.n, self.n), "x"), _stream(stream)))
+        return x
+
+    def grad(self, u, p=None, stream=None):
+        p = self.empty_image(2) if p is None else p
+        _check(load().ctr_grad(self._h, self._t(u, (self.n, self.n), "u"), self._t(p, (2, self.n, self.n), "p"),
+                               _stream(stream)))
+        return p
+
+    def div(self, p, d=None, stream=None):
+        d = self.empty_image() if d is None else d
+        _check(load().ctr_div(self._h, self._t(p, (2, self.n, self.n), "p"), self._t(d, (self.n, self.n), "d"),
+                              _stream(stream)))
+        return d
+
+    def power_beta(self, iters: int = 50, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(load().ctr_power_beta(self._h, iters, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def power_lambda(self, beta: float, eps: float, iters: int = 50, stream=None) -> float:
+        out = ctypes.c_double()
+        _check(load().ctr_power_lambda(self._h, beta, eps, iters, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def tv_pd_solve(self, f, metal_mask, alpha: float, delta: float, iters: int, params: Optional[Params] = None,
+                    u_out=None, stream=None):
+        """Alg. 4 from u = 0 on problem (C_h); returns (u, diag dict)."""
+        import torch
+        u_out = self.empty_image() if u_out is None else u_out
+        if metal_mask is not None:
+            if metal_mask.dtype != torch.uint8 or not metal_mask.is_cuda or not metal_mask.is_contiguous() \
+                    or tuple(metal_mask.shape) != (self.n_angles, self.n_bins):
+                raise ValueError("metal_mask must be a contiguous CUDA uint8 tensor of the sinogram's shape")
+            mptr = ctypes.c_void_p(metal_mask.data_ptr())
+        else:
+            mptr = ctypes.c_void_p()
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_pd_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), mptr, float(alpha),
+                                  float(delta), int(iters), ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"),
+                                  ctypes.byref(diag), _stream(stream)))
+        return u_out, diag.as_dict()
+
+    def new_state(self):
+        import torch
+        z = dict(device="cuda", dtype=self.torch_dtype)
+        return {"u": torch.zeros((self.n, self.n), **z), "Ru": torch.zeros((self.n_angles, self.n_bins), **z),
+                "v1b": torch.zeros((self.n_angles, self.n_bins), **z), "v2b": torch.zeros((2, self.n, self.n), **z)}
+
+    def tv_pd_run(self, w, a, lo, hi, alpha: float, iters: int, params: Optional[Params] = None, state=None,
+                  u_out=None, want_diag: bool = True, stream=None):
+        """General per-bin data term; `state` (dict of tensors, see new_state) is updated in place."""
+        sino = (self.n_angles, self.n_bins)
+        st = None
+        if state is not None:
+            st = State(self._t(state["u"], (self.n, self.n), "u").value, self._t(state["Ru"], sino, "Ru").value,
+                       self._t(state["v1b"], sino, "v1b").value,
+                       self._t(state["v2b"], (2, self.n, self.n), "v2b").value)
+        if state is None and u_out is None:
+            u_out = self.empty_image()
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_pd_run(self._h, self._t(w, sino, "w"), self._t(a, sino, "a"), self._t(lo, sino, "lo"),
+                                self._t(hi, sino, "hi"), float(alpha), int(iters), ctypes.byref(prm),
+                                ctypes.byref(st) if st is not None else None,
+                                self._t(u_out, (self.n, self.n), "u_out") if u_out is not None else None,
+                                ctypes.byref(diag) if want_diag else None, _stream(stream)))
+        return (u_out if u_out is not None else state["u"]), diag.as_dict()

@@ -1,0 +1,65 @@
+"""GPU parity of grad/div, the Fourier preconditioner and the power iterations."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import TOL, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ct():
+    from paper_1810_03275_gb300 import ctrecon
+    return ctrecon
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n,h", [(1, 1.0), (2, 1.0), (37, 1.0), (64, 0.5)])
+def test_grad_div(ct, n, h, dtype):
+    plan = ct.Plan(n, 3, 5, h=h, dtype=dtype)
+    rng = np.random.default_rng(n)
+    u = rng.standard_normal((n, n))
+    p = rng.standard_normal((2, n, n))
+    gx, gy = oracle.grad(u, h)
+    got = to_np(plan.grad(to_dev(u, plan.torch_dtype)))
+    assert rel_l2(got, np.stack([gx, gy])) < TOL[dtype]
+    got = to_np(plan.div(to_dev(p, plan.torch_dtype)))
+    ref = oracle.div(p[0], p[1], h)
+    assert rel_l2(got, ref) < TOL[dtype] or np.abs(ref).max() == 0
+
+
+@pytest.mark.parametrize("dtype,n", [("f64", 64), ("f32", 64), ("f32", 48), ("f32", 384), ("f32", 512),
+                                     ("f64", 27), ("f32", 1), ("f32", 2048)])
+def test_precond_apply(ct, n, dtype):
+    """M^{-1} y of Alg. 4 vs numpy's FFT on the oracle's symbol (radix 2, 3, 4 paths)."""
+    plan = ct.Plan(n, 4, 5, dtype=dtype)
+    sigma, tau, c, eps = 1.3, 0.35, 0.7, np.pi / n
+    prm = ct.default_params(sigma=sigma, tau=tau, c=c, eps=eps)
+    y = np.random.default_rng(n).standard_normal((n, n))
+    got = to_np(plan.precond_apply(to_dev(y, plan.torch_dtype), prm))
+    ref = oracle.precond_apply(y, oracle.precond_symbol(n, sigma, tau, c, eps))
+    assert rel_l2(got, ref) < (2e-6 if dtype == "f32" else 1e-12)
+
+
+def test_precond_rejects_other_sizes(ct):
+    plan = ct.Plan(10, 4, 5)
+    with pytest.raises(ct.CtrError) as e:
+        plan.precond_apply(to_dev(np.zeros((10, 10)), plan.torch_dtype), ct.default_params(c=1.0))
+    assert e.value.status == -6
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_power_iterations(ct, dtype):
+    """beta and lambda_max from the GPU power iterations follow the oracle's
+    (same start vector, same step count)."""
+    n, N, M = 32, 40, 47
+    plan = ct.Plan(n, N, M, dtype=dtype)
+    geo = oracle.Geometry(n, N, M)
+    beta_ref = oracle.power_beta(geo, 30)
+    beta = plan.power_beta(30)
+    assert beta == pytest.approx(beta_ref, rel=1e-6 if dtype == "f32" else 1e-12)
+    eps = np.pi / n
+    lam_ref = oracle.power_c(geo, beta_ref, eps, 30, margin=1.0)
+    lam = plan.power_lambda(beta_ref, eps, 30)
+    assert lam == pytest.approx(lam_ref, rel=1e-5 if dtype == "f32" else 1e-11)
