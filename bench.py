@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark: preconditioned primal-dual (Alg. 4, PDRQS1) iterations per second on
+the 512 x 512, 720-view, 729-bin metal-artifact-reduction workload (FP32), one full
+solve per step (power iterations for beta and c, 500 iterations, diagnostics).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on the
+same workload instead (a bounded sample per step).  Multi-GPU (torchrun): every
+rank solves its own copy of the workload (independent slices, no collective on the
+data path); value = all ranks' iterations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "preconditioned PD iters/sec and Gray-samples/s (R_h+R_h^T) at 512²×720 views; %HBM peak"
+UNIT = "PD iters/s"
+WORKLOAD = "mar_fp32_512x512_720views_729bins_500iters"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+OPS_PER_SAMPLE = 4   # advance p, split floor/frac, interpolate (FMA), accumulate
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def src_sha(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        rec = d.get(kernel)
+        if rec and rec.get("src_sha") == src_sha("paper_1810_03275_gb300/csrc/radon.cu"):
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_oracle_rate(problem, budget_s: float = 12.0, max_iters: int = 40):
+    """The FP64 oracle's Alg. 4 on the same problem: iterations/s on the host cores.
+    beta and c are fixed constants (the per-iteration cost does not depend on them)."""
+    import oracle
+    geo = oracle.Geometry(problem.n, problem.n_angles, problem.n_bins, theta=problem.theta)
+    desc = oracle.make_descriptors(problem.f, problem.mask, problem.delta)
+    kw = dict(sigma=1.0, tau=1 / np.sqrt(8), eps=np.pi / problem.n, beta=100.0, c=1.0)
+    st = oracle.pdrq_solve(geo, desc, problem.alpha, 1, **kw)      # warm-up (page-in, OpenMP pool)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_iters and (time.perf_counter() - t0) < budget_s:
+        st = oracle.pdrq_solve(geo, desc, problem.alpha, 1, state=st, **kw)
+        k += 1
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt, oracle.num_threads()
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    from paper_1810_03275_gb300 import phantom
+    pr = phantom.config_mar_fp32()
+    import oracle
+    geo = oracle.Geometry(pr.n, pr.n_angles, pr.n_bins, theta=pr.theta)
+    desc = oracle.make_descriptors(pr.f, pr.mask, pr.delta)
+    kw = dict(sigma=1.0, tau=1 / np.sqrt(8), eps=np.pi / pr.n, beta=100.0, c=1.0)
+    per_step = 2
+    st = None
+    for _ in range(args.warmup):
+        st = oracle.pdrq_solve(geo, desc, pr.alpha, 1, state=st, **kw)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = oracle.pdrq_solve(geo, desc, pr.alpha, per_step, state=st, **kw)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": pr.n, "views": pr.n_angles, "bins": pr.n_bins,
+                   "iters_per_solve": pr.iters, "step": f"{per_step} oracle iterations (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} PDRQS1 iterations per step of the 512x512/720/729 problem, FP64 C+numpy"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=None, help="override iterations per solve (profiling only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.iters is None:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, rank, ws)
+
+    import torch
+    from paper_1810_03275_gb300 import ctrecon as ct
+    from paper_1810_03275_gb300 import phantom
+
+    torch.cuda.set_device(local)
+    pr = phantom.config_mar_fp32(seed=2 + rank)     # each rank: its own slice
+    iters = args.iters or pr.iters
+    n, N, M = pr.n, pr.n_angles, pr.n_bins
+    plan = ct.Plan(n, N, M, angles=pr.theta, dtype="f32")
+    f = torch.as_tensor(pr.f, dtype=torch.float32, device="cuda")
+    mask = torch.as_tensor(pr.mask, device="cuda")
+    u = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    prm = ct.default_params()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm, u_out=u)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if not args.no_clocks:
+        clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    diag = None
+    for k in range(args.steps):
+        flush.fill_(float(k))                       # evict L2 between steps
+        ev[k][0].record(stream)
+        _, diag = plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm, u_out=u)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = (plan.launch_count - launches0) / args.steps
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop() if not args.no_clocks else None
+    t_step = max_over_ranks(sum(step_ms) / args.steps / 1e3, ws)
+    value = ws * iters / t_step
+    samples = 2.0 * n * n * N * iters
+
+    # --- dominant kernels, timed alone on the launching stream -------------------------
+    uT = u.t().contiguous()
+    g = torch.empty((N, M), dtype=torch.float32, device="cuda")
+    reps = 20
+    kt = {}
+    for name, fn in (("k_backproject", lambda: plan.rh_adjoint(f, u)), ("k_forward", lambda: plan.rh_forward_t(u, uT, g))):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt[name] = a.elapsed_time(b) / reps / 1e3
+    dom = max(kt, key=kt.get)
+    hbm_peak, peak_kind = peaks()
+    alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e9        # Gop/s, FP32 lanes x max clock
+    ops = OPS_PER_SAMPLE * n * n * N
+    bytes_alg = 4.0 * (n * n + N * M)
+    kernels = {k: {"ms": 1e3 * v, "gsamples_per_s": n * n * N / v / 1e9, "gops": ops / v / 1e9,
+                   "alu_frac": ops / v / 1e9 / alu_peak, "hbm_gbs": bytes_alg / v / 1e9,
+                   "hbm_frac": bytes_alg / v / 1e9 / hbm_peak} for k, v in kt.items()}
+    roof = {"bound": "alu", "kernel": dom, "achieved": ops / kt[dom] / 1e9, "peak": alu_peak, "unit": "Gop/s",
+            "frac": ops / kt[dom] / 1e9 / alu_peak, "traffic": traffic_record(dom),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)",
+            "hbm": {"achieved_gbs": bytes_alg / kt[dom] / 1e9, "peak_gbs": hbm_peak, "peak_source": peak_kind,
+                    "frac": bytes_alg / kt[dom] / 1e9 / hbm_peak}}
+
+    # --- end to end through the C ABI with host buffers ---------------------------------
+    f_h = torch.as_tensor(pr.f, dtype=torch.float32).pin_memory()
+    m_h = torch.as_tensor(pr.mask).pin_memory()
+    u_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        f.copy_(f_h, non_blocking=True)
+        mask.copy_(m_h, non_blocking=True)
+        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm, u_out=u)
+        u_h.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_t = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, k, dt, cores = cpu_oracle_rate(pr)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{k} PDRQS1 iterations ({dt:.1f} s) of the same 512x512/720/729 problem, FP64 C+numpy, "
+                         f"beta and c fixed"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "views": N, "bins": M, "iters_per_solve": iters,
+                       "step": "one tv_pd_solve: power iterations (50+50) + iterations + diagnostics",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "gsamples_per_s": ws * samples / t_step / 1e9,
+            "roofline": roof,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(f_h.numel() * 4 + m_h.numel()),
+                    "d2h_bytes_per_step": int(u_h.numel() * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "diag": {k: diag[k] for k in ("objective", "violation", "gap", "dual_residual", "rel_change")},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
