@@ -344,6 +344,17 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->t1, es * nm);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
+    {
+        // split the backprojection's angles into groups so that tiles x groups fills
+        // the GPU (~8 CTAs of 4 warps per SM on 152 SMs); partial images are summed
+        const int tiles = ((p->n + 31) / 32) * ((p->n + 31) / 32);
+        int G = (1216 + tiles - 1) / tiles;
+        if (G > 8) G = 8;
+        const int maxg = p->N / 32 > 1 ? p->N / 32 : 1;
+        if (G > maxg) G = maxg;
+        p->bp_groups = G < 1 ? 1 : G;
+        if (p->bp_groups > 1) ALLOC(p->bp_part, es * nn * p->bp_groups);
+    }
     ALLOC(p->d_red, sizeof(double) * 8 * p->red_blocks);
     ALLOC(p->d_scal, sizeof(double) * 64);
 #undef ALLOC

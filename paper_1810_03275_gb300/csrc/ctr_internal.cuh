@@ -101,6 +101,8 @@ struct ctr_plan {
     int device = 0;
     int wstride = 48;       // adjoint footprint stride (bins per staged angle)
     int ncand = 2;          // forward candidates per (ray, row)
+    int bp_groups = 1;      // angle groups of the backprojection (partial images summed)
+    void *bp_part = nullptr;   // bp_groups * n*n partial images (bp_groups > 1)
     std::vector<double> theta;
     std::vector<int> radices;    // FFT radices, product n
     bool fft_ok = false;         // n = 2^a 3^b (needed by the preconditioner only)

@@ -1,11 +1,13 @@
 // The discrete Radon transform R_h and its adjoint R_h^* (linear backprojection)
 // of Sec. 3.1, as an exact transpose pair of gather kernels for sm_103a.
 //
-//  * R_h^* (pixel-driven): a CTA owns a tile of pixels; per chunk of angles it
-//    stages, for every angle, the tile's detector footprint into shared memory as
-//    interpolation-ready pairs, then each thread walks its pixels' exact
-//    fixed-point detector coordinate P and accumulates one shared-memory load and
-//    one FMA per (pixel, angle).  No atomics.
+//  * R_h^* (pixel-driven): a CTA owns a 32 x 32 tile of pixels and one group of
+//    angles; per chunk of 32 angles it stages, for every angle, the tile's
+//    detector footprint into shared memory as interpolation-ready pairs, then each
+//    thread walks its 8 pixels' exact fixed-point detector coordinate P and spends
+//    one shared-memory load and one FMA per (pixel, angle).  With several angle
+//    groups the groups' partial images are summed by a small epilogue kernel
+//    (enough CTAs to fill 152 SMs at n = 512).  No atomics.
 //  * R_h (ray-driven): one lane per detector interval [k, k+1) of one angle
 //    marches across the image rows, tracking exactly (integer arithmetic) the
 //    first pixel whose coordinate falls in its interval; it accumulates
@@ -22,11 +24,22 @@ namespace ctr {
 namespace {
 
 constexpr int BP_TJ = 32;    // tile width along j (one warp)
+constexpr int BP_TY = 4;     // warps per CTA
+constexpr int BP_R = 8;      // pixels per thread (rows i0 + ty + 4 r)
+constexpr int BP_TI = BP_TY * BP_R;
 constexpr int BP_ACH = 32;   // angles per staged chunk
 
 template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
 template <> struct Pair<double> { using type = double2; };
+
+// floor(p) = P >> F; the FP32 path has F = 32, so it is the high word.
+template <typename T>
+__device__ __forceinline__ int bin_of(long long P, int F)
+{
+    if constexpr (sizeof(T) == 4) return (int)(P >> 32);
+    else return (int)(P >> F);
+}
 
 // 1 + frac(p) in [1, 2) from the low 32 bits of P (F = 32): the top 23 fraction
 // bits become the mantissa of a float, so the weight is exact and identical in
@@ -74,14 +87,30 @@ __device__ __forceinline__ T div_at(const T *__restrict__ px, int n, int i, int 
     return (d1 + d2) * inv_h;
 }
 
-template <typename T, int TY, int R>
-__global__ void __launch_bounds__(32 * TY)
-k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride,
-              const AngleGeom *__restrict__ geom, BackprojEpi<T> epi)
+template <typename T>
+__device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, int i, int j, T acc)
+{
+    T v = acc * epi.scale;
+    if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
+    v *= epi.outscale;
+    const size_t o = (size_t)i * n + j;
+    if (epi.complex_out) {
+        epi.out[2 * o] = v;
+        epi.out[2 * o + 1] = T(0);
+    } else {
+        epi.out[o] = v;
+    }
+}
+
+// part == nullptr: apply the epilogue directly (one angle group).  Otherwise write
+// this group's partial sums to part[blockIdx.z][n][n].
+template <typename T>
+__global__ void __launch_bounds__(32 * BP_TY)
+k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride, int angles_per_group,
+              const AngleGeom *__restrict__ geom, BackprojEpi<T> epi, T *__restrict__ part)
 {
     using T2 = typename Pair<T>::type;
-    constexpr int NT = 32 * TY;
-    constexpr int TI = TY * R;
+    constexpr int NT = 32 * BP_TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *stage = reinterpret_cast<T2 *>(smem_raw);
     long long *sPb = reinterpret_cast<long long *>(stage + BP_ACH * wstride);
@@ -91,21 +120,23 @@ k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride,
 
     const int tx = threadIdx.x & 31;
     const int ty = threadIdx.x >> 5;
-    const int i0 = blockIdx.y * TI;
+    const int i0 = blockIdx.y * BP_TI;
     const int j0 = blockIdx.x * BP_TJ;
+    const int la = blockIdx.z * angles_per_group;
+    const int lb = min(N, la + angles_per_group);
     const double inv2F = ldexp(1.0, -F);
 
-    T acc[R];
+    T acc[BP_R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int r = 0; r < BP_R; ++r) acc[r] = T(0);
 
-    for (int l0 = 0; l0 < N; l0 += BP_ACH) {
-        const int na = min(BP_ACH, N - l0);
+    for (int l0 = la; l0 < lb; l0 += BP_ACH) {
+        const int na = min(BP_ACH, lb - l0);
         __syncthreads();
         if (threadIdx.x < na) {
             const AngleGeom ag = geom[l0 + threadIdx.x];
             const long long P00 = (long long)i0 * ag.C + (long long)j0 * ag.S + ag.O;
-            const long long P10 = P00 + (long long)(TI - 1) * ag.C;
+            const long long P10 = P00 + (long long)(BP_TI - 1) * ag.C;
             const long long P01 = P00 + (long long)(BP_TJ - 1) * ag.S;
             const long long P11 = P10 + (long long)(BP_TJ - 1) * ag.S;
             const long long pmin = min(min(P00, P10), min(P01, P11));
@@ -125,15 +156,15 @@ k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride,
             stage[e] = make_stage(g0, g1);
         }
         __syncthreads();
+#pragma unroll 2
         for (int a = 0; a < na; ++a) {
             const long long C = sC[a];
             long long P = sPb[a] + (long long)ty * C + (long long)tx * sS[a];
-            const long long D = C * TY;
+            const long long D = C * BP_TY;
             const T2 *row = stage + a * wstride;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int idx = (int)(P >> F);
-                acc[r] = interp(acc[r], row[idx], P, F, inv2F);
+            for (int r = 0; r < BP_R; ++r) {
+                acc[r] = interp(acc[r], row[bin_of<T>(P, F)], P, F, inv2F);
                 P += D;
             }
         }
@@ -141,20 +172,25 @@ k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride,
 
     const int j = j0 + tx;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = i0 + ty + TY * r;
+    for (int r = 0; r < BP_R; ++r) {
+        const int i = i0 + ty + BP_TY * r;
         if (i < n && j < n) {
-            T v = acc[r] * epi.scale;
-            if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
-            v *= epi.outscale;
-            const size_t o = (size_t)i * n + j;
-            if (epi.complex_out) {
-                epi.out[2 * o] = v;
-                epi.out[2 * o + 1] = T(0);
-            } else {
-                epi.out[o] = v;
-            }
+            if (part) part[((size_t)blockIdx.z * n + i) * n + j] = acc[r];
+            else bp_epilogue(epi, n, i, j, acc[r]);
         }
+    }
+}
+
+// Sum of the angle groups' partial images, then the backprojection epilogue.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_bp_reduce(const T *__restrict__ part, int groups, int n, BackprojEpi<T> epi)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T s = part[e];
+        for (int z = 1; z < groups; ++z) s += part[(size_t)z * nn + e];
+        bp_epilogue(epi, n, (int)(e / n), (int)(e % n), s);
     }
 }
 
@@ -166,7 +202,7 @@ __device__ __forceinline__ long long ceil_div_ll(long long a, long long b)
     return q;
 }
 
-__device__ __forceinline__ void acc_sample(float &Su, float &Sf, float v, long long P)
+__device__ __forceinline__ void acc_sample(float &Su, float &Sf, float v, long long P, int, double)
 {
     Su += v;
     Sf = fmaf(one_plus_frac32(P), v, Sf);     // sum (1 + frac) u
@@ -203,7 +239,32 @@ __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_
     if (epi.t1) epi.t1[r] = t;
 }
 
-template <typename T, int NC>
+// One row of the march: the NC candidate pixels q, q+1, ... of the lane's interval.
+// EXACT1: the first candidate is always inside the interval (A <= 2^F, i.e. h <= ds).
+template <typename T, int NC, bool EXACT1>
+__device__ __forceinline__ void march_row(const T *__restrict__ rowp, int dq, int n, int k, int F, double inv2F,
+                                          long long Pa, int q, long long A, T &Su, T &Sf)
+{
+    {
+        bool ok = (unsigned)q < (unsigned)n;
+        if (!EXACT1) ok = ok && bin_of<T>(Pa, F) == k;
+        const T v = ok ? rowp[dq * q] : T(0);
+        acc_sample(Su, Sf, v, Pa, F, inv2F);
+    }
+    long long P = Pa;
+#pragma unroll
+    for (int c = 1; c < NC; ++c) {
+        P += A;
+        const int qq = q + c;
+        const bool ok = bin_of<T>(P, F) == k && (unsigned)qq < (unsigned)n;
+        if (__any_sync(0xffffffffu, ok)) {
+            const T v = ok ? rowp[dq * qq] : T(0);
+            acc_sample(Su, Sf, v, P, F, inv2F);
+        }
+    }
+}
+
+template <typename T, int NC, bool EXACT1>
 __global__ void __launch_bounds__(128)
 k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F,
           const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
@@ -215,8 +276,10 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
     if (kb >= M) return;                              // warp-uniform
     const AngleMarch am = march[l];
     const int k = kb + lane - 1;                      // this lane's interval [k, k+1)
-    const T *__restrict__ src = am.layout ? u : uT;
     const double inv2F = ldexp(1.0, -F);
+    // pixel (m, q) of the march is at base[m*n + dq*q]
+    const int dq = am.flip ? -1 : 1;
+    const T *__restrict__ base = (am.layout ? u : uT) + (am.flip ? (n - 1) : 0);
 
     // Rows m where the lane's pixel run may be inside [0, n): q*(m) = Q0 - m b.
     int mlo = n, mhi = -1;
@@ -241,32 +304,86 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
     const int mhi_w = __reduce_max_sync(0xffffffffu, mhi);
 
     T Su = T(0), Sf = T(0);
-    if (mlo_w <= mhi_w) {
+    if constexpr (sizeof(T) == 4 && EXACT1 && NC == 2) {
+        if (mlo_w <= mhi_w) {
+            // FP32 march with 2^32 > A >= 2^31.5: r = P(q_a) - k 2^32 in [0, A) fits in 32
+            // bits and is the fixed-point fraction of the interval's first pixel; the
+            // second pixel (q_a + 1) lies in the interval iff r + A < 2^32.
+            const long long K = (long long)k << 32;
+            const long long A = am.A, B = am.B;
+            const long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
+            unsigned r = (unsigned)(qa * A + (long long)mlo_w * B + am.Op - K);
+            int q = (int)qa;
+            int off = mlo_w * n + dq * q;                 // element offset of pixel (m, q)
+            const unsigned A32 = (unsigned)A;             // A = 2^32 wraps to 0 (then B = 0)
+            const unsigned lim = (unsigned)((1ll << 32) - A);
+            const int rows = mhi_w - mlo_w + 1;
+            const float *__restrict__ b1 = base + dq;     // pixel (m, q + 1)
+            if (B == 0) {
+#pragma unroll 2
+                for (int rr = 0; rr < rows; ++rr) {
+                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    Su += v1 + v2;
+                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
+                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
+                    off += n;
+                }
+            } else if (B > 0) {
+                const unsigned B32 = (unsigned)B, thr = (unsigned)(A - B);   // step back when r >= A - B
+#pragma unroll 2
+                for (int rr = 0; rr < rows; ++rr) {
+                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    Su += v1 + v2;
+                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
+                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
+                    const bool back = r >= thr;
+                    r += back ? B32 - A32 : B32;
+                    q -= back ? 1 : 0;
+                    off += back ? n - dq : n;
+                }
+            } else {
+                const unsigned nb = (unsigned)(-B);       // step forward when r < |B|
+#pragma unroll 2
+                for (int rr = 0; rr < rows; ++rr) {
+                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    Su += v1 + v2;
+                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
+                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
+                    const bool fwd = r < nb;
+                    r += fwd ? A32 - nb : 0u - nb;
+                    q += fwd ? 1 : 0;
+                    off += fwd ? n + dq : n;
+                }
+            }
+        }
+    } else if (mlo_w <= mhi_w) {
         const long long K = (long long)k << F;
         const long long A = am.A, B = am.B;
         long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
         long long Pa = qa * A + (long long)mlo_w * B + am.Op;   // in [K, K + A)
         int q = (int)qa;
-        for (int m = mlo_w; m <= mhi_w; ++m) {
-            const T *rowp = src + (size_t)m * n;
-            long long P = Pa;
-            int qq = q;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                if ((P >> F) == (long long)k && (unsigned)qq < (unsigned)n) {
-                    const int qp = am.flip ? (n - 1 - qq) : qq;
-                    if constexpr (sizeof(T) == 4) acc_sample(Su, Sf, rowp[qp], P);
-                    else acc_sample(Su, Sf, rowp[qp], P, F, inv2F);
-                }
-                P += A;
-                ++qq;
+        const T *rowp = base + (size_t)mlo_w * n;
+        const int rows = mhi_w - mlo_w + 1;
+        // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
+        if (B >= 0) {
+            const long long KA = K + A;
+#pragma unroll 2
+            for (int r = 0; r < rows; ++r) {
+                march_row<T, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+                Pa += B;
+                if (Pa >= KA) { Pa -= A; --q; }
+                rowp += n;
             }
-            // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
-            Pa += B;
-            if (B >= 0) {
-                if (Pa - A >= K) { Pa -= A; --q; }
-            } else {
+        } else {
+#pragma unroll 2
+            for (int r = 0; r < rows; ++r) {
+                march_row<T, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+                Pa += B;
                 if (Pa < K) { Pa += A; ++q; }
+                rowp += n;
             }
         }
     }
@@ -293,27 +410,17 @@ __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ in, T *
     }
 }
 
-template <typename T, int TY, int R>
-ctr_status launch_bp_cfg(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+template <typename T>
+size_t bp_smem(const ctr_plan *p)
 {
     using T2 = typename Pair<T>::type;
-    const size_t smem = sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
-    auto kern = k_backproject<T, TY, R>;
-    dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + TY * R - 1) / (TY * R));
-    p->launches++;
-    kern<<<grid, 32 * TY, smem, s>>>(g, p->n, p->N, p->M, p->F, p->wstride, p->d_geom, epi);
-    CTR_CHECK_LAUNCH("k_backproject");
-    return CTR_OK;
+    return sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
 }
 
-template <typename T, int TY, int R>
-ctr_status configure_bp_cfg(const ctr_plan *p)
+template <typename T, int NC, bool EXACT1>
+void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
-    using T2 = typename Pair<T>::type;
-    const size_t smem = sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
-    if (smem > 48 * 1024)
-        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T, TY, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return CTR_OK;
+    k_forward<T, NC, EXACT1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi);
 }
 
 }  // namespace
@@ -321,30 +428,49 @@ ctr_status configure_bp_cfg(const ctr_plan *p)
 template <typename T>
 ctr_status configure_radon(const ctr_plan *p)
 {
-    ctr_status st = configure_bp_cfg<T, 8, 4>(p);
-    if (st != CTR_OK) return st;
-    return configure_bp_cfg<T, 4, 4>(p);
+    const size_t smem = bp_smem<T>(p);
+    if (smem > 48 * 1024)
+        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return CTR_OK;
 }
 
 template <typename T>
 ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
 {
-    // 16 x 32 tiles (4 warps, 4 rows each) keep enough CTAs in flight at n <= 1024;
-    // 32 x 32 tiles (8 warps) above.
-    if (p->n > 1024) return launch_bp_cfg<T, 8, 4>(p, g, epi, s);
-    return launch_bp_cfg<T, 4, 4>(p, g, epi, s);
+    const int G = p->bp_groups;
+    const int per = (p->N + G - 1) / G;
+    dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
+    T *part = G > 1 ? (T *)p->bp_part : nullptr;
+    p->launches++;
+    k_backproject<T><<<grid, 32 * BP_TY, bp_smem<T>(p), s>>>(g, p->n, p->N, p->M, p->F, p->wstride, per, p->d_geom,
+                                                              epi, part);
+    CTR_CHECK_LAUNCH("k_backproject");
+    if (G > 1) {
+        const size_t nn = (size_t)p->n * p->n;
+        int blocks = (int)((nn + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        p->launches++;
+        k_bp_reduce<T><<<blocks, 256, 0, s>>>(part, G, p->n, epi);
+        CTR_CHECK_LAUNCH("k_bp_reduce");
+    }
+    return CTR_OK;
 }
 
 template <typename T>
 ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
     dim3 grid((p->M + 4 * 31 - 1) / (4 * 31), p->N);
+    const bool exact1 = p->h <= p->ds;
     p->launches++;
-    switch (p->ncand) {
-    case 1: k_forward<T, 1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
-    case 2: k_forward<T, 2><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
-    case 3: k_forward<T, 3><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
-    case 4: k_forward<T, 4><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi); break;
+    switch (p->ncand * 2 + (exact1 ? 1 : 0)) {
+    case 2: launch_fwd_cfg<T, 1, false>(p, grid, u, uT, epi, s); break;
+    case 3: launch_fwd_cfg<T, 1, true>(p, grid, u, uT, epi, s); break;
+    case 4: launch_fwd_cfg<T, 2, false>(p, grid, u, uT, epi, s); break;
+    case 5: launch_fwd_cfg<T, 2, true>(p, grid, u, uT, epi, s); break;
+    case 6: launch_fwd_cfg<T, 3, false>(p, grid, u, uT, epi, s); break;
+    case 7: launch_fwd_cfg<T, 3, true>(p, grid, u, uT, epi, s); break;
+    case 8: launch_fwd_cfg<T, 4, false>(p, grid, u, uT, epi, s); break;
+    case 9: launch_fwd_cfg<T, 4, true>(p, grid, u, uT, epi, s); break;
     default: return fail(CTR_EUNSUPPORTED, "forward projector: too many pixels per detector interval");
     }
     CTR_CHECK_LAUNCH("k_forward");
@@ -360,6 +486,8 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
     CTR_CHECK_LAUNCH("k_transpose");
     return CTR_OK;
 }
+
+int backproject_tile_rows() { return BP_TI; }
 
 template ctr_status launch_backproject<float>(const ctr_plan *, const float *, const BackprojEpi<float> &, cudaStream_t);
 template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &, cudaStream_t);
