@@ -131,6 +131,26 @@ ctr_status rh_adjoint(ctr_plan *plan, const void *g_dev, void *u_dev, void *stre
 ctr_status precond_apply(ctr_plan *plan, const ctr_params *params, const void *y_dev,
                          void *x_dev, void *stream);
 
+/* precond_apply for callers that cannot allocate device memory: no plan, no
+ * cudaMalloc/cudaFree, no allocating library call.  Meant for code embedded in a
+ * host application that owns all device memory (a fixed pool handed out at start-up)
+ * and forbids allocation afterwards -- cudaMalloc/cudaFree may synchronise the
+ * device and fragment that budget, which a real-time reconstruction loop cannot
+ * accept.  The thesis has no counterpart: this is a packaging of precond_apply.
+ * FP32 only; y_dev, x_dev: n*n floats owned by the caller (may alias); n must be
+ * 2^a 3^b with n <= 1024 (larger n: CTR_EINVAL with a message).  sigma, tau, c,
+ * eps as in precond_apply (all > 0).
+ * Scratch: 12 MiB of static device arrays (the complex FFT buffer, the symbol, the
+ * twiddles for n = 1024) that every GPU loading this library holds until the
+ * process exits.  Each call overwrites all of the scratch it reads, so no state
+ * carries over, but every call shares the same arrays: calls that overlap on the
+ * GPU (concurrent streams or host threads) race and give wrong results.  The first
+ * call on a device looks up the arrays' device addresses (cudaGetSymbolAddress) and
+ * sets kernel attributes for that device; make that first call from one thread, on
+ * the device it will run on, before any stream capture. */
+ctr_status precond_apply_static(int n, double sigma, double tau, double c, double eps, const float *y_dev,
+                                float *x_dev, void *stream);
+
 /* Solve problem (C_h) (Sec. 3.2, with the data tolerance) by `iters` iterations of
  * Alg. 4 (PDRQS1) from u = 0:
  *   min_u  sum_{r off trace} 1/2 ((R_h u)_r - f_r)^2 + alpha ||grad_h u||_1

@@ -346,4 +346,107 @@ template ctr_status configure_fft<double>(const ctr_plan *);
 template ctr_status launch_symbols<float>(const ctr_plan *, double, double, double, double, cudaStream_t);
 template ctr_status launch_symbols<double>(const ctr_plan *, double, double, double, double, cudaStream_t);
 
+// ------------------------------------------------------------------------------
+// precond_apply_static: the FP32 preconditioner without any device allocation.
+// Its scratch (the complex FFT buffer, the symbol and the twiddles for one image of
+// up to STATIC_MAX_N x STATIC_MAX_N) lives in file-scope __device__ arrays that every
+// GPU loading this library holds until the process exits (12 MiB + 8 KiB).  Host
+// code cannot use these names as device addresses, so the addresses are looked up
+// once per device with cudaGetSymbolAddress, with that device current, on the
+// first call made on it.  All calls share the arrays: calls that overlap on the GPU
+// (different streams, or different host threads) race on them.
+// ------------------------------------------------------------------------------
+namespace {
+
+constexpr int STATIC_MAX_N = 1024;
+constexpr int STATIC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) float2 g_static_cbuf[STATIC_MAX_N * STATIC_MAX_N];
+static __device__ __align__(256) float g_static_sym[STATIC_MAX_N * STATIC_MAX_N];
+static __device__ __align__(256) float2 g_static_tw[STATIC_MAX_N];
+
+struct StaticScratch {
+    float2 *cbuf = nullptr;
+    float *sym = nullptr;
+    float2 *tw = nullptr;
+    bool ready = false;
+};
+static StaticScratch g_scratch[STATIC_MAX_DEVICES];
+
+// tw[t] = exp(-2 pi i t/n), computed in double and rounded to float
+__global__ void k_static_twiddles(float2 *tw, int n)
+{
+    const double pi = 3.14159265358979323846;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        tw[t] = make_float2((float)cos(2.0 * pi * t / n), (float)(-sin(2.0 * pi * t / n)));
+}
+
+// Set-up for the current device (first call on it): symbol addresses and the
+// shared-memory limits of the FFT kernels.  Not thread-safe against a concurrent
+// first call on the same device.
+ctr_status static_setup(int dev)
+{
+    StaticScratch &s = g_scratch[dev];
+    if (s.ready) return CTR_OK;
+    CTR_CUDA(cudaGetSymbolAddress((void **)&s.cbuf, g_static_cbuf));
+    CTR_CUDA(cudaGetSymbolAddress((void **)&s.sym, g_static_sym));
+    CTR_CUDA(cudaGetSymbolAddress((void **)&s.tw, g_static_tw));
+    const int smax = 2 * 4 * (STATIC_MAX_N + 1) * (int)sizeof(float2);   // column kernel at n = 1024
+    CTR_CUDA(cudaFuncSetAttribute(k_fft_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    s.ready = true;
+    return CTR_OK;
+}
+
+}  // namespace
+
 }  // namespace ctr
+
+extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, double c, double eps, const float *y_dev,
+                                           float *x_dev, void *stream)
+{
+    using namespace ctr;
+    if (n < 1 || n > STATIC_MAX_N)
+        return fail(CTR_EINVAL, "precond_apply_static: n must be in [1, " + std::to_string(STATIC_MAX_N) +
+                                    "] (the size of its static scratch)");
+    if (!y_dev || !x_dev) return fail(CTR_EINVAL, "precond_apply_static: null buffer");
+    if (!(sigma > 0) || !(tau > 0) || !(c > 0) || !(eps > 0) || !std::isfinite(sigma) || !std::isfinite(tau) ||
+        !std::isfinite(c) || !std::isfinite(eps))
+        return fail(CTR_EINVAL, "precond_apply_static: sigma, tau, c and eps must be finite and > 0");
+    FftPasses fp;
+    {
+        int m = n, cnt = 0;
+        while (m % 4 == 0) { fp.radix[cnt++] = 4; m /= 4; }
+        while (m % 2 == 0) { fp.radix[cnt++] = 2; m /= 2; }
+        while (m % 3 == 0) { fp.radix[cnt++] = 3; m /= 3; }
+        if (m != 1) return fail(CTR_EUNSUPPORTED, "precond_apply_static: n must be of the form 2^a 3^b");
+        fp.count = cnt;
+    }
+    int dev = -1;
+    CTR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return fail(CTR_EUNSUPPORTED, "precond_apply_static: device index too large");
+    ctr_status st = static_setup(dev);
+    if (st != CTR_OK) return st;
+    const StaticScratch &s = g_scratch[dev];
+    cudaStream_t str = (cudaStream_t)stream;
+    // the same three FFT passes as precond_apply, with every scratch in the static arrays
+    k_static_twiddles<<<(n + 255) / 256, 256, 0, str>>>(s.tw, n);
+    const size_t nn = (size_t)n * n;
+    int blocks = (int)((nn + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps);
+    int rpc = 2048 / n;
+    rpc = rpc < 1 ? 1 : (rpc > 8 ? 8 : rpc);
+    int cw = 1;
+    for (int w = 4; w > 1; w /= 2)
+        if (2 * (size_t)w * (n + 1) * sizeof(float2) <= 160 * 1024) { cw = w; break; }
+    const size_t smr = 2 * (size_t)rpc * n * sizeof(float2), smc = 2 * (size_t)cw * (n + 1) * sizeof(float2);
+    const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
+    k_fft_rows_fwd<float><<<gr, FFT_THREADS, smr, str>>>(y_dev, s.cbuf, n, rpc, fp, s.tw);
+    k_fft_cols<float><<<gc, FFT_THREADS, smc, str>>>(s.cbuf, s.sym, n, cw, fp, s.tw);
+    k_fft_rows_inv<float><<<gr, FFT_THREADS, smr, str>>>(s.cbuf, n, rpc, fp, s.tw, x_dev, 0, nullptr, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "precond_apply_static launch");
+    return CTR_OK;
+}

@@ -61,7 +61,7 @@ class State(ctypes.Structure):
 
 EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_last_error", "ctr_plan_device_bytes",
            "ctr_plan_launch_count", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
-           "ctr_power_lambda", "ctr_grad", "ctr_div"]
+           "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static"]
 
 
 def load(path: str = LIB_PATH):
@@ -95,6 +95,9 @@ def load(path: str = LIB_PATH):
                                   P(Diag), vp]
         lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
         lib.ctr_power_lambda.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(ctypes.c_double), vp]
+        lib.precond_apply_static.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, vp, vp, vp]
+        lib.precond_apply_static.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
         lib.ctr_div.argtypes = [vp, vp, vp, vp]
         for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
@@ -117,6 +120,20 @@ def default_params(**kw) -> Params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def precond_apply_static(y, sigma: float, tau: float, c: float, eps: float, x=None, stream=None):
+    """precond_apply without a plan and without device allocation inside the library
+    (static scratch, FP32, n <= 1024): for callers that own all device memory.  Calls
+    that overlap on the GPU race on the shared scratch."""
+    import torch
+    if not isinstance(y, torch.Tensor) or not y.is_cuda or y.dtype != torch.float32 or not y.is_contiguous() \
+            or y.dim() != 2 or y.shape[0] != y.shape[1]:
+        raise TypeError("y must be a contiguous square float32 CUDA tensor")
+    x = torch.empty_like(y) if x is None else x
+    _check(load().precond_apply_static(int(y.shape[0]), float(sigma), float(tau), float(c), float(eps),
+                                       ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), _stream(stream)))
+    return x
 
 
 def _stream(stream):
