@@ -160,6 +160,41 @@ def cpu_oracle_rate(problem, budget_s: float = 12.0, max_iters: int = 40):
     return k / dt, k, dt, oracle.num_threads()
 
 
+def measure_forms(iters: int = 30):
+    """The BF16 form against the plain FP32 path on the 2048 x 2048 / 2048 views /
+    2897 bins geometry: iterations/s of Alg. 4 (fixed beta and c, so only the
+    iteration is timed), CUDA events on the torch stream."""
+    import torch
+    from paper_1810_03275_gb300 import ctrecon as ct
+    from paper_1810_03275_gb300 import phantom
+    pr = phantom.make_problem("forms_2048", 2048, 2048, 2897, seed=5, n_ellipses=2, n_metal=1, noise="poisson",
+                              alpha=0.3, iters=iters)
+    f = torch.as_tensor(pr.f, dtype=torch.float32, device="cuda")
+    mask = torch.as_tensor(pr.mask, device="cuda")
+    out = {}
+    beta = c = None
+    for dt in ("f32", "bf16"):
+        plan = ct.Plan(pr.n, pr.n_angles, pr.n_bins, angles=pr.theta, dtype=dt)
+        if beta is None:
+            beta = plan.power_beta(20)
+            c = 1.05 * plan.power_lambda(beta, np.pi / pr.n, 20)
+        prm = ct.default_params(beta=beta, c=c)
+        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, 5, params=prm)      # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        out[dt] = {"iters_per_s": iters / t, "gsamples_per_s": 2.0 * pr.n * pr.n * pr.n_angles * iters / t / 1e9}
+        del plan
+        torch.cuda.empty_cache()
+    out["bf16_speedup"] = out["bf16"]["iters_per_s"] / out["f32"]["iters_per_s"]
+    out["workload"] = f"2048x2048, 2048 views, 2897 bins, {iters} iterations per timing (beta, c fixed)"
+    return out
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
@@ -204,6 +239,7 @@ def main():
     ap.add_argument("--iters", type=int, default=None, help="override iterations per solve (profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16-vs-FP32 2048^2 timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.iters is None:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -298,6 +334,10 @@ def main():
         torch.cuda.synchronize()
     e2e_t = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = measure_forms()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, k, dt, cores = cpu_oracle_rate(pr)
@@ -316,6 +356,7 @@ def main():
             "gsamples_per_s": ws * samples / t_step / 1e9,
             "roofline": roof,
             "kernels": kernels,
+            "forms": forms,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(f_h.numel() * 4 + m_h.numel()),
                     "d2h_bytes_per_step": int(u_h.numel() * 4)},

@@ -93,6 +93,11 @@ typedef struct {
 
 /* Create a plan for `geo` computing in `dtype` (CTR_F32 or CTR_F64; CTR_BF16 stores
  * sinogram and image operands of R_h/R_h^* in bfloat16 with FP32 accumulation).
+ * In a CTR_BF16 plan every buffer is float except the operands the projectors read:
+ * u_dev (and uT_dev) of rh_forward / rh_forward_t and g_dev of rh_adjoint are
+ * bfloat16 (uint16 storage); the solver keeps bfloat16 copies of its projector
+ * operands internally and everything else (duals, preconditioner, power iterations,
+ * diagnostics) in FP32/FP64.
  * Allocates all device workspace on the current device; nothing is allocated later.
  * Returns CTR_EINVAL for n < 1, n_angles < 1, n_bins < 1, h or ds <= 0 or a null
  * angles_host; CTR_EUNSUPPORTED for n > 4096 or an FFT length with a prime factor

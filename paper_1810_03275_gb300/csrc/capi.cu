@@ -32,6 +32,8 @@ template <typename T> ctr_status op_grad(ctr_plan *, const T *, T *, cudaStream_
 template <typename T> ctr_status op_div(ctr_plan *, const T *, T *, cudaStream_t);
 template <typename T> ctr_status op_forward(ctr_plan *, const T *, const T *, T *, double, cudaStream_t);
 template <typename T> ctr_status op_adjoint(ctr_plan *, const T *, T *, double, cudaStream_t);
+ctr_status op_forward_bf16(ctr_plan *, const __nv_bfloat16 *, const __nv_bfloat16 *, float *, cudaStream_t);
+ctr_status op_adjoint_bf16(ctr_plan *, const __nv_bfloat16 *, float *, cudaStream_t);
 template <typename T> ctr_status power_beta(ctr_plan *, int, double *, cudaStream_t);
 template <typename T> ctr_status power_lambda(ctr_plan *, double, double, int, double *, cudaStream_t);
 template <typename T>
@@ -286,7 +288,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     if (g->n > 4096) return fail(CTR_EUNSUPPORTED, "n > 4096");
     if (g->n_angles > 65535) return fail(CTR_EUNSUPPORTED, "more than 65535 angles");
     if (g->ds / g->h > 2.5) return fail(CTR_EUNSUPPORTED, "ds/h > 2.5");
-    if (dtype != CTR_F32 && dtype != CTR_F64) return fail(CTR_EUNSUPPORTED, "dtype not supported by this build");
+    if (dtype != CTR_F32 && dtype != CTR_F64 && dtype != CTR_BF16) return fail(CTR_EINVAL, "unknown dtype");
     for (int l = 0; l < g->n_angles; ++l)
         if (!std::isfinite(g->angles_host[l])) return fail(CTR_EINVAL, "non-finite angle");
     const double pmax = g->n_bins + 4.0 + 2.0 * g->n * (g->h / g->ds);
@@ -306,6 +308,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     } else {
         p->F = 32;
         p->esize = 4;
+        p->bf16 = (dtype == CTR_BF16);
         if (pmax > (double)(1 << 28)) { destroy(p); return fail(CTR_EUNSUPPORTED, "geometry too large"); }
     }
     ctr_status st = fft_radices(p->n, p->radices);
@@ -344,6 +347,11 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->t1, es * nm);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
+    if (p->bf16) {
+        ALLOC(p->uh, sizeof(__nv_bfloat16) * nn);
+        ALLOC(p->uTh, sizeof(__nv_bfloat16) * nn);
+        ALLOC(p->y1h, sizeof(__nv_bfloat16) * nm);
+    }
     {
         // split the backprojection's angles into groups so that tiles x groups fills
         // the GPU (~8 CTAs of 4 warps per SM on 152 SMs); partial images are summed
@@ -398,6 +406,10 @@ ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
         if ((st = launch_transpose<double>(p, (const double *)u, (double *)p->uT, s)) != CTR_OK) return st;
         return op_forward<double>(p, (const double *)u, (const double *)p->uT, (double *)g, 1.0, s);
     }
+    if (p->bf16) {
+        if ((st = launch_transpose<__nv_bfloat16>(p, (const __nv_bfloat16 *)u, p->uTh, s)) != CTR_OK) return st;
+        return op_forward_bf16(p, (const __nv_bfloat16 *)u, p->uTh, (float *)g, s);
+    }
     if ((st = launch_transpose<float>(p, (const float *)u, (float *)p->uT, s)) != CTR_OK) return st;
     return op_forward<float>(p, (const float *)u, (const float *)p->uT, (float *)g, 1.0, s);
 }
@@ -407,6 +419,7 @@ ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, voi
     CTR_GUARD(p);
     if (!u || !uT || !g) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->bf16) return op_forward_bf16(p, (const __nv_bfloat16 *)u, (const __nv_bfloat16 *)uT, (float *)g, s);
     return CTR_DISPATCH(p, op_forward<float>(p, (const float *)u, (const float *)uT, (float *)g, 1.0, s),
                         op_forward<double>(p, (const double *)u, (const double *)uT, (double *)g, 1.0, s));
 }
@@ -418,6 +431,7 @@ ctr_status rh_adjoint(ctr_plan *p, const void *g, void *u, void *stream)
     CTR_GUARD(p);
     if (!u || !g) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->bf16) return op_adjoint_bf16(p, (const __nv_bfloat16 *)g, (float *)u, s);
     return CTR_DISPATCH(p, op_adjoint<float>(p, (const float *)g, (float *)u, 1.0, s),
                         op_adjoint<double>(p, (const double *)g, (double *)u, 1.0, s));
 }

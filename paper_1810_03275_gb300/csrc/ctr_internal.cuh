@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libctrecon.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,6 +85,7 @@ struct ForwardEpi {
     T *Ru;             // out: Rt u_new
     T *v1b;            // in/out: bar v1
     T *y1;             // out: bar v1_new + sigma Rt u_new
+    __nv_bfloat16 *y1h;   // if set: y1 is stored here in bfloat16 instead (BF16 operand storage)
     T *t1;             // optional out: resolvent output (dual certificate)
     const T *dw, *da, *dlo, *dhi;   // per-bin data term, beta-scaled
 };
@@ -101,6 +103,8 @@ struct ctr_plan {
     int device = 0;
     int wstride = 48;       // adjoint footprint stride (bins per staged angle)
     int ncand = 2;          // forward candidates per (ray, row)
+    bool bf16 = false;      // CTR_BF16: projector operands stored in bfloat16, compute in FP32
+    __nv_bfloat16 *uh = nullptr, *uTh = nullptr, *y1h = nullptr;   // bfloat16 operand copies
     int bp_groups = 1;      // angle groups of the backprojection (partial images summed)
     void *bp_part = nullptr;   // bp_groups * n*n partial images (bp_groups > 1)
     std::vector<double> theta;
@@ -145,6 +149,12 @@ namespace ctr {
 // Launch helpers implemented in the .cu files ------------------------------------
 template <typename T>
 ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s);
+// the same with the sinogram operand stored in bfloat16 (FP32 accumulation)
+ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, const BackprojEpi<float> &epi,
+                                   cudaStream_t s);
+// the forward projector with the image operands stored in bfloat16 (FP32 accumulation)
+ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT,
+                               const ForwardEpi<float> &epi, cudaStream_t s);
 template <typename T>
 ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s);
 template <typename T>
@@ -156,7 +166,8 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
 // result before accumulation.
 template <typename T>
 ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf, const T *sym, T *out,
-                            int mode, T *outT, T *dout, cudaStream_t s);
+                            int mode, T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh = nullptr,
+                            __nv_bfloat16 *outTh = nullptr);
 template <typename T>
 ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s);
 

@@ -205,7 +205,8 @@ k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
 template <typename T>
 __global__ void __launch_bounds__(FFT_THREADS)
 k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_per_cta, FftPasses fp,
-               const typename C2<T>::type *__restrict__ tw, T *out, int mode, T *outT, T *dout)
+               const typename C2<T>::type *__restrict__ tw, T *out, int mode, T *outT, T *dout,
+               __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -224,14 +225,17 @@ k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_pe
         T o = v;
         if (mode == 1) o += out[g];
         out[g] = o;
+        if (outh) outh[g] = __float2bfloat16_rn((float)o);   // bfloat16 operand copy
         res[e].y = o;     // keep the final value for the transposed write
     }
-    if (outT) {
+    if (outT || outTh) {
         __syncthreads();
         // column-major writes: consecutive threads take consecutive rows of one column
         for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
             const int col = e / cnt, r = e - col * cnt;
-            outT[(size_t)col * n + r0 + r] = res[(size_t)r * n + col].y;
+            const T o = res[(size_t)r * n + col].y;
+            if (outT) outT[(size_t)col * n + r0 + r] = o;
+            if (outTh) outTh[(size_t)col * n + r0 + r] = __float2bfloat16_rn((float)o);
         }
     }
 }
@@ -291,7 +295,7 @@ size_t fft_smem_bytes(const ctr_plan *p, int which)
 
 template <typename T>
 ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf, const T *sym, T *out, int mode,
-                            T *outT, T *dout, cudaStream_t s)
+                            T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
 {
     using T2 = typename C2<T>::type;
     const int n = p->n;
@@ -309,7 +313,7 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
     k_fft_cols<T><<<gc, FFT_THREADS, smc, s>>>(cb, sym, n, cw, fp, tw);
     CTR_CHECK_LAUNCH("k_fft_cols");
     p->launches++;
-    k_fft_rows_inv<T><<<gr, FFT_THREADS, smr, s>>>(cb, n, rpc, fp, tw, out, mode, outT, dout);
+    k_fft_rows_inv<T><<<gr, FFT_THREADS, smr, s>>>(cb, n, rpc, fp, tw, out, mode, outT, dout, outh, outTh);
     CTR_CHECK_LAUNCH("k_fft_rows_inv");
     return CTR_OK;
 }
@@ -339,8 +343,8 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
     return CTR_OK;
 }
 
-template ctr_status launch_circulant<float>(const ctr_plan *, const float *, bool, const float *, float *, int, float *, float *, cudaStream_t);
-template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int, double *, double *, cudaStream_t);
+template ctr_status launch_circulant<float>(const ctr_plan *, const float *, bool, const float *, float *, int, float *, float *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
+template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int, double *, double *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
 template ctr_status configure_fft<float>(const ctr_plan *);
 template ctr_status configure_fft<double>(const ctr_plan *);
 template ctr_status launch_symbols<float>(const ctr_plan *, double, double, double, double, cudaStream_t);
@@ -445,7 +449,8 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
     k_fft_rows_fwd<float><<<gr, FFT_THREADS, smr, str>>>(y_dev, s.cbuf, n, rpc, fp, s.tw);
     k_fft_cols<float><<<gc, FFT_THREADS, smc, str>>>(s.cbuf, s.sym, n, cw, fp, s.tw);
-    k_fft_rows_inv<float><<<gr, FFT_THREADS, smr, str>>>(s.cbuf, n, rpc, fp, s.tw, x_dev, 0, nullptr, nullptr);
+    k_fft_rows_inv<float><<<gr, FFT_THREADS, smr, str>>>(s.cbuf, n, rpc, fp, s.tw, x_dev, 0, nullptr, nullptr,
+                                                         nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "precond_apply_static launch");
     return CTR_OK;

@@ -33,6 +33,11 @@ template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
 template <> struct Pair<double> { using type = double2; };
 
+// operand loads: FP32/FP64 as stored, bfloat16 widened to FP32
+__device__ __forceinline__ float ldv(const float *p) { return *p; }
+__device__ __forceinline__ double ldv(const double *p) { return *p; }
+__device__ __forceinline__ float ldv(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
 // floor(p) = P >> F; the FP32 path has F = 32, so it is the high word.
 template <typename T>
 __device__ __forceinline__ int bin_of(long long P, int F)
@@ -104,9 +109,9 @@ __device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, in
 
 // part == nullptr: apply the epilogue directly (one angle group).  Otherwise write
 // this group's partial sums to part[blockIdx.z][n][n].
-template <typename T>
+template <typename T, typename S>
 __global__ void __launch_bounds__(32 * BP_TY)
-k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride, int angles_per_group,
+k_backproject(const S *__restrict__ g, int n, int N, int M, int F, int wstride, int angles_per_group,
               const AngleGeom *__restrict__ geom, BackprojEpi<T> epi, T *__restrict__ part)
 {
     using T2 = typename Pair<T>::type;
@@ -150,9 +155,9 @@ k_backproject(const T *__restrict__ g, int n, int N, int M, int F, int wstride, 
         for (int e = threadIdx.x; e < na * wstride; e += NT) {
             const int a = e / wstride;
             const int k = sK[a] + (e - a * wstride);
-            const T *row = g + (size_t)(l0 + a) * M;
-            const T g0 = (k >= 0 && k < M) ? row[k] : T(0);
-            const T g1 = (k + 1 >= 0 && k + 1 < M) ? row[k + 1] : T(0);
+            const S *row = g + (size_t)(l0 + a) * M;
+            const T g0 = (k >= 0 && k < M) ? (T)ldv(row + k) : T(0);
+            const T g1 = (k + 1 >= 0 && k + 1 < M) ? (T)ldv(row + k + 1) : T(0);
             stage[e] = make_stage(g0, g1);
         }
         __syncthreads();
@@ -235,20 +240,25 @@ __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_
     const T vbn = vb + t - v1;
     epi.Ru[r] = Ru;
     epi.v1b[r] = vbn;
-    epi.y1[r] = vbn + sigma * Ru;
+    if constexpr (sizeof(T) == 4) {
+        if (epi.y1h) epi.y1h[r] = __float2bfloat16_rn(vbn + sigma * Ru);
+        else epi.y1[r] = vbn + sigma * Ru;
+    } else {
+        epi.y1[r] = vbn + sigma * Ru;
+    }
     if (epi.t1) epi.t1[r] = t;
 }
 
 // One row of the march: the NC candidate pixels q, q+1, ... of the lane's interval.
 // EXACT1: the first candidate is always inside the interval (A <= 2^F, i.e. h <= ds).
-template <typename T, int NC, bool EXACT1>
-__device__ __forceinline__ void march_row(const T *__restrict__ rowp, int dq, int n, int k, int F, double inv2F,
+template <typename T, typename S, int NC, bool EXACT1>
+__device__ __forceinline__ void march_row(const S *__restrict__ rowp, int dq, int n, int k, int F, double inv2F,
                                           long long Pa, int q, long long A, T &Su, T &Sf)
 {
     {
         bool ok = (unsigned)q < (unsigned)n;
         if (!EXACT1) ok = ok && bin_of<T>(Pa, F) == k;
-        const T v = ok ? rowp[dq * q] : T(0);
+        const T v = ok ? (T)ldv(rowp + dq * q) : T(0);
         acc_sample(Su, Sf, v, Pa, F, inv2F);
     }
     long long P = Pa;
@@ -258,15 +268,15 @@ __device__ __forceinline__ void march_row(const T *__restrict__ rowp, int dq, in
         const int qq = q + c;
         const bool ok = bin_of<T>(P, F) == k && (unsigned)qq < (unsigned)n;
         if (__any_sync(0xffffffffu, ok)) {
-            const T v = ok ? rowp[dq * qq] : T(0);
+            const T v = ok ? (T)ldv(rowp + dq * qq) : T(0);
             acc_sample(Su, Sf, v, P, F, inv2F);
         }
     }
 }
 
-template <typename T, int NC, bool EXACT1>
+template <typename T, typename S, int NC, bool EXACT1>
 __global__ void __launch_bounds__(128)
-k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F,
+k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
           const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
 {
     const int l = blockIdx.y;
@@ -279,7 +289,7 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
     const double inv2F = ldexp(1.0, -F);
     // pixel (m, q) of the march is at base[m*n + dq*q]
     const int dq = am.flip ? -1 : 1;
-    const T *__restrict__ base = (am.layout ? u : uT) + (am.flip ? (n - 1) : 0);
+    const S *__restrict__ base = (am.layout ? u : uT) + (am.flip ? (n - 1) : 0);
 
     // Rows m where the lane's pixel run may be inside [0, n): q*(m) = Q0 - m b.
     int mlo = n, mhi = -1;
@@ -318,12 +328,12 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
             const unsigned A32 = (unsigned)A;             // A = 2^32 wraps to 0 (then B = 0)
             const unsigned lim = (unsigned)((1ll << 32) - A);
             const int rows = mhi_w - mlo_w + 1;
-            const float *__restrict__ b1 = base + dq;     // pixel (m, q + 1)
+            const S *__restrict__ b1 = base + dq;         // pixel (m, q + 1)
             if (B == 0) {
 #pragma unroll 2
                 for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
                     Su += v1 + v2;
                     Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
                     Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
@@ -333,8 +343,8 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
                 const unsigned B32 = (unsigned)B, thr = (unsigned)(A - B);   // step back when r >= A - B
 #pragma unroll 2
                 for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
                     Su += v1 + v2;
                     Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
                     Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
@@ -347,8 +357,8 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
                 const unsigned nb = (unsigned)(-B);       // step forward when r < |B|
 #pragma unroll 2
                 for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? base[off] : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? b1[off] : 0.f;
+                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
+                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
                     Su += v1 + v2;
                     Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
                     Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
@@ -365,14 +375,14 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
         long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
         long long Pa = qa * A + (long long)mlo_w * B + am.Op;   // in [K, K + A)
         int q = (int)qa;
-        const T *rowp = base + (size_t)mlo_w * n;
+        const S *rowp = base + (size_t)mlo_w * n;
         const int rows = mhi_w - mlo_w + 1;
         // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
         if (B >= 0) {
             const long long KA = K + A;
 #pragma unroll 2
             for (int r = 0; r < rows; ++r) {
-                march_row<T, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+                march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
                 Pa += B;
                 if (Pa >= KA) { Pa -= A; --q; }
                 rowp += n;
@@ -380,7 +390,7 @@ k_forward(const T *__restrict__ u, const T *__restrict__ uT, int n, int M, int F
         } else {
 #pragma unroll 2
             for (int r = 0; r < rows; ++r) {
-                march_row<T, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+                march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
                 Pa += B;
                 if (Pa < K) { Pa += A; ++q; }
                 rowp += n;
@@ -417,33 +427,22 @@ size_t bp_smem(const ctr_plan *p)
     return sizeof(T2) * BP_ACH * p->wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
 }
 
-template <typename T, int NC, bool EXACT1>
-void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+template <typename T, typename S, int NC, bool EXACT1>
+void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
-    k_forward<T, NC, EXACT1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi);
+    k_forward<T, S, NC, EXACT1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi);
 }
 
-}  // namespace
-
-template <typename T>
-ctr_status configure_radon(const ctr_plan *p)
-{
-    const size_t smem = bp_smem<T>(p);
-    if (smem > 48 * 1024)
-        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return CTR_OK;
-}
-
-template <typename T>
-ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+template <typename T, typename S>
+ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cudaStream_t s)
 {
     const int G = p->bp_groups;
     const int per = (p->N + G - 1) / G;
     dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
     T *part = G > 1 ? (T *)p->bp_part : nullptr;
     p->launches++;
-    k_backproject<T><<<grid, 32 * BP_TY, bp_smem<T>(p), s>>>(g, p->n, p->N, p->M, p->F, p->wstride, per, p->d_geom,
-                                                              epi, part);
+    k_backproject<T, S><<<grid, 32 * BP_TY, bp_smem<T>(p), s>>>(g, p->n, p->N, p->M, p->F, p->wstride, per,
+                                                                 p->d_geom, epi, part);
     CTR_CHECK_LAUNCH("k_backproject");
     if (G > 1) {
         const size_t nn = (size_t)p->n * p->n;
@@ -456,25 +455,64 @@ ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T
     return CTR_OK;
 }
 
-template <typename T>
-ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+template <typename T, typename S>
+ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
     dim3 grid((p->M + 4 * 31 - 1) / (4 * 31), p->N);
     const bool exact1 = p->h <= p->ds;
     p->launches++;
     switch (p->ncand * 2 + (exact1 ? 1 : 0)) {
-    case 2: launch_fwd_cfg<T, 1, false>(p, grid, u, uT, epi, s); break;
-    case 3: launch_fwd_cfg<T, 1, true>(p, grid, u, uT, epi, s); break;
-    case 4: launch_fwd_cfg<T, 2, false>(p, grid, u, uT, epi, s); break;
-    case 5: launch_fwd_cfg<T, 2, true>(p, grid, u, uT, epi, s); break;
-    case 6: launch_fwd_cfg<T, 3, false>(p, grid, u, uT, epi, s); break;
-    case 7: launch_fwd_cfg<T, 3, true>(p, grid, u, uT, epi, s); break;
-    case 8: launch_fwd_cfg<T, 4, false>(p, grid, u, uT, epi, s); break;
-    case 9: launch_fwd_cfg<T, 4, true>(p, grid, u, uT, epi, s); break;
+    case 2: launch_fwd_cfg<T, S, 1, false>(p, grid, u, uT, epi, s); break;
+    case 3: launch_fwd_cfg<T, S, 1, true>(p, grid, u, uT, epi, s); break;
+    case 4: launch_fwd_cfg<T, S, 2, false>(p, grid, u, uT, epi, s); break;
+    case 5: launch_fwd_cfg<T, S, 2, true>(p, grid, u, uT, epi, s); break;
+    case 6: launch_fwd_cfg<T, S, 3, false>(p, grid, u, uT, epi, s); break;
+    case 7: launch_fwd_cfg<T, S, 3, true>(p, grid, u, uT, epi, s); break;
+    case 8: launch_fwd_cfg<T, S, 4, false>(p, grid, u, uT, epi, s); break;
+    case 9: launch_fwd_cfg<T, S, 4, true>(p, grid, u, uT, epi, s); break;
     default: return fail(CTR_EUNSUPPORTED, "forward projector: too many pixels per detector interval");
     }
     CTR_CHECK_LAUNCH("k_forward");
     return CTR_OK;
+}
+
+}  // namespace
+
+template <typename T>
+ctr_status configure_radon(const ctr_plan *p)
+{
+    const size_t smem = bp_smem<T>(p);
+    if (smem > 48 * 1024) {
+        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if constexpr (sizeof(T) == 4)
+            CTR_CUDA(cudaFuncSetAttribute(k_backproject<float, __nv_bfloat16>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    return CTR_OK;
+}
+
+ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, const BackprojEpi<float> &epi,
+                                   cudaStream_t s)
+{
+    return bp_impl<float, __nv_bfloat16>(p, g, epi, s);
+}
+
+ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT,
+                               const ForwardEpi<float> &epi, cudaStream_t s)
+{
+    return fwd_impl<float, __nv_bfloat16>(p, u, uT, epi, s);
+}
+
+template <typename T>
+ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+{
+    return bp_impl<T, T>(p, g, epi, s);
+}
+
+template <typename T>
+ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+{
+    return fwd_impl<T, T>(p, u, uT, epi, s);
 }
 
 template <typename T>
@@ -497,5 +535,6 @@ template ctr_status configure_radon<float>(const ctr_plan *);
 template ctr_status configure_radon<double>(const ctr_plan *);
 template ctr_status launch_transpose<float>(const ctr_plan *, const float *, float *, cudaStream_t);
 template ctr_status launch_transpose<double>(const ctr_plan *, const double *, double *, cudaStream_t);
+template ctr_status launch_transpose<__nv_bfloat16>(const ctr_plan *, const __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
 
 }  // namespace ctr

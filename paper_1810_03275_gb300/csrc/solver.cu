@@ -151,6 +151,12 @@ k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b
     }
 }
 
+__global__ void k_to_bf16(const float *__restrict__ x, size_t len, __nv_bfloat16 *y)
+{
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
+        y[r] = __float2bfloat16_rn(x[r]);
+}
+
 // Power-iteration start pattern x_ij = frac(1/2 + i/g + j/g^2) - 1/2, g the plastic number.
 template <typename T>
 __global__ void k_start_pattern(T *x, int n)
@@ -355,6 +361,27 @@ ctr_status op_adjoint(ctr_plan *p, const T *g, T *u, double scale, cudaStream_t 
     return launch_backproject<T>(p, g, e, s);
 }
 
+// BF16 operand storage: g = R_h u with u, uT in bfloat16; u = R_h^* g with g in bfloat16
+// (FP32 accumulation, FP32 results)
+ctr_status op_forward_bf16(ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT, float *g, cudaStream_t s)
+{
+    ForwardEpi<float> e{};
+    e.mode = 0;
+    e.g = g;
+    e.scale = 1.f;
+    return launch_forward_bf16(p, u, uT, e, s);
+}
+
+ctr_status op_adjoint_bf16(ctr_plan *p, const __nv_bfloat16 *g, float *u, cudaStream_t s)
+{
+    BackprojEpi<float> e{};
+    e.out = u;
+    e.scale = 1.f;
+    e.outscale = 1.f;
+    e.inv_h = (float)(1.0 / p->h);
+    return launch_backproject_bf16(p, g, e, s);
+}
+
 // Power iteration for beta ~ ||R_h||: x <- R^*R x / ||R^*R x|| from the R2 start.
 template <typename T>
 ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
@@ -440,10 +467,16 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     ea.divtau = a.tau;
     ea.outscale = -a.sigma;
     ea.inv_h = a.inv_h;
-    if ((st = launch_backproject<T>(p, (const T *)p->y1, ea, s)) != CTR_OK) return st;
-    // B: u += F^{-1}(F(u_tmp) m), and uT
-    if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, (T *)p->uT,
-                                  diag ? (T *)p->du : nullptr, s)) != CTR_OK)
+    const bool h = sizeof(T) == 4 && p->bf16;   // projector operands in bfloat16
+    if (h) {
+        if constexpr (sizeof(T) == 4)
+            if ((st = launch_backproject_bf16(p, p->y1h, ea, s)) != CTR_OK) return st;
+    } else if ((st = launch_backproject<T>(p, (const T *)p->y1, ea, s)) != CTR_OK) {
+        return st;
+    }
+    // B: u += F^{-1}(F(u_tmp) m), and uT (or the bfloat16 copies of u and uT)
+    if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, h ? nullptr : (T *)p->uT,
+                                  diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr, h ? p->uTh : nullptr)) != CTR_OK)
         return st;
     // C: ray-driven Rt u with the data-dual step
     ForwardEpi<T> ec{};
@@ -459,7 +492,14 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     ec.da = d + nm;
     ec.dlo = d + 2 * nm;
     ec.dhi = d + 3 * nm;
-    if ((st = launch_forward<T>(p, (const T *)p->u, (const T *)p->uT, ec, s)) != CTR_OK) return st;
+    if (h) {
+        if constexpr (sizeof(T) == 4) {
+            ec.y1h = p->y1h;
+            if ((st = launch_forward_bf16(p, p->uh, p->uTh, ec, s)) != CTR_OK) return st;
+        }
+    } else if ((st = launch_forward<T>(p, (const T *)p->u, (const T *)p->uT, ec, s)) != CTR_OK) {
+        return st;
+    }
     // D: TV dual step
     const size_t nn = (size_t)n * n;
     p->launches++;
@@ -540,6 +580,10 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
     k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->v1b, (const T *)p->Ru, a.sigma, nm, (T *)p->y1);
     p->launches++;
     k_init_y2<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, (const T *)p->v2b, n, a.sigma * a.tau, a.inv_h, (T *)p->y2);
+    if (sizeof(T) == 4 && p->bf16) {
+        p->launches++;
+        k_to_bf16<<<grid_for(nm, 256, 4096), 256, 0, s>>>((const float *)p->y1, nm, p->y1h);
+    }
     CTR_CHECK_LAUNCH("pdrq init");
     if (iters <= 0) {
         CTR_CUDA(cudaMemsetAsync(p->du, 0, nn * sizeof(T), s));

@@ -157,7 +157,9 @@ class Plan:
         self.angles = np.ascontiguousarray(angles, dtype=np.float64)
         self.n, self.n_angles, self.n_bins, self.h, self.ds = n, n_angles, n_bins, h, ds
         self.dtype = dtype
-        self.torch_dtype = {"f32": torch.float32, "f64": torch.float64}[dtype]
+        # compute / input-output dtype, and the storage dtype of the projectors' operands
+        self.torch_dtype = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.float32}[dtype]
+        self.op_dtype = torch.bfloat16 if dtype == "bf16" else self.torch_dtype
         code = {"f32": CTR_F32, "f64": CTR_F64, "bf16": CTR_BF16}[dtype]
         geo = Geometry(n, n_angles, n_bins, h, ds, self.angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         handle = ctypes.c_void_p()
@@ -180,12 +182,13 @@ class Plan:
     def device_bytes(self) -> int:
         return int(load().ctr_plan_device_bytes(self._h))
 
-    def _t(self, x, shape, name):
+    def _t(self, x, shape, name, dtype=None):
         import torch
+        dtype = self.torch_dtype if dtype is None else dtype
         if not isinstance(x, torch.Tensor) or not x.is_cuda:
             raise TypeError(f"{name} must be a CUDA tensor")
-        if x.dtype != self.torch_dtype:
-            raise TypeError(f"{name} must be {self.torch_dtype}, got {x.dtype}")
+        if x.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
         if tuple(x.shape) != tuple(shape) or not x.is_contiguous():
             raise ValueError(f"{name} must be contiguous with shape {shape}, got {tuple(x.shape)}")
         return ctypes.c_void_p(x.data_ptr())
@@ -202,13 +205,14 @@ class Plan:
     # -- the C ABI -------------------------------------------------------------
     def rh_forward(self, u, g=None, stream=None):
         g = self.empty_sino() if g is None else g
-        _check(load().rh_forward(self._h, self._t(u, (self.n, self.n), "u"),
+        _check(load().rh_forward(self._h, self._t(u, (self.n, self.n), "u", self.op_dtype),
                                  self._t(g, (self.n_angles, self.n_bins), "g"), _stream(stream)))
         return g
 
     def rh_forward_t(self, u, uT, g=None, stream=None):
         g = self.empty_sino() if g is None else g
-        _check(load().rh_forward_t(self._h, self._t(u, (self.n, self.n), "u"), self._t(uT, (self.n, self.n), "uT"),
+        _check(load().rh_forward_t(self._h, self._t(u, (self.n, self.n), "u", self.op_dtype),
+                                   self._t(uT, (self.n, self.n), "uT", self.op_dtype),
                                    self._t(g, (self.n_angles, self.n_bins), "g"), _stream(stream)))
         return g
 
@@ -218,7 +222,7 @@ class Plan:
 
     def rh_adjoint(self, g, u=None, stream=None):
         u = self.empty_image() if u is None else u
-        _check(load().rh_adjoint(self._h, self._t(g, (self.n_angles, self.n_bins), "g"),
+        _check(load().rh_adjoint(self._h, self._t(g, (self.n_angles, self.n_bins), "g", self.op_dtype),
                                  self._t(u, (self.n, self.n), "u"), _stream(stream)))
         return u
 

@@ -120,8 +120,12 @@ def line_integrals(ph: Phantom, theta: np.ndarray, n_bins: int, ds: float = 1.0,
     ray at angle theta_l and detector offset s_k: along each ray the phantom is
     piecewise constant between ellipse boundary crossings, and each segment takes
     the value of the last-painted shape containing it."""
-    shapes = {"all": ph.all, "tissue": ph.tissue, "metal": ph.metal}[which]
     theta = np.asarray(theta, dtype=np.float64)
+    chunk = max(1, 2_000_000 // max(n_bins * max(len(ph.all), 1), 1))
+    if theta.shape[0] > chunk:
+        return np.concatenate([line_integrals(ph, theta[a:a + chunk], n_bins, ds, which)
+                               for a in range(0, theta.shape[0], chunk)], axis=0)
+    shapes = {"all": ph.all, "tissue": ph.tissue, "metal": ph.metal}[which]
     s = bin_centres(n_bins, ds)[None, :]
     ct = np.cos(theta)[:, None]
     st = np.sin(theta)[:, None]
@@ -237,6 +241,14 @@ def config_plain_fp64(seed: int = 1) -> Problem:
     alpha = 0.01, delta = 3 sigma_n, 200 iterations, FP64."""
     return make_problem("plain_fp64_64", 64, 90, 95, seed=seed, n_ellipses=6, noise="gaussian",
                         alpha=0.01, iters=200, dtype="f64")
+
+
+def config_bf16_2048(seed: int = 5) -> Problem:
+    """2048x2048 ellipse phantom with 6 metal disks, 2048 angles, 2897 bins
+    (ceil(sqrt(2) 2048)), 1e5-photon Poisson noise, 300 iterations; the projector
+    operands are stored in bfloat16."""
+    return make_problem("bf16_2048", 2048, 2048, 2897, seed=seed, n_ellipses=10, n_metal=6,
+                        noise="poisson", alpha=0.3, iters=300, dtype="bf16")
 
 
 def config_mar_fp32(seed: int = 2, n_metal: Optional[int] = None) -> Problem:
