@@ -177,6 +177,34 @@ ctr_status tv_pd_run(ctr_plan *plan, const void *w_dev, const void *a_dev, const
                      const void *hi_dev, double alpha, int iters, const ctr_params *params,
                      ctr_state *state, void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* Tuning hook: split the backprojection's angles into `groups` groups whose partial
+ * images are summed (more CTAs for small images).  1 <= groups <= the capacity the
+ * plan allocated (up to 8 for n <= 1024), else CTR_EINVAL.  No allocation. */
+ctr_status ctr_plan_set_bp_groups(ctr_plan *plan, int groups);
+int ctr_plan_get_bp_groups(const ctr_plan *plan);
+
+/* Batches: many independent slices (each its own geometry, image size and view
+ * count), FP32, solved together.  Each stage of an iteration of Alg. 4 is ONE kernel
+ * launch covering every slice (a block-offset table maps CTAs to slices), and the
+ * iterations are captured as CUDA graphs.  Slices need n = 2^a 3^b and 1 <= ds/h <
+ * sqrt(2).  The batch owns one plan per slice (ctr_batch_plan returns it; do not
+ * destroy it separately). */
+typedef struct ctr_batch ctr_batch;
+ctr_status ctr_batch_create(const ctr_geometry *geos, int count, ctr_batch **out);
+void ctr_batch_destroy(ctr_batch *batch);
+ctr_plan *ctr_batch_plan(ctr_batch *batch, int index);
+/* Rebuild the batch's launch tables after ctr_plan_set_bp_groups on its plans. */
+ctr_status ctr_batch_retune(ctr_batch *batch);
+unsigned long long ctr_batch_launch_count(const ctr_batch *batch);
+/* tv_pd_solve for every slice i: f_devs[i] (N_i*M_i floats), masks[i] (bytes or NULL;
+ * masks may be NULL), alphas[i], deltas[i], shared iters and params; betas/cs (may
+ * be NULL, or entries <= 0) select power iterations per slice; u_outs[i] (n_i^2
+ * floats); diags (NULL or count entries, host) filled after an internal sync. */
+ctr_status tv_pd_solve_batched(ctr_batch *batch, const void *const *f_devs, const uint8_t *const *masks,
+                               const double *alphas, const double *deltas, int iters, const ctr_params *params,
+                               const double *betas, const double *cs, void *const *u_outs, ctr_diag *diags,
+                               void *stream);
+
 /* Power iterations of Sec. 4.3 / 5.1 from the fixed R2 start pattern
  * x_ij = frac(1/2 + i/g + j/g^2) - 1/2 (g the plastic number): beta ~ ||R_h||
  * (iters steps on R_h^* R_h) and lambda_max(Mt^{-1} Rt^* Rt) with Rt = R_h/beta,

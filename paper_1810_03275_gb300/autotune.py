@@ -1,0 +1,134 @@
+"""Project-written autotuner for the backprojection's angle split.
+
+The pixel-driven R_h^* runs one CTA per (32 x 32 tile, angle group); splitting the
+angles into G groups (partial images summed by a small epilogue kernel) trades an
+extra pass for more CTAs in flight.  The best G depends on the image size, the view
+count and, in a batch, on the other slices.  The tuner times the candidates with
+CUDA events through the C ABI and keeps the fastest; results are cached in a JSON
+file keyed by (device, n, views, bins) for single plans and by the batch signature
+for batches.  Tuning never changes results beyond FP32 summation order.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+from typing import Dict, Iterable, Optional
+
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("CTR_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ctrecon", "tune.json"))
+
+
+def _load_cache() -> Dict[str, int]:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _store(key: str, value) -> None:
+    with _lock:
+        d = _load_cache()
+        d[key] = value
+        path = cache_path()
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(d, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def _device_key() -> str:
+    import torch
+    return torch.cuda.get_device_name().replace(" ", "_")
+
+
+def _time(fn, reps: int) -> float:
+    import torch
+    for _ in range(2):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int = 5, use_cache: bool = True) -> int:
+    """Pick the angle-group count of `plan`'s backprojection; sets and returns it."""
+    import torch
+    key = f"plan/{_device_key()}/{plan.dtype}/n{plan.n}/N{plan.n_angles}/M{plan.n_bins}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit is not None:
+            try:
+                plan.set_bp_groups(int(hit))
+                return int(hit)
+            except Exception:
+                pass
+    g = torch.randn((plan.n_angles, plan.n_bins), device="cuda").to(plan.op_dtype)
+    u = torch.empty((plan.n, plan.n), device="cuda", dtype=plan.torch_dtype)
+    best, best_t = plan.bp_groups, None
+    for G in candidates:
+        try:
+            plan.set_bp_groups(G)
+        except Exception:
+            continue
+        t = _time(lambda: plan.rh_adjoint(g, u), reps)
+        if best_t is None or t < best_t:
+            best, best_t = G, t
+    plan.set_bp_groups(best)
+    _store(key, best)
+    return best
+
+
+def tune_batch(batch, fs, masks, alphas, deltas, policies: Iterable[Optional[int]] = (None, 1, 2, 4),
+               iters: int = 4, betas=None, cs=None, use_cache: bool = True):
+    """Pick the batch's angle-split policy: None keeps each slice's size-based default,
+    an integer G applies min(G, capacity) to every slice.  Timed on `iters` batched
+    iterations with the given data.  Sets the policy, rebuilds the launch tables and
+    returns it."""
+    from . import ctrecon as ct
+    sig = "|".join(f"{g['n']}x{g['n_angles']}x{g['n_bins']}" for g in batch.geoms)
+    import hashlib
+    key = f"batch/{_device_key()}/{hashlib.sha1(sig.encode()).hexdigest()[:16]}"
+    defaults = [p.bp_groups for p in batch.plans]
+
+    def apply(policy):
+        for p, d in zip(batch.plans, defaults):
+            want = d if policy is None else policy
+            for G in (want, want // 2, 2, 1):
+                try:
+                    p.set_bp_groups(max(1, G))
+                    break
+                except ct.CtrError:
+                    continue
+        batch.retune()
+
+    if use_cache:
+        hit = _load_cache().get(key, "missing")
+        if hit != "missing":
+            apply(hit)
+            return hit
+    if betas is None or cs is None:
+        import numpy as np
+        betas = [p.power_beta(10) for p in batch.plans]
+        cs = [1.05 * p.power_lambda(b, np.pi / p.n, 10) for p, b in zip(batch.plans, betas)]
+    prm = ct.default_params(graph_block=0)
+    best, best_t = None, None
+    for pol in policies:
+        apply(pol)
+        t = _time(lambda: batch.solve(fs, masks, alphas, deltas, iters, params=prm, betas=betas, cs=cs,
+                                      want_diag=False), 1)
+        if best_t is None or t < best_t:
+            best, best_t = pol, t
+    apply(best)
+    _store(key, best)
+    return best

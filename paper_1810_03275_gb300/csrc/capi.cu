@@ -32,6 +32,9 @@ template <typename T> ctr_status op_grad(ctr_plan *, const T *, T *, cudaStream_
 template <typename T> ctr_status op_div(ctr_plan *, const T *, T *, cudaStream_t);
 template <typename T> ctr_status op_forward(ctr_plan *, const T *, const T *, T *, double, cudaStream_t);
 template <typename T> ctr_status op_adjoint(ctr_plan *, const T *, T *, double, cudaStream_t);
+ctr_status batch_solve(ctr_batch *, const float *const *, const uint8_t *const *, const double *, const double *, int,
+                       const ctr_params &, const double *, const double *, float *const *, ctr_diag *, cudaStream_t);
+ctr_status batch_prepare(ctr_batch *);
 ctr_status op_forward_bf16(ctr_plan *, const __nv_bfloat16 *, const __nv_bfloat16 *, float *, cudaStream_t);
 ctr_status op_adjoint_bf16(ctr_plan *, const __nv_bfloat16 *, float *, cudaStream_t);
 template <typename T> ctr_status power_beta(ctr_plan *, int, double *, cudaStream_t);
@@ -361,7 +364,11 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
         const int maxg = p->N / 32 > 1 ? p->N / 32 : 1;
         if (G > maxg) G = maxg;
         p->bp_groups = G < 1 ? 1 : G;
-        if (p->bp_groups > 1) ALLOC(p->bp_part, es * nn * p->bp_groups);
+        // room for up to 8 groups at n <= 1024 so a tuner can change the split later
+        int cap = p->bp_groups;
+        if (p->n <= 1024) cap = maxg < 8 ? (maxg > cap ? maxg : cap) : 8;
+        p->bp_cap = cap;
+        if (cap > 1) ALLOC(p->bp_part, es * nn * cap);
     }
     ALLOC(p->d_red, sizeof(double) * 8 * p->red_blocks);
     ALLOC(p->d_scal, sizeof(double) * 64);
@@ -490,6 +497,116 @@ ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, 
     return CTR_DISPATCH(p,
                         solve_impl<float>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream),
                         solve_impl<double>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream));
+}
+
+ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)
+{
+    if (!p) return fail(CTR_EINVAL, "plan is NULL");
+    if (groups < 1 || groups > p->bp_cap || groups > p->N)
+        return fail(CTR_EINVAL, "groups must be in [1, " + std::to_string(p->bp_cap < p->N ? p->bp_cap : p->N) + "]");
+    p->bp_groups = groups;
+    return CTR_OK;
+}
+
+int ctr_plan_get_bp_groups(const ctr_plan *p) { return p ? p->bp_groups : 0; }
+
+void ctr_batch_destroy(ctr_batch *b)
+{
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    cudaDeviceSynchronize();
+    for (ctr_plan *p : b->plans) ctr_plan_destroy(p);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    delete b;
+}
+
+ctr_status ctr_batch_create(const ctr_geometry *geos, int count, ctr_batch **out)
+{
+    if (!out || !geos || count < 1) return fail(CTR_EINVAL, "geos/out NULL or count < 1");
+    *out = nullptr;
+    ctr_batch *b = new (std::nothrow) ctr_batch();
+    if (!b) return fail(CTR_ENOMEM, "host allocation failed");
+    if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return fail(CTR_ECUDA, "no CUDA device"); }
+    ctr_status st = CTR_OK;
+    for (int i = 0; i < count && st == CTR_OK; ++i) {
+        ctr_plan *p = nullptr;
+        st = ctr_plan_create(&geos[i], CTR_F32, &p);
+        if (st != CTR_OK) break;
+        b->plans.push_back(p);
+        if (!p->fft_ok) st = fail(CTR_EUNSUPPORTED, "slice " + std::to_string(i) + ": n must be 2^a 3^b");
+        else if (p->ncand != 2 || p->h > p->ds)
+            st = fail(CTR_EUNSUPPORTED, "slice " + std::to_string(i) + ": batched solve needs ds/h in [1, sqrt(2))");
+    }
+    if (st == CTR_OK) {
+        if (cudaMalloc((void **)&b->d_desc, sizeof(SliceDesc) * count) != cudaSuccess ||
+            cudaMalloc((void **)&b->d_prefix, sizeof(int) * BS_COUNT * (count + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(CTR_ENOMEM, "batch tables: cudaMalloc failed");
+        }
+    }
+    if (st == CTR_OK && (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess))
+        st = fail(CTR_ECUDA, "stream/event creation failed");
+    if (st == CTR_OK) st = batch_prepare(b);
+    if (st != CTR_OK) {
+        std::string msg = g_last_error;
+        ctr_batch_destroy(b);
+        return fail(st, msg);
+    }
+    *out = b;
+    return CTR_OK;
+}
+
+ctr_status ctr_batch_retune(ctr_batch *b)
+{
+    if (!b) return fail(CTR_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    return batch_prepare(b);
+}
+
+ctr_plan *ctr_batch_plan(ctr_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->plans.size()) return nullptr;
+    return b->plans[i];
+}
+
+unsigned long long ctr_batch_launch_count(const ctr_batch *b) { return b ? b->launches : 0ull; }
+
+ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const uint8_t *const *masks,
+                               const double *alphas, const double *deltas, int iters, const ctr_params *prm,
+                               const double *betas, const double *cs, void *const *u_outs, ctr_diag *diags,
+                               void *stream)
+{
+    if (!b) return fail(CTR_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(CTR_ECUDA, "cannot select the batch's device");
+    const int ns = (int)b->plans.size();
+    if (!f_devs || !alphas || !deltas || !u_outs) return fail(CTR_EINVAL, "f_devs, alphas, deltas, u_outs must not be NULL");
+    for (int i = 0; i < ns; ++i) {
+        if (!f_devs[i] || !u_outs[i]) return fail(CTR_EINVAL, "slice " + std::to_string(i) + ": NULL buffer");
+        if (!(alphas[i] >= 0) || !std::isfinite(alphas[i]) || std::isnan(deltas[i]))
+            return fail(CTR_EINVAL, "slice " + std::to_string(i) + ": alpha must be finite >= 0, delta not NaN");
+    }
+    if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
+    ctr_params q;
+    ctr_default_params(&q);
+    if (prm) q = *prm;
+    ctr_params qc = q;
+    if (!(qc.eps > 0)) qc.eps = 1.0;     // validated per slice (pi/n when unset)
+    ctr_status st = check_params(qc);
+    if (st != CTR_OK) return st;
+    CTR_CUDA(cudaEventRecord(b->ev_in, (cudaStream_t)stream));
+    CTR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    st = batch_solve(b, (const float *const *)f_devs, masks, alphas, deltas, iters, q, betas, cs,
+                     (float *const *)u_outs, diags, b->stream);
+    cudaEventRecord(b->ev_out, b->stream);
+    cudaStreamWaitEvent((cudaStream_t)stream, b->ev_out, 0);
+    return st;
 }
 
 ctr_status ctr_power_beta(ctr_plan *p, int iters, double *beta_out, void *stream)

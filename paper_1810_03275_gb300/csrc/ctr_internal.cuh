@@ -90,6 +90,33 @@ struct ForwardEpi {
     const T *dw, *da, *dlo, *dhi;   // per-bin data term, beta-scaled
 };
 
+// Radix sequence of the shared-memory Stockham FFT (product = n).
+struct FftPasses {
+    int count;
+    int radix[16];
+};
+
+// One slice of a batch: everything a batched stage kernel needs (FP32).
+struct SliceDesc {
+    int n, N, M, wstride, bp_groups, per_group;
+    int bp_tiles_x, bp_tiles_y;   // backprojection tiles
+    int fwd_chunks;               // forward-projector CTAs per angle
+    int rpc, cw;                  // FFT rows / columns per CTA
+    const AngleGeom *geom;
+    const AngleMarch *march;
+    float2 *cbuf;
+    const float2 *tw;
+    const float *sym;
+    FftPasses fp;
+    float *u, *uT, *y1, *y2, *v2b, *bp_part;
+    BackprojEpi<float> bpe;       // step A epilogue
+    ForwardEpi<float> fwe;        // step C epilogue
+    float sigma, tau, lam, inv_h;
+};
+
+// Stages of one batched iteration (block counts per slice are prefix-summed).
+enum BatchStage { BS_BP = 0, BS_BP_REDUCE, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_FWD, BS_TV, BS_COUNT };
+
 }  // namespace ctr
 
 // ---------------------------------------------------------------------------
@@ -106,6 +133,7 @@ struct ctr_plan {
     bool bf16 = false;      // CTR_BF16: projector operands stored in bfloat16, compute in FP32
     __nv_bfloat16 *uh = nullptr, *uTh = nullptr, *y1h = nullptr;   // bfloat16 operand copies
     int bp_groups = 1;      // angle groups of the backprojection (partial images summed)
+    int bp_cap = 1;         // groups the partial-image workspace has room for
     void *bp_part = nullptr;   // bp_groups * n*n partial images (bp_groups > 1)
     std::vector<double> theta;
     std::vector<int> radices;    // FFT radices, product n
@@ -176,4 +204,31 @@ template <typename T> ctr_status configure_fft(const ctr_plan *p);
 ctr_status fft_radices(int n, std::vector<int> &out);
 size_t fft_smem_bytes(const ctr_plan *p, int which);
 
+// batched stages (one launch per stage over all slices of a batch)
+size_t bp_smem_bytes(int wstride);
+void bp_tiles(int n, int &tx, int &ty);
+int fft_rows_per_cta(int n);
+int fft_cols_per_cta(int n, size_t esize);
+ctr_status configure_batch_radon(size_t bp_smem);
+ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem);
+ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
+                              cudaStream_t s);
+ctr_status launch_batch_fft(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
+                            cudaStream_t s);
+ctr_status launch_batch_tv(const SliceDesc *sd, const int *prefix, int ns, int blocks, cudaStream_t s);
+
 }  // namespace ctr
+
+// A batch of independent slices (FP32), each with its own plan, solved together:
+// every stage of an iteration is one launch over all slices.
+struct ctr_batch {
+    std::vector<ctr_plan *> plans;
+    int device = 0;
+    ctr::SliceDesc *d_desc = nullptr;   // one per slice
+    int *d_prefix = nullptr;            // BS_COUNT x (slices + 1) block-offset tables
+    int blocks[ctr::BS_COUNT] = {};
+    size_t smem[ctr::BS_COUNT] = {};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    unsigned long long launches = 0;
+};

@@ -31,10 +31,6 @@ namespace {
 constexpr int FFT_THREADS = 256;
 constexpr int MAX_PASSES = 16;
 
-struct FftPasses {
-    int count;
-    int radix[MAX_PASSES];
-};
 
 template <typename T> struct C2;
 template <> struct C2<float> { using type = float2; };
@@ -138,15 +134,15 @@ __device__ typename C2<T>::type *fft_smem(typename C2<T>::type *a, typename C2<T
 // Forward row FFTs.  in_real != null: real input promoted to complex; else the
 // complex buffer itself is transformed in place.
 template <typename T>
-__global__ void __launch_bounds__(FFT_THREADS)
-k_fft_rows_fwd(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n, int rows_per_cta,
-               FftPasses fp, const typename C2<T>::type *__restrict__ tw)
+__device__ __forceinline__ void fft_rows_fwd_body(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n,
+                                                  int rows_per_cta, const FftPasses &fp,
+                                                  const typename C2<T>::type *__restrict__ tw, int bx)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)rows_per_cta * n;
-    const int r0 = blockIdx.x * rows_per_cta;
+    const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
     for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
         const size_t g = (size_t)r0 * n + e;
@@ -164,18 +160,26 @@ k_fft_rows_fwd(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n,
     for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) cbuf[(size_t)r0 * n + e] = res[e];
 }
 
-// Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf).
 template <typename T>
 __global__ void __launch_bounds__(FFT_THREADS)
-k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw, FftPasses fp,
-           const typename C2<T>::type *__restrict__ tw)
+k_fft_rows_fwd(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n, int rows_per_cta,
+               FftPasses fp, const typename C2<T>::type *__restrict__ tw)
+{
+    fft_rows_fwd_body<T>(in_real, cbuf, n, rows_per_cta, fp, tw, blockIdx.x);
+}
+
+// Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf).
+template <typename T>
+__device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
+                                              const FftPasses &fp, const typename C2<T>::type *__restrict__ tw,
+                                              int bx)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ld = n + 1;
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)cw * ld;
-    const int c0 = blockIdx.x * cw;
+    const int c0 = bx * cw;
     const int cnt = min(cw, n - c0);
     for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
         const int row = e / cnt, c = e - row * cnt;
@@ -199,20 +203,29 @@ k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw, FftPasses fp,
+           const typename C2<T>::type *__restrict__ tw)
+{
+    fft_cols_body<T>(cbuf, sym, n, cw, fp, tw, blockIdx.x);
+}
+
 // Inverse row FFTs and the epilogue on the real part v:
 //   mode 0: out = v;  mode 1: out += v.   dout (optional) = v; outT (optional) =
 //   transpose of the final out.
 template <typename T>
-__global__ void __launch_bounds__(FFT_THREADS)
-k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_per_cta, FftPasses fp,
-               const typename C2<T>::type *__restrict__ tw, T *out, int mode, T *outT, T *dout,
-               __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
+__device__ __forceinline__ void fft_rows_inv_body(const typename C2<T>::type *__restrict__ cbuf, int n,
+                                                  int rows_per_cta, const FftPasses &fp,
+                                                  const typename C2<T>::type *__restrict__ tw, T *out, int mode,
+                                                  T *outT, T *dout, __nv_bfloat16 *outh, __nv_bfloat16 *outTh,
+                                                  int bx)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)rows_per_cta * n;
-    const int r0 = blockIdx.x * rows_per_cta;
+    const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
     for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) a[e] = cbuf[(size_t)r0 * n + e];
     __syncthreads();
@@ -238,6 +251,52 @@ k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_pe
             if (outTh) outTh[(size_t)col * n + r0 + r] = __float2bfloat16_rn((float)o);
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_per_cta, FftPasses fp,
+               const typename C2<T>::type *__restrict__ tw, T *out, int mode, T *outT, T *dout,
+               __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
+{
+    fft_rows_inv_body<T>(cbuf, n, rows_per_cta, fp, tw, out, mode, outT, dout, outh, outTh, blockIdx.x);
+}
+
+__device__ __forceinline__ int find_slice_fft(const int *__restrict__ prefix, int ns, int b)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched preconditioner passes (step B of every slice in one launch each).
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_rows_fwd_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice_fft(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    fft_rows_fwd_body<float>(nullptr, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
+}
+
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_cols_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice_fft(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, blockIdx.x - prefix[s]);
+}
+
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice_fft(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.uT, nullptr, nullptr, nullptr,
+                             blockIdx.x - prefix[s]);
 }
 
 // Preconditioner symbols (Alg. 4, Sec. 4.3.1), with 1/n^2 of the inverse DFT:
@@ -345,6 +404,45 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
 
 template ctr_status launch_circulant<float>(const ctr_plan *, const float *, bool, const float *, float *, int, float *, float *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
 template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int, double *, double *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
+ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem)
+{
+    if (rows_smem > 48 * 1024) {
+        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_fwd_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
+        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_inv_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
+    }
+    if (cols_smem > 48 * 1024)
+        CTR_CUDA(cudaFuncSetAttribute(k_fft_cols_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem));
+    return CTR_OK;
+}
+
+// One batched preconditioner pass over all slices.
+ctr_status launch_batch_fft(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
+                            cudaStream_t s)
+{
+    if (blocks <= 0) return CTR_OK;
+    switch (stage) {
+    case BS_FFT_ROWS: k_fft_rows_fwd_batch<<<blocks, FFT_THREADS, smem, s>>>(sd, prefix, ns); break;
+    case BS_FFT_COLS: k_fft_cols_batch<<<blocks, FFT_THREADS, smem, s>>>(sd, prefix, ns); break;
+    case BS_FFT_ROWS_INV: k_fft_rows_inv_batch<<<blocks, FFT_THREADS, smem, s>>>(sd, prefix, ns); break;
+    default: return fail(CTR_EINVAL, "not an FFT stage");
+    }
+    CTR_CHECK_LAUNCH("batched FFT stage");
+    return CTR_OK;
+}
+
+int fft_rows_per_cta(int n)
+{
+    int r = 2048 / n;
+    return r < 1 ? 1 : (r > 8 ? 8 : r);
+}
+
+int fft_cols_per_cta(int n, size_t esize)
+{
+    for (int cw = 4; cw > 1; cw /= 2)
+        if (2 * (size_t)cw * (n + 1) * 2 * esize <= 160 * 1024) return cw;
+    return 1;
+}
+
 template ctr_status configure_fft<float>(const ctr_plan *);
 template ctr_status configure_fft<double>(const ctr_plan *);
 template ctr_status launch_symbols<float>(const ctr_plan *, double, double, double, double, cudaStream_t);

@@ -107,12 +107,13 @@ __device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, in
     }
 }
 
+// One CTA of the backprojection: tile (bx, by), angle group bz.
 // part == nullptr: apply the epilogue directly (one angle group).  Otherwise write
-// this group's partial sums to part[blockIdx.z][n][n].
+// this group's partial sums to part[bz][n][n].
 template <typename T, typename S>
-__global__ void __launch_bounds__(32 * BP_TY)
-k_backproject(const S *__restrict__ g, int n, int N, int M, int F, int wstride, int angles_per_group,
-              const AngleGeom *__restrict__ geom, BackprojEpi<T> epi, T *__restrict__ part)
+__device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, int M, int F, int wstride,
+                                        int angles_per_group, const AngleGeom *__restrict__ geom,
+                                        const BackprojEpi<T> &epi, T *__restrict__ part, int bx, int by, int bz)
 {
     using T2 = typename Pair<T>::type;
     constexpr int NT = 32 * BP_TY;
@@ -125,9 +126,9 @@ k_backproject(const S *__restrict__ g, int n, int N, int M, int F, int wstride, 
 
     const int tx = threadIdx.x & 31;
     const int ty = threadIdx.x >> 5;
-    const int i0 = blockIdx.y * BP_TI;
-    const int j0 = blockIdx.x * BP_TJ;
-    const int la = blockIdx.z * angles_per_group;
+    const int i0 = by * BP_TI;
+    const int j0 = bx * BP_TJ;
+    const int la = bz * angles_per_group;
     const int lb = min(N, la + angles_per_group);
     const double inv2F = ldexp(1.0, -F);
 
@@ -180,23 +181,39 @@ k_backproject(const S *__restrict__ g, int n, int N, int M, int F, int wstride, 
     for (int r = 0; r < BP_R; ++r) {
         const int i = i0 + ty + BP_TY * r;
         if (i < n && j < n) {
-            if (part) part[((size_t)blockIdx.z * n + i) * n + j] = acc[r];
+            if (part) part[((size_t)bz * n + i) * n + j] = acc[r];
             else bp_epilogue(epi, n, i, j, acc[r]);
         }
     }
 }
 
-// Sum of the angle groups' partial images, then the backprojection epilogue.
+template <typename T, typename S>
+__global__ void __launch_bounds__(32 * BP_TY)
+k_backproject(const S *__restrict__ g, int n, int N, int M, int F, int wstride, int angles_per_group,
+              const AngleGeom *__restrict__ geom, BackprojEpi<T> epi, T *__restrict__ part)
+{
+    bp_body<T, S>(g, n, N, M, F, wstride, angles_per_group, geom, epi, part, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Sum of the angle groups' partial images, then the backprojection epilogue
+// (block b of nb, grid-stride over the n*n pixels).
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_bp_reduce(const T *__restrict__ part, int groups, int n, BackprojEpi<T> epi)
+__device__ __forceinline__ void bp_reduce_body(const T *__restrict__ part, int groups, int n,
+                                               const BackprojEpi<T> &epi, int b, int nb)
 {
     const size_t nn = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x) {
         T s = part[e];
         for (int z = 1; z < groups; ++z) s += part[(size_t)z * nn + e];
         bp_epilogue(epi, n, (int)(e / n), (int)(e % n), s);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_bp_reduce(const T *__restrict__ part, int groups, int n, BackprojEpi<T> epi)
+{
+    bp_reduce_body<T>(part, groups, n, epi, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b)
@@ -274,15 +291,14 @@ __device__ __forceinline__ void march_row(const S *__restrict__ rowp, int dq, in
     }
 }
 
+// One CTA of the forward projector: angle l, bins (bx * 4 + warp) * 31 + [0, 31).
 template <typename T, typename S, int NC, bool EXACT1>
-__global__ void __launch_bounds__(128)
-k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
-          const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
+__device__ __forceinline__ void fwd_body(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
+                                         const AngleMarch *__restrict__ march, const ForwardEpi<T> &epi, int bx, int l)
 {
-    const int l = blockIdx.y;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int kb = (blockIdx.x * 4 + warp) * 31;     // first output bin of this warp
+    const int kb = (bx * 4 + warp) * 31;              // first output bin of this warp
     if (kb >= M) return;                              // warp-uniform
     const AngleMarch am = march[l];
     const int k = kb + lane - 1;                      // this lane's interval [k, k+1)
@@ -402,6 +418,57 @@ k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F
     else { Bk = Sf; Ak = Su - Sf; }
     const T Bprev = __shfl_up_sync(0xffffffffu, Bk, 1);
     if (lane >= 1 && k < M) forward_epilogue(epi, (size_t)l * M + k, Ak + Bprev);
+}
+
+template <typename T, typename S, int NC, bool EXACT1>
+__global__ void __launch_bounds__(128)
+k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
+          const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
+{
+    fwd_body<T, S, NC, EXACT1>(u, uT, n, M, F, march, epi, blockIdx.x, blockIdx.y);
+}
+
+// Batched stages: block b of the launch belongs to the slice s with
+// prefix[s] <= b < prefix[s+1]; the slice's parameters come from its SliceDesc.
+__device__ __forceinline__ int find_slice(const int *__restrict__ prefix, int ns, int b)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(32 * BP_TY)
+k_backproject_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    const int local = blockIdx.x - prefix[s];
+    const int bx = local % d.bp_tiles_x, rest = local / d.bp_tiles_x;
+    const int by = rest % d.bp_tiles_y, bz = rest / d.bp_tiles_y;
+    bp_body<float, float>(d.y1, d.n, d.N, d.M, 32, d.wstride, d.per_group, d.geom, d.bpe,
+                          d.bp_groups > 1 ? d.bp_part : nullptr, bx, by, bz);
+}
+
+__global__ void __launch_bounds__(256)
+k_bp_reduce_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    bp_reduce_body<float>(d.bp_part, d.bp_groups, d.n, d.bpe, blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
+}
+
+__global__ void __launch_bounds__(128)
+k_forward_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    const int local = blockIdx.x - prefix[s];
+    fwd_body<float, float, 2, true>(d.u, d.uT, d.n, d.M, 32, d.march, d.fwe, local % d.fwd_chunks,
+                                    local / d.fwd_chunks);
 }
 
 template <typename T>
@@ -526,6 +593,39 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
 }
 
 int backproject_tile_rows() { return BP_TI; }
+
+size_t bp_smem_bytes(int wstride)
+{
+    return sizeof(float2) * BP_ACH * wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
+}
+
+void bp_tiles(int n, int &tx, int &ty)
+{
+    tx = (n + BP_TJ - 1) / BP_TJ;
+    ty = (n + BP_TI - 1) / BP_TI;
+}
+
+ctr_status configure_batch_radon(size_t bp_smem)
+{
+    if (bp_smem > 48 * 1024)
+        CTR_CUDA(cudaFuncSetAttribute(k_backproject_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp_smem));
+    return CTR_OK;
+}
+
+// One batched projector stage over all slices (blocks = total CTAs of the stage).
+ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
+                              cudaStream_t s)
+{
+    if (blocks <= 0) return CTR_OK;
+    switch (stage) {
+    case BS_BP: k_backproject_batch<<<blocks, 32 * BP_TY, smem, s>>>(sd, prefix, ns); break;
+    case BS_BP_REDUCE: k_bp_reduce_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns); break;
+    case BS_FWD: k_forward_batch<<<blocks, 128, 0, s>>>(sd, prefix, ns); break;
+    default: return fail(CTR_EINVAL, "not a projector stage");
+    }
+    CTR_CHECK_LAUNCH("batched projector stage");
+    return CTR_OK;
+}
 
 template ctr_status launch_backproject<float>(const ctr_plan *, const float *, const BackprojEpi<float> &, cudaStream_t);
 template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &, cudaStream_t);

@@ -122,12 +122,12 @@ __global__ void k_init_y2(const T *__restrict__ u, const T *__restrict__ v2b, in
 
 // Step D of Alg. 4: TV dual update with the projection onto the ball of radius lam/tau.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b, T *y2, T *t2)
+__device__ __forceinline__ void tv_dual_body(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b,
+                                             T *y2, T *t2, int b, int nb)
 {
     const size_t nn = (size_t)n * n;
     const T st = sigma * tau;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x) {
         T gx, gy;
         grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
         const T bx = v2b[e], by = v2b[e + nn];
@@ -149,6 +149,27 @@ k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b
             t2[e + nn] = ty;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b, T *y2, T *t2)
+{
+    tv_dual_body<T>(u, n, sigma, tau, lam, inv_h, v2b, y2, t2, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256)
+k_tv_dual_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const SliceDesc &d = sd[lo];
+    tv_dual_body<float>(d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, blockIdx.x - prefix[lo],
+                        prefix[lo + 1] - prefix[lo]);
 }
 
 __global__ void k_to_bf16(const float *__restrict__ x, size_t len, __nv_bfloat16 *y)
@@ -655,7 +676,220 @@ ctr_status build_desc_from_arrays(ctr_plan *p, const T *w, const T *a, const T *
     return CTR_OK;
 }
 
-#define CTR_INST(T)                                                                                                   \
+ctr_status launch_batch_tv(const SliceDesc *sd, const int *prefix, int ns, int blocks, cudaStream_t s)
+{
+    if (blocks <= 0) return CTR_OK;
+    k_tv_dual_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns);
+    CTR_CHECK_LAUNCH("k_tv_dual_batch");
+    return CTR_OK;
+}
+
+// ------------------------------------------------------------------------------
+// Batched solve: per-slice set-up (power iterations, data term, start state,
+// symbols) on the batch stream, then iterations 1..iters-1 with one launch per
+// stage over all slices (captured as CUDA graphs of graph_block iterations), and the
+// last iteration per slice so that each slice keeps the dual certificates for its
+// diagnostics.
+// ------------------------------------------------------------------------------
+ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const *mask, const double *alpha,
+                       const double *delta, int iters, const ctr_params &prm, const double *betas, const double *cs,
+                       float *const *u_out, ctr_diag *diags, cudaStream_t s)
+{
+    const int ns = (int)b->plans.size();
+    std::vector<SliceDesc> hd(ns);
+    std::vector<IterArgs<float>> args(ns);
+    std::vector<double> beta(ns), c(ns);
+    ctr_status st;
+    for (int i = 0; i < ns; ++i) {
+        ctr_plan *p = b->plans[i];
+        const unsigned long long l0 = p->launches;
+        beta[i] = betas ? betas[i] : 0.0;
+        if (!(beta[i] > 0)) {
+            if ((st = power_beta<float>(p, prm.power_iters, &beta[i], s)) != CTR_OK) return st;
+            if (!(beta[i] > 0)) return fail(CTR_ENUMERIC, "power iteration gave ||R_h|| = 0");
+        }
+        const double eps = prm.eps > 0 ? prm.eps : 3.14159265358979323846 / p->n;
+        c[i] = cs ? cs[i] : 0.0;
+        if (!(c[i] > 0)) {
+            double lam = 0;
+            if ((st = power_lambda<float>(p, beta[i], eps, prm.power_iters, &lam, s)) != CTR_OK) return st;
+            c[i] = prm.c_margin * lam;
+        }
+        if ((st = build_desc_from_data<float>(p, f[i], mask ? mask[i] : nullptr, delta[i], prm.trace_ratio, beta[i], s)) != CTR_OK)
+            return st;
+        const size_t nn = (size_t)p->n * p->n, nm = (size_t)p->N * p->M;
+        CTR_CUDA(cudaMemsetAsync(p->u, 0, nn * sizeof(float), s));
+        CTR_CUDA(cudaMemsetAsync(p->Ru, 0, nm * sizeof(float), s));
+        CTR_CUDA(cudaMemsetAsync(p->v1b, 0, nm * sizeof(float), s));
+        CTR_CUDA(cudaMemsetAsync(p->v2b, 0, 2 * nn * sizeof(float), s));
+        if ((st = launch_symbols<float>(p, prm.sigma, prm.tau, c[i], eps, s)) != CTR_OK) return st;
+        IterArgs<float> &a = args[i];
+        a.sigma = (float)prm.sigma;
+        a.tau = (float)prm.tau;
+        a.lam = (float)(alpha[i] / (beta[i] * beta[i]));
+        a.inv_beta = (float)(1.0 / beta[i]);
+        a.inv_h = (float)(1.0 / p->h);
+        p->launches += 2;
+        k_axpy<float><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const float *)p->v1b, (const float *)p->Ru, a.sigma, nm,
+                                                            (float *)p->y1);
+        k_init_y2<float><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const float *)p->u, (const float *)p->v2b, p->n,
+                                                               a.sigma * a.tau, a.inv_h, (float *)p->y2);
+        CTR_CHECK_LAUNCH("batch init");
+        SliceDesc &d = hd[i];
+        d.n = p->n;
+        d.N = p->N;
+        d.M = p->M;
+        d.wstride = p->wstride;
+        d.bp_groups = p->bp_groups;
+        d.per_group = (p->N + p->bp_groups - 1) / p->bp_groups;
+        bp_tiles(p->n, d.bp_tiles_x, d.bp_tiles_y);
+        d.fwd_chunks = (p->M + 4 * 31 - 1) / (4 * 31);
+        d.rpc = fft_rows_per_cta(p->n);
+        d.cw = fft_cols_per_cta(p->n, 4);
+        d.geom = p->d_geom;
+        d.march = p->d_march;
+        d.cbuf = (float2 *)p->cbuf;
+        d.tw = (const float2 *)p->d_twiddle;
+        d.sym = (const float *)p->sym;
+        d.fp.count = (int)p->radices.size();
+        for (int r = 0; r < d.fp.count && r < 16; ++r) d.fp.radix[r] = p->radices[r];
+        d.u = (float *)p->u;
+        d.uT = (float *)p->uT;
+        d.y1 = (float *)p->y1;
+        d.y2 = (float *)p->y2;
+        d.v2b = (float *)p->v2b;
+        d.bp_part = (float *)p->bp_part;
+        d.bpe = BackprojEpi<float>{};
+        d.bpe.out = (float *)p->cbuf;
+        d.bpe.complex_out = 1;
+        d.bpe.scale = a.inv_beta;
+        d.bpe.px = (const float *)p->y2;
+        d.bpe.divtau = a.tau;
+        d.bpe.outscale = -a.sigma;
+        d.bpe.inv_h = a.inv_h;
+        d.fwe = ForwardEpi<float>{};
+        d.fwe.mode = 1;
+        d.fwe.scale = a.inv_beta;
+        d.fwe.sigma = a.sigma;
+        d.fwe.Ru = (float *)p->Ru;
+        d.fwe.v1b = (float *)p->v1b;
+        d.fwe.y1 = (float *)p->y1;
+        const float *dd = (const float *)p->desc;
+        d.fwe.dw = dd;
+        d.fwe.da = dd + nm;
+        d.fwe.dlo = dd + 2 * nm;
+        d.fwe.dhi = dd + 3 * nm;
+        d.sigma = a.sigma;
+        d.tau = a.tau;
+        d.lam = a.lam;
+        d.inv_h = a.inv_h;
+        b->launches += p->launches - l0;
+    }
+    CTR_CUDA(cudaMemcpyAsync(b->d_desc, hd.data(), sizeof(SliceDesc) * ns, cudaMemcpyHostToDevice, s));
+    const int body = iters > 0 ? iters - 1 : 0;
+    auto one_iteration = [&]() -> ctr_status {
+        ctr_status r;
+        const int *pre = b->d_prefix;
+        const int stride = ns + 1;
+        if ((r = launch_batch_radon(BS_BP, b->d_desc, pre + BS_BP * stride, ns, b->blocks[BS_BP], b->smem[BS_BP], s)) != CTR_OK) return r;
+        if ((r = launch_batch_radon(BS_BP_REDUCE, b->d_desc, pre + BS_BP_REDUCE * stride, ns, b->blocks[BS_BP_REDUCE], 0, s)) != CTR_OK) return r;
+        for (int stg = BS_FFT_ROWS; stg <= BS_FFT_ROWS_INV; ++stg)
+            if ((r = launch_batch_fft(stg, b->d_desc, pre + stg * stride, ns, b->blocks[stg], b->smem[stg], s)) != CTR_OK) return r;
+        if ((r = launch_batch_radon(BS_FWD, b->d_desc, pre + BS_FWD * stride, ns, b->blocks[BS_FWD], 0, s)) != CTR_OK) return r;
+        if ((r = launch_batch_tv(b->d_desc, pre + BS_TV * stride, ns, b->blocks[BS_TV], s)) != CTR_OK) return r;
+        int nl = 0;
+        for (int stg = 0; stg < BS_COUNT; ++stg) nl += b->blocks[stg] > 0 ? 1 : 0;
+        b->launches += nl;
+        return CTR_OK;
+    };
+    int done = 0;
+    const int blk = prm.graph_block;
+    if (blk > 0 && body >= blk) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long before = b->launches;
+        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = CTR_OK;
+        for (int k = 0; k < blk && st == CTR_OK; ++k) st = one_iteration();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const unsigned long long per_graph = b->launches - before;
+        b->launches = before;
+        if (st != CTR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (batch)");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate (batch)");
+        for (; done + blk <= body; done += blk) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(ce, "cudaGraphLaunch (batch)");
+            }
+            b->launches += per_graph;
+        }
+        cudaGraphExecDestroy(exec);
+    }
+    for (; done < body; ++done)
+        if ((st = one_iteration()) != CTR_OK) return st;
+    for (int i = 0; i < ns; ++i) {
+        ctr_plan *p = b->plans[i];
+        const unsigned long long l0 = p->launches;
+        if (iters > 0 && (st = pdrq_iteration<float>(p, args[i], true, s)) != CTR_OK) return st;
+        if (diags) {
+            if (iters <= 0) {
+                CTR_CUDA(cudaMemsetAsync(p->du, 0, sizeof(float) * p->n * p->n, s));
+                CTR_CUDA(cudaMemsetAsync(p->t1, 0, sizeof(float) * p->N * p->M, s));
+                CTR_CUDA(cudaMemsetAsync(p->t2, 0, sizeof(float) * 2 * p->n * p->n, s));
+            }
+            if ((st = compute_diag<float>(p, alpha[i], beta[i], prm.tau, c[i], iters, &diags[i], s)) != CTR_OK)
+                return st;
+        }
+        if (u_out && u_out[i])
+            CTR_CUDA(cudaMemcpyAsync(u_out[i], p->u, sizeof(float) * p->n * p->n, cudaMemcpyDeviceToDevice, s));
+        b->launches += p->launches - l0;
+    }
+    return CTR_OK;
+}
+
+// Block tables and shared-memory sizes of the batched stages.
+ctr_status batch_prepare(ctr_batch *b)
+{
+    const int ns = (int)b->plans.size();
+    std::vector<int> pre((size_t)BS_COUNT * (ns + 1), 0);
+    for (int stg = 0; stg < BS_COUNT; ++stg) b->smem[stg] = 0;
+    for (int i = 0; i < ns; ++i) {
+        const ctr_plan *p = b->plans[i];
+        int tx, ty;
+        bp_tiles(p->n, tx, ty);
+        const size_t nn = (size_t)p->n * p->n;
+        const int rpc = fft_rows_per_cta(p->n), cw = fft_cols_per_cta(p->n, 4);
+        int cnt[BS_COUNT];
+        cnt[BS_BP] = tx * ty * p->bp_groups;
+        cnt[BS_BP_REDUCE] = p->bp_groups > 1 ? grid_for(nn, 256, 1024) : 0;
+        cnt[BS_FFT_ROWS] = (p->n + rpc - 1) / rpc;
+        cnt[BS_FFT_COLS] = (p->n + cw - 1) / cw;
+        cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
+        cnt[BS_FWD] = ((p->M + 4 * 31 - 1) / (4 * 31)) * p->N;
+        cnt[BS_TV] = grid_for(nn, 256, 1024);
+        for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
+        const size_t smb = bp_smem_bytes(p->wstride);
+        const size_t smr = 2 * (size_t)rpc * p->n * sizeof(float2), smc = 2 * (size_t)cw * (p->n + 1) * sizeof(float2);
+        if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
+        if (smr > b->smem[BS_FFT_ROWS]) b->smem[BS_FFT_ROWS] = smr;
+        if (smr > b->smem[BS_FFT_ROWS_INV]) b->smem[BS_FFT_ROWS_INV] = smr;
+        if (smc > b->smem[BS_FFT_COLS]) b->smem[BS_FFT_COLS] = smc;
+    }
+    for (int stg = 0; stg < BS_COUNT; ++stg) b->blocks[stg] = pre[(size_t)stg * (ns + 1) + ns];
+    CTR_CUDA(cudaMemcpy(b->d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
+    ctr_status st = configure_batch_radon(b->smem[BS_BP]);
+    if (st == CTR_OK) st = configure_batch_fft(b->smem[BS_FFT_ROWS], b->smem[BS_FFT_COLS]);
+    return st;
+}
+
+#define CTR_INST(T)                                                                                                 \
     template ctr_status dot2<T>(ctr_plan *, const T *, const T *, size_t, double *, cudaStream_t);                  \
     template ctr_status op_grad<T>(ctr_plan *, const T *, T *, cudaStream_t);                                         \
     template ctr_status op_div<T>(ctr_plan *, const T *, T *, cudaStream_t);                                          \

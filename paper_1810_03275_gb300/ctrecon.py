@@ -61,7 +61,9 @@ class State(ctypes.Structure):
 
 EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_last_error", "ctr_plan_device_bytes",
            "ctr_plan_launch_count", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
-           "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static"]
+           "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
+           "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
+           "ctr_batch_launch_count", "tv_pd_solve_batched"]
 
 
 def load(path: str = LIB_PATH):
@@ -98,6 +100,23 @@ def load(path: str = LIB_PATH):
         lib.precond_apply_static.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, vp, vp, vp]
         lib.precond_apply_static.restype = ctypes.c_int
+        lib.ctr_plan_set_bp_groups.argtypes = [vp, ctypes.c_int]
+        lib.ctr_plan_set_bp_groups.restype = ctypes.c_int
+        lib.ctr_plan_get_bp_groups.argtypes = [vp]
+        lib.ctr_plan_get_bp_groups.restype = ctypes.c_int
+        lib.ctr_batch_create.argtypes = [P(Geometry), ctypes.c_int, P(vp)]
+        lib.ctr_batch_create.restype = ctypes.c_int
+        lib.ctr_batch_destroy.argtypes = [vp]
+        lib.ctr_batch_destroy.restype = None
+        lib.ctr_batch_plan.argtypes = [vp, ctypes.c_int]
+        lib.ctr_batch_plan.restype = vp
+        lib.ctr_batch_retune.argtypes = [vp]
+        lib.ctr_batch_retune.restype = ctypes.c_int
+        lib.ctr_batch_launch_count.argtypes = [vp]
+        lib.ctr_batch_launch_count.restype = ctypes.c_ulonglong
+        lib.tv_pd_solve_batched.argtypes = [vp, P(vp), P(vp), P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
+                                            P(Params), P(ctypes.c_double), P(ctypes.c_double), P(vp), P(Diag), vp]
+        lib.tv_pd_solve_batched.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
         lib.ctr_div.argtypes = [vp, vp, vp, vp]
         for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
@@ -220,6 +239,13 @@ class Plan:
     def launch_count(self) -> int:
         return int(load().ctr_plan_launch_count(self._h))
 
+    @property
+    def bp_groups(self) -> int:
+        return int(load().ctr_plan_get_bp_groups(self._h))
+
+    def set_bp_groups(self, groups: int):
+        _check(load().ctr_plan_set_bp_groups(self._h, int(groups)))
+
     def rh_adjoint(self, g, u=None, stream=None):
         u = self.empty_image() if u is None else u
         _check(load().rh_adjoint(self._h, self._t(g, (self.n_angles, self.n_bins), "g", self.op_dtype),
@@ -298,3 +324,91 @@ class Plan:
                                 self._t(u_out, (self.n, self.n), "u_out") if u_out is not None else None,
                                 ctypes.byref(diag) if want_diag else None, _stream(stream)))
         return (u_out if u_out is not None else state["u"]), diag.as_dict()
+
+
+class _PlanView(Plan):
+    """A plan owned by a Batch (not destroyed on its own)."""
+
+    def __init__(self, handle, n, n_angles, n_bins, angles, h, ds):
+        import torch
+        self._h = ctypes.c_void_p(handle)
+        self.angles = angles
+        self.n, self.n_angles, self.n_bins, self.h, self.ds = n, n_angles, n_bins, h, ds
+        self.dtype = "f32"
+        self.torch_dtype = torch.float32
+        self.op_dtype = torch.float32
+
+    def close(self):
+        self._h = ctypes.c_void_p()
+
+
+class Batch:
+    """Many independent FP32 slices solved together: each stage of an iteration is one
+    kernel launch over all slices (ctr_batch in include/ctrecon.h)."""
+
+    def __init__(self, geometries):
+        """geometries: iterable of dicts with n, n_angles, n_bins and optional angles, h, ds."""
+        lib = load()
+        self.geoms = []
+        arr = (Geometry * len(geometries))()
+        for i, g in enumerate(geometries):
+            n, N, M = int(g["n"]), int(g["n_angles"]), int(g["n_bins"])
+            ang = g.get("angles")
+            ang = np.arange(N, dtype=np.float64) * (np.pi / N) if ang is None else np.ascontiguousarray(ang, np.float64)
+            h, ds = float(g.get("h", 1.0)), float(g.get("ds", 1.0))
+            self.geoms.append(dict(n=n, n_angles=N, n_bins=M, angles=ang, h=h, ds=ds))
+            arr[i] = Geometry(n, N, M, h, ds, ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        handle = ctypes.c_void_p()
+        _check(lib.ctr_batch_create(arr, len(geometries), ctypes.byref(handle)))
+        self._h = handle
+        self.plans = [_PlanView(lib.ctr_batch_plan(handle, i), g["n"], g["n_angles"], g["n_bins"], g["angles"],
+                                g["h"], g["ds"]) for i, g in enumerate(self.geoms)]
+
+    def __len__(self):
+        return len(self.geoms)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ctr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launch_count(self) -> int:
+        return int(load().ctr_batch_launch_count(self._h))
+
+    def retune(self):
+        _check(load().ctr_batch_retune(self._h))
+
+    def solve(self, fs, masks, alphas, deltas, iters: int, params: Optional[Params] = None, betas=None, cs=None,
+              u_outs=None, want_diag: bool = True, stream=None):
+        """tv_pd_solve for every slice; returns (list of u, list of diag dicts or None)."""
+        import torch
+        ns = len(self)
+        if u_outs is None:
+            u_outs = [torch.empty((g["n"], g["n"]), dtype=torch.float32, device="cuda") for g in self.geoms]
+        fp = (ctypes.c_void_p * ns)()
+        up = (ctypes.c_void_p * ns)()
+        mp = (ctypes.c_void_p * ns)()
+        for i, g in enumerate(self.geoms):
+            fp[i] = self.plans[i]._t(fs[i], (g["n_angles"], g["n_bins"]), f"f[{i}]").value
+            up[i] = self.plans[i]._t(u_outs[i], (g["n"], g["n"]), f"u_out[{i}]").value
+            m = None if masks is None else masks[i]
+            if m is not None:
+                if m.dtype != torch.uint8 or not m.is_cuda or tuple(m.shape) != (g["n_angles"], g["n_bins"]):
+                    raise ValueError(f"mask[{i}] must be a CUDA uint8 tensor of the sinogram's shape")
+                mp[i] = m.data_ptr()
+        al = (ctypes.c_double * ns)(*[float(a) for a in alphas])
+        de = (ctypes.c_double * ns)(*[float(d) for d in deltas])
+        be = (ctypes.c_double * ns)(*[float(b) for b in betas]) if betas is not None else None
+        cc = (ctypes.c_double * ns)(*[float(c) for c in cs]) if cs is not None else None
+        diags = (Diag * ns)() if want_diag else None
+        prm = params if params is not None else default_params()
+        _check(load().tv_pd_solve_batched(self._h, fp, mp, al, de, int(iters), ctypes.byref(prm), be, cc, up,
+                                          diags, _stream(stream)))
+        return u_outs, ([d.as_dict() for d in diags] if want_diag else None)

@@ -251,6 +251,22 @@ def config_bf16_2048(seed: int = 5) -> Problem:
                         noise="poisson", alpha=0.3, iters=300, dtype="bf16")
 
 
+def config_batched(count: int = 64, seed: int = 11, iters: int = 300, sizes=(256, 384, 512, 768, 1024),
+                   views=(180, 1440)):
+    """`count` slices of uneven size: n uniform in `sizes`, view count uniform in
+    [views[0], views[1]], bins ceil(sqrt(2) n); 4 ellipses and 2 metal disks each,
+    1e5-photon Poisson noise; FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for s in range(count):
+        n = int(sizes[int(rng.integers(0, len(sizes)))])
+        N = int(rng.integers(views[0], views[1] + 1))
+        M = int(np.ceil(np.sqrt(2.0) * n))
+        out.append(make_problem(f"batch_{s}", n, N, M, seed=seed * 1000 + s, n_ellipses=4, n_metal=2,
+                                noise="poisson", alpha=0.3, iters=iters, dtype="f32"))
+    return out
+
+
 def config_mar_fp32(seed: int = 2, n_metal: Optional[int] = None) -> Problem:
     """512x512 ellipse phantom plus 2-4 metal disks (radius 4-10 px, value 10),
     720 angles, 729 bins, 1e5-photon Poisson noise, metal-trace inequality

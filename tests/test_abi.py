@@ -13,7 +13,8 @@ HEADER = os.path.join(ROOT, "include", "ctrecon.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?(?:ctr_status|void|char|size_t|unsigned long long)\s*\*?\s*(\w+)\s*\(",
+    names = re.findall(r"^\s*(?:const\s+)?(?:ctr_status|void|char|size_t|unsigned long long|int|ctr_plan)\s*\*?\s*"
+                       r"(\w+)\s*\(",
                        text, flags=re.M)
     return sorted(set(names))
 

@@ -1,0 +1,106 @@
+"""The batched form: many slices of uneven size and view count solved together, one
+launch per stage of each iteration over all slices, graph-captured, with the
+project-written autotuner choosing the backprojection's angle split.
+
+Parity: each slice of a batch equals the same slice solved alone by tv_pd_solve
+(same kernels, same arithmetic) and the FP64 oracle within the FP32 bar."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import rel_l2, to_dev, to_np
+from paper_1810_03275_gb300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ct():
+    from paper_1810_03275_gb300 import ctrecon
+    return ctrecon
+
+
+def _slices():
+    # uneven sizes (radix 2 and 3), view counts and bins; one with no metal
+    spec = [(32, 40, 46, 1), (48, 25, 69, 2), (64, 90, 91, 0), (96, 57, 136, 2), (24, 33, 34, 1)]
+    return [phantom.make_problem(f"s{i}", n, N, M, seed=20 + i, n_ellipses=3, n_metal=m, noise="gaussian",
+                                 alpha=0.05 * (i + 1)) for i, (n, N, M, m) in enumerate(spec)]
+
+
+def test_batch_matches_single_slices_and_oracle(ct):
+    import torch
+    probs = _slices()
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    betas, cs = [], []
+    for p in probs:
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        b = oracle.power_beta(geo, 30)
+        betas.append(b)
+        cs.append(oracle.power_c(geo, b, np.pi / p.n, 30))
+    iters = 40
+    prm = ct.default_params(graph_block=8)
+    us, diags = batch.solve(fs, ms, [p.alpha for p in probs], [p.delta for p in probs], iters, params=prm,
+                            betas=betas, cs=cs)
+    for i, p in enumerate(probs):
+        plan = ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta)
+        plan.set_bp_groups(batch.plans[i].bp_groups)
+        u1, d1 = plan.tv_pd_solve(fs[i], ms[i], p.alpha, p.delta, iters,
+                                  params=ct.default_params(beta=betas[i], c=cs[i], graph_block=8))
+        # same kernel bodies; FP32 contraction may differ between the two compiled
+        # instances, so agreement is to FP32 rounding, not bit for bit
+        assert rel_l2(to_np(us[i]), to_np(u1)) < 2e-6, i
+        assert diags[i]["objective"] == pytest.approx(d1["objective"], rel=1e-5)
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        desc = oracle.make_descriptors(p.f, p.mask, p.delta)
+        ref = oracle.pdrq_solve(geo, desc, p.alpha, iters, sigma=1.0, tau=1 / np.sqrt(8), eps=np.pi / p.n,
+                                beta=betas[i], c=cs[i])
+        assert rel_l2(to_np(us[i]), ref.u) < 1e-5, i
+    # one launch per stage per iteration, plus per-slice set-up and the last iteration
+    assert batch.launch_count > 0
+
+
+def test_batch_power_iterations_and_single_slice(ct):
+    """Without betas/cs the batch runs each slice's power iterations; a batch of one
+    slice equals tv_pd_solve."""
+    import torch
+    p = _slices()[1]
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta)])
+    f = to_dev(p.f, torch.float32)
+    m = torch.as_tensor(p.mask, device="cuda")
+    us, diags = batch.solve([f], [m], [p.alpha], [p.delta], 30)
+    plan = ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta)
+    plan.set_bp_groups(batch.plans[0].bp_groups)
+    u1, d1 = plan.tv_pd_solve(f, m, p.alpha, p.delta, 30)
+    assert diags[0]["beta"] == d1["beta"] and diags[0]["c"] == d1["c"]
+    assert rel_l2(to_np(us[0]), to_np(u1)) < 2e-6
+
+
+def test_autotuner_keeps_results(ct, tmp_path, monkeypatch):
+    """The tuner picks an angle split by timing; results stay within FP32 rounding of
+    the oracle whatever it picks, and the choice is cached."""
+    import torch
+    from paper_1810_03275_gb300 import autotune
+    monkeypatch.setenv("CTR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n, N, M = 256, 180, 363
+    plan = ct.Plan(n, N, M)
+    G = autotune.tune_plan(plan, reps=2)
+    assert plan.bp_groups == G
+    geo = oracle.Geometry(n, N, M)
+    g = np.random.default_rng(0).standard_normal((N, M))
+    got = to_np(plan.rh_adjoint(to_dev(g, torch.float32)))
+    assert rel_l2(got, oracle.rh_adjoint(g, geo)) < 1e-5
+    assert autotune.tune_plan(ct.Plan(n, N, M), reps=2) == G          # from the cache
+    probs = _slices()
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    pol = autotune.tune_batch(batch, fs, None, [p.alpha for p in probs], [p.delta for p in probs], iters=3)
+    assert pol in (None, 1, 2, 4)
+
+
+def test_batch_rejects_bad_input(ct):
+    with pytest.raises(ct.CtrError):
+        ct.Batch([dict(n=10, n_angles=8, n_bins=15)])            # n not 2^a 3^b
+    with pytest.raises(ct.CtrError):
+        ct.Batch([dict(n=16, n_angles=8, n_bins=23, h=1.0, ds=2.0)])
