@@ -195,6 +195,57 @@ def measure_forms(iters: int = 30):
     return out
 
 
+def measure_batched(iters: int = 30, count: int = 64):
+    """The batched form on 64 slices of uneven size (n in {256..1024}, 180-1440 views,
+    ceil(sqrt(2) n) bins): slice-iterations/s of one batched solve (one launch per
+    stage over all slices, graph-captured, autotuned angle split) against solving the
+    same slices one after another with tv_pd_solve.  beta and c fixed per slice."""
+    import torch
+    from paper_1810_03275_gb300 import autotune
+    from paper_1810_03275_gb300 import ctrecon as ct
+    from paper_1810_03275_gb300 import phantom
+    probs = phantom.config_batched(count, iters=iters, n_ellipses=2, n_metal=1)
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [torch.as_tensor(p.f, dtype=torch.float32, device="cuda") for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    al = [p.alpha for p in probs]
+    de = [p.delta for p in probs]
+    betas = [pl.power_beta(10) for pl in batch.plans]
+    cs = [1.05 * pl.power_lambda(b, np.pi / pl.n, 10) for pl, b in zip(batch.plans, betas)]
+    policy = autotune.tune_batch(batch, fs, ms, al, de, iters=3, betas=betas, cs=cs, use_cache=False)
+    prm = ct.default_params()
+    batch.solve(fs, ms, al, de, 5, params=prm, betas=betas, cs=cs, want_diag=False)      # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = batch.launch_count
+    a.record()
+    batch.solve(fs, ms, al, de, iters, params=prm, betas=betas, cs=cs, want_diag=False)
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3
+    launches = batch.launch_count - l0
+    us = [torch.empty((p.n, p.n), dtype=torch.float32, device="cuda") for p in probs]
+    plans = [ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta) for p in probs]
+    for pl, bp in zip(plans, batch.plans):
+        pl.set_bp_groups(bp.bp_groups)
+    for pl, f, m, p, bb, cc, u in zip(plans, fs, ms, probs, betas, cs, us):
+        pl.tv_pd_solve(f, m, p.alpha, p.delta, 2, params=ct.default_params(beta=bb, c=cc), u_out=u)
+    torch.cuda.synchronize()
+    a.record()
+    for pl, f, m, p, bb, cc, u in zip(plans, fs, ms, probs, betas, cs, us):
+        pl.tv_pd_solve(f, m, p.alpha, p.delta, iters, params=ct.default_params(beta=bb, c=cc), u_out=u)
+    b.record()
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    samples = sum(2.0 * p.n * p.n * p.n_angles for p in probs) * iters
+    return {"slices": count, "iters": iters, "policy": policy,
+            "batched": {"slice_iters_per_s": count * iters / t_batch, "gsamples_per_s": samples / t_batch / 1e9,
+                        "kernel_launches": launches},
+            "sequential": {"slice_iters_per_s": count * iters / t_seq, "gsamples_per_s": samples / t_seq / 1e9},
+            "speedup": t_seq / t_batch,
+            "workload": "64 slices, n in {256,384,512,768,1024}, 180-1440 views, ceil(sqrt(2) n) bins, FP32"}
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
@@ -336,7 +387,7 @@ def main():
 
     forms = None
     if rank == 0 and not args.no_forms:
-        forms = measure_forms()
+        forms = {"bf16": measure_forms(), "batched": measure_batched()}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

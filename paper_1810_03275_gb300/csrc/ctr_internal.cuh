@@ -31,6 +31,19 @@ ctr_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::ctr::cuda_fail(e_, what);   \
     } while (0)
 
+// The dynamic shared-memory limit is an attribute of the kernel function for the
+// whole process, shared by every plan: only ever raise it.
+template <typename K>
+inline ctr_status raise_smem_limit(K *kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return CTR_OK;
+    cudaFuncAttributes a;
+    CTR_CUDA(cudaFuncGetAttributes(&a, (const void *)kernel));
+    if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return CTR_OK;
+    CTR_CUDA(cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return CTR_OK;
+}
+
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };

@@ -381,13 +381,10 @@ template <typename T>
 ctr_status configure_fft(const ctr_plan *p)
 {
     const size_t smr = fft_smem_bytes(p, 0), smc = fft_smem_bytes(p, 1);
-    if (smr > 48 * 1024) {
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    }
-    if (smc > 48 * 1024)
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-    return CTR_OK;
+    ctr_status st = raise_smem_limit(k_fft_rows_fwd<T>, smr);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv<T>, smr);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_cols<T>, smc);
+    return st;
 }
 
 template <typename T>
@@ -406,13 +403,10 @@ template ctr_status launch_circulant<float>(const ctr_plan *, const float *, boo
 template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int, double *, double *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
 ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem)
 {
-    if (rows_smem > 48 * 1024) {
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_fwd_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_inv_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
-    }
-    if (cols_smem > 48 * 1024)
-        CTR_CUDA(cudaFuncSetAttribute(k_fft_cols_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem));
-    return CTR_OK;
+    ctr_status st = raise_smem_limit(k_fft_rows_fwd_batch, rows_smem);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv_batch, rows_smem);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_cols_batch, cols_smem);
+    return st;
 }
 
 // One batched preconditioner pass over all slices.
@@ -494,9 +488,10 @@ ctr_status static_setup(int dev)
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.sym, g_static_sym));
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.tw, g_static_tw));
     const int smax = 2 * 4 * (STATIC_MAX_N + 1) * (int)sizeof(float2);   // column kernel at n = 1024
-    CTR_CUDA(cudaFuncSetAttribute(k_fft_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    CTR_CUDA(cudaFuncSetAttribute(k_fft_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    ctr_status st = raise_smem_limit(k_fft_cols<float>, smax);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_fwd<float>, smax);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv<float>, smax);
+    if (st != CTR_OK) return st;
     s.ready = true;
     return CTR_OK;
 }

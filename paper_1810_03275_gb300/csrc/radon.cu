@@ -549,13 +549,10 @@ template <typename T>
 ctr_status configure_radon(const ctr_plan *p)
 {
     const size_t smem = bp_smem<T>(p);
-    if (smem > 48 * 1024) {
-        CTR_CUDA(cudaFuncSetAttribute(k_backproject<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if constexpr (sizeof(T) == 4)
-            CTR_CUDA(cudaFuncSetAttribute(k_backproject<float, __nv_bfloat16>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    return CTR_OK;
+    ctr_status st = raise_smem_limit(k_backproject<T, T>, smem);
+    if constexpr (sizeof(T) == 4)
+        if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
+    return st;
 }
 
 ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, const BackprojEpi<float> &epi,
@@ -607,9 +604,7 @@ void bp_tiles(int n, int &tx, int &ty)
 
 ctr_status configure_batch_radon(size_t bp_smem)
 {
-    if (bp_smem > 48 * 1024)
-        CTR_CUDA(cudaFuncSetAttribute(k_backproject_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp_smem));
-    return CTR_OK;
+    return raise_smem_limit(k_backproject_batch, bp_smem);
 }
 
 // One batched projector stage over all slices (blocks = total CTAs of the stage).

@@ -252,17 +252,17 @@ def config_bf16_2048(seed: int = 5) -> Problem:
 
 
 def config_batched(count: int = 64, seed: int = 11, iters: int = 300, sizes=(256, 384, 512, 768, 1024),
-                   views=(180, 1440)):
+                   views=(180, 1440), n_ellipses: int = 4, n_metal: int = 2):
     """`count` slices of uneven size: n uniform in `sizes`, view count uniform in
-    [views[0], views[1]], bins ceil(sqrt(2) n); 4 ellipses and 2 metal disks each,
-    1e5-photon Poisson noise; FP32."""
+    [views[0], views[1]], bins ceil(sqrt(2) n); `n_ellipses` ellipses and `n_metal`
+    metal disks each, 1e5-photon Poisson noise; FP32."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for s in range(count):
         n = int(sizes[int(rng.integers(0, len(sizes)))])
         N = int(rng.integers(views[0], views[1] + 1))
         M = int(np.ceil(np.sqrt(2.0) * n))
-        out.append(make_problem(f"batch_{s}", n, N, M, seed=seed * 1000 + s, n_ellipses=4, n_metal=2,
+        out.append(make_problem(f"batch_{s}", n, N, M, seed=seed * 1000 + s, n_ellipses=n_ellipses, n_metal=n_metal,
                                 noise="poisson", alpha=0.3, iters=iters, dtype="f32"))
     return out
 

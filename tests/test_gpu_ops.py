@@ -42,6 +42,19 @@ def test_precond_apply(ct, n, dtype):
     assert rel_l2(got, ref) < (2e-6 if dtype == "f32" else 1e-12)
 
 
+def test_plans_of_different_sizes_coexist(ct):
+    """Kernel shared-memory limits are process-wide: creating a smaller plan after a
+    larger one must not break the larger plan's launches (regression)."""
+    big = ct.Plan(2048, 4, 5)
+    ct.Plan(768, 4, 5)
+    ct.Plan(1024, 4, 5)
+    prm = ct.default_params(c=1.0, eps=0.01)
+    y = np.random.default_rng(0).standard_normal((2048, 2048))
+    got = to_np(big.precond_apply(to_dev(y, big.torch_dtype), prm))
+    ref = oracle.precond_apply(y, oracle.precond_symbol(2048, 1.0, prm.tau, 1.0, 0.01))
+    assert rel_l2(got, ref) < 2e-6
+
+
 def test_precond_rejects_other_sizes(ct):
     plan = ct.Plan(10, 4, 5)
     with pytest.raises(ct.CtrError) as e:
