@@ -177,6 +177,26 @@ ctr_status tv_pd_run(ctr_plan *plan, const void *w_dev, const void *a_dev, const
                      const void *hi_dev, double alpha, int iters, const ctr_params *params,
                      ctr_state *state, void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* tv_pd_solve continuing from `state` (in/out, FP32/FP64 plans): runs `iters`
+ * iterations of Alg. 4 from the given (u, Ru, v1b, v2b) and leaves the new state in
+ * the same buffers (checkpoint / resume, and the forward replay of the reverse mode).
+ * params->beta and ->c should be given so that every call uses the same scaling. */
+ctr_status tv_pd_solve_state(ctr_plan *plan, const void *f_dev, const uint8_t *metal_mask_dev, double alpha,
+                             double delta, int iters, const ctr_params *params, ctr_state *state,
+                             ctr_diag *diag_out, void *stream);
+
+/* Reverse mode of one iteration of Alg. 4 (vector-Jacobian product) for the
+ * iteration that took state s0 to s1 (both as produced by tv_pd_solve_state with the
+ * same f, mask, alpha, delta, params; params->beta, ->c > 0 required).
+ * In: bu, b1, b2 = cotangents of s1's u (n*n), v1b (N*M), v2b (2*n*n).  Out (in
+ * place): the cotangents of s0's u, v1b, v2b.  Accumulated: gf (N*M) += d/df,
+ * *galpha_dev (device double) += d/dalpha.  beta and c are constants (they depend on
+ * the geometry only).  Where clip or the TV projection has a kink the inside branch
+ * is differentiated. */
+ctr_status tv_pd_vjp_step(ctr_plan *plan, const void *f_dev, const uint8_t *metal_mask_dev, double alpha,
+                          double delta, const ctr_params *params, const ctr_state *s0, const ctr_state *s1,
+                          void *bu, void *b1, void *b2, void *gf, double *galpha_dev, void *stream);
+
 /* Tuning hook: split the backprojection's angles into `groups` groups whose partial
  * images are summed (more CTAs for small images).  1 <= groups <= the capacity the
  * plan allocated (up to 8 for n <= 1024), else CTR_EINVAL.  No allocation. */

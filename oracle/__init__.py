@@ -31,6 +31,7 @@ from .pdrq_ref import (
     pdrq_solve,
     cp_solve,
     diagnostics,
+    pdrq_grad,
 )
 
 __all__ = [
@@ -38,5 +39,5 @@ __all__ = [
     "build_oracle", "num_threads", "grad", "div", "tv_norm", "lap_symbol", "freq_norm",
     "precond_symbol", "precond_apply", "prox_dual", "tv_project", "conj_data_term",
     "make_descriptors", "power_beta", "power_c", "power_start", "PDRQState", "pdrq_solve", "cp_solve",
-    "diagnostics",
+    "diagnostics", "pdrq_grad",
 ]

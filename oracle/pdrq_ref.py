@@ -341,3 +341,69 @@ def diagnostics(geo: Geometry, desc, alpha: float, u: np.ndarray, *, beta: float
         out["gap"] = g1 + g2
         out["dual_residual"] = float(np.linalg.norm(kt))
     return out
+
+
+def pdrq_grad(geo: Geometry, f, mask, delta: float, alpha: float, iters: int, cot_u, *, sigma: float, tau: float,
+              eps: float, beta: float, c: float, trace_ratio: float = 0.8):
+    """Reverse mode of `iters` iterations of Alg. 4 from zero: the derivatives of
+    <cot_u, u_iters> with respect to the data f (through the data term of
+    make_descriptors) and to alpha, by the chain rule through each step of the
+    iteration in reverse order (beta and c held fixed).  Where clip or the TV
+    projection has a kink the inside branch is taken.  Returns (df, dalpha).
+    Pinned by central finite differences of pdrq_solve (tests/test_oracle_grad.py)."""
+    h = geo.h
+    f = np.asarray(f, dtype=np.float64)
+    m = np.zeros(f.shape, bool) if mask is None else np.asarray(mask).astype(bool)
+    desc = make_descriptors(f, m, delta, trace_ratio)
+    w, a, lo, hi = desc
+    at, lot, hit = a / beta, lo / beta, hi / beta
+    lam = alpha / (beta * beta)
+    sym = precond_symbol(geo.n, sigma, tau, c, eps)
+    kw = dict(sigma=sigma, tau=tau, eps=eps, beta=beta, c=c)
+    states = [PDRQState.zeros(geo)]
+    for _ in range(iters):
+        states.append(pdrq_solve(geo, desc, alpha, 1, state=states[-1], **kw))
+    bu = np.array(cot_u, dtype=np.float64)
+    b1 = np.zeros(geo.sino_shape)
+    b2x = np.zeros(geo.image_shape)
+    b2y = np.zeros(geo.image_shape)
+    df = np.zeros(geo.sino_shape)
+    dlam = 0.0
+    st_ = sigma * tau
+    for k in reversed(range(iters)):
+        s0, s1 = states[k], states[k + 1]
+        # t1 = z1 - sigma clip(q, lo, hi), q = (z1 + w a)/(sigma + w), z1 = v1b + 2 sigma Rt u'
+        z1 = s0.v1b + 2.0 * sigma * s1.Ru
+        q = (z1 + w * at) / (sigma + w)
+        below, above = q < lot, q > hit
+        inside = ~(below | above)
+        A1 = b1
+        dz1 = np.where(inside, A1 * (1.0 - sigma / (sigma + w)), A1)
+        da = np.where(inside, -sigma * w / (sigma + w) * A1, 0.0)
+        dlo = np.where(below, -sigma * A1, 0.0)
+        dhi = np.where(above, -sigma * A1, 0.0)
+        df += np.where(m, trace_ratio * dlo, da + dlo + dhi) / beta
+        dRu = -sigma * A1 + 2.0 * sigma * dz1
+        # t2 = P(z2), z2 = v2b + 2 sigma tau grad u'
+        gx, gy = grad(s1.u, h)
+        zx, zy = s0.v2bx + 2.0 * st_ * gx, s0.v2by + 2.0 * st_ * gy
+        nz = np.sqrt(zx * zx + zy * zy)
+        proj = tau * nz > lam
+        with np.errstate(invalid="ignore", divide="ignore"):
+            nx, ny = np.where(proj, zx / nz, 0.0), np.where(proj, zy / nz, 0.0)
+            dot = nx * b2x + ny * b2y
+            sc = np.where(proj, lam / (tau * nz), 1.0)
+        dx = np.where(proj, sc * (b2x - nx * dot), b2x)
+        dy = np.where(proj, sc * (b2y - ny * dot), b2y)
+        dlam += float(np.sum(np.where(proj, dot / tau, 0.0)))
+        dgx, dgy = -st_ * b2x + 2.0 * st_ * dx, -st_ * b2y + 2.0 * st_ * dy
+        # u' = u - sigma P(Rt^* y1 - tau div y2)
+        du1 = bu + rh_adjoint(dRu, geo) / beta - div(dgx, dgy, h)
+        dr = -sigma * precond_apply(du1, sym)
+        dy1 = rh_forward(dr, geo) / beta
+        ex, ey = grad(dr, h)
+        dy2x, dy2y = tau * ex, tau * ey
+        bu = du1 + sigma * rh_adjoint(dy1, geo) / beta - st_ * div(dy2x, dy2y, h)
+        b1 = dz1 + dy1
+        b2x, b2y = dx + dy2x, dy + dy2y
+    return df, dlam / (beta * beta)

@@ -1,0 +1,122 @@
+"""Differentiable forms: R_h and R_h^* as torch.autograd.Functions (each other's
+hand-written adjoint kernels), and K unrolled iterations of Alg. 4 as a function of
+the data f and of alpha, with checkpoints every few iterates.
+
+Forward: the iterations run through tv_pd_solve_state in segments of `ckpt`
+iterations; the state (u, R u, v1b, v2b) at the start of each segment is kept.
+Backward: each segment is replayed one iteration at a time from its checkpoint and
+then reversed with tv_pd_vjp_step (the library's reverse-mode kernels), newest
+segment first.  beta and c are fixed per plan (they depend on the geometry only).
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import torch
+
+from . import ctrecon as ct
+
+
+class RadonFn(torch.autograd.Function):
+    """g = R_h u; the VJP is R_h^* (the exact transpose kernel)."""
+
+    @staticmethod
+    def forward(ctx, u, plan):
+        ctx.plan = plan
+        return plan.rh_forward(u.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.rh_adjoint(g.contiguous()), None
+
+
+class BackprojFn(torch.autograd.Function):
+    """u = R_h^* g; the VJP is R_h."""
+
+    @staticmethod
+    def forward(ctx, g, plan):
+        ctx.plan = plan
+        return plan.rh_adjoint(g.contiguous())
+
+    @staticmethod
+    def backward(ctx, u):
+        return ctx.plan.rh_forward(u.contiguous()), None
+
+
+def radon(u, plan):
+    return RadonFn.apply(u, plan)
+
+
+def backproject(g, plan):
+    return BackprojFn.apply(g, plan)
+
+
+def _clone(st):
+    return {k: v.clone() for k, v in st.items()}
+
+
+class UnrolledPDRQ(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f, alpha, plan, mask, delta, iters, ckpt, params):
+        a = float(alpha.detach().cpu()) if isinstance(alpha, torch.Tensor) else float(alpha)
+        f = f.detach().contiguous()
+        state = plan.new_state()
+        ckpts = []
+        done = 0
+        while done < iters:
+            ckpts.append((done, _clone(state)))
+            k = min(ckpt, iters - done)
+            plan.tv_pd_solve_state(f, mask, a, delta, k, params, state)
+            done += k
+        ctx.plan, ctx.mask, ctx.delta, ctx.iters, ctx.params, ctx.alpha = plan, mask, delta, iters, params, a
+        ctx.ckpts = ckpts
+        ctx.save_for_backward(f)
+        ctx.alpha_is_tensor = isinstance(alpha, torch.Tensor)
+        return state["u"].clone()
+
+    @staticmethod
+    def backward(ctx, gu):
+        (f,) = ctx.saved_tensors
+        plan, mask, delta, params, a = ctx.plan, ctx.mask, ctx.delta, ctx.params, ctx.alpha
+        dt = plan.torch_dtype
+        n, N, M = plan.n, plan.n_angles, plan.n_bins
+        bu = gu.detach().to(dt).contiguous().clone()
+        b1 = torch.zeros((N, M), dtype=dt, device="cuda")
+        b2 = torch.zeros((2, n, n), dtype=dt, device="cuda")
+        gf = torch.zeros((N, M), dtype=dt, device="cuda")
+        galpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+        bounds = [k for k, _ in ctx.ckpts] + [ctx.iters]
+        for seg in reversed(range(len(ctx.ckpts))):
+            start, st0 = ctx.ckpts[seg]
+            length = bounds[seg + 1] - start
+            states = [st0]
+            cur = _clone(st0)
+            for _ in range(length):                      # replay the segment
+                plan.tv_pd_solve_state(f, mask, a, delta, 1, params, cur)
+                states.append(_clone(cur))
+            for k in reversed(range(length)):            # and reverse it
+                plan.tv_pd_vjp_step(f, mask, a, delta, params, states[k], states[k + 1], bu, b1, b2, gf, galpha)
+        ga = galpha.to(torch.float64) if ctx.alpha_is_tensor else None
+        if ga is not None:
+            ga = ga.reshape(()).to(dtype=torch.float64)
+        return gf, ga, None, None, None, None, None, None
+
+
+def fixed_scaling(plan, power_iters: int = 50, margin: float = 1.05, eps: Optional[float] = None) -> ct.Params:
+    """Solver parameters with beta and c from the plan's power iterations, computed once."""
+    eps = math.pi / plan.n if eps is None else eps
+    beta = plan.power_beta(power_iters)
+    c = margin * plan.power_lambda(beta, eps, power_iters)
+    return ct.default_params(beta=beta, c=c, eps=eps)
+
+
+def unrolled_pdrq(f, alpha, plan, mask=None, delta: float = -1.0, iters: int = 20, ckpt: int = 5,
+                  params: Optional[ct.Params] = None):
+    """u_K of K = `iters` iterations of Alg. 4 from zero, differentiable in f and alpha
+    (alpha a 0-d float64 tensor to get its gradient).  params must fix beta and c."""
+    if params is None:
+        params = fixed_scaling(plan)
+    if not (params.beta > 0 and params.c > 0):
+        raise ValueError("params must fix beta and c (see fixed_scaling)")
+    return UnrolledPDRQ.apply(f, alpha, plan, mask, float(delta), int(iters), int(ckpt), params)

@@ -35,6 +35,10 @@ template <typename T> ctr_status op_adjoint(ctr_plan *, const T *, T *, double, 
 ctr_status batch_solve(ctr_batch *, const float *const *, const uint8_t *const *, const double *, const double *, int,
                        const ctr_params &, const double *, const double *, float *const *, ctr_diag *, cudaStream_t);
 ctr_status batch_prepare(ctr_batch *);
+template <typename T>
+ctr_status pdrq_vjp_step(ctr_plan *, const T *, const T *, const T *, const T *, const T *, const T *, const uint8_t *,
+                         double, double, double, double, double, const ctr_params &, T *, T *, T *, T *, double *,
+                         cudaStream_t);
 ctr_status op_forward_bf16(ctr_plan *, const __nv_bfloat16 *, const __nv_bfloat16 *, float *, cudaStream_t);
 ctr_status op_adjoint_bf16(ctr_plan *, const __nv_bfloat16 *, float *, cudaStream_t);
 template <typename T> ctr_status power_beta(ctr_plan *, int, double *, cudaStream_t);
@@ -497,6 +501,46 @@ ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, 
     return CTR_DISPATCH(p,
                         solve_impl<float>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream),
                         solve_impl<double>(p, nullptr, nullptr, w, a, lo, hi, alpha, 0.0, iters, q, state, u_out, diag, stream));
+}
+
+ctr_status tv_pd_solve_state(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,
+                             const ctr_params *prm, ctr_state *state, ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !state || !state->u || !state->Ru || !state->v1b || !state->v2b)
+        return fail(CTR_EINVAL, "f and every state buffer must be given");
+    if (std::isnan(delta)) return fail(CTR_EINVAL, "delta is NaN");
+    if (p->bf16) return fail(CTR_EUNSUPPORTED, "state-carrying solves need an FP32 or FP64 plan");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, iters, q);
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p,
+                        solve_impl<float>(p, f, mask, nullptr, nullptr, nullptr, nullptr, alpha, delta, iters, q, state, nullptr, diag, stream),
+                        solve_impl<double>(p, f, mask, nullptr, nullptr, nullptr, nullptr, alpha, delta, iters, q, state, nullptr, diag, stream));
+}
+
+ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta,
+                          const ctr_params *prm, const ctr_state *s0, const ctr_state *s1, void *bu, void *b1,
+                          void *b2, void *gf, double *galpha_dev, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !s0 || !s1 || !bu || !b1 || !b2 || !gf || !galpha_dev) return fail(CTR_EINVAL, "null argument");
+    if (!s0->u || !s0->v1b || !s0->v2b || !s1->u || !s1->Ru) return fail(CTR_EINVAL, "state buffer missing");
+    if (p->bf16) return fail(CTR_EUNSUPPORTED, "the reverse mode needs an FP32 or FP64 plan");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, 1, q);
+    if (st != CTR_OK) return st;
+    if (!(q.beta > 0) || !(q.c > 0)) return fail(CTR_EINVAL, "the reverse mode needs beta and c given (> 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->dtype == CTR_F64)
+        return pdrq_vjp_step<double>(p, (const double *)s0->u, (const double *)s0->v1b, (const double *)s0->v2b,
+                                     (const double *)s1->u, (const double *)s1->Ru, (const double *)f, mask, delta,
+                                     q.trace_ratio, alpha, q.beta, q.c, q, (double *)bu, (double *)b1, (double *)b2,
+                                     (double *)gf, galpha_dev, s);
+    return pdrq_vjp_step<float>(p, (const float *)s0->u, (const float *)s0->v1b, (const float *)s0->v2b,
+                                (const float *)s1->u, (const float *)s1->Ru, (const float *)f, mask, delta,
+                                q.trace_ratio, alpha, q.beta, q.c, q, (float *)bu, (float *)b1, (float *)b2,
+                                (float *)gf, galpha_dev, s);
 }
 
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)

@@ -676,6 +676,173 @@ ctr_status build_desc_from_arrays(ctr_plan *p, const T *w, const T *a, const T *
     return CTR_OK;
 }
 
+// ------------------------------------------------------------------------------
+// Reverse mode of one iteration of Alg. 4 (hand-written vector-Jacobian product).
+// The iteration maps s_k = (u, v1b, v2b) to s_{k+1}; with Ru = Rt u,
+//   u'   = u - sigma P( Rt^*(v1b + sigma Rt u) - tau div(v2b + sigma tau grad u) )
+//   z1   = v1b + 2 sigma Rt u',  t1 = z1 - sigma clip((z1 + w a)/(sigma + w), lo, hi)
+//   v1b' = t1 - sigma Rt u'
+//   z2   = v2b + 2 sigma tau grad u',  t2 = z2 / max(1, tau |z2| / lam)
+//   v2b' = t2 - sigma tau grad u'
+// Given cotangents (bu, b1, b2) of (u', v1b', v2b') it returns those of (u, v1b,
+// v2b) in place and accumulates the cotangents of the data f (through a, lo, hi)
+// and of alpha (through lam = alpha/beta^2).  z1, z2 are recomputed from s_k and
+// s_{k+1}.  Kinks of clip and of the projection take the inside branch.
+// ------------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+__global__ void k_vjp_data(const T *__restrict__ v1b0, const T *__restrict__ Ru1, const T *__restrict__ f,
+                           const uint8_t *__restrict__ mask, size_t len, double delta, double ratio, double inv_beta,
+                           T sigma, T *b1, T *dRu, T *gf)
+{
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x) {
+        // the beta-scaled data term exactly as k_make_desc builds it
+        const double fv = (double)f[r];
+        const bool tr = mask && mask[r];
+        const T w = tr ? T(0) : T(1);
+        const T a = tr ? T(0) : (T)(fv * inv_beta);
+        const T lo = tr ? (T)(ratio * fv * inv_beta) : (T)(delta >= 0 ? (fv - delta) * inv_beta : -inf);
+        const T hi = tr ? (T)inf : (T)(delta >= 0 ? (fv + delta) * inv_beta : inf);
+        const T z1 = v1b0[r] + T(2) * sigma * Ru1[r];
+        const T q = (z1 + w * a) / (sigma + w);
+        const bool below = q < lo, above = q > hi, in = !below && !above;
+        const T A1 = b1[r];
+        const T dz1 = in ? A1 * (T(1) - sigma / (sigma + w)) : A1;
+        const T da = in ? -sigma * w / (sigma + w) * A1 : T(0);
+        const T dlo = below ? -sigma * A1 : T(0);
+        const T dhi = above ? -sigma * A1 : T(0);
+        // d(a, lo, hi)/df: off the trace 1/beta each (lo, hi only when bounded); on it ratio/beta for lo
+        const T ib = (T)inv_beta;
+        gf[r] += tr ? (T)ratio * ib * dlo : ib * (da + dlo + dhi);
+        dRu[r] = -sigma * A1 + T(2) * sigma * dz1;
+        b1[r] = dz1;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+k_vjp_tv(const T *__restrict__ u1, const T *__restrict__ v2b0, int n, T sigma, T tau, T lam, T inv_h, T *b2, T *dg,
+         double *part)
+{
+    const size_t nn = (size_t)n * n;
+    const T st = sigma * tau;
+    double v[1] = {0.0};
+    for (size_t e = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; e < nn; e += (size_t)gridDim.x * RED_THREADS) {
+        T gx, gy;
+        grad_at(u1, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        const T zx = v2b0[e] + T(2) * st * gx, zy = v2b0[e + nn] + T(2) * st * gy;
+        const T ax = b2[e], ay = b2[e + nn];
+        const T nz = sqrt(zx * zx + zy * zy);
+        T dx = ax, dy = ay;
+        if (tau * nz > lam) {            // projected: t2 = (lam/tau) z/|z|
+            const T nx = zx / nz, ny = zy / nz;
+            const T dot = nx * ax + ny * ay;
+            const T s = lam / (tau * nz);
+            dx = s * (ax - nx * dot);
+            dy = s * (ay - ny * dot);
+            v[0] += (double)dot / (double)tau;     // d t2 / d lam = z / (tau |z|)
+        }
+        b2[e] = dx;
+        b2[e + nn] = dy;
+        dg[e] = -st * ax + T(2) * st * dx;
+        dg[e + nn] = -st * ay + T(2) * st * dy;
+    }
+    block_reduce<1>(v, 0u, part + blockIdx.x);
+}
+
+__global__ void k_accum_scalar(const double *__restrict__ src, double scale, double *dst)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst += scale * *src;
+}
+
+template <typename T>
+__global__ void k_scal(const T *__restrict__ x, T s, size_t len, T *y)
+{
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
+        y[r] = s * x[r];
+}
+
+}  // namespace
+
+template <typename T>
+ctr_status pdrq_vjp_step(ctr_plan *p, const T *u0, const T *v1b0, const T *v2b0, const T *u1, const T *Ru1,
+                         const T *f, const uint8_t *mask, double delta, double ratio, double alpha, double beta,
+                         double c, const ctr_params &prm, T *bu, T *b1, T *b2, T *gf, double *galpha, cudaStream_t s)
+{
+    (void)u0;
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    const T sigma = (T)prm.sigma, tau = (T)prm.tau, inv_h = (T)(1.0 / p->h);
+    const double ib = 1.0 / beta;
+    const T lam = (T)(alpha * ib * ib);
+    T *dRu = (T *)p->gs;            // sinogram scratch
+    T *dy1 = (T *)p->t1;            // sinogram scratch
+    T *dg = (T *)p->y2;             // 2 n^2
+    T *dy2 = (T *)p->t2;            // 2 n^2
+    T *du1 = (T *)p->du;            // n^2
+    T *dr = (T *)p->x;              // n^2
+    T *drT = (T *)p->xt;            // n^2
+    T *tmp = (T *)p->u;             // n^2
+    ctr_status st;
+    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s)) != CTR_OK) return st;
+    // data and TV pointwise steps
+    p->launches += 4;
+    k_vjp_data<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(v1b0, Ru1, f, mask, nm, delta, ratio, ib, sigma, b1, dRu, gf);
+    const int nb = grid_for(nn, RED_THREADS, p->red_blocks);
+    k_vjp_tv<T><<<nb, RED_THREADS, 0, s>>>(u1, v2b0, n, sigma, tau, lam, inv_h, b2, dg, p->d_red);
+    k_finalize<1><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 0u, p->d_scal + 20);
+    k_accum_scalar<<<1, 32, 0, s>>>(p->d_scal + 20, ib * ib, galpha);
+    CTR_CHECK_LAUNCH("vjp pointwise");
+    // du' = bu + Rt^* dRu - div(dg)
+    BackprojEpi<T> e{};
+    e.out = du1;
+    e.scale = (T)ib;
+    e.px = dg;
+    e.divtau = T(1);
+    e.outscale = T(1);
+    e.inv_h = inv_h;
+    if ((st = launch_backproject<T>(p, dRu, e, s)) != CTR_OK) return st;
+    p->launches += 1;
+    k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(du1, bu, T(1), nn, du1);
+    // dr = -sigma P(du')
+    if ((st = launch_circulant<T>(p, du1, false, (const T *)p->sym, dr, 0, drT, nullptr, s)) != CTR_OK) return st;
+    p->launches += 2;
+    k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(dr, -sigma, nn, dr);
+    k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(drT, -sigma, nn, drT);
+    // dy1 = Rt dr ; dy2 = tau grad dr
+    if ((st = op_forward<T>(p, dr, drT, dy1, ib, s)) != CTR_OK) return st;
+    if ((st = op_grad<T>(p, dr, dy2, s)) != CTR_OK) return st;
+    p->launches += 1;
+    k_scal<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(dy2, tau, 2 * nn, dy2);
+    // du = du' + sigma Rt^* dy1 - sigma tau div(dy2)
+    BackprojEpi<T> e2{};
+    e2.out = tmp;
+    e2.scale = (T)(prm.sigma * ib);
+    e2.px = dy2;
+    e2.divtau = sigma * tau;
+    e2.outscale = T(1);
+    e2.inv_h = inv_h;
+    if ((st = launch_backproject<T>(p, dy1, e2, s)) != CTR_OK) return st;
+    p->launches += 3;
+    k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(du1, tmp, T(1), nn, bu);
+    // dv1b = dz1 + dy1 ; dv2b = dz2 + dy2
+    k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(b1, dy1, T(1), nm, b1);
+    k_axpy<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(b2, dy2, T(1), 2 * nn, b2);
+    CTR_CHECK_LAUNCH("vjp step");
+    return CTR_OK;
+}
+
+template ctr_status pdrq_vjp_step<float>(ctr_plan *, const float *, const float *, const float *, const float *,
+                                         const float *, const float *, const uint8_t *, double, double, double, double,
+                                         double, const ctr_params &, float *, float *, float *, float *, double *,
+                                         cudaStream_t);
+template ctr_status pdrq_vjp_step<double>(ctr_plan *, const double *, const double *, const double *, const double *,
+                                          const double *, const double *, const uint8_t *, double, double, double,
+                                          double, double, const ctr_params &, double *, double *, double *, double *,
+                                          double *, cudaStream_t);
+
 ctr_status launch_batch_tv(const SliceDesc *sd, const int *prefix, int ns, int blocks, cudaStream_t s)
 {
     if (blocks <= 0) return CTR_OK;

@@ -63,7 +63,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_plan_launch_count", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
-           "ctr_batch_launch_count", "tv_pd_solve_batched"]
+           "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step"]
 
 
 def load(path: str = LIB_PATH):
@@ -117,6 +117,12 @@ def load(path: str = LIB_PATH):
         lib.tv_pd_solve_batched.argtypes = [vp, P(vp), P(vp), P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
                                             P(Params), P(ctypes.c_double), P(ctypes.c_double), P(vp), P(Diag), vp]
         lib.tv_pd_solve_batched.restype = ctypes.c_int
+        lib.tv_pd_solve_state.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(Params),
+                                          P(State), P(Diag), vp]
+        lib.tv_pd_solve_state.restype = ctypes.c_int
+        lib.tv_pd_vjp_step.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, P(Params), P(State), P(State),
+                                       vp, vp, vp, vp, vp, vp]
+        lib.tv_pd_vjp_step.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
         lib.ctr_div.argtypes = [vp, vp, vp, vp]
         for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
@@ -298,6 +304,44 @@ class Plan:
                                   float(delta), int(iters), ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"),
                                   ctypes.byref(diag), _stream(stream)))
         return u_out, diag.as_dict()
+
+    def _state(self, st):
+        sino = (self.n_angles, self.n_bins)
+        return State(self._t(st["u"], (self.n, self.n), "u").value, self._t(st["Ru"], sino, "Ru").value,
+                     self._t(st["v1b"], sino, "v1b").value, self._t(st["v2b"], (2, self.n, self.n), "v2b").value)
+
+    def _mask(self, metal_mask):
+        import torch
+        if metal_mask is None:
+            return ctypes.c_void_p()
+        if metal_mask.dtype != torch.uint8 or not metal_mask.is_cuda or not metal_mask.is_contiguous() \
+                or tuple(metal_mask.shape) != (self.n_angles, self.n_bins):
+            raise ValueError("metal_mask must be a contiguous CUDA uint8 tensor of the sinogram's shape")
+        return ctypes.c_void_p(metal_mask.data_ptr())
+
+    def tv_pd_solve_state(self, f, metal_mask, alpha: float, delta: float, iters: int, params: Params, state,
+                          stream=None):
+        """Continue Alg. 4 from `state` (dict of tensors, updated in place)."""
+        st = self._state(state)
+        _check(load().tv_pd_solve_state(self._h, self._t(f, (self.n_angles, self.n_bins), "f"),
+                                        self._mask(metal_mask), float(alpha), float(delta), int(iters),
+                                        ctypes.byref(params), ctypes.byref(st), None, _stream(stream)))
+        return state
+
+    def tv_pd_vjp_step(self, f, metal_mask, alpha: float, delta: float, params: Params, s0, s1, bu, b1, b2, gf,
+                       galpha, stream=None):
+        """Reverse mode of the iteration s0 -> s1 (cotangents bu, b1, b2 updated in place;
+        gf and the float64 device scalar galpha accumulate)."""
+        import torch
+        if galpha.dtype != torch.float64 or not galpha.is_cuda:
+            raise TypeError("galpha must be a float64 CUDA tensor")
+        a, b = self._state(s0), self._state(s1)
+        sino = (self.n_angles, self.n_bins)
+        _check(load().tv_pd_vjp_step(self._h, self._t(f, sino, "f"), self._mask(metal_mask), float(alpha),
+                                     float(delta), ctypes.byref(params), ctypes.byref(a), ctypes.byref(b),
+                                     self._t(bu, (self.n, self.n), "bu"), self._t(b1, sino, "b1"),
+                                     self._t(b2, (2, self.n, self.n), "b2"), self._t(gf, sino, "gf"),
+                                     ctypes.c_void_p(galpha.data_ptr()), _stream(stream)))
 
     def new_state(self):
         import torch
