@@ -43,35 +43,18 @@ def peaks():
 
 
 def dist_init():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    if ws <= 1:
-        return 0, 1, 0
-    import torch
-    import torch.distributed as dist
-    rank = int(os.environ["RANK"])
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    backend = "nccl" if torch.cuda.is_available() else "gloo"
-    if backend == "nccl":
-        torch.cuda.set_device(local)
-    dist.init_process_group(backend=backend)
-    return rank, ws, local
+    from paper_1810_03275_gb300 import dist
+    return dist.init()
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1810_03275_gb300 import dist
+    dist.barrier()
 
 
 def max_over_ranks(x, ws):
-    if ws <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1810_03275_gb300 import dist
+    return dist.max_over_ranks(x)
 
 
 class ClockSampler:
