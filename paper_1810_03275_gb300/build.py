@@ -33,7 +33,10 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out_dir: str = None) -> str:
+    """Compile libctrecon.so (into out_dir, default _build/) and return its path."""
+    OUT = out_dir or globals()["OUT"]
+    LIB = os.path.join(OUT, "libctrecon.so")
     os.makedirs(OUT, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                     "-I" + os.path.join(ROOT, "include")] + list(extra_flags or [])

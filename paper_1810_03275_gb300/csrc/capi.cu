@@ -107,7 +107,8 @@ ctr_status build_tables(ctr_plan *p)
         geo[l] = AngleGeom{C, S, O};
         const long long aC = C < 0 ? -C : C, aS = S < 0 ? -S : S;
         if (aC == 0 && aS == 0) return fail(CTR_EINVAL, "degenerate geometry (h/ds too small)");
-        const long long w = ((31 * aC + 31 * aS) >> p->F) + 2;
+        // a backprojection tile spans (rows-1)|C| + 31|S| of P: its footprint in bins
+        const long long w = (((long long)(backproject_tile_rows() - 1) * aC + 31 * aS) >> p->F) + 2;
         if (w > wmax) wmax = w;
         AngleMarch am{};
         if (aC >= aS) {
@@ -121,9 +122,10 @@ ctr_status build_tables(ctr_plan *p)
             else { am.A = -S; am.Op = O + (long long)(n - 1) * S; am.flip = 1; }
             am.B = C;
         }
-        am.kA = (double)one / (double)am.A;
-        am.oA = (double)am.Op / (double)am.A;
-        am.bA = (double)am.B / (double)am.A;
+        am.kA = (float)((double)one / (double)am.A);
+        am.oA = (float)((double)am.Op / (double)am.A);
+        const double bA = (double)am.B / (double)am.A;
+        am.binv = fabs(bA) > 1e-9 ? (float)(1.0 / bA) : 0.f;
         mar[l] = am;
         const long long nc = (one + am.A - 1) / am.A;
         if (nc > ncand) ncand = (int)nc;

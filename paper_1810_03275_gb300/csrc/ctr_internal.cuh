@@ -71,9 +71,9 @@ struct AngleGeom {
 struct AngleMarch {
     long long A, B, Op;
     int layout, flip;
-    double kA;   // 2^F / A
-    double oA;   // Op / A
-    double bA;   // B / A
+    float kA;     // 2^F / A
+    float oA;     // Op / A
+    float binv;   // A / B (0 when |B/A| < 1e-9: rays parallel to the march axis)
 };
 
 // Kernel-side parameter blocks ------------------------------------------------
@@ -216,6 +216,10 @@ template <typename T> ctr_status configure_radon(const ctr_plan *p);   // smem a
 template <typename T> ctr_status configure_fft(const ctr_plan *p);
 ctr_status fft_radices(int n, std::vector<int> &out);
 size_t fft_smem_bytes(const ctr_plan *p, int which);
+
+int backproject_tile_rows();   // pixel rows of a backprojection tile (its width is 32)
+int fwd_grid_x(int M);         // forward-projector grid: bin chunks
+int fwd_grid_y(int N);         // forward-projector grid: angle groups
 
 // batched stages (one launch per stage over all slices of a batch)
 size_t bp_smem_bytes(int wstride);

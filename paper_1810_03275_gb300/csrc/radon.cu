@@ -14,6 +14,8 @@
 //    sum u and sum frac*u over the pixels of its interval, and the two neighbouring
 //    intervals' sums are combined with one warp shuffle:
 //        g_k = sum_{floor p = k} (1 - frac) u  +  sum_{floor p = k-1} frac u.
+//    A CTA takes 4 adjacent angles (one warp each) over 31 bins; the rows on which
+//    every lane of a warp stays inside the image run without bounds checks.
 //    No atomics; each output bin is written once.
 // Both kernels derive each weight from the same integer P (see ctr_internal.cuh),
 // so they are transposes of one matrix, bit for bit in the weights.
@@ -23,11 +25,20 @@ namespace ctr {
 
 namespace {
 
-constexpr int BP_TJ = 32;    // tile width along j (one warp)
-constexpr int BP_TY = 4;     // warps per CTA
-constexpr int BP_R = 8;      // pixels per thread (rows i0 + ty + 4 r)
+#ifndef CTR_BP_TY
+#define CTR_BP_TY 4
+#endif
+#ifndef CTR_BP_R
+#define CTR_BP_R 8
+#endif
+#ifndef CTR_BP_ACH
+#define CTR_BP_ACH 32
+#endif
+constexpr int BP_TJ = 32;          // tile width along j (one warp)
+constexpr int BP_TY = CTR_BP_TY;   // warps per CTA
+constexpr int BP_R = CTR_BP_R;     // pixels per thread (rows i0 + ty + BP_TY r)
 constexpr int BP_TI = BP_TY * BP_R;
-constexpr int BP_ACH = 32;   // angles per staged chunk
+constexpr int BP_ACH = CTR_BP_ACH; // angles per staged chunk
 
 template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
@@ -46,12 +57,22 @@ __device__ __forceinline__ int bin_of(long long P, int F)
     else return (int)(P >> F);
 }
 
+#ifndef CTR_FWD_UNROLL
+#define CTR_FWD_UNROLL 8
+#endif
+constexpr int FWD_UNROLL = CTR_FWD_UNROLL;   // rows per unrolled step of the ray march
+
 // 1 + frac(p) in [1, 2) from the low 32 bits of P (F = 32): the top 23 fraction
 // bits become the mantissa of a float, so the weight is exact and identical in
 // both projectors.
 __device__ __forceinline__ float one_plus_frac32(long long P)
 {
     return __uint_as_float((((unsigned)(unsigned long long)P) >> 9) | 0x3F800000u);
+}
+
+__device__ __forceinline__ float one_plus_frac32u(unsigned lo)
+{
+    return __uint_as_float((lo >> 9) | 0x3F800000u);
 }
 
 __device__ __forceinline__ float2 make_stage(float g0, float g1)
@@ -291,126 +312,169 @@ __device__ __forceinline__ void march_row(const S *__restrict__ rowp, int dq, in
     }
 }
 
-// One CTA of the forward projector: angle l, bins (bx * 4 + warp) * 31 + [0, 31).
+constexpr int FWD_AW = 4;                     // adjacent angles per CTA, one warp each
+constexpr int FWD_THREADS = 32 * FWD_AW;
+
+// FP32 ray march over `rows` rows (F = 32, 2^31 <= A <= 2^32).  State: r = P(q_a) - k 2^32
+// in [0, A) (the fixed-point fraction of the interval's first pixel q_a), off = element
+// offset of pixel (m, q_a), and q_a itself where CHECK.  The second pixel q_a + 1 lies in
+// the interval iff r + A < 2^32, i.e. r < lim.  Next row: P += B; B > 0 (BPOS) steps
+// q_a back when r >= thr = A - B, B <= 0 steps it forward when r < thr = |B|.
+// CHECK = false: every lane's q_a and q_a + 1 are inside [0, n) on these rows.
+template <int DQ, bool BPOS, bool CHECK, typename S>
+__device__ __forceinline__ void march32(const S *__restrict__ base, int n, int rows, unsigned &r, int &q, int &off,
+                                        unsigned A32, unsigned lim, unsigned B32, unsigned thr, float &Su, float &Sf)
+{
+#pragma unroll FWD_UNROLL
+    for (int rr = 0; rr < rows; ++rr) {
+        float v1, v2;
+        if constexpr (CHECK) {
+            v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
+            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(base + off + DQ) : 0.f;
+        } else {
+            v1 = ldv(base + off);
+            v2 = r < lim ? ldv(base + off + DQ) : 0.f;
+        }
+        Su += v1 + v2;
+        Sf = fmaf(one_plus_frac32u(r), v1, Sf);
+        Sf = fmaf(one_plus_frac32u(r + A32), v2, Sf);
+        if constexpr (BPOS) {
+            const bool s = r >= thr;
+            r += s ? B32 - A32 : B32;
+            off += s ? n - DQ : n;
+            if constexpr (CHECK) q -= s ? 1 : 0;
+        } else {
+            const bool s = r < thr;
+            r += s ? A32 - thr : 0u - thr;
+            off += s ? n + DQ : n;
+            if constexpr (CHECK) q += s ? 1 : 0;
+        }
+    }
+}
+
+// The FP32 march of one lane over rows [mlo, mhi] of the warp, without bounds checks on
+// the warp's interior rows [ilo, ihi] (mlo <= ilo, ihi <= mhi; ilo > ihi: none).
+template <int DQ, bool BPOS, typename S>
+__device__ __forceinline__ void march32_rows(const S *__restrict__ base, int n, long long K, const AngleMarch &am,
+                                             int mlo, int mhi, int ilo, int ihi, float &Su, float &Sf)
+{
+    const long long A = am.A, B = am.B;
+    const long long qa = ceil_div_ll(K - (long long)mlo * B - am.Op, A);
+    unsigned r = (unsigned)(qa * A + (long long)mlo * B + am.Op - K);
+    int q = (int)qa;
+    int off = mlo * n + DQ * q;
+    const unsigned A32 = (unsigned)A;             // A = 2^32 wraps to 0 (then B = 0)
+    const unsigned lim = (unsigned)((1ll << 32) - A);
+    const unsigned B32 = (unsigned)B;
+    const unsigned thr = BPOS ? (unsigned)(A - B) : (unsigned)(-B);
+    if (ilo > ihi) {
+        march32<DQ, BPOS, true>(base, n, mhi - mlo + 1, r, q, off, A32, lim, B32, thr, Su, Sf);
+        return;
+    }
+    march32<DQ, BPOS, true>(base, n, ilo - mlo, r, q, off, A32, lim, B32, thr, Su, Sf);
+    march32<DQ, BPOS, false>(base, n, ihi - ilo + 1, r, q, off, A32, lim, B32, thr, Su, Sf);
+    q = DQ * (off - (ihi + 1) * n);               // off = m n + DQ q
+    march32<DQ, BPOS, true>(base, n, mhi - ihi, r, q, off, A32, lim, B32, thr, Su, Sf);
+}
+
+// Sum u and sum frac u (FP64) or sum (1 + frac) u (generic FP32) over the pixels of rows
+// m0 .. m0 + rows - 1 whose detector coordinate lies in the lane's interval [k, k+1).
 template <typename T, typename S, int NC, bool EXACT1>
-__device__ __forceinline__ void fwd_body(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
-                                         const AngleMarch *__restrict__ march, const ForwardEpi<T> &epi, int bx, int l)
+__device__ __forceinline__ void fwd_march(const S *__restrict__ base, int dq, int n, int k, int F,
+                                          const AngleMarch &am, int m0, int rows, T &Su, T &Sf)
+{
+    const double inv2F = ldexp(1.0, -F);
+    const long long K = (long long)k << F;
+    const long long A = am.A, B = am.B;
+    long long qa = ceil_div_ll(K - (long long)m0 * B - am.Op, A);
+    long long Pa = qa * A + (long long)m0 * B + am.Op;   // in [K, K + A)
+    int q = (int)qa;
+    const S *rowp = base + (size_t)m0 * n;
+    // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
+    if (B >= 0) {
+        const long long KA = K + A;
+#pragma unroll 2
+        for (int r = 0; r < rows; ++r) {
+            march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+            Pa += B;
+            if (Pa >= KA) { Pa -= A; --q; }
+            rowp += n;
+        }
+    } else {
+#pragma unroll 2
+        for (int r = 0; r < rows; ++r) {
+            march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
+            Pa += B;
+            if (Pa < K) { Pa += A; ++q; }
+            rowp += n;
+        }
+    }
+}
+
+// Rows m of [0, n) on which q*(m) = Q0 - m b lies in [qlo, qhi] (FP32; the callers'
+// margins of half a pixel or more absorb its rounding).  OUTER rounds the range out
+// (rows that may touch), otherwise in (rows that surely lie inside).  lo > hi: none.
+template <bool OUTER>
+__device__ __forceinline__ void rows_in(float Q0, float binv, float qlo, float qhi, int n, int &lo, int &hi)
+{
+    lo = n;
+    hi = -1;
+    if (qlo > qhi) return;
+    if (binv != 0.f) {
+        const float m1 = (Q0 - qhi) * binv, m2 = (Q0 - qlo) * binv;
+        float a0 = fminf(m1, m2), a1 = fmaxf(m1, m2);
+        a0 = fmaxf(0.f, OUTER ? floorf(a0) : ceilf(a0));
+        a1 = fminf((float)(n - 1), OUTER ? ceilf(a1) : floorf(a1));
+        if (a0 <= a1) {
+            lo = (int)a0;
+            hi = (int)a1;
+        }
+    } else if (Q0 > qlo && Q0 < qhi) {            // rays parallel to the march axis
+        lo = 0;
+        hi = n - 1;
+    }
+}
+
+// One CTA of the forward projector: warp w takes angle by*FWD_AW + w and bins
+// bx*31 + [0, 31).  The angles are adjacent, so their rays nearly coincide and the
+// image rows they read are shared in L1.
+template <typename T, typename S, int NC, bool EXACT1>
+__device__ __forceinline__ void fwd_body(const S *__restrict__ u, const S *__restrict__ uT, int n, int N, int M, int F,
+                                         const AngleMarch *__restrict__ march, const ForwardEpi<T> &epi, int bx, int by)
 {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int kb = (bx * 4 + warp) * 31;              // first output bin of this warp
-    if (kb >= M) return;                              // warp-uniform
-    const AngleMarch am = march[l];
+    const int l = by * FWD_AW + warp;
+    const int kb = bx * 31;                           // first output bin of this warp
     const int k = kb + lane - 1;                      // this lane's interval [k, k+1)
-    const double inv2F = ldexp(1.0, -F);
+    if (l >= N || kb >= M) return;                    // warp-uniform
+    const AngleMarch am = march[l];
     // pixel (m, q) of the march is at base[m*n + dq*q]
-    const int dq = am.flip ? -1 : 1;
     const S *__restrict__ base = (am.layout ? u : uT) + (am.flip ? (n - 1) : 0);
-
-    // Rows m where the lane's pixel run may be inside [0, n): q*(m) = Q0 - m b.
-    int mlo = n, mhi = -1;
-    {
-        const double Q0 = (double)k * am.kA - am.oA;
-        const double b = am.bA;
-        const double lo_q = -(double)NC - 1.0, hi_q = (double)n + 1.0;
-        if (fabs(b) > 1e-9) {
-            const double m1 = (Q0 - hi_q) / b, m2 = (Q0 - lo_q) / b;
-            const double a0 = fmax(0.0, floor(fmin(m1, m2)));
-            const double a1 = fmin((double)(n - 1), ceil(fmax(m1, m2)));
-            if (a0 <= a1) {
-                mlo = (int)a0;
-                mhi = (int)a1;
-            }
-        } else if (Q0 > lo_q && Q0 < hi_q) {
-            mlo = 0;
-            mhi = n - 1;
-        }
-    }
+    // q*(m) = Q0 - m b: the real pick coordinate where P(q, m) = k 2^F
+    const float Q0 = (float)k * am.kA - am.oA;
+    int mlo, mhi;                                     // rows where the lane's pixel run may be inside [0, n)
+    rows_in<true>(Q0, am.binv, -(float)NC - 1.f, (float)n + 1.f, n, mlo, mhi);
     const int mlo_w = __reduce_min_sync(0xffffffffu, mlo);
     const int mhi_w = __reduce_max_sync(0xffffffffu, mhi);
-
     T Su = T(0), Sf = T(0);
-    if constexpr (sizeof(T) == 4 && EXACT1 && NC == 2) {
-        if (mlo_w <= mhi_w) {
-            // FP32 march with 2^32 > A >= 2^31.5: r = P(q_a) - k 2^32 in [0, A) fits in 32
-            // bits and is the fixed-point fraction of the interval's first pixel; the
-            // second pixel (q_a + 1) lies in the interval iff r + A < 2^32.
+    if (mlo_w <= mhi_w) {
+        if constexpr (sizeof(T) == 4 && EXACT1 && NC == 2) {
+            // interior rows: q_a in [1, n - 3] for every lane, no bounds checks needed
+            int ilo, ihi;
+            rows_in<false>(Q0, am.binv, 0.5f, (float)n - 3.5f, n, ilo, ihi);
+            const int ilo_w = max(__reduce_max_sync(0xffffffffu, ilo), mlo_w);
+            const int ihi_w = min(__reduce_min_sync(0xffffffffu, ihi), mhi_w);
             const long long K = (long long)k << 32;
-            const long long A = am.A, B = am.B;
-            const long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
-            unsigned r = (unsigned)(qa * A + (long long)mlo_w * B + am.Op - K);
-            int q = (int)qa;
-            int off = mlo_w * n + dq * q;                 // element offset of pixel (m, q)
-            const unsigned A32 = (unsigned)A;             // A = 2^32 wraps to 0 (then B = 0)
-            const unsigned lim = (unsigned)((1ll << 32) - A);
-            const int rows = mhi_w - mlo_w + 1;
-            const S *__restrict__ b1 = base + dq;         // pixel (m, q + 1)
-            if (B == 0) {
-#pragma unroll 2
-                for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
-                    Su += v1 + v2;
-                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
-                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
-                    off += n;
-                }
-            } else if (B > 0) {
-                const unsigned B32 = (unsigned)B, thr = (unsigned)(A - B);   // step back when r >= A - B
-#pragma unroll 2
-                for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
-                    Su += v1 + v2;
-                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
-                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
-                    const bool back = r >= thr;
-                    r += back ? B32 - A32 : B32;
-                    q -= back ? 1 : 0;
-                    off += back ? n - dq : n;
-                }
+            if (am.B > 0) {                           // B = 0 takes the B < 0 march (thr = 0: never steps)
+                if (am.flip) march32_rows<-1, true>(base, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                else march32_rows<1, true>(base, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
             } else {
-                const unsigned nb = (unsigned)(-B);       // step forward when r < |B|
-#pragma unroll 2
-                for (int rr = 0; rr < rows; ++rr) {
-                    const float v1 = ((unsigned)q < (unsigned)n) ? ldv(base + off) : 0.f;
-                    const float v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ldv(b1 + off) : 0.f;
-                    Su += v1 + v2;
-                    Sf = fmaf(__uint_as_float((r >> 9) | 0x3F800000u), v1, Sf);
-                    Sf = fmaf(__uint_as_float(((r + A32) >> 9) | 0x3F800000u), v2, Sf);
-                    const bool fwd = r < nb;
-                    r += fwd ? A32 - nb : 0u - nb;
-                    q += fwd ? 1 : 0;
-                    off += fwd ? n + dq : n;
-                }
-            }
-        }
-    } else if (mlo_w <= mhi_w) {
-        const long long K = (long long)k << F;
-        const long long A = am.A, B = am.B;
-        long long qa = ceil_div_ll(K - (long long)mlo_w * B - am.Op, A);
-        long long Pa = qa * A + (long long)mlo_w * B + am.Op;   // in [K, K + A)
-        int q = (int)qa;
-        const S *rowp = base + (size_t)mlo_w * n;
-        const int rows = mhi_w - mlo_w + 1;
-        // next row: restore P(q_a) in [K, K + A) (|B| <= A: at most one step)
-        if (B >= 0) {
-            const long long KA = K + A;
-#pragma unroll 2
-            for (int r = 0; r < rows; ++r) {
-                march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
-                Pa += B;
-                if (Pa >= KA) { Pa -= A; --q; }
-                rowp += n;
+                if (am.flip) march32_rows<-1, false>(base, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                else march32_rows<1, false>(base, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
             }
         } else {
-#pragma unroll 2
-            for (int r = 0; r < rows; ++r) {
-                march_row<T, S, NC, EXACT1>(rowp, dq, n, k, F, inv2F, Pa, q, A, Su, Sf);
-                Pa += B;
-                if (Pa < K) { Pa += A; ++q; }
-                rowp += n;
-            }
+            fwd_march<T, S, NC, EXACT1>(base, am.flip ? -1 : 1, n, k, F, am, mlo_w, mhi_w - mlo_w + 1, Su, Sf);
         }
     }
     T Bk, Ak;
@@ -421,11 +485,11 @@ __device__ __forceinline__ void fwd_body(const S *__restrict__ u, const S *__res
 }
 
 template <typename T, typename S, int NC, bool EXACT1>
-__global__ void __launch_bounds__(128)
-k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int M, int F,
+__global__ void __launch_bounds__(FWD_THREADS)
+k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int N, int M, int F,
           const AngleMarch *__restrict__ march, ForwardEpi<T> epi)
 {
-    fwd_body<T, S, NC, EXACT1>(u, uT, n, M, F, march, epi, blockIdx.x, blockIdx.y);
+    fwd_body<T, S, NC, EXACT1>(u, uT, n, N, M, F, march, epi, blockIdx.x, blockIdx.y);
 }
 
 // Batched stages: block b of the launch belongs to the slice s with
@@ -461,13 +525,13 @@ k_bp_reduce_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ pref
     bp_reduce_body<float>(d.bp_part, d.bp_groups, d.n, d.bpe, blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(FWD_THREADS)
 k_forward_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
 {
     const int s = find_slice(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
     const int local = blockIdx.x - prefix[s];
-    fwd_body<float, float, 2, true>(d.u, d.uT, d.n, d.M, 32, d.march, d.fwe, local % d.fwd_chunks,
+    fwd_body<float, float, 2, true>(d.u, d.uT, d.n, d.N, d.M, 32, d.march, d.fwe, local % d.fwd_chunks,
                                     local / d.fwd_chunks);
 }
 
@@ -497,7 +561,7 @@ size_t bp_smem(const ctr_plan *p)
 template <typename T, typename S, int NC, bool EXACT1>
 void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
-    k_forward<T, S, NC, EXACT1><<<grid, 128, 0, s>>>(u, uT, p->n, p->M, p->F, p->d_march, epi);
+    k_forward<T, S, NC, EXACT1><<<grid, FWD_THREADS, 0, s>>>(u, uT, p->n, p->N, p->M, p->F, p->d_march, epi);
 }
 
 template <typename T, typename S>
@@ -525,9 +589,9 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
 template <typename T, typename S>
 ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
-    dim3 grid((p->M + 4 * 31 - 1) / (4 * 31), p->N);
     const bool exact1 = p->h <= p->ds;
     p->launches++;
+    dim3 grid(fwd_grid_x(p->M), fwd_grid_y(p->N));
     switch (p->ncand * 2 + (exact1 ? 1 : 0)) {
     case 2: launch_fwd_cfg<T, S, 1, false>(p, grid, u, uT, epi, s); break;
     case 3: launch_fwd_cfg<T, S, 1, true>(p, grid, u, uT, epi, s); break;
@@ -591,6 +655,9 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
 
 int backproject_tile_rows() { return BP_TI; }
 
+int fwd_grid_x(int M) { return (M + 30) / 31; }
+int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
+
 size_t bp_smem_bytes(int wstride)
 {
     return sizeof(float2) * BP_ACH * wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
@@ -615,7 +682,7 @@ ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix,
     switch (stage) {
     case BS_BP: k_backproject_batch<<<blocks, 32 * BP_TY, smem, s>>>(sd, prefix, ns); break;
     case BS_BP_REDUCE: k_bp_reduce_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns); break;
-    case BS_FWD: k_forward_batch<<<blocks, 128, 0, s>>>(sd, prefix, ns); break;
+    case BS_FWD: k_forward_batch<<<blocks, FWD_THREADS, 0, s>>>(sd, prefix, ns); break;
     default: return fail(CTR_EINVAL, "not a projector stage");
     }
     CTR_CHECK_LAUNCH("batched projector stage");

@@ -910,7 +910,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.bp_groups = p->bp_groups;
         d.per_group = (p->N + p->bp_groups - 1) / p->bp_groups;
         bp_tiles(p->n, d.bp_tiles_x, d.bp_tiles_y);
-        d.fwd_chunks = (p->M + 4 * 31 - 1) / (4 * 31);
+        d.fwd_chunks = fwd_grid_x(p->M);
         d.rpc = fft_rows_per_cta(p->n);
         d.cw = fft_cols_per_cta(p->n, 4);
         d.geom = p->d_geom;
@@ -1039,7 +1039,7 @@ ctr_status batch_prepare(ctr_batch *b)
         cnt[BS_FFT_ROWS] = (p->n + rpc - 1) / rpc;
         cnt[BS_FFT_COLS] = (p->n + cw - 1) / cw;
         cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
-        cnt[BS_FWD] = ((p->M + 4 * 31 - 1) / (4 * 31)) * p->N;
+        cnt[BS_FWD] = fwd_grid_x(p->M) * fwd_grid_y(p->N);
         cnt[BS_TV] = grid_for(nn, 256, 1024);
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
         const size_t smb = bp_smem_bytes(p->wstride);

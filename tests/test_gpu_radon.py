@@ -18,6 +18,9 @@ GEOMS = [
     (33, 17, 1, 1.0, 1.0, "uniform"),           # single bin
     (1, 5, 3, 1.0, 1.0, "uniform"),             # single pixel
     (130, 7, 60, 1.0, 1.0, "uniform"),          # detector narrower than the image
+    (60, 24, 90, 0.9, 1.0, "uniform"),          # two pixels per interval, four per interval pair
+    (70, 36, 100, 0.95, 1.0, "random"),         # at most three pixels per interval pair
+    (200, 45, 283, 1.0, 1.0, "uniform"),        # several 63-bin chunks with a ragged tail
 ]
 
 
