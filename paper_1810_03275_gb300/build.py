@@ -35,16 +35,16 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None, out_dir: str = None) -> str:
     """Compile libctrecon.so (into out_dir, default _build/) and return its path."""
-    OUT = out_dir or globals()["OUT"]
-    LIB = os.path.join(OUT, "libctrecon.so")
-    os.makedirs(OUT, exist_ok=True)
+    out = out_dir or OUT
+    lib = os.path.join(out, "libctrecon.so")
+    os.makedirs(out, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                     "-I" + os.path.join(ROOT, "include")] + list(extra_flags or [])
     objs = []
     jobs = []
     for u in UNITS:
         src = os.path.join(SRC, u)
-        obj = os.path.join(OUT, u.replace(".cu", ".o"))
+        obj = os.path.join(out, u.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + HEADERS):
             jobs.append([nvcc()] + flags + ["-c", src, "-o", obj])
@@ -61,11 +61,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out_dir:
     if jobs:
         with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <utility>
 
 #include "ctr_internal.cuh"
 
@@ -88,6 +90,73 @@ long long floor_div2(__int128 v)
     return (long long)q;
 }
 
+// Groups the angles of an FP32 plan into the forward projector's symmetric jobs
+// (OrbitJob): every angle's (C, S) must be one of (a, b), (-a, b), (b, a), (-b, a) of
+// its canonical pair a = max(|C|, |S|), b = min(|C|, |S|) (true for angles in
+// [0, pi)); angles with equal canonical pairs share a job, one per channel.  The
+// path is taken when the jobs hold two angles or more on average.
+ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
+{
+    const int n = p->n, N = p->N, M = p->M;
+    std::vector<OrbitJob> jobs;
+    std::map<std::pair<long long, long long>, std::vector<int>> by_pair;   // canonical pair -> jobs
+    for (int l = 0; l < N; ++l) {
+        const long long C = geo[l].C, S = geo[l].S;
+        const long long aC = C < 0 ? -C : C, aS = S < 0 ? -S : S;
+        const long long a = aC >= aS ? aC : aS, b = aC >= aS ? aS : aC;
+        const long long img[4][2] = {{a, b}, {-a, b}, {b, a}, {-b, a}};
+        bool placed = false, member = false;
+        std::vector<int> &js = by_pair[{a, b}];
+        for (int v = 0; v < 4 && !placed; ++v) {
+            if (img[v][0] != C || img[v][1] != S) continue;
+            member = true;
+            for (int j : js)
+                if (jobs[j].l[v] < 0) {
+                    jobs[j].l[v] = l;
+                    placed = true;
+                    break;
+                }
+        }
+        if (!member) return CTR_OK;                 // outside the symmetric set: per-angle path
+        if (!placed) {
+            OrbitJob jb{};
+            for (int v = 0; v < 4; ++v) jb.l[v] = -1;
+            AngleMarch &am = jb.am;
+            am.layout = 0;
+            am.flip = 0;
+            am.A = a;
+            am.B = b;
+            am.Op = floor_div2(((__int128)(M - 1) << 32) - (__int128)(n - 1) * ((__int128)a + (__int128)b));
+            am.kA = (float)(4294967296.0 / (double)a);
+            am.oA = (float)((double)am.Op / (double)a);
+            const double bA = (double)b / (double)a;
+            am.binv = bA > 1e-9 ? (float)(1.0 / bA) : 0.f;
+            for (int v = 0; v < 4; ++v)
+                if (img[v][0] == C && img[v][1] == S) { jb.l[v] = l; break; }
+            js.push_back((int)jobs.size());
+            jobs.push_back(jb);
+        }
+    }
+    if (2 * jobs.size() > (size_t)N) return CTR_OK;
+    ctr_status st;
+    void *tmp = nullptr;
+    if ((st = alloc(p, &tmp, sizeof(OrbitJob) * jobs.size())) != CTR_OK) return st;
+    p->d_jobs = (OrbitJob *)tmp;
+    if ((st = alloc(p, &p->ubar, sizeof(float4) * (size_t)n * n)) != CTR_OK) return st;
+    // the symmetric backprojection: job groups so that tiles x groups fills the GPU
+    // (~8 CTAs of 4 warps per SM on 152 SMs), at least 8 jobs per group
+    const int tiles = ((n + 31) / 32) * ((n + 31) / 32);
+    int G = (1216 + tiles - 1) / tiles;
+    if (G > MAX_BP_GROUPS) G = MAX_BP_GROUPS;
+    const int gmax = (int)jobs.size() / 8 > 1 ? (int)jobs.size() / 8 : 1;
+    p->obp_groups = G > gmax ? gmax : (G < 1 ? 1 : G);
+    if ((st = alloc(p, &p->obp_part, sizeof(float) * 4 * (size_t)p->obp_groups * n * n)) != CTR_OK) return st;
+    CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
+    p->n_jobs = (int)jobs.size();
+    p->orbit = true;
+    return CTR_OK;
+}
+
 ctr_status build_tables(ctr_plan *p)
 {
     const int n = p->n, N = p->N, M = p->M;
@@ -135,6 +204,7 @@ ctr_status build_tables(ctr_plan *p)
     p->wstride = (int)wmax;
     CTR_CUDA(cudaMemcpy(p->d_geom, geo.data(), sizeof(AngleGeom) * N, cudaMemcpyHostToDevice));
     CTR_CUDA(cudaMemcpy(p->d_march, mar.data(), sizeof(AngleMarch) * N, cudaMemcpyHostToDevice));
+    if (p->F == 32 && !p->bf16 && p->h <= p->ds && ncand == 2) return build_orbit_jobs(p, geo);
     return CTR_OK;
 }
 
@@ -366,13 +436,13 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
         // the GPU (~8 CTAs of 4 warps per SM on 152 SMs); partial images are summed
         const int tiles = ((p->n + 31) / 32) * ((p->n + 31) / 32);
         int G = (1216 + tiles - 1) / tiles;
-        if (G > 8) G = 8;
+        if (G > MAX_BP_GROUPS) G = MAX_BP_GROUPS;
         const int maxg = p->N / 32 > 1 ? p->N / 32 : 1;
         if (G > maxg) G = maxg;
         p->bp_groups = G < 1 ? 1 : G;
-        // room for up to 8 groups at n <= 1024 so a tuner can change the split later
+        // room for up to MAX_BP_GROUPS groups at n <= 1024 so a tuner can change the split later
         int cap = p->bp_groups;
-        if (p->n <= 1024) cap = maxg < 8 ? (maxg > cap ? maxg : cap) : 8;
+        if (p->n <= 1024) cap = maxg < MAX_BP_GROUPS ? (maxg > cap ? maxg : cap) : MAX_BP_GROUPS;
         p->bp_cap = cap;
         if (cap > 1) ALLOC(p->bp_part, es * nn * cap);
     }

@@ -12,6 +12,8 @@
 
 namespace ctr {
 
+constexpr int MAX_BP_GROUPS = 8;   // angle groups of the backprojection (partial images)
+
 // ---------------------------------------------------------------------------
 // Error reporting (thread-local message, returned through ctr_last_error()).
 // ---------------------------------------------------------------------------
@@ -76,6 +78,17 @@ struct AngleMarch {
     float binv;   // A / B (0 when |B/A| < 1e-9: rays parallel to the march axis)
 };
 
+// A job of the forward projector's symmetric path.  The fixed-point geometry is
+// exactly invariant under the symmetries of the pixel grid: an angle whose (C, S) is
+// (a, b), (-a, b), (b, a) or (-b, a) has P_l(i, j) = P_c(T(i, j)) for the canonical
+// pair (a, b), a >= b >= 0, with T = id, (n-1-i, j), (j, i), (j, n-1-i).  One ray
+// march of (a, b) over the "orbit image" (channel v at march pixel (q, m) holds
+// u(T_v^{-1}(q, m))) therefore serves up to four angles.
+struct OrbitJob {
+    AngleMarch am;                // canonical march: layout 0, flip 0, A = a, B = b
+    alignas(16) int l[4];         // angle of each channel (-1: none)
+};
+
 // Kernel-side parameter blocks ------------------------------------------------
 template <typename T>
 struct BackprojEpi {
@@ -87,6 +100,48 @@ struct BackprojEpi {
     T outscale;        // final multiplier
     T inv_h;
 };
+
+// div_h p at pixel (i, j): (d1 + d2)/h, backward differences with Dirichlet ends
+// (Sec. 3.1); px holds the x plane, px + n*n the y plane.
+template <typename T>
+__device__ __forceinline__ T div_at(const T *__restrict__ px, int n, int i, int j, T inv_h)
+{
+    if (n < 2) return T(0);
+    const T *py = px + (size_t)n * n;
+    T d1, d2;
+    if (i == 0) d1 = px[j];
+    else if (i == n - 1) d1 = -px[(size_t)(n - 2) * n + j];
+    else d1 = px[(size_t)i * n + j] - px[(size_t)(i - 1) * n + j];
+    const size_t row = (size_t)i * n;
+    if (j == 0) d2 = py[row];
+    else if (j == n - 1) d2 = -py[row + n - 2];
+    else d2 = py[row + j] - py[row + j - 1];
+    return (d1 + d2) * inv_h;
+}
+
+// The backprojection epilogue at pixel (i, j) for the sum acc:
+// outscale (scale acc - divtau div p).
+template <typename T>
+__device__ __forceinline__ T bp_epilogue_value(const BackprojEpi<T> &epi, int n, int i, int j, T acc)
+{
+    T v = acc * epi.scale;
+    if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
+    return v * epi.outscale;
+}
+
+// The fold of the symmetric backprojection (OrbitJob path): its partial planes
+// [group][v][row][col] summed at image pixel (i, j) in a fixed order.
+__device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int groups, int n, int i, int j)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t e = (size_t)i * n + j, em = (size_t)(n - 1 - i) * n + j;
+    float s = 0.f;
+    for (int z = 0; z < groups; ++z) {
+        const float *pz = part + (size_t)z * 4 * nn;
+        s += pz[e] + pz[nn + em] + pz[2 * nn + e] + pz[3 * nn + em];
+    }
+    return s;
+}
 
 template <typename T>
 struct ForwardEpi {
@@ -157,6 +212,12 @@ struct ctr_plan {
 
     ctr::AngleGeom *d_geom = nullptr;
     ctr::AngleMarch *d_march = nullptr;
+    bool orbit = false;                  // FP32 forward projector on the symmetric path
+    int n_jobs = 0;
+    ctr::OrbitJob *d_jobs = nullptr;
+    void *ubar = nullptr;                // n*n float4 orbit image
+    int obp_groups = 1;                  // job groups of the symmetric backprojection
+    void *obp_part = nullptr;            // obp_groups * 4 * n*n partial planes
     void *d_twiddle = nullptr;  // n complex exp(-2 pi i t/n)
 
     // workspace, element type T (sizeof(T) = esize)
@@ -188,11 +249,15 @@ struct ctr_plan {
 namespace ctr {
 
 // Launch helpers implemented in the .cu files ------------------------------------
+// defer_reduce with bp_groups > 1 (or on the symmetric path): only the partial
+// images are written (bp_part, obp_part); the caller sums them (launch_circulant's
+// bp_in).  bp_deferred(p) tells whether defer_reduce takes effect.
 template <typename T>
-ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s);
+ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s,
+                              bool defer_reduce = false);
 // the same with the sinogram operand stored in bfloat16 (FP32 accumulation)
 ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, const BackprojEpi<float> &epi,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool defer_reduce = false);
 // the forward projector with the image operands stored in bfloat16 (FP32 accumulation)
 ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT,
                                const ForwardEpi<float> &epi, cudaStream_t s);
@@ -204,11 +269,14 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
 // FFT-based circulant operators: out = F^{-1}(sym * F(in)) (sym includes 1/n^2).
 // mode 0: out = result; mode 1: out += result (accumulate, solver update).
 // outT (optional) receives the transpose of the final out; dout (optional) the
-// result before accumulation.
+// result before accumulation.  bp_in (optional): the input is the backprojection
+// left as angle-group partial images, or as the symmetric path's partial planes
+// (launch_backproject with defer_reduce), summed and passed through *bp_in inside the
+// first FFT pass.
 template <typename T>
 ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf, const T *sym, T *out,
                             int mode, T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh = nullptr,
-                            __nv_bfloat16 *outTh = nullptr);
+                            __nv_bfloat16 *outTh = nullptr, const BackprojEpi<T> *bp_in = nullptr);
 template <typename T>
 ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s);
 
@@ -218,6 +286,7 @@ ctr_status fft_radices(int n, std::vector<int> &out);
 size_t fft_smem_bytes(const ctr_plan *p, int which);
 
 int backproject_tile_rows();   // pixel rows of a backprojection tile (its width is 32)
+template <typename T> bool bp_deferred(const ctr_plan *p);
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
 int fwd_grid_y(int N);         // forward-projector grid: angle groups
 

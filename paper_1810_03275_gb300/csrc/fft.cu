@@ -19,6 +19,7 @@ ctr_status fft_radices(int n, std::vector<int> &out)
     out.clear();
     if (n < 1) return fail(CTR_EINVAL, "FFT length must be >= 1");
     int m = n;
+    while (m % 8 == 0) { out.push_back(8); m /= 8; }
     while (m % 4 == 0) { out.push_back(4); m /= 4; }
     while (m % 2 == 0) { out.push_back(2); m /= 2; }
     while (m % 3 == 0) { out.push_back(3); m /= 3; }
@@ -28,7 +29,13 @@ ctr_status fft_radices(int n, std::vector<int> &out)
 
 namespace {
 
-constexpr int FFT_THREADS = 256;
+#ifndef CTR_FFT_THREADS
+#define CTR_FFT_THREADS 128
+#endif
+#ifndef CTR_FFT_POINTS
+#define CTR_FFT_POINTS 1024
+#endif
+constexpr int FFT_THREADS = CTR_FFT_THREADS;
 constexpr int MAX_PASSES = 16;
 
 
@@ -46,6 +53,27 @@ template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { a.x += b.x; a.y += b.y; return a; }
 template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { a.x -= b.x; a.y -= b.y; return a; }
 
+// x / d for 0 <= x, x d < 2^32 through a multiply-high: m = floor(2^32 / d) + 1
+// (d = 1 handled apart).  Exact under that bound (x, d <= 2^14 here).
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int fast_div(int x, int d, unsigned m) { return d <= 1 ? x : (int)__umulhi((unsigned)x, m); }
+
+// 4-point DFT with sign s (y_m = sum_k x_k e^{s 2 pi i k m / 4}), in place.
+template <typename T, typename T2>
+__device__ __forceinline__ void dft4(T2 &x0, T2 &x1, T2 &x2, T2 &x3, T s)
+{
+    const T2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
+    const T2 t2 = cadd(x1, x3);
+    const T2 d = csub(x1, x3);
+    T2 t3;                                           // d * (s i)
+    t3.x = -s * d.y;
+    t3.y = s * d.x;
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
 // One Stockham pass of radix R over `cnt` transforms of length n stored with
 // leading dimension ld.  Ns = product of the radices already applied.
 // sign = -1 forward, +1 inverse.  tw[t] = exp(-2 pi i t / n).
@@ -57,39 +85,58 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::type *src, t
     using T2 = typename C2<T>::type;
     const int nr = n / R;
     const int stride_tw = n / (Ns * R);
+    const unsigned m_nr = div_magic(nr), m_ns = div_magic(Ns);
+    const T s = (T)sign;
     for (int b = threadIdx.x; b < cnt * nr; b += blockDim.x) {
-        const int t = b / nr;
+        const int t = cnt == 1 ? 0 : fast_div(b, nr, m_nr);
         const int j = b - t * nr;
+        const int jq = fast_div(j, Ns, m_ns);
+        const int k = j - jq * Ns;
         const T2 *in = src + (size_t)t * ld;
         T2 *out = dst + (size_t)t * ld;
-        const int k = j % Ns;
         T2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = in[j + r * nr];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                T2 w = tw[(r * k * stride_tw) % n];
+                T2 w = __ldg(tw + r * k * stride_tw);   // r k stride_tw < R Ns n/(Ns R) = n
                 if (sign > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
         }
-        const T s = (T)sign;
         if (R == 2) {
             const T2 a = v[0], c = v[1];
             v[0] = cadd(a, c);
             v[1] = csub(a, c);
         } else if (R == 4) {
-            const T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-            const T2 t2 = cadd(v[1], v[3]);
-            const T2 d = csub(v[1], v[3]);
-            T2 t3;                                  // d * (s i)
-            t3.x = -s * d.y;
-            t3.y = s * d.x;
-            v[0] = cadd(t0, t2);
-            v[2] = csub(t0, t2);
-            v[1] = cadd(t1, t3);
-            v[3] = csub(t1, t3);
+            dft4<T, T2>(v[0], v[1], v[2], v[3], s);
+        } else if (R == 8) {
+            // X_{2m} = DFT4(v_k + v_{k+4})_m, X_{2m+1} = DFT4((v_k - v_{k+4}) W^k)_m, W = e^{s i pi/4}
+            const T h = (T)0.70710678118654752440;
+            T2 a[4], c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = cadd(v[q], v[q + 4]);
+                c[q] = csub(v[q], v[q + 4]);
+            }
+            T2 e;
+            e.x = h * (c[1].x - s * c[1].y);             // c1 (1 + s i) h
+            e.y = h * (c[1].y + s * c[1].x);
+            c[1] = e;
+            e.x = -s * c[2].y;                           // c2 (s i)
+            e.y = s * c[2].x;
+            c[2] = e;
+            e.x = -h * (c[3].x + s * c[3].y);            // c3 (-1 + s i) h
+            e.y = h * (s * c[3].x - c[3].y);
+            c[3] = e;
+            dft4<T, T2>(a[0], a[1], a[2], a[3], s);
+            dft4<T, T2>(c[0], c[1], c[2], c[3], s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[2 * q] = a[q];
+                v[2 * q + 1] = c[q];
+            }
         } else if (R == 3) {
             const T c3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
             const T2 a0 = v[0];
@@ -105,7 +152,7 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::type *src, t
             v[1] = cadd(m, e);
             v[2] = csub(m, e);
         }
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
     }
@@ -121,7 +168,8 @@ __device__ typename C2<T>::type *fft_smem(typename C2<T>::type *a, typename C2<T
     int Ns = 1;
     for (int p = 0; p < fp.count; ++p) {
         const int R = fp.radix[p];
-        if (R == 4) stockham_pass<T, 4>(src, dst, n, cnt, ld, Ns, sign, tw);
+        if (R == 8) stockham_pass<T, 8>(src, dst, n, cnt, ld, Ns, sign, tw);
+        else if (R == 4) stockham_pass<T, 4>(src, dst, n, cnt, ld, Ns, sign, tw);
         else if (R == 2) stockham_pass<T, 2>(src, dst, n, cnt, ld, Ns, sign, tw);
         else stockham_pass<T, 3>(src, dst, n, cnt, ld, Ns, sign, tw);
         __syncthreads();
@@ -131,10 +179,44 @@ __device__ typename C2<T>::type *fft_smem(typename C2<T>::type *a, typename C2<T
     return src;
 }
 
-// Forward row FFTs.  in_real != null: real input promoted to complex; else the
-// complex buffer itself is transformed in place.
+// Element-wise copy phase of a CTA: store(e, load(e)) for e in [0, total), with
+// LD_UNROLL independent loads in flight per thread (the data are L2-resident and
+// the kernels few-warp: latency, not bandwidth, bounds these phases).
+constexpr int LD_UNROLL = 4;
+template <typename L, typename W>
+__device__ __forceinline__ void staged_copy(int total, L load, W store)
+{
+    for (int e0 = threadIdx.x; e0 < total; e0 += LD_UNROLL * blockDim.x) {
+        decltype(load(0)) v[LD_UNROLL];
+#pragma unroll
+        for (int q = 0; q < LD_UNROLL; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < total) v[q] = load(e);
+        }
+#pragma unroll
+        for (int q = 0; q < LD_UNROLL; ++q) {
+            const int e = e0 + q * blockDim.x;
+            if (e < total) store(e, v[q]);
+        }
+    }
+}
+
+// Input of the forward row pass.  part != null: the angle-group partial images of
+// the backprojection, summed in group order and passed through the backprojection
+// epilogue (this fuses the group reduction into the pass); else in_real != null: a
+// real image; else the complex buffer itself.
 template <typename T>
-__device__ __forceinline__ void fft_rows_fwd_body(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n,
+struct RowsInput {
+    const T *in_real;
+    const T *part;
+    int groups;
+    int orbit;                // part holds the symmetric path's partial planes (FP32)
+    BackprojEpi<T> epi;
+};
+
+// Forward row FFTs (in place on cbuf).
+template <typename T>
+__device__ __forceinline__ void fft_rows_fwd_body(const RowsInput<T> &src, typename C2<T>::type *cbuf, int n,
                                                   int rows_per_cta, const FftPasses &fp,
                                                   const typename C2<T>::type *__restrict__ tw, int bx)
 {
@@ -144,28 +226,50 @@ __device__ __forceinline__ void fft_rows_fwd_body(const T *__restrict__ in_real,
     T2 *b = a + (size_t)rows_per_cta * n;
     const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-        const size_t g = (size_t)r0 * n + e;
-        if (in_real) {
+    const size_t g0 = (size_t)r0 * n;
+    const auto put = [&](int e, T2 v) { a[e] = v; };
+    if (src.part) {
+        const size_t nn = (size_t)n * n;
+        const unsigned mn = div_magic(n);
+        staged_copy(cnt * n, [&](int e) {
+            const int di = fast_div(e, n, mn);
+            T acc;
+            if constexpr (sizeof(T) == 4) {
+                if (src.orbit) acc = orbit_fold(src.part, src.groups, n, r0 + di, e - di * n);
+            }
+            if (!(sizeof(T) == 4 && src.orbit)) {
+                const T *pp = src.part + g0 + e;
+                acc = pp[0];
+#pragma unroll
+                for (int z = 1; z < MAX_BP_GROUPS; ++z)
+                    if (z < src.groups) acc += pp[(size_t)z * nn];
+            }
             T2 v;
-            v.x = in_real[g];
+            v.x = bp_epilogue_value(src.epi, n, r0 + di, e - di * n, acc);
             v.y = T(0);
-            a[e] = v;
-        } else {
-            a[e] = cbuf[g];
-        }
+            return v;
+        }, put);
+    } else if (src.in_real) {
+        staged_copy(cnt * n, [&](int e) {
+            T2 v;
+            v.x = src.in_real[g0 + e];
+            v.y = T(0);
+            return v;
+        }, put);
+    } else {
+        staged_copy(cnt * n, [&](int e) { return cbuf[g0 + e]; }, put);
     }
     __syncthreads();
     T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, -1, tw);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) cbuf[(size_t)r0 * n + e] = res[e];
+    staged_copy(cnt * n, [&](int e) { return res[e]; }, [&](int e, T2 v) { cbuf[g0 + e] = v; });
 }
 
 template <typename T>
 __global__ void __launch_bounds__(FFT_THREADS)
-k_fft_rows_fwd(const T *__restrict__ in_real, typename C2<T>::type *cbuf, int n, int rows_per_cta,
-               FftPasses fp, const typename C2<T>::type *__restrict__ tw)
+k_fft_rows_fwd(RowsInput<T> src, typename C2<T>::type *cbuf, int n, int rows_per_cta, FftPasses fp,
+               const typename C2<T>::type *__restrict__ tw)
 {
-    fft_rows_fwd_body<T>(in_real, cbuf, n, rows_per_cta, fp, tw, blockIdx.x);
+    fft_rows_fwd_body<T>(src, cbuf, n, rows_per_cta, fp, tw, blockIdx.x);
 }
 
 // Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf).
@@ -181,26 +285,36 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
     T2 *b = a + (size_t)cw * ld;
     const int c0 = bx * cw;
     const int cnt = min(cw, n - c0);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-        const int row = e / cnt, c = e - row * cnt;
-        a[(size_t)c * ld + row] = cbuf[(size_t)row * n + c0 + c];
-    }
+    const unsigned mc = div_magic(cnt);
+    // element e: row e / cnt, column c0 + e % cnt (consecutive threads: consecutive columns)
+    staged_copy(cnt * n, [&](int e) {
+        const int row = fast_div(e, cnt, mc);
+        return cbuf[(size_t)row * n + c0 + (e - row * cnt)];
+    }, [&](int e, T2 v) {
+        const int row = fast_div(e, cnt, mc);
+        a[(size_t)(e - row * cnt) * ld + row] = v;
+    });
     __syncthreads();
     T2 *res = fft_smem<T>(a, b, n, cnt, ld, fp, -1, tw);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-        const int row = e / cnt, c = e - row * cnt;
-        const T m = sym[(size_t)row * n + c0 + c];
-        T2 &v = res[(size_t)c * ld + row];
+    staged_copy(cnt * n, [&](int e) {
+        const int row = fast_div(e, cnt, mc);
+        return sym[(size_t)row * n + c0 + (e - row * cnt)];
+    }, [&](int e, T m) {
+        const int row = fast_div(e, cnt, mc);
+        T2 &v = res[(size_t)(e - row * cnt) * ld + row];
         v.x *= m;
         v.y *= m;
-    }
+    });
     __syncthreads();
     T2 *other = (res == a) ? b : a;
     T2 *res2 = fft_smem<T>(res, other, n, cnt, ld, fp, +1, tw);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-        const int row = e / cnt, c = e - row * cnt;
-        cbuf[(size_t)row * n + c0 + c] = res2[(size_t)c * ld + row];
-    }
+    staged_copy(cnt * n, [&](int e) {
+        const int row = fast_div(e, cnt, mc);
+        return res2[(size_t)(e - row * cnt) * ld + row];
+    }, [&](int e, T2 v) {
+        const int row = fast_div(e, cnt, mc);
+        cbuf[(size_t)row * n + c0 + (e - row * cnt)] = v;
+    });
 }
 
 template <typename T>
@@ -227,25 +341,25 @@ __device__ __forceinline__ void fft_rows_inv_body(const typename C2<T>::type *__
     T2 *b = a + (size_t)rows_per_cta * n;
     const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) a[e] = cbuf[(size_t)r0 * n + e];
+    const size_t g0 = (size_t)r0 * n;
+    staged_copy(cnt * n, [&](int e) { return cbuf[g0 + e]; }, [&](int e, T2 v) { a[e] = v; });
     __syncthreads();
     T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, +1, tw);
     // row-major outputs
-    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-        const size_t g = (size_t)r0 * n + e;
+    staged_copy(cnt * n, [&](int e) { return mode == 1 ? out[g0 + e] : T(0); }, [&](int e, T prev) {
         const T v = res[e].x;
-        if (dout) dout[g] = v;
-        T o = v;
-        if (mode == 1) o += out[g];
-        out[g] = o;
-        if (outh) outh[g] = __float2bfloat16_rn((float)o);   // bfloat16 operand copy
+        if (dout) dout[g0 + e] = v;
+        const T o = v + prev;
+        out[g0 + e] = o;
+        if (outh) outh[g0 + e] = __float2bfloat16_rn((float)o);   // bfloat16 operand copy
         res[e].y = o;     // keep the final value for the transposed write
-    }
+    });
     if (outT || outTh) {
         __syncthreads();
         // column-major writes: consecutive threads take consecutive rows of one column
+        const unsigned mc = div_magic(cnt);
         for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
-            const int col = e / cnt, r = e - col * cnt;
+            const int col = fast_div(e, cnt, mc), r = e - col * cnt;
             const T o = res[(size_t)r * n + col].y;
             if (outT) outT[(size_t)col * n + r0 + r] = o;
             if (outTh) outTh[(size_t)col * n + r0 + r] = __float2bfloat16_rn((float)o);
@@ -279,7 +393,7 @@ k_fft_rows_fwd_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_rows_fwd_body<float>(nullptr, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
+    fft_rows_fwd_body<float>(RowsInput<float>{}, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS)
@@ -329,19 +443,8 @@ FftPasses make_passes(const ctr_plan *p)
     return fp;
 }
 
-int rows_per_cta(const ctr_plan *p)
-{
-    int r = 2048 / p->n;
-    return r < 1 ? 1 : (r > 8 ? 8 : r);
-}
-
-int cols_per_cta(const ctr_plan *p)
-{
-    const size_t c2 = 2 * p->esize;
-    for (int cw = 4; cw > 1; cw /= 2)
-        if (2 * (size_t)cw * (p->n + 1) * c2 <= 160 * 1024) return cw;
-    return 1;
-}
+int rows_per_cta(const ctr_plan *p) { return fft_rows_per_cta(p->n); }
+int cols_per_cta(const ctr_plan *p) { return fft_cols_per_cta(p->n, p->esize); }
 
 }  // namespace
 
@@ -354,7 +457,8 @@ size_t fft_smem_bytes(const ctr_plan *p, int which)
 
 template <typename T>
 ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf, const T *sym, T *out, int mode,
-                            T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
+                            T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh, __nv_bfloat16 *outTh,
+                            const BackprojEpi<T> *bp_in)
 {
     using T2 = typename C2<T>::type;
     const int n = p->n;
@@ -366,7 +470,16 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
     const size_t smr = fft_smem_bytes(p, 0), smc = fft_smem_bytes(p, 1);
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
     p->launches++;
-    k_fft_rows_fwd<T><<<gr, FFT_THREADS, smr, s>>>(in_is_cbuf ? nullptr : in_real, cb, n, rpc, fp, tw);
+    RowsInput<T> src{};
+    if (bp_in) {
+        src.orbit = sizeof(T) == 4 && p->orbit;
+        src.part = (const T *)(src.orbit ? p->obp_part : p->bp_part);
+        src.groups = src.orbit ? p->obp_groups : p->bp_groups;
+        src.epi = *bp_in;
+    } else if (!in_is_cbuf) {
+        src.in_real = in_real;
+    }
+    k_fft_rows_fwd<T><<<gr, FFT_THREADS, smr, s>>>(src, cb, n, rpc, fp, tw);
     CTR_CHECK_LAUNCH("k_fft_rows_fwd");
     p->launches++;
     k_fft_cols<T><<<gc, FFT_THREADS, smc, s>>>(cb, sym, n, cw, fp, tw);
@@ -399,8 +512,12 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
     return CTR_OK;
 }
 
-template ctr_status launch_circulant<float>(const ctr_plan *, const float *, bool, const float *, float *, int, float *, float *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
-template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int, double *, double *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *);
+template ctr_status launch_circulant<float>(const ctr_plan *, const float *, bool, const float *, float *, int, float *,
+                                           float *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *,
+                                           const BackprojEpi<float> *);
+template ctr_status launch_circulant<double>(const ctr_plan *, const double *, bool, const double *, double *, int,
+                                            double *, double *, cudaStream_t, __nv_bfloat16 *, __nv_bfloat16 *,
+                                            const BackprojEpi<double> *);
 ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem)
 {
     ctr_status st = raise_smem_limit(k_fft_rows_fwd_batch, rows_smem);
@@ -424,17 +541,20 @@ ctr_status launch_batch_fft(int stage, const SliceDesc *sd, const int *prefix, i
     return CTR_OK;
 }
 
+// Work split of the FFT passes: about 1024 points per CTA of 128 threads, so that an
+// n = 512 image gives 256 CTAs per pass.
 int fft_rows_per_cta(int n)
 {
-    int r = 2048 / n;
-    return r < 1 ? 1 : (r > 8 ? 8 : r);
+    const int r = CTR_FFT_POINTS / n;
+    return r < 1 ? 1 : (r > 16 ? 16 : r);
 }
 
 int fft_cols_per_cta(int n, size_t esize)
 {
-    for (int cw = 4; cw > 1; cw /= 2)
-        if (2 * (size_t)cw * (n + 1) * 2 * esize <= 160 * 1024) return cw;
-    return 1;
+    int cw = CTR_FFT_POINTS / n;
+    cw = cw < 1 ? 1 : (cw > 8 ? 8 : cw);
+    while (cw > 1 && 2 * (size_t)cw * (n + 1) * 2 * esize > 160 * 1024) cw /= 2;
+    return cw;
 }
 
 template ctr_status configure_fft<float>(const ctr_plan *);
@@ -487,7 +607,8 @@ ctr_status static_setup(int dev)
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.cbuf, g_static_cbuf));
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.sym, g_static_sym));
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.tw, g_static_tw));
-    const int smax = 2 * 4 * (STATIC_MAX_N + 1) * (int)sizeof(float2);   // column kernel at n = 1024
+    // n <= 1024: rows_per_cta * n <= 1024 and cols_per_cta * (n + 1) <= 1024 + 8 points
+    const int smax = 2 * (1024 + 8) * (int)sizeof(float2);
     ctr_status st = raise_smem_limit(k_fft_cols<float>, smax);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_fwd<float>, smax);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv<float>, smax);
@@ -513,12 +634,11 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
         return fail(CTR_EINVAL, "precond_apply_static: sigma, tau, c and eps must be finite and > 0");
     FftPasses fp;
     {
-        int m = n, cnt = 0;
-        while (m % 4 == 0) { fp.radix[cnt++] = 4; m /= 4; }
-        while (m % 2 == 0) { fp.radix[cnt++] = 2; m /= 2; }
-        while (m % 3 == 0) { fp.radix[cnt++] = 3; m /= 3; }
-        if (m != 1) return fail(CTR_EUNSUPPORTED, "precond_apply_static: n must be of the form 2^a 3^b");
-        fp.count = cnt;
+        std::vector<int> rad;
+        if (fft_radices(n, rad) != CTR_OK)
+            return fail(CTR_EUNSUPPORTED, "precond_apply_static: n must be of the form 2^a 3^b");
+        fp.count = (int)rad.size();
+        for (int i = 0; i < fp.count; ++i) fp.radix[i] = rad[i];
     }
     int dev = -1;
     CTR_CUDA(cudaGetDevice(&dev));
@@ -533,14 +653,12 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     int blocks = (int)((nn + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps);
-    int rpc = 2048 / n;
-    rpc = rpc < 1 ? 1 : (rpc > 8 ? 8 : rpc);
-    int cw = 1;
-    for (int w = 4; w > 1; w /= 2)
-        if (2 * (size_t)w * (n + 1) * sizeof(float2) <= 160 * 1024) { cw = w; break; }
+    const int rpc = fft_rows_per_cta(n), cw = fft_cols_per_cta(n, sizeof(float));
     const size_t smr = 2 * (size_t)rpc * n * sizeof(float2), smc = 2 * (size_t)cw * (n + 1) * sizeof(float2);
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
-    k_fft_rows_fwd<float><<<gr, FFT_THREADS, smr, str>>>(y_dev, s.cbuf, n, rpc, fp, s.tw);
+    RowsInput<float> src{};
+    src.in_real = y_dev;
+    k_fft_rows_fwd<float><<<gr, FFT_THREADS, smr, str>>>(src, s.cbuf, n, rpc, fp, s.tw);
     k_fft_cols<float><<<gc, FFT_THREADS, smc, str>>>(s.cbuf, s.sym, n, cw, fp, s.tw);
     k_fft_rows_inv<float><<<gr, FFT_THREADS, smr, str>>>(s.cbuf, n, rpc, fp, s.tw, x_dev, 0, nullptr, nullptr,
                                                          nullptr, nullptr);

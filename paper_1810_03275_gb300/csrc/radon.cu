@@ -61,6 +61,10 @@ __device__ __forceinline__ int bin_of(long long P, int F)
 #define CTR_FWD_UNROLL 8
 #endif
 constexpr int FWD_UNROLL = CTR_FWD_UNROLL;   // rows per unrolled step of the ray march
+#ifndef CTR_FWD_UNROLL_ORBIT
+#define CTR_FWD_UNROLL_ORBIT 8
+#endif
+constexpr int FWD_UNROLL_ORBIT = CTR_FWD_UNROLL_ORBIT;
 
 // 1 + frac(p) in [1, 2) from the low 32 bits of P (F = 32): the top 23 fraction
 // bits become the mantissa of a float, so the weight is exact and identical in
@@ -97,28 +101,9 @@ __device__ __forceinline__ double interp(double acc, double2 pr, long long P, in
 }
 
 template <typename T>
-__device__ __forceinline__ T div_at(const T *__restrict__ px, int n, int i, int j, T inv_h)
-{
-    // div_h p = (d1 + d2)/h, backward differences with Dirichlet ends (Sec. 3.1)
-    if (n < 2) return T(0);
-    const T *py = px + (size_t)n * n;
-    T d1, d2;
-    if (i == 0) d1 = px[j];
-    else if (i == n - 1) d1 = -px[(size_t)(n - 2) * n + j];
-    else d1 = px[(size_t)i * n + j] - px[(size_t)(i - 1) * n + j];
-    const size_t row = (size_t)i * n;
-    if (j == 0) d2 = py[row];
-    else if (j == n - 1) d2 = -py[row + n - 2];
-    else d2 = py[row + j] - py[row + j - 1];
-    return (d1 + d2) * inv_h;
-}
-
-template <typename T>
 __device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, int i, int j, T acc)
 {
-    T v = acc * epi.scale;
-    if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
-    v *= epi.outscale;
+    const T v = bp_epilogue_value(epi, n, i, j, acc);
     const size_t o = (size_t)i * n + j;
     if (epi.complex_out) {
         epi.out[2 * o] = v;
@@ -492,6 +477,330 @@ k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int N, int M
     fwd_body<T, S, NC, EXACT1>(u, uT, n, N, M, F, march, epi, blockIdx.x, blockIdx.y);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric forward path (OrbitJob): one canonical ray march per job serves the
+// job's up to four angles, reading the four channels of the orbit image at once.
+// ---------------------------------------------------------------------------
+
+// ubar[m][q] = (u[q][m], u[n-1-q][m], u[m][q], u[n-1-m][q]): channel v holds
+// u(T_v^{-1}(q, m)) for the canonical march pixel (q, m) (pick q = i, march m = j).
+// 32 x 32 tiles: four coalesced tile loads (two of them transposed through shared
+// memory), one coalesced float4 store per record.
+__global__ void __launch_bounds__(256) k_orbit_image(const float *__restrict__ u, float4 *__restrict__ ubar, int n)
+{
+    __shared__ float tA[32][33], tB[32][33], tC[32][33], tD[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int q0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+    for (int r = ty; r < 32; r += 8) {
+        const int mr = m0 + r, qc = q0 + tx;          // tiles A, B: rows m, columns q
+        if (mr < n && qc < n) {
+            tA[r][tx] = u[(size_t)mr * n + qc];
+            tB[r][tx] = u[(size_t)(n - 1 - mr) * n + qc];
+        }
+        const int qr = q0 + r, mc = m0 + tx;          // tiles C, D: rows q, columns m
+        if (qr < n && mc < n) {
+            tC[r][tx] = u[(size_t)qr * n + mc];
+            tD[r][tx] = u[(size_t)(n - 1 - qr) * n + mc];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int m = m0 + r, q = q0 + tx;
+        if (m < n && q < n) ubar[(size_t)m * n + q] = make_float4(tC[tx][r], tD[tx][r], tA[r][tx], tB[r][tx]);
+    }
+}
+
+__device__ __forceinline__ void acc4(float4 &Su, float4 &Sf, float4 v, float f)
+{
+    Su.x += v.x;
+    Su.y += v.y;
+    Su.z += v.z;
+    Su.w += v.w;
+    Sf.x = fmaf(f, v.x, Sf.x);
+    Sf.y = fmaf(f, v.y, Sf.y);
+    Sf.z = fmaf(f, v.z, Sf.z);
+    Sf.w = fmaf(f, v.w, Sf.w);
+}
+
+// The canonical march (flip 0, B >= 0) over `rows` rows of the orbit image; the
+// state and the second-pixel rule are those of march32.
+template <bool BPOS, bool CHECK>
+__device__ __forceinline__ void march_orbit(const float4 *__restrict__ ub, int n, int rows, unsigned &r, int &q,
+                                            int &off, unsigned A32, unsigned lim, unsigned B32, unsigned thr,
+                                            float4 &Su, float4 &Sf)
+{
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll FWD_UNROLL_ORBIT
+    for (int rr = 0; rr < rows; ++rr) {
+        float4 v1, v2;
+        if constexpr (CHECK) {
+            v1 = ((unsigned)q < (unsigned)n) ? ub[off] : zero;
+            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ub[off + 1] : zero;
+        } else {
+            v1 = ub[off];
+            v2 = r < lim ? ub[off + 1] : zero;
+        }
+        acc4(Su, Sf, v1, one_plus_frac32u(r));
+        acc4(Su, Sf, v2, one_plus_frac32u(r + A32));
+        if constexpr (BPOS) {
+            const bool s = r >= thr;
+            r += s ? B32 - A32 : B32;
+            off += s ? n - 1 : n;
+            if constexpr (CHECK) q -= s ? 1 : 0;
+        } else {
+            const bool s = r < thr;
+            r += s ? A32 - thr : 0u - thr;
+            off += s ? n + 1 : n;
+            if constexpr (CHECK) q += s ? 1 : 0;
+        }
+    }
+}
+
+template <bool BPOS>
+__device__ __forceinline__ void march_orbit_rows(const float4 *__restrict__ ub, int n, long long K,
+                                                 const AngleMarch &am, int mlo, int mhi, int ilo, int ihi,
+                                                 float4 &Su, float4 &Sf)
+{
+    const long long A = am.A, B = am.B;
+    const long long qa = ceil_div_ll(K - (long long)mlo * B - am.Op, A);
+    unsigned r = (unsigned)(qa * A + (long long)mlo * B + am.Op - K);
+    int q = (int)qa;
+    int off = mlo * n + q;
+    const unsigned A32 = (unsigned)A;
+    const unsigned lim = (unsigned)((1ll << 32) - A);
+    const unsigned B32 = (unsigned)B;
+    const unsigned thr = BPOS ? (unsigned)(A - B) : (unsigned)(-B);
+    if (ilo > ihi) {
+        march_orbit<BPOS, true>(ub, n, mhi - mlo + 1, r, q, off, A32, lim, B32, thr, Su, Sf);
+        return;
+    }
+    march_orbit<BPOS, true>(ub, n, ilo - mlo, r, q, off, A32, lim, B32, thr, Su, Sf);
+    march_orbit<BPOS, false>(ub, n, ihi - ilo + 1, r, q, off, A32, lim, B32, thr, Su, Sf);
+    q = off - (ihi + 1) * n;
+    march_orbit<BPOS, true>(ub, n, mhi - ihi, r, q, off, A32, lim, B32, thr, Su, Sf);
+}
+
+__device__ __forceinline__ void orbit_out(const ForwardEpi<float> &epi, int l, int M, int k, int lane, float Su,
+                                          float Sf)
+{
+    const float Bk = Sf - Su, Ak = Su - Bk;
+    const float Bprev = __shfl_up_sync(0xffffffffu, Bk, 1);
+    if (l >= 0 && lane >= 1 && k < M) forward_epilogue(epi, (size_t)l * M + k, Ak + Bprev);
+}
+
+#ifndef CTR_ORBIT_SEGS
+#define CTR_ORBIT_SEGS 4
+#endif
+constexpr int ORBIT_SEGS = CTR_ORBIT_SEGS;    // row segments of a job's rays (one warp each)
+constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
+#ifndef CTR_ORBIT_MINB
+#define CTR_ORBIT_MINB 2
+#endif
+#ifndef CTR_OBP_MINB
+#define CTR_OBP_MINB 6
+#endif
+
+// Warp w of the CTA takes job by*4 + (w & 3), bins bx*31 + [0, 31) and the
+// (w >> 2)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
+// are added in a fixed order through shared memory.
+__global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
+k_forward_orbit(const float4 *__restrict__ ubar, int n, int n_jobs, int M, const OrbitJob *__restrict__ jobs,
+                ForwardEpi<float> epi)
+{
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int slot = warp & 3, seg = warp >> 2;
+    const int jb = blockIdx.y * 4 + slot;
+    const int kb = blockIdx.x * 31;
+    const int k = kb + lane - 1;
+    const bool active = jb < n_jobs && kb < M;        // warp-uniform
+    float4 Su = make_float4(0.f, 0.f, 0.f, 0.f), Sf = Su;
+    int4 ls = make_int4(-1, -1, -1, -1);             // the job's angles
+    if (active) {
+        const AngleMarch am = jobs[jb].am;
+        ls = *reinterpret_cast<const int4 *>(jobs[jb].l);
+        const float Q0 = (float)k * am.kA - am.oA;
+        int mlo, mhi;
+        rows_in<true>(Q0, am.binv, -3.f, (float)n + 1.f, n, mlo, mhi);
+        int mlo_w = __reduce_min_sync(0xffffffffu, mlo);
+        int mhi_w = __reduce_max_sync(0xffffffffu, mhi);
+        if (mlo_w <= mhi_w) {
+            int ilo, ihi;
+            rows_in<false>(Q0, am.binv, 0.5f, (float)n - 3.5f, n, ilo, ihi);
+            int ilo_w = max(__reduce_max_sync(0xffffffffu, ilo), mlo_w);
+            int ihi_w = min(__reduce_min_sync(0xffffffffu, ihi), mhi_w);
+            if (ORBIT_SEGS > 1) {                     // this warp's part of the rows
+                const int per = (mhi_w - mlo_w + ORBIT_SEGS) / ORBIT_SEGS;
+                const int a = mlo_w + seg * per, b = min(mhi_w, a + per - 1);
+                mlo_w = a;
+                mhi_w = b;
+                ilo_w = max(ilo_w, a);
+                ihi_w = min(ihi_w, b);
+            }
+            if (mlo_w <= mhi_w) {
+                const long long K = (long long)k << 32;
+                if (am.B > 0) march_orbit_rows<true>(ubar, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                else march_orbit_rows<false>(ubar, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+            }
+        }
+    }
+    if constexpr (ORBIT_SEGS > 1) {
+        __shared__ float4 s_part[ORBIT_SEGS > 1 ? ORBIT_SEGS - 1 : 1][2][4][32];
+        if (seg > 0) {
+            s_part[seg - 1][0][slot][lane] = Su;
+            s_part[seg - 1][1][slot][lane] = Sf;
+        }
+        __syncthreads();
+        if (seg > 0) return;
+#pragma unroll
+        for (int z = 0; z < ORBIT_SEGS - 1; ++z) {
+            const float4 a = s_part[z][0][slot][lane], b = s_part[z][1][slot][lane];
+            Su.x += a.x; Su.y += a.y; Su.z += a.z; Su.w += a.w;
+            Sf.x += b.x; Sf.y += b.y; Sf.z += b.z; Sf.w += b.w;
+        }
+    }
+    if (!active) return;
+    orbit_out(epi, ls.x, M, k, lane, Su.x, Sf.x);
+    orbit_out(epi, ls.y, M, k, lane, Su.y, Sf.y);
+    orbit_out(epi, ls.z, M, k, lane, Su.z, Sf.z);
+    orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric backprojection (OrbitJob): a CTA owns a 32 x 32 tile of canonical
+// pixels x and a group of jobs; per job it stages the four channels' sinogram rows
+// side by side, so one fixed-point P(x) and one pair of 16-byte shared loads serve
+// four angles.  Channel v's sum at x belongs to image pixel T_v^{-1}(x); the four
+// channel images are written as partial planes [group][v][row][col] with
+//   plane 0 at x, plane 1 at x (its pixel is row-mirrored), planes 2 and 3 transposed
+// so that the fold reads rows only:
+//   u(i, j) = sum_groups P0[i][j] + P1[n-1-i][j] + P2[i][j] + P3[n-1-i][j].
+// ---------------------------------------------------------------------------
+#ifndef CTR_OBP_JCH
+#define CTR_OBP_JCH 8
+#endif
+constexpr int OBP_JCH = CTR_OBP_JCH;   // jobs per staged chunk
+
+size_t obp_smem(int wstride)
+{
+    const size_t stage = sizeof(float4) * 2 * OBP_JCH * wstride + (3 * sizeof(long long) + 5 * sizeof(int)) * OBP_JCH;
+    const size_t tr = sizeof(float) * 2 * 32 * 33;
+    return stage > tr ? stage : tr;
+}
+
+__global__ void __launch_bounds__(32 * BP_TY, CTR_OBP_MINB)
+k_backproject_orbit(const float *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
+                    const OrbitJob *__restrict__ jobs, float *__restrict__ part)
+{
+    static_assert(BP_TI == 32 && BP_TJ == 32, "square tiles");
+    constexpr int NT = 32 * BP_TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *stage = reinterpret_cast<float4 *>(smem_raw);               // [job][channel pair][bin]
+    long long *sPb = reinterpret_cast<long long *>(stage + 2 * OBP_JCH * wstride);
+    long long *sC = sPb + OBP_JCH;
+    long long *sS = sC + OBP_JCH;
+    int *sK = reinterpret_cast<int *>(sS + OBP_JCH);
+    int *sL = sK + OBP_JCH;                                               // [job][channel]
+
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = blockIdx.y * BP_TI, j0 = blockIdx.x * BP_TJ;
+    const int la = blockIdx.z * jobs_per_group;
+    const int lb = min(n_jobs, la + jobs_per_group);
+    float acc[BP_R][4];
+#pragma unroll
+    for (int r = 0; r < BP_R; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+
+    for (int c0 = la; c0 < lb; c0 += OBP_JCH) {
+        const int na = min(OBP_JCH, lb - c0);
+        __syncthreads();
+        if (threadIdx.x < na) {
+            const AngleMarch am = jobs[c0 + threadIdx.x].am;     // canonical P(i, j) = i A + j B + Op
+            const long long C = am.A, S = am.B;
+            const long long P00 = (long long)i0 * C + (long long)j0 * S + am.Op;
+            const long long kmin = P00 >> 32;                    // C, S >= 0: P00 is the tile's minimum
+            sK[threadIdx.x] = (int)kmin;
+            sPb[threadIdx.x] = P00 - (kmin << 32);
+            sC[threadIdx.x] = C;
+            sS[threadIdx.x] = S;
+        }
+        if (threadIdx.x < 4 * na) sL[threadIdx.x] = jobs[c0 + (threadIdx.x >> 2)].l[threadIdx.x & 3];
+        __syncthreads();
+        float2 *st2 = reinterpret_cast<float2 *>(stage);
+        for (int e = threadIdx.x; e < na * wstride * 4; e += NT) {
+            const int c = e & 3, rest = e >> 2;
+            const int a = rest / wstride, w = rest - a * wstride;
+            const int k = sK[a] + w, l = sL[4 * a + c];
+            const float *row = g + (size_t)(l < 0 ? 0 : l) * M;
+            const float g0 = (l >= 0 && k >= 0 && k < M) ? row[k] : 0.f;
+            const float g1 = (l >= 0 && k + 1 >= 0 && k + 1 < M) ? row[k + 1] : 0.f;
+            // float4 planes (ch0 ch1) and (ch2 ch3) of the job, consecutive bins adjacent
+            st2[((size_t)(2 * a + (c >> 1)) * wstride + w) * 2 + (c & 1)] = make_stage(g0, g1);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int a = 0; a < na; ++a) {
+            const long long C = sC[a];
+            long long P = sPb[a] + (long long)ty * C + (long long)tx * sS[a];
+            const long long D = C * BP_TY;
+            const float4 *row01 = stage + 2 * a * wstride;
+            const float4 *row23 = row01 + wstride;
+#pragma unroll
+            for (int r = 0; r < BP_R; ++r) {
+                const int b = (int)(P >> 32);
+                const float f = one_plus_frac32(P);
+                const float4 s01 = row01[b], s23 = row23[b];
+                acc[r][0] = fmaf(f, s01.y, acc[r][0] + s01.x);
+                acc[r][1] = fmaf(f, s01.w, acc[r][1] + s01.z);
+                acc[r][2] = fmaf(f, s23.y, acc[r][2] + s23.x);
+                acc[r][3] = fmaf(f, s23.w, acc[r][3] + s23.z);
+                P += D;
+            }
+        }
+    }
+
+    const size_t nn = (size_t)n * n;
+    float *pg = part + (size_t)blockIdx.z * 4 * nn;
+    const int j = j0 + tx;
+#pragma unroll
+    for (int r = 0; r < BP_R; ++r) {
+        const int i = i0 + ty + BP_TY * r;
+        if (i < n && j < n) {
+            pg[(size_t)i * n + j] = acc[r][0];
+            pg[nn + (size_t)i * n + j] = acc[r][1];
+        }
+    }
+    // planes 2 and 3 transposed through shared memory (coalesced rows j)
+    __syncthreads();
+    float(*tr)[32][33] = reinterpret_cast<float(*)[32][33]>(smem_raw);
+#pragma unroll
+    for (int r = 0; r < BP_R; ++r) {
+        tr[0][ty + BP_TY * r][tx] = acc[r][2];
+        tr[1][ty + BP_TY * r][tx] = acc[r][3];
+    }
+    __syncthreads();
+    const int it = i0 + tx;
+#pragma unroll
+    for (int r = 0; r < BP_R; ++r) {
+        const int jl = ty + BP_TY * r, jt = j0 + jl;
+        if (it < n && jt < n) {
+            pg[2 * nn + (size_t)jt * n + it] = tr[0][tx][jl];
+            pg[3 * nn + (size_t)jt * n + it] = tr[1][tx][jl];
+        }
+    }
+}
+
+// The fold of the symmetric backprojection's partial planes, then the
+// backprojection epilogue (grid-stride over the pixels).
+__global__ void __launch_bounds__(256)
+k_bp_fold(const float *__restrict__ part, int groups, int n, BackprojEpi<float> epi)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        bp_epilogue(epi, n, i, j, orbit_fold(part, groups, n, i, j));
+    }
+}
+
 // Batched stages: block b of the launch belongs to the slice s with
 // prefix[s] <= b < prefix[s+1]; the slice's parameters come from its SliceDesc.
 __device__ __forceinline__ int find_slice(const int *__restrict__ prefix, int ns, int b)
@@ -565,8 +874,28 @@ void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const S *u, const S *uT, const
 }
 
 template <typename T, typename S>
-ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cudaStream_t s)
+ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cudaStream_t s, bool defer_reduce)
 {
+    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+        if (p->orbit) {
+            const int G = p->obp_groups;
+            dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
+            float *part = (float *)p->obp_part;
+            p->launches++;
+            k_backproject_orbit<<<grid, 32 * BP_TY, obp_smem(p->wstride), s>>>(
+                g, p->n, p->M, p->wstride, (p->n_jobs + G - 1) / G, p->n_jobs, p->d_jobs, part);
+            CTR_CHECK_LAUNCH("k_backproject_orbit");
+            if (!defer_reduce) {
+                const size_t nn = (size_t)p->n * p->n;
+                int blocks = (int)((nn + 255) / 256);
+                if (blocks > 4096) blocks = 4096;
+                p->launches++;
+                k_bp_fold<<<blocks, 256, 0, s>>>(part, G, p->n, epi);
+                CTR_CHECK_LAUNCH("k_bp_fold");
+            }
+            return CTR_OK;
+        }
+    }
     const int G = p->bp_groups;
     const int per = (p->N + G - 1) / G;
     dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
@@ -575,7 +904,7 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
     k_backproject<T, S><<<grid, 32 * BP_TY, bp_smem<T>(p), s>>>(g, p->n, p->N, p->M, p->F, p->wstride, per,
                                                                  p->d_geom, epi, part);
     CTR_CHECK_LAUNCH("k_backproject");
-    if (G > 1) {
+    if (G > 1 && !defer_reduce) {
         const size_t nn = (size_t)p->n * p->n;
         int blocks = (int)((nn + 255) / 256);
         if (blocks > 4096) blocks = 4096;
@@ -590,6 +919,19 @@ template <typename T, typename S>
 ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
     const bool exact1 = p->h <= p->ds;
+    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+        if (p->orbit) {
+            float4 *ub = (float4 *)p->ubar;
+            p->launches++;
+            k_orbit_image<<<dim3((p->n + 31) / 32, (p->n + 31) / 32), 256, 0, s>>>(u, ub, p->n);
+            CTR_CHECK_LAUNCH("k_orbit_image");
+            p->launches++;
+            k_forward_orbit<<<dim3(fwd_grid_x(p->M), (p->n_jobs + 3) / 4), ORBIT_THREADS, 0, s>>>(
+                ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
+            CTR_CHECK_LAUNCH("k_forward_orbit");
+            return CTR_OK;
+        }
+    }
     p->launches++;
     dim3 grid(fwd_grid_x(p->M), fwd_grid_y(p->N));
     switch (p->ncand * 2 + (exact1 ? 1 : 0)) {
@@ -614,15 +956,16 @@ ctr_status configure_radon(const ctr_plan *p)
 {
     const size_t smem = bp_smem<T>(p);
     ctr_status st = raise_smem_limit(k_backproject<T, T>, smem);
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit, obp_smem(p->wstride));
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
     return st;
 }
 
 ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, const BackprojEpi<float> &epi,
-                                   cudaStream_t s)
+                                   cudaStream_t s, bool defer_reduce)
 {
-    return bp_impl<float, __nv_bfloat16>(p, g, epi, s);
+    return bp_impl<float, __nv_bfloat16>(p, g, epi, s, defer_reduce);
 }
 
 ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT,
@@ -632,9 +975,10 @@ ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const 
 }
 
 template <typename T>
-ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s)
+ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T> &epi, cudaStream_t s,
+                              bool defer_reduce)
 {
-    return bp_impl<T, T>(p, g, epi, s);
+    return bp_impl<T, T>(p, g, epi, s, defer_reduce);
 }
 
 template <typename T>
@@ -654,6 +998,14 @@ ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t
 }
 
 int backproject_tile_rows() { return BP_TI; }
+
+template <typename T>
+bool bp_deferred(const ctr_plan *p)
+{
+    return p->bp_groups > 1 || (sizeof(T) == 4 && p->orbit);
+}
+template bool bp_deferred<float>(const ctr_plan *);
+template bool bp_deferred<double>(const ctr_plan *);
 
 int fwd_grid_x(int M) { return (M + 30) / 31; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
@@ -689,8 +1041,10 @@ ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix,
     return CTR_OK;
 }
 
-template ctr_status launch_backproject<float>(const ctr_plan *, const float *, const BackprojEpi<float> &, cudaStream_t);
-template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &, cudaStream_t);
+template ctr_status launch_backproject<float>(const ctr_plan *, const float *, const BackprojEpi<float> &, cudaStream_t,
+                                             bool);
+template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &,
+                                              cudaStream_t, bool);
 template ctr_status launch_forward<float>(const ctr_plan *, const float *, const float *, const ForwardEpi<float> &, cudaStream_t);
 template ctr_status launch_forward<double>(const ctr_plan *, const double *, const double *, const ForwardEpi<double> &, cudaStream_t);
 template ctr_status configure_radon<float>(const ctr_plan *);

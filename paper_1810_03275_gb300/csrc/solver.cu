@@ -489,15 +489,17 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     ea.outscale = -a.sigma;
     ea.inv_h = a.inv_h;
     const bool h = sizeof(T) == 4 && p->bf16;   // projector operands in bfloat16
+    const bool fuse = bp_deferred<T>(p);        // partial-image sum and epilogue inside the first FFT pass
     if (h) {
         if constexpr (sizeof(T) == 4)
-            if ((st = launch_backproject_bf16(p, p->y1h, ea, s)) != CTR_OK) return st;
-    } else if ((st = launch_backproject<T>(p, (const T *)p->y1, ea, s)) != CTR_OK) {
+            if ((st = launch_backproject_bf16(p, p->y1h, ea, s, fuse)) != CTR_OK) return st;
+    } else if ((st = launch_backproject<T>(p, (const T *)p->y1, ea, s, fuse)) != CTR_OK) {
         return st;
     }
     // B: u += F^{-1}(F(u_tmp) m), and uT (or the bfloat16 copies of u and uT)
     if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, h ? nullptr : (T *)p->uT,
-                                  diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr, h ? p->uTh : nullptr)) != CTR_OK)
+                                  diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr, h ? p->uTh : nullptr,
+                                  fuse ? &ea : nullptr)) != CTR_OK)
         return st;
     // C: ray-driven Rt u with the data-dual step
     ForwardEpi<T> ec{};
