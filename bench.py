@@ -111,16 +111,16 @@ def src_sha(*rel):
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+def traffic_record(call: str):
+    """DRAM bytes per operator call (summed over the kernels it launches) from the
+    committed ncu summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        rec = d.get(kernel)
+        rec = d.get(call)
         if rec and rec.get("src_sha") == src_sha("paper_1810_03275_gb300/csrc/radon.cu"):
-            return rec.get("dram_bytes_per_launch")
+            return rec.get("dram_bytes_per_call")
     except Exception:
         pass
     return None
@@ -328,7 +328,11 @@ def main():
     g = torch.empty((N, M), dtype=torch.float32, device="cuda")
     reps = 20
     kt = {}
-    for name, fn in (("k_backproject", lambda: plan.rh_adjoint(f, u)), ("k_forward", lambda: plan.rh_forward_t(u, uT, g))):
+    sym = plan.symmetric_jobs > 0
+    call_kernels = {"rh_adjoint": ["k_backproject_orbit", "k_bp_fold"] if sym else
+                    (["k_backproject", "k_bp_reduce"] if plan.bp_groups > 1 else ["k_backproject"]),
+                    "rh_forward_t": ["k_orbit_image", "k_forward_orbit"] if sym else ["k_forward"]}
+    for name, fn in (("rh_adjoint", lambda: plan.rh_adjoint(f, u)), ("rh_forward_t", lambda: plan.rh_forward_t(u, uT, g))):
         for _ in range(3):
             fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -344,10 +348,12 @@ def main():
     alu_peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e9        # Gop/s, FP32 lanes x max clock
     ops = OPS_PER_SAMPLE * n * n * N
     bytes_alg = 4.0 * (n * n + N * M)
-    kernels = {k: {"ms": 1e3 * v, "gsamples_per_s": n * n * N / v / 1e9, "gops": ops / v / 1e9,
-                   "alu_frac": ops / v / 1e9 / alu_peak, "hbm_gbs": bytes_alg / v / 1e9,
+    kernels = {k: {"ms": 1e3 * v, "kernels": call_kernels[k], "gsamples_per_s": n * n * N / v / 1e9,
+                   "gops": ops / v / 1e9, "alu_frac": ops / v / 1e9 / alu_peak, "hbm_gbs": bytes_alg / v / 1e9,
                    "hbm_frac": bytes_alg / v / 1e9 / hbm_peak} for k, v in kt.items()}
-    roof = {"bound": "alu", "kernel": dom, "achieved": ops / kt[dom] / 1e9, "peak": alu_peak, "unit": "Gop/s",
+    roof = {"bound": "alu", "kernel": f"{dom} ({' + '.join(call_kernels[dom])})", "path":
+            f"symmetric, {plan.symmetric_jobs} jobs for {N} angles" if sym else "per angle",
+            "achieved": ops / kt[dom] / 1e9, "peak": alu_peak, "unit": "Gop/s",
             "frac": ops / kt[dom] / 1e9 / alu_peak, "traffic": traffic_record(dom),
             "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)",
             "hbm": {"achieved_gbs": bytes_alg / kt[dom] / 1e9, "peak_gbs": hbm_peak, "peak_source": peak_kind,

@@ -111,6 +111,15 @@ size_t ctr_plan_device_bytes(const ctr_plan *plan);
 /* Number of this library's kernels the plan has launched so far (kernels replayed
  * inside CUDA graphs included). */
 unsigned long long ctr_plan_launch_count(const ctr_plan *plan);
+/* Number of jobs of the projectors' symmetric path, 0 when the plan projects angle by
+ * angle.  The discrete geometry of Sec. 3.1 is exactly invariant under the symmetries
+ * of the pixel grid: angles whose fixed-point (C, S) are (a, b), (-a, b), (b, a) and
+ * (-b, a) (e.g. theta, pi - theta, pi/2 - theta, pi/2 + theta) share one job, one ray
+ * march and one staged detector coordinate per pixel.  FP32 plans with ds >= h take
+ * the path when every angle is such an image of its canonical pair and the jobs hold
+ * two angles or more on average (uniform angles over [0, pi) with an even count).
+ * Results equal those of the per-angle path up to the order of FP32 summation. */
+int ctr_plan_symmetric_jobs(const ctr_plan *plan);
 
 /* g = R_h u, the discrete Radon transform of Sec. 3.1 (the adjoint of linear
  * backprojection): bin k of angle l gets sum_ij u_ij Lambda(p_ijl - k) with

@@ -493,7 +493,8 @@ ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
         if ((st = launch_transpose<__nv_bfloat16>(p, (const __nv_bfloat16 *)u, p->uTh, s)) != CTR_OK) return st;
         return op_forward_bf16(p, (const __nv_bfloat16 *)u, p->uTh, (float *)g, s);
     }
-    if ((st = launch_transpose<float>(p, (const float *)u, (float *)p->uT, s)) != CTR_OK) return st;
+    if (fwd_needs_transpose<float>(p) && (st = launch_transpose<float>(p, (const float *)u, (float *)p->uT, s)) != CTR_OK)
+        return st;
     return op_forward<float>(p, (const float *)u, (const float *)p->uT, (float *)g, 1.0, s);
 }
 
@@ -508,6 +509,7 @@ ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, voi
 }
 
 unsigned long long ctr_plan_launch_count(const ctr_plan *p) { return p ? p->launches : 0ull; }
+int ctr_plan_symmetric_jobs(const ctr_plan *p) { return p && p->orbit ? p->n_jobs : 0; }
 
 ctr_status rh_adjoint(ctr_plan *p, const void *g, void *u, void *stream)
 {

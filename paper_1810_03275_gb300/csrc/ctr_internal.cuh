@@ -287,6 +287,9 @@ size_t fft_smem_bytes(const ctr_plan *p, int which);
 
 int backproject_tile_rows();   // pixel rows of a backprojection tile (its width is 32)
 template <typename T> bool bp_deferred(const ctr_plan *p);
+// false when the forward projector reads only u (the symmetric path builds its own
+// orbit image): callers may then skip making the transposed copy uT
+template <typename T> inline bool fwd_needs_transpose(const ctr_plan *p) { return !(sizeof(T) == 4 && p->orbit); }
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
 int fwd_grid_y(int N);         // forward-projector grid: angle groups
 

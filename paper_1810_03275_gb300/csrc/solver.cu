@@ -417,7 +417,7 @@ ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
     k_normalize<T><<<grid_for(nn), 256, 0, s>>>(x, nn, p->d_scal, 1, x);
     CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
     for (int it = 0; it < iters; ++it) {
-        if ((st = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return st;
+        if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return st;
         if ((st = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return st;
         if ((st = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return st;
         if ((st = dot2<T>(p, x, y, nn, p->d_scal, s)) != CTR_OK) return st;
@@ -450,7 +450,9 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
     CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
     const double ib = 1.0 / beta;
     for (int it = 0; it < iters; ++it) {
-        if ((st = launch_circulant<T>(p, z, false, (const T *)p->symh, x, 0, xt, nullptr, s)) != CTR_OK) return st;
+        if ((st = launch_circulant<T>(p, z, false, (const T *)p->symh, x, 0, fwd_needs_transpose<T>(p) ? xt : nullptr,
+                                      nullptr, s)) != CTR_OK)
+            return st;
         if ((st = op_forward<T>(p, x, xt, g, ib, s)) != CTR_OK) return st;
         if ((st = op_adjoint<T>(p, g, yp, ib, s)) != CTR_OK) return st;
         if ((st = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s)) != CTR_OK) return st;
@@ -497,7 +499,8 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
         return st;
     }
     // B: u += F^{-1}(F(u_tmp) m), and uT (or the bfloat16 copies of u and uT)
-    if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, h ? nullptr : (T *)p->uT,
+    T *uT_out = (h || !fwd_needs_transpose<T>(p)) ? nullptr : (T *)p->uT;
+    if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, uT_out,
                                   diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr, h ? p->uTh : nullptr,
                                   fuse ? &ea : nullptr)) != CTR_OK)
         return st;
@@ -809,10 +812,12 @@ ctr_status pdrq_vjp_step(ctr_plan *p, const T *u0, const T *v1b0, const T *v2b0,
     p->launches += 1;
     k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(du1, bu, T(1), nn, du1);
     // dr = -sigma P(du')
-    if ((st = launch_circulant<T>(p, du1, false, (const T *)p->sym, dr, 0, drT, nullptr, s)) != CTR_OK) return st;
-    p->launches += 2;
+    const bool tr = fwd_needs_transpose<T>(p);
+    if ((st = launch_circulant<T>(p, du1, false, (const T *)p->sym, dr, 0, tr ? drT : nullptr, nullptr, s)) != CTR_OK)
+        return st;
+    p->launches += tr ? 2 : 1;
     k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(dr, -sigma, nn, dr);
-    k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(drT, -sigma, nn, drT);
+    if (tr) k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(drT, -sigma, nn, drT);
     // dy1 = Rt dr ; dy2 = tau grad dr
     if ((st = op_forward<T>(p, dr, drT, dy1, ib, s)) != CTR_OK) return st;
     if ((st = op_grad<T>(p, dr, dy2, s)) != CTR_OK) return st;

@@ -60,7 +60,7 @@ class State(ctypes.Structure):
 
 
 EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_last_error", "ctr_plan_device_bytes",
-           "ctr_plan_launch_count", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
+           "ctr_plan_launch_count", "ctr_plan_symmetric_jobs", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step"]
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         lib.rh_forward_t.restype = ctypes.c_int
         lib.ctr_plan_launch_count.argtypes = [vp]
         lib.ctr_plan_launch_count.restype = ctypes.c_ulonglong
+        lib.ctr_plan_symmetric_jobs.argtypes = [vp]
+        lib.ctr_plan_symmetric_jobs.restype = ctypes.c_int
         lib.precond_apply.argtypes = [vp, P(Params), vp, vp, vp]
         lib.tv_pd_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(Params), vp,
                                     P(Diag), vp]
@@ -244,6 +246,11 @@ class Plan:
     @property
     def launch_count(self) -> int:
         return int(load().ctr_plan_launch_count(self._h))
+
+    @property
+    def symmetric_jobs(self) -> int:
+        """Jobs of the projectors' symmetric path (0: angle-by-angle path)."""
+        return int(load().ctr_plan_symmetric_jobs(self._h))
 
     @property
     def bp_groups(self) -> int:

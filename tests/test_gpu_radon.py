@@ -13,7 +13,8 @@ GEOMS = [
     (37, 50, 53, 1.0, 1.0, "uniform"),          # ragged tiles, odd n
     (64, 90, 95, 1.0, 1.0, "uniform"),          # the 64x64 configuration's geometry
     (100, 33, 142, 1.0, 1.0, "random"),         # angles anywhere in [0, 2 pi)
-    (48, 40, 70, 0.8, 1.0, "uniform"),          # ds/h = 1.25 (3 pixels per interval)
+    (48, 40, 70, 0.8, 1.0, "uniform"),          # ds/h = 1.25
+    (48, 40, 90, 0.6, 1.0, "uniform"),          # ds/h = 1.67 (3 pixels per interval)
     (40, 30, 45, 1.3, 1.0, "uniform"),          # h > ds
     (33, 17, 1, 1.0, 1.0, "uniform"),           # single bin
     (1, 5, 3, 1.0, 1.0, "uniform"),             # single pixel
@@ -55,6 +56,47 @@ def test_forward_adjoint_match_oracle(ct, geom, dtype):
     assert rel_l2(got_b, ref_b) < tol, rel_l2(got_b, ref_b)
     assert rel_max(got_f, ref_f) < 10 * tol
     assert rel_max(got_b, ref_b) < 10 * tol
+
+
+def test_symmetric_path_selection(ct):
+    """FP32 plans with uniform angles over [0, pi) and an even count take the symmetric
+    path (at most one job per two angles); odd counts, angles outside [0, pi), FP64 and
+    BF16 plans project angle by angle."""
+    uni = lambda N: np.arange(N) * (np.pi / N)
+    p = ct.Plan(64, 90, 95, angles=uni(90))
+    assert 0 < p.symmetric_jobs <= 45
+    assert ct.Plan(512, 720, 729, angles=uni(720)).symmetric_jobs == 181
+    assert ct.Plan(64, 45, 95, angles=uni(45)).symmetric_jobs == 0
+    assert ct.Plan(64, 33, 95, angles=_angles(33, "random", 1)).symmetric_jobs == 0
+    assert ct.Plan(64, 90, 95, angles=uni(90), dtype="f64").symmetric_jobs == 0
+    assert ct.Plan(64, 90, 95, angles=uni(90), dtype="bf16").symmetric_jobs == 0
+    assert ct.Plan(48, 40, 70, angles=uni(40), h=0.8).symmetric_jobs > 0      # two pixels per interval
+    assert ct.Plan(48, 40, 70, angles=uni(40), h=0.6).symmetric_jobs == 0     # three pixels per interval
+
+
+@pytest.mark.parametrize("case", ["duplicated", "shuffled", "partial"])
+def test_symmetric_path_angle_sets(ct, case):
+    """The symmetric path on angle sets that fill its jobs unevenly: every angle twice,
+    a shuffled uniform set, and a set where most jobs miss channels."""
+    n, M = 70, 101
+    base = np.arange(36) * (np.pi / 36)
+    if case == "duplicated":
+        th = np.concatenate([base, base])
+    elif case == "shuffled":
+        th = np.random.default_rng(4).permutation(base)
+    else:
+        th = base[np.arange(36) % 3 != 1]       # 24 angles, two per job on average
+    N = th.shape[0]
+    plan = ct.Plan(n, N, M, angles=th)
+    assert plan.symmetric_jobs > 0
+    geo = oracle.Geometry(n, N, M, theta=th)
+    rng = np.random.default_rng(N)
+    u = rng.standard_normal((n, n))
+    g = rng.standard_normal((N, M))
+    got_f = to_np(plan.rh_forward(to_dev(u, plan.torch_dtype)))
+    got_b = to_np(plan.rh_adjoint(to_dev(g, plan.torch_dtype)))
+    assert rel_l2(got_f, oracle.rh_forward(u, geo)) < TOL["f32"]
+    assert rel_l2(got_b, oracle.rh_adjoint(g, geo)) < TOL["f32"]
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
