@@ -115,8 +115,8 @@ unsigned long long ctr_plan_launch_count(const ctr_plan *plan);
  * angle.  The discrete geometry of Sec. 3.1 is exactly invariant under the symmetries
  * of the pixel grid: angles whose fixed-point (C, S) are (a, b), (-a, b), (b, a) and
  * (-b, a) (e.g. theta, pi - theta, pi/2 - theta, pi/2 + theta) share one job, one ray
- * march and one staged detector coordinate per pixel.  FP32 plans with ds >= h take
- * the path when every angle is such an image of its canonical pair and the jobs hold
+ * march and one staged detector coordinate per pixel.  FP32 and BF16 plans with
+ * ds >= h take the path when every angle is such an image of its canonical pair and the jobs hold
  * two angles or more on average (uniform angles over [0, pi) with an even count).
  * Results equal those of the per-angle path up to the order of FP32 summation. */
 int ctr_plan_symmetric_jobs(const ctr_plan *plan);

@@ -143,6 +143,7 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     if ((st = alloc(p, &tmp, sizeof(OrbitJob) * jobs.size())) != CTR_OK) return st;
     p->d_jobs = (OrbitJob *)tmp;
     if ((st = alloc(p, &p->ubar, sizeof(float4) * (size_t)n * n)) != CTR_OK) return st;
+    // (the orbit image holds FP32 records; a BF16 plan's bfloat16 records use its first half)
     // the symmetric backprojection: job groups so that tiles x groups fills the GPU
     // (~8 CTAs of 4 warps per SM on 152 SMs), at least 8 jobs per group
     const int tiles = ((n + 31) / 32) * ((n + 31) / 32);
@@ -204,7 +205,7 @@ ctr_status build_tables(ctr_plan *p)
     p->wstride = (int)wmax;
     CTR_CUDA(cudaMemcpy(p->d_geom, geo.data(), sizeof(AngleGeom) * N, cudaMemcpyHostToDevice));
     CTR_CUDA(cudaMemcpy(p->d_march, mar.data(), sizeof(AngleMarch) * N, cudaMemcpyHostToDevice));
-    if (p->F == 32 && !p->bf16 && p->h <= p->ds && ncand == 2) return build_orbit_jobs(p, geo);
+    if (p->F == 32 && p->h <= p->ds && ncand == 2) return build_orbit_jobs(p, geo);
     return CTR_OK;
 }
 
@@ -490,7 +491,9 @@ ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
         return op_forward<double>(p, (const double *)u, (const double *)p->uT, (double *)g, 1.0, s);
     }
     if (p->bf16) {
-        if ((st = launch_transpose<__nv_bfloat16>(p, (const __nv_bfloat16 *)u, p->uTh, s)) != CTR_OK) return st;
+        if (fwd_needs_transpose<float>(p) &&
+            (st = launch_transpose<__nv_bfloat16>(p, (const __nv_bfloat16 *)u, p->uTh, s)) != CTR_OK)
+            return st;
         return op_forward_bf16(p, (const __nv_bfloat16 *)u, p->uTh, (float *)g, s);
     }
     if (fwd_needs_transpose<float>(p) && (st = launch_transpose<float>(p, (const float *)u, (float *)p->uT, s)) != CTR_OK)

@@ -482,13 +482,33 @@ k_forward(const S *__restrict__ u, const S *__restrict__ uT, int n, int N, int M
 // job's up to four angles, reading the four channels of the orbit image at once.
 // ---------------------------------------------------------------------------
 
+// Orbit-image records: the four channels of one pixel, FP32 (float4) or bfloat16
+// (uint2, channel 0 in the low half of x).  rec_f32 widens a record to FP32.
+template <typename S> struct OrbitRec;
+template <> struct OrbitRec<float> { using type = float4; };
+template <> struct OrbitRec<__nv_bfloat16> { using type = uint2; };
+__device__ __forceinline__ float4 rec_f32(float4 v) { return v; }
+__device__ __forceinline__ float4 rec_f32(uint2 v)
+{
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u), __uint_as_float(v.y << 16),
+                       __uint_as_float(v.y & 0xFFFF0000u));
+}
+__device__ __forceinline__ float4 make_rec(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ uint2 make_rec(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d)
+{
+    return make_uint2((unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16),
+                      (unsigned)__bfloat16_as_ushort(c) | ((unsigned)__bfloat16_as_ushort(d) << 16));
+}
+
 // ubar[m][q] = (u[q][m], u[n-1-q][m], u[m][q], u[n-1-m][q]): channel v holds
 // u(T_v^{-1}(q, m)) for the canonical march pixel (q, m) (pick q = i, march m = j).
 // 32 x 32 tiles: four coalesced tile loads (two of them transposed through shared
-// memory), one coalesced float4 store per record.
-__global__ void __launch_bounds__(256) k_orbit_image(const float *__restrict__ u, float4 *__restrict__ ubar, int n)
+// memory), one coalesced record store per pixel.
+template <typename S>
+__global__ void __launch_bounds__(256)
+k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar, int n)
 {
-    __shared__ float tA[32][33], tB[32][33], tC[32][33], tD[32][33];
+    __shared__ S tA[32][33], tB[32][33], tC[32][33], tD[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int q0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
     for (int r = ty; r < 32; r += 8) {
@@ -506,7 +526,7 @@ __global__ void __launch_bounds__(256) k_orbit_image(const float *__restrict__ u
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int m = m0 + r, q = q0 + tx;
-        if (m < n && q < n) ubar[(size_t)m * n + q] = make_float4(tC[tx][r], tD[tx][r], tA[r][tx], tB[r][tx]);
+        if (m < n && q < n) ubar[(size_t)m * n + q] = make_rec(tC[tx][r], tD[tx][r], tA[r][tx], tB[r][tx]);
     }
 }
 
@@ -524,8 +544,8 @@ __device__ __forceinline__ void acc4(float4 &Su, float4 &Sf, float4 v, float f)
 
 // The canonical march (flip 0, B >= 0) over `rows` rows of the orbit image; the
 // state and the second-pixel rule are those of march32.
-template <bool BPOS, bool CHECK>
-__device__ __forceinline__ void march_orbit(const float4 *__restrict__ ub, int n, int rows, unsigned &r, int &q,
+template <bool BPOS, bool CHECK, typename R>
+__device__ __forceinline__ void march_orbit(const R *__restrict__ ub, int n, int rows, unsigned &r, int &q,
                                             int &off, unsigned A32, unsigned lim, unsigned B32, unsigned thr,
                                             float4 &Su, float4 &Sf)
 {
@@ -534,11 +554,11 @@ __device__ __forceinline__ void march_orbit(const float4 *__restrict__ ub, int n
     for (int rr = 0; rr < rows; ++rr) {
         float4 v1, v2;
         if constexpr (CHECK) {
-            v1 = ((unsigned)q < (unsigned)n) ? ub[off] : zero;
-            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ub[off + 1] : zero;
+            v1 = ((unsigned)q < (unsigned)n) ? rec_f32(ub[off]) : zero;
+            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? rec_f32(ub[off + 1]) : zero;
         } else {
-            v1 = ub[off];
-            v2 = r < lim ? ub[off + 1] : zero;
+            v1 = rec_f32(ub[off]);
+            v2 = r < lim ? rec_f32(ub[off + 1]) : zero;
         }
         acc4(Su, Sf, v1, one_plus_frac32u(r));
         acc4(Su, Sf, v2, one_plus_frac32u(r + A32));
@@ -556,8 +576,8 @@ __device__ __forceinline__ void march_orbit(const float4 *__restrict__ ub, int n
     }
 }
 
-template <bool BPOS>
-__device__ __forceinline__ void march_orbit_rows(const float4 *__restrict__ ub, int n, long long K,
+template <bool BPOS, typename R>
+__device__ __forceinline__ void march_orbit_rows(const R *__restrict__ ub, int n, long long K,
                                                  const AngleMarch &am, int mlo, int mhi, int ilo, int ihi,
                                                  float4 &Su, float4 &Sf)
 {
@@ -603,9 +623,10 @@ constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
 // Warp w of the CTA takes job by*4 + (w & 3), bins bx*31 + [0, 31) and the
 // (w >> 2)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
+template <typename S>
 __global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
-k_forward_orbit(const float4 *__restrict__ ubar, int n, int n_jobs, int M, const OrbitJob *__restrict__ jobs,
-                ForwardEpi<float> epi)
+k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
+                const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
 {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -688,8 +709,9 @@ size_t obp_smem(int wstride)
     return stage > tr ? stage : tr;
 }
 
+template <typename S>
 __global__ void __launch_bounds__(32 * BP_TY, CTR_OBP_MINB)
-k_backproject_orbit(const float *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
+k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
                     const OrbitJob *__restrict__ jobs, float *__restrict__ part)
 {
     static_assert(BP_TI == 32 && BP_TJ == 32, "square tiles");
@@ -715,13 +737,13 @@ k_backproject_orbit(const float *__restrict__ g, int n, int M, int wstride, int 
         __syncthreads();
         if (threadIdx.x < na) {
             const AngleMarch am = jobs[c0 + threadIdx.x].am;     // canonical P(i, j) = i A + j B + Op
-            const long long C = am.A, S = am.B;
-            const long long P00 = (long long)i0 * C + (long long)j0 * S + am.Op;
-            const long long kmin = P00 >> 32;                    // C, S >= 0: P00 is the tile's minimum
+            const long long Cc = am.A, Sc = am.B;
+            const long long P00 = (long long)i0 * Cc + (long long)j0 * Sc + am.Op;
+            const long long kmin = P00 >> 32;                    // Cc, Sc >= 0: P00 is the tile's minimum
             sK[threadIdx.x] = (int)kmin;
             sPb[threadIdx.x] = P00 - (kmin << 32);
-            sC[threadIdx.x] = C;
-            sS[threadIdx.x] = S;
+            sC[threadIdx.x] = Cc;
+            sS[threadIdx.x] = Sc;
         }
         if (threadIdx.x < 4 * na) sL[threadIdx.x] = jobs[c0 + (threadIdx.x >> 2)].l[threadIdx.x & 3];
         __syncthreads();
@@ -730,9 +752,9 @@ k_backproject_orbit(const float *__restrict__ g, int n, int M, int wstride, int 
             const int c = e & 3, rest = e >> 2;
             const int a = rest / wstride, w = rest - a * wstride;
             const int k = sK[a] + w, l = sL[4 * a + c];
-            const float *row = g + (size_t)(l < 0 ? 0 : l) * M;
-            const float g0 = (l >= 0 && k >= 0 && k < M) ? row[k] : 0.f;
-            const float g1 = (l >= 0 && k + 1 >= 0 && k + 1 < M) ? row[k + 1] : 0.f;
+            const S *row = g + (size_t)(l < 0 ? 0 : l) * M;
+            const float g0 = (l >= 0 && k >= 0 && k < M) ? ldv(row + k) : 0.f;
+            const float g1 = (l >= 0 && k + 1 >= 0 && k + 1 < M) ? ldv(row + k + 1) : 0.f;
             // float4 planes (ch0 ch1) and (ch2 ch3) of the job, consecutive bins adjacent
             st2[((size_t)(2 * a + (c >> 1)) * wstride + w) * 2 + (c & 1)] = make_stage(g0, g1);
         }
@@ -876,13 +898,13 @@ void launch_fwd_cfg(const ctr_plan *p, dim3 grid, const S *u, const S *uT, const
 template <typename T, typename S>
 ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cudaStream_t s, bool defer_reduce)
 {
-    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+    if constexpr (sizeof(T) == 4) {
         if (p->orbit) {
             const int G = p->obp_groups;
             dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
             float *part = (float *)p->obp_part;
             p->launches++;
-            k_backproject_orbit<<<grid, 32 * BP_TY, obp_smem(p->wstride), s>>>(
+            k_backproject_orbit<S><<<grid, 32 * BP_TY, obp_smem(p->wstride), s>>>(
                 g, p->n, p->M, p->wstride, (p->n_jobs + G - 1) / G, p->n_jobs, p->d_jobs, part);
             CTR_CHECK_LAUNCH("k_backproject_orbit");
             if (!defer_reduce) {
@@ -919,14 +941,15 @@ template <typename T, typename S>
 ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
 {
     const bool exact1 = p->h <= p->ds;
-    if constexpr (sizeof(T) == 4 && sizeof(S) == 4) {
+    if constexpr (sizeof(T) == 4) {
         if (p->orbit) {
-            float4 *ub = (float4 *)p->ubar;
+            using R = typename OrbitRec<S>::type;
+            R *ub = (R *)p->ubar;
             p->launches++;
-            k_orbit_image<<<dim3((p->n + 31) / 32, (p->n + 31) / 32), 256, 0, s>>>(u, ub, p->n);
+            k_orbit_image<S><<<dim3((p->n + 31) / 32, (p->n + 31) / 32), 256, 0, s>>>(u, ub, p->n);
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
-            k_forward_orbit<<<dim3(fwd_grid_x(p->M), (p->n_jobs + 3) / 4), ORBIT_THREADS, 0, s>>>(
+            k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + 3) / 4), ORBIT_THREADS, 0, s>>>(
                 ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
             CTR_CHECK_LAUNCH("k_forward_orbit");
             return CTR_OK;
@@ -956,7 +979,8 @@ ctr_status configure_radon(const ctr_plan *p)
 {
     const size_t smem = bp_smem<T>(p);
     ctr_status st = raise_smem_limit(k_backproject<T, T>, smem);
-    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit, obp_smem(p->wstride));
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float>, obp_smem(p->wstride));
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, obp_smem(p->wstride));
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
     return st;

@@ -501,7 +501,8 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     // B: u += F^{-1}(F(u_tmp) m), and uT (or the bfloat16 copies of u and uT)
     T *uT_out = (h || !fwd_needs_transpose<T>(p)) ? nullptr : (T *)p->uT;
     if ((st = launch_circulant<T>(p, nullptr, true, (const T *)p->sym, (T *)p->u, 1, uT_out,
-                                  diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr, h ? p->uTh : nullptr,
+                                  diag ? (T *)p->du : nullptr, s, h ? p->uh : nullptr,
+                                  (h && fwd_needs_transpose<T>(p)) ? p->uTh : nullptr,
                                   fuse ? &ea : nullptr)) != CTR_OK)
         return st;
     // C: ray-driven Rt u with the data-dual step

@@ -59,9 +59,9 @@ def test_forward_adjoint_match_oracle(ct, geom, dtype):
 
 
 def test_symmetric_path_selection(ct):
-    """FP32 plans with uniform angles over [0, pi) and an even count take the symmetric
-    path (at most one job per two angles); odd counts, angles outside [0, pi), FP64 and
-    BF16 plans project angle by angle."""
+    """FP32 and BF16 plans with uniform angles over [0, pi) and an even count take the
+    symmetric path (at most one job per two angles); odd counts, angles outside [0, pi),
+    FP64 plans and pixels smaller than ds/2 (three per interval) project angle by angle."""
     uni = lambda N: np.arange(N) * (np.pi / N)
     p = ct.Plan(64, 90, 95, angles=uni(90))
     assert 0 < p.symmetric_jobs <= 45
@@ -69,7 +69,7 @@ def test_symmetric_path_selection(ct):
     assert ct.Plan(64, 45, 95, angles=uni(45)).symmetric_jobs == 0
     assert ct.Plan(64, 33, 95, angles=_angles(33, "random", 1)).symmetric_jobs == 0
     assert ct.Plan(64, 90, 95, angles=uni(90), dtype="f64").symmetric_jobs == 0
-    assert ct.Plan(64, 90, 95, angles=uni(90), dtype="bf16").symmetric_jobs == 0
+    assert ct.Plan(64, 90, 95, angles=uni(90), dtype="bf16").symmetric_jobs > 0
     assert ct.Plan(48, 40, 70, angles=uni(40), h=0.8).symmetric_jobs > 0      # two pixels per interval
     assert ct.Plan(48, 40, 70, angles=uni(40), h=0.6).symmetric_jobs == 0     # three pixels per interval
 
