@@ -176,14 +176,21 @@ struct SliceDesc {
     const float2 *tw;
     const float *sym;
     FftPasses fp;
-    float *u, *uT, *y1, *y2, *v2b, *bp_part;
+    float *u, *uT, *y1, *y2, *v2b, *bp_part;   // bp_part: angle-group images, or the symmetric planes
+    int orbit;                    // symmetric projector path (per_group, bp_groups count jobs)
+    int n_jobs;
+    const OrbitJob *jobs;
+    float4 *ubar;
     BackprojEpi<float> bpe;       // step A epilogue
     ForwardEpi<float> fwe;        // step C epilogue
     float sigma, tau, lam, inv_h;
 };
 
 // Stages of one batched iteration (block counts per slice are prefix-summed).
-enum BatchStage { BS_BP = 0, BS_BP_REDUCE, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_FWD, BS_TV, BS_COUNT };
+// The angle-group sum / symmetric fold of the backprojection runs inside BS_FFT_ROWS;
+// BS_ORBIT and BS_FWD_SYM serve the slices on the symmetric path, BS_FWD the others.
+enum BatchStage { BS_BP = 0, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_ORBIT, BS_FWD, BS_FWD_SYM, BS_TV,
+                  BS_COUNT };
 
 }  // namespace ctr
 
@@ -295,6 +302,7 @@ int fwd_grid_y(int N);         // forward-projector grid: angle groups
 
 // batched stages (one launch per stage over all slices of a batch)
 size_t bp_smem_bytes(int wstride);
+size_t obp_smem_bytes(int wstride);   // the symmetric backprojection's dynamic shared memory
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
 int fft_cols_per_cta(int n, size_t esize);

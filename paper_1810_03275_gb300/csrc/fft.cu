@@ -393,7 +393,14 @@ k_fft_rows_fwd_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_rows_fwd_body<float>(RowsInput<float>{}, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
+    RowsInput<float> src{};
+    if (d.orbit || d.bp_groups > 1) {             // the backprojection left partial images
+        src.part = d.bp_part;
+        src.groups = d.bp_groups;
+        src.orbit = d.orbit;
+        src.epi = d.bpe;
+    }
+    fft_rows_fwd_body<float>(src, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS)
@@ -409,8 +416,8 @@ k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.uT, nullptr, nullptr, nullptr,
-                             blockIdx.x - prefix[s]);
+    fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr, nullptr,
+                             nullptr, blockIdx.x - prefix[s]);
 }
 
 // Preconditioner symbols (Alg. 4, Sec. 4.3.1), with 1/n^2 of the inverse DFT:

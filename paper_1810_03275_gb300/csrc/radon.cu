@@ -505,12 +505,12 @@ __device__ __forceinline__ uint2 make_rec(__nv_bfloat16 a, __nv_bfloat16 b, __nv
 // 32 x 32 tiles: four coalesced tile loads (two of them transposed through shared
 // memory), one coalesced record store per pixel.
 template <typename S>
-__global__ void __launch_bounds__(256)
-k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar, int n)
+__device__ __forceinline__ void orbit_image_body(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar,
+                                                 int n, int bx, int by)
 {
     __shared__ S tA[32][33], tB[32][33], tC[32][33], tD[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int q0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+    const int q0 = bx * 32, m0 = by * 32;
     for (int r = ty; r < 32; r += 8) {
         const int mr = m0 + r, qc = q0 + tx;          // tiles A, B: rows m, columns q
         if (mr < n && qc < n) {
@@ -528,6 +528,13 @@ k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ 
         const int m = m0 + r, q = q0 + tx;
         if (m < n && q < n) ubar[(size_t)m * n + q] = make_rec(tC[tx][r], tD[tx][r], tA[r][tx], tB[r][tx]);
     }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256)
+k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar, int n)
+{
+    orbit_image_body<S>(u, ubar, n, blockIdx.x, blockIdx.y);
 }
 
 __device__ __forceinline__ void acc4(float4 &Su, float4 &Sf, float4 v, float f)
@@ -624,15 +631,15 @@ constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
 // (w >> 2)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
 template <typename S>
-__global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
-k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
-                const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
+__device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
+                                                   int n_jobs, int M, const OrbitJob *__restrict__ jobs,
+                                                   const ForwardEpi<float> &epi, int bx, int by)
 {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int slot = warp & 3, seg = warp >> 2;
-    const int jb = blockIdx.y * 4 + slot;
-    const int kb = blockIdx.x * 31;
+    const int jb = by * 4 + slot;
+    const int kb = bx * 31;
     const int k = kb + lane - 1;
     const bool active = jb < n_jobs && kb < M;        // warp-uniform
     float4 Su = make_float4(0.f, 0.f, 0.f, 0.f), Sf = Su;
@@ -687,6 +694,14 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
     orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
 }
 
+template <typename S>
+__global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
+k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
+                const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
+{
+    forward_orbit_body<S>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Symmetric backprojection (OrbitJob): a CTA owns a 32 x 32 tile of canonical
 // pixels x and a group of jobs; per job it stages the four channels' sinogram rows
@@ -710,9 +725,9 @@ size_t obp_smem(int wstride)
 }
 
 template <typename S>
-__global__ void __launch_bounds__(32 * BP_TY, CTR_OBP_MINB)
-k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
-                    const OrbitJob *__restrict__ jobs, float *__restrict__ part)
+__device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group,
+                                         int n_jobs, const OrbitJob *__restrict__ jobs, float *__restrict__ part,
+                                         int bx, int by, int bz)
 {
     static_assert(BP_TI == 32 && BP_TJ == 32, "square tiles");
     constexpr int NT = 32 * BP_TY;
@@ -725,8 +740,8 @@ k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs
     int *sL = sK + OBP_JCH;                                               // [job][channel]
 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int i0 = blockIdx.y * BP_TI, j0 = blockIdx.x * BP_TJ;
-    const int la = blockIdx.z * jobs_per_group;
+    const int i0 = by * BP_TI, j0 = bx * BP_TJ;
+    const int la = bz * jobs_per_group;
     const int lb = min(n_jobs, la + jobs_per_group);
     float acc[BP_R][4];
 #pragma unroll
@@ -781,7 +796,7 @@ k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs
     }
 
     const size_t nn = (size_t)n * n;
-    float *pg = part + (size_t)blockIdx.z * 4 * nn;
+    float *pg = part + (size_t)bz * 4 * nn;
     const int j = j0 + tx;
 #pragma unroll
     for (int r = 0; r < BP_R; ++r) {
@@ -809,6 +824,14 @@ k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs
             pg[3 * nn + (size_t)jt * n + it] = tr[1][tx][jl];
         }
     }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(32 * BP_TY, CTR_OBP_MINB)
+k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
+                    const OrbitJob *__restrict__ jobs, float *__restrict__ part)
+{
+    obp_body<S>(g, n, M, wstride, jobs_per_group, n_jobs, jobs, part, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The fold of the symmetric backprojection's partial planes, then the
@@ -844,16 +867,29 @@ k_backproject_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ pr
     const int local = blockIdx.x - prefix[s];
     const int bx = local % d.bp_tiles_x, rest = local / d.bp_tiles_x;
     const int by = rest % d.bp_tiles_y, bz = rest / d.bp_tiles_y;
-    bp_body<float, float>(d.y1, d.n, d.N, d.M, 32, d.wstride, d.per_group, d.geom, d.bpe,
-                          d.bp_groups > 1 ? d.bp_part : nullptr, bx, by, bz);
+    if (d.orbit)                                  // block-uniform: one slice per block
+        obp_body<float>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
+    else
+        bp_body<float, float>(d.y1, d.n, d.N, d.M, 32, d.wstride, d.per_group, d.geom, d.bpe,
+                              d.bp_groups > 1 ? d.bp_part : nullptr, bx, by, bz);
 }
 
 __global__ void __launch_bounds__(256)
-k_bp_reduce_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+k_orbit_image_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
 {
     const int s = find_slice(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    bp_reduce_body<float>(d.bp_part, d.bp_groups, d.n, d.bpe, blockIdx.x - prefix[s], prefix[s + 1] - prefix[s]);
+    const int local = blockIdx.x - prefix[s], tiles = (d.n + 31) / 32;
+    orbit_image_body<float>(d.u, d.ubar, d.n, local % tiles, local / tiles);
+}
+
+__global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
+k_forward_orbit_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    const int local = blockIdx.x - prefix[s];
+    forward_orbit_body<float>(d.ubar, d.n, d.n_jobs, d.M, d.jobs, d.fwe, local % d.fwd_chunks, local / d.fwd_chunks);
 }
 
 __global__ void __launch_bounds__(FWD_THREADS)
@@ -1034,6 +1070,8 @@ template bool bp_deferred<double>(const ctr_plan *);
 int fwd_grid_x(int M) { return (M + 30) / 31; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
 
+size_t obp_smem_bytes(int wstride) { return obp_smem(wstride); }
+
 size_t bp_smem_bytes(int wstride)
 {
     return sizeof(float2) * BP_ACH * wstride + 3 * sizeof(long long) * BP_ACH + sizeof(int) * BP_ACH;
@@ -1057,7 +1095,8 @@ ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix,
     if (blocks <= 0) return CTR_OK;
     switch (stage) {
     case BS_BP: k_backproject_batch<<<blocks, 32 * BP_TY, smem, s>>>(sd, prefix, ns); break;
-    case BS_BP_REDUCE: k_bp_reduce_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns); break;
+    case BS_ORBIT: k_orbit_image_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns); break;
+    case BS_FWD_SYM: k_forward_orbit_batch<<<blocks, ORBIT_THREADS, 0, s>>>(sd, prefix, ns); break;
     case BS_FWD: k_forward_batch<<<blocks, FWD_THREADS, 0, s>>>(sd, prefix, ns); break;
     default: return fail(CTR_EINVAL, "not a projector stage");
     }

@@ -915,8 +915,13 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.N = p->N;
         d.M = p->M;
         d.wstride = p->wstride;
-        d.bp_groups = p->bp_groups;
-        d.per_group = (p->N + p->bp_groups - 1) / p->bp_groups;
+        d.orbit = p->orbit ? 1 : 0;
+        d.n_jobs = p->n_jobs;
+        d.jobs = p->d_jobs;
+        d.ubar = (float4 *)p->ubar;
+        d.bp_groups = p->orbit ? p->obp_groups : p->bp_groups;
+        d.per_group = p->orbit ? (p->n_jobs + p->obp_groups - 1) / p->obp_groups
+                               : (p->N + p->bp_groups - 1) / p->bp_groups;
         bp_tiles(p->n, d.bp_tiles_x, d.bp_tiles_y);
         d.fwd_chunks = fwd_grid_x(p->M);
         d.rpc = fft_rows_per_cta(p->n);
@@ -933,7 +938,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.y1 = (float *)p->y1;
         d.y2 = (float *)p->y2;
         d.v2b = (float *)p->v2b;
-        d.bp_part = (float *)p->bp_part;
+        d.bp_part = (float *)(p->orbit ? p->obp_part : p->bp_part);
         d.bpe = BackprojEpi<float>{};
         d.bpe.out = (float *)p->cbuf;
         d.bpe.complex_out = 1;
@@ -967,10 +972,10 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         const int *pre = b->d_prefix;
         const int stride = ns + 1;
         if ((r = launch_batch_radon(BS_BP, b->d_desc, pre + BS_BP * stride, ns, b->blocks[BS_BP], b->smem[BS_BP], s)) != CTR_OK) return r;
-        if ((r = launch_batch_radon(BS_BP_REDUCE, b->d_desc, pre + BS_BP_REDUCE * stride, ns, b->blocks[BS_BP_REDUCE], 0, s)) != CTR_OK) return r;
         for (int stg = BS_FFT_ROWS; stg <= BS_FFT_ROWS_INV; ++stg)
             if ((r = launch_batch_fft(stg, b->d_desc, pre + stg * stride, ns, b->blocks[stg], b->smem[stg], s)) != CTR_OK) return r;
-        if ((r = launch_batch_radon(BS_FWD, b->d_desc, pre + BS_FWD * stride, ns, b->blocks[BS_FWD], 0, s)) != CTR_OK) return r;
+        for (int stg : {BS_ORBIT, BS_FWD, BS_FWD_SYM})
+            if ((r = launch_batch_radon(stg, b->d_desc, pre + stg * stride, ns, b->blocks[stg], 0, s)) != CTR_OK) return r;
         if ((r = launch_batch_tv(b->d_desc, pre + BS_TV * stride, ns, b->blocks[BS_TV], s)) != CTR_OK) return r;
         int nl = 0;
         for (int stg = 0; stg < BS_COUNT; ++stg) nl += b->blocks[stg] > 0 ? 1 : 0;
@@ -1042,15 +1047,17 @@ ctr_status batch_prepare(ctr_batch *b)
         const size_t nn = (size_t)p->n * p->n;
         const int rpc = fft_rows_per_cta(p->n), cw = fft_cols_per_cta(p->n, 4);
         int cnt[BS_COUNT];
-        cnt[BS_BP] = tx * ty * p->bp_groups;
-        cnt[BS_BP_REDUCE] = p->bp_groups > 1 ? grid_for(nn, 256, 1024) : 0;
+        const int t32 = (p->n + 31) / 32;
+        cnt[BS_BP] = tx * ty * (p->orbit ? p->obp_groups : p->bp_groups);
         cnt[BS_FFT_ROWS] = (p->n + rpc - 1) / rpc;
         cnt[BS_FFT_COLS] = (p->n + cw - 1) / cw;
         cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
-        cnt[BS_FWD] = fwd_grid_x(p->M) * fwd_grid_y(p->N);
+        cnt[BS_ORBIT] = p->orbit ? t32 * t32 : 0;
+        cnt[BS_FWD] = p->orbit ? 0 : fwd_grid_x(p->M) * fwd_grid_y(p->N);
+        cnt[BS_FWD_SYM] = p->orbit ? fwd_grid_x(p->M) * ((p->n_jobs + 3) / 4) : 0;
         cnt[BS_TV] = grid_for(nn, 256, 1024);
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
-        const size_t smb = bp_smem_bytes(p->wstride);
+        const size_t smb = p->orbit ? obp_smem_bytes(p->wstride) : bp_smem_bytes(p->wstride);
         const size_t smr = 2 * (size_t)rpc * p->n * sizeof(float2), smc = 2 * (size_t)cw * (p->n + 1) * sizeof(float2);
         if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
         if (smr > b->smem[BS_FFT_ROWS]) b->smem[BS_FFT_ROWS] = smr;

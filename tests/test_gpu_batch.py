@@ -33,6 +33,8 @@ def test_batch_matches_single_slices_and_oracle(ct):
     batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
     fs = [to_dev(p.f, torch.float32) for p in probs]
     ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    # even view counts take the symmetric path, odd ones the per-angle path: both in one batch
+    assert [pl.symmetric_jobs > 0 for pl in batch.plans] == [True, False, True, False, False]
     betas, cs = [], []
     for p in probs:
         geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
