@@ -188,9 +188,10 @@ struct SliceDesc {
 
 // Stages of one batched iteration (block counts per slice are prefix-summed).
 // The angle-group sum / symmetric fold of the backprojection runs inside BS_FFT_ROWS;
-// BS_ORBIT and BS_FWD_SYM serve the slices on the symmetric path, BS_FWD the others.
-enum BatchStage { BS_BP = 0, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_ORBIT, BS_FWD, BS_FWD_SYM, BS_TV,
-                  BS_COUNT };
+// BS_BP_SYM, BS_ORBIT and BS_FWD_SYM serve the slices on the symmetric path, BS_BP and
+// BS_FWD the others.
+enum BatchStage { BS_BP = 0, BS_BP_SYM, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_ORBIT, BS_FWD, BS_FWD_SYM,
+                  BS_TV, BS_COUNT };
 
 }  // namespace ctr
 
@@ -306,7 +307,7 @@ size_t obp_smem_bytes(int wstride);   // the symmetric backprojection's dynamic 
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
 int fft_cols_per_cta(int n, size_t esize);
-ctr_status configure_batch_radon(size_t bp_smem);
+ctr_status configure_batch_radon(size_t bp_smem, size_t obp_smem_max);
 ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem);
 ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
                               cudaStream_t s);

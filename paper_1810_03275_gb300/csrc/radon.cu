@@ -624,7 +624,7 @@ constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
 #define CTR_ORBIT_MINB 2
 #endif
 #ifndef CTR_OBP_MINB
-#define CTR_OBP_MINB 6
+#define CTR_OBP_MINB 4
 #endif
 
 // Warp w of the CTA takes job by*4 + (w & 3), bins bx*31 + [0, 31) and the
@@ -712,6 +712,14 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
 // so that the fold reads rows only:
 //   u(i, j) = sum_groups P0[i][j] + P1[n-1-i][j] + P2[i][j] + P3[n-1-i][j].
 // ---------------------------------------------------------------------------
+#ifndef CTR_OBP_TY
+#define CTR_OBP_TY 8
+#endif
+#ifndef CTR_OBP_R
+#define CTR_OBP_R 4
+#endif
+constexpr int OBP_TY = CTR_OBP_TY;     // warps of a symmetric-backprojection CTA (32 x 32 tile)
+constexpr int OBP_R = CTR_OBP_R;       // pixels per thread (rows i0 + ty + OBP_TY r)
 #ifndef CTR_OBP_JCH
 #define CTR_OBP_JCH 8
 #endif
@@ -729,8 +737,8 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
                                          int n_jobs, const OrbitJob *__restrict__ jobs, float *__restrict__ part,
                                          int bx, int by, int bz)
 {
-    static_assert(BP_TI == 32 && BP_TJ == 32, "square tiles");
-    constexpr int NT = 32 * BP_TY;
+    static_assert(OBP_TY * OBP_R == 32, "32 x 32 tiles");
+    constexpr int NT = 32 * OBP_TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *stage = reinterpret_cast<float4 *>(smem_raw);               // [job][channel pair][bin]
     long long *sPb = reinterpret_cast<long long *>(stage + 2 * OBP_JCH * wstride);
@@ -740,12 +748,12 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
     int *sL = sK + OBP_JCH;                                               // [job][channel]
 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int i0 = by * BP_TI, j0 = bx * BP_TJ;
+    const int i0 = by * 32, j0 = bx * 32;
     const int la = bz * jobs_per_group;
     const int lb = min(n_jobs, la + jobs_per_group);
-    float acc[BP_R][4];
+    float acc[OBP_R][4];
 #pragma unroll
-    for (int r = 0; r < BP_R; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+    for (int r = 0; r < OBP_R; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
 
     for (int c0 = la; c0 < lb; c0 += OBP_JCH) {
         const int na = min(OBP_JCH, lb - c0);
@@ -778,11 +786,11 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
         for (int a = 0; a < na; ++a) {
             const long long C = sC[a];
             long long P = sPb[a] + (long long)ty * C + (long long)tx * sS[a];
-            const long long D = C * BP_TY;
+            const long long D = C * OBP_TY;
             const float4 *row01 = stage + 2 * a * wstride;
             const float4 *row23 = row01 + wstride;
 #pragma unroll
-            for (int r = 0; r < BP_R; ++r) {
+            for (int r = 0; r < OBP_R; ++r) {
                 const int b = (int)(P >> 32);
                 const float f = one_plus_frac32(P);
                 const float4 s01 = row01[b], s23 = row23[b];
@@ -799,8 +807,8 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
     float *pg = part + (size_t)bz * 4 * nn;
     const int j = j0 + tx;
 #pragma unroll
-    for (int r = 0; r < BP_R; ++r) {
-        const int i = i0 + ty + BP_TY * r;
+    for (int r = 0; r < OBP_R; ++r) {
+        const int i = i0 + ty + OBP_TY * r;
         if (i < n && j < n) {
             pg[(size_t)i * n + j] = acc[r][0];
             pg[nn + (size_t)i * n + j] = acc[r][1];
@@ -810,15 +818,15 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
     __syncthreads();
     float(*tr)[32][33] = reinterpret_cast<float(*)[32][33]>(smem_raw);
 #pragma unroll
-    for (int r = 0; r < BP_R; ++r) {
-        tr[0][ty + BP_TY * r][tx] = acc[r][2];
-        tr[1][ty + BP_TY * r][tx] = acc[r][3];
+    for (int r = 0; r < OBP_R; ++r) {
+        tr[0][ty + OBP_TY * r][tx] = acc[r][2];
+        tr[1][ty + OBP_TY * r][tx] = acc[r][3];
     }
     __syncthreads();
     const int it = i0 + tx;
 #pragma unroll
-    for (int r = 0; r < BP_R; ++r) {
-        const int jl = ty + BP_TY * r, jt = j0 + jl;
+    for (int r = 0; r < OBP_R; ++r) {
+        const int jl = ty + OBP_TY * r, jt = j0 + jl;
         if (it < n && jt < n) {
             pg[2 * nn + (size_t)jt * n + it] = tr[0][tx][jl];
             pg[3 * nn + (size_t)jt * n + it] = tr[1][tx][jl];
@@ -827,7 +835,7 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
 }
 
 template <typename S>
-__global__ void __launch_bounds__(32 * BP_TY, CTR_OBP_MINB)
+__global__ void __launch_bounds__(32 * OBP_TY, CTR_OBP_MINB)
 k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
                     const OrbitJob *__restrict__ jobs, float *__restrict__ part)
 {
@@ -867,11 +875,19 @@ k_backproject_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ pr
     const int local = blockIdx.x - prefix[s];
     const int bx = local % d.bp_tiles_x, rest = local / d.bp_tiles_x;
     const int by = rest % d.bp_tiles_y, bz = rest / d.bp_tiles_y;
-    if (d.orbit)                                  // block-uniform: one slice per block
-        obp_body<float>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
-    else
-        bp_body<float, float>(d.y1, d.n, d.N, d.M, 32, d.wstride, d.per_group, d.geom, d.bpe,
-                              d.bp_groups > 1 ? d.bp_part : nullptr, bx, by, bz);
+    bp_body<float, float>(d.y1, d.n, d.N, d.M, 32, d.wstride, d.per_group, d.geom, d.bpe,
+                          d.bp_groups > 1 ? d.bp_part : nullptr, bx, by, bz);
+}
+
+__global__ void __launch_bounds__(32 * OBP_TY, CTR_OBP_MINB)
+k_backproject_orbit_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix, int ns)
+{
+    const int s = find_slice(prefix, ns, blockIdx.x);
+    const SliceDesc &d = sd[s];
+    const int local = blockIdx.x - prefix[s];
+    const int bx = local % d.bp_tiles_x, rest = local / d.bp_tiles_x;
+    const int by = rest % d.bp_tiles_y, bz = rest / d.bp_tiles_y;
+    obp_body<float>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
 }
 
 __global__ void __launch_bounds__(256)
@@ -940,7 +956,7 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
             dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
             float *part = (float *)p->obp_part;
             p->launches++;
-            k_backproject_orbit<S><<<grid, 32 * BP_TY, obp_smem(p->wstride), s>>>(
+            k_backproject_orbit<S><<<grid, 32 * OBP_TY, obp_smem(p->wstride), s>>>(
                 g, p->n, p->M, p->wstride, (p->n_jobs + G - 1) / G, p->n_jobs, p->d_jobs, part);
             CTR_CHECK_LAUNCH("k_backproject_orbit");
             if (!defer_reduce) {
@@ -1083,9 +1099,11 @@ void bp_tiles(int n, int &tx, int &ty)
     ty = (n + BP_TI - 1) / BP_TI;
 }
 
-ctr_status configure_batch_radon(size_t bp_smem)
+ctr_status configure_batch_radon(size_t bp_smem, size_t obp_smem_max)
 {
-    return raise_smem_limit(k_backproject_batch, bp_smem);
+    ctr_status st = raise_smem_limit(k_backproject_batch, bp_smem);
+    if (st == CTR_OK) st = raise_smem_limit(k_backproject_orbit_batch, obp_smem_max);
+    return st;
 }
 
 // One batched projector stage over all slices (blocks = total CTAs of the stage).
@@ -1095,6 +1113,7 @@ ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix,
     if (blocks <= 0) return CTR_OK;
     switch (stage) {
     case BS_BP: k_backproject_batch<<<blocks, 32 * BP_TY, smem, s>>>(sd, prefix, ns); break;
+    case BS_BP_SYM: k_backproject_orbit_batch<<<blocks, 32 * OBP_TY, smem, s>>>(sd, prefix, ns); break;
     case BS_ORBIT: k_orbit_image_batch<<<blocks, 256, 0, s>>>(sd, prefix, ns); break;
     case BS_FWD_SYM: k_forward_orbit_batch<<<blocks, ORBIT_THREADS, 0, s>>>(sd, prefix, ns); break;
     case BS_FWD: k_forward_batch<<<blocks, FWD_THREADS, 0, s>>>(sd, prefix, ns); break;

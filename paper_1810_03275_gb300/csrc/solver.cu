@@ -971,7 +971,9 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         ctr_status r;
         const int *pre = b->d_prefix;
         const int stride = ns + 1;
-        if ((r = launch_batch_radon(BS_BP, b->d_desc, pre + BS_BP * stride, ns, b->blocks[BS_BP], b->smem[BS_BP], s)) != CTR_OK) return r;
+        for (int stg : {BS_BP, BS_BP_SYM})
+            if ((r = launch_batch_radon(stg, b->d_desc, pre + stg * stride, ns, b->blocks[stg], b->smem[stg], s)) != CTR_OK)
+                return r;
         for (int stg = BS_FFT_ROWS; stg <= BS_FFT_ROWS_INV; ++stg)
             if ((r = launch_batch_fft(stg, b->d_desc, pre + stg * stride, ns, b->blocks[stg], b->smem[stg], s)) != CTR_OK) return r;
         for (int stg : {BS_ORBIT, BS_FWD, BS_FWD_SYM})
@@ -1048,7 +1050,8 @@ ctr_status batch_prepare(ctr_batch *b)
         const int rpc = fft_rows_per_cta(p->n), cw = fft_cols_per_cta(p->n, 4);
         int cnt[BS_COUNT];
         const int t32 = (p->n + 31) / 32;
-        cnt[BS_BP] = tx * ty * (p->orbit ? p->obp_groups : p->bp_groups);
+        cnt[BS_BP] = p->orbit ? 0 : tx * ty * p->bp_groups;
+        cnt[BS_BP_SYM] = p->orbit ? tx * ty * p->obp_groups : 0;
         cnt[BS_FFT_ROWS] = (p->n + rpc - 1) / rpc;
         cnt[BS_FFT_COLS] = (p->n + cw - 1) / cw;
         cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
@@ -1057,7 +1060,8 @@ ctr_status batch_prepare(ctr_batch *b)
         cnt[BS_FWD_SYM] = p->orbit ? fwd_grid_x(p->M) * ((p->n_jobs + 3) / 4) : 0;
         cnt[BS_TV] = grid_for(nn, 256, 1024);
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
-        const size_t smb = p->orbit ? obp_smem_bytes(p->wstride) : bp_smem_bytes(p->wstride);
+        const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride) : 0;
+        if (smo > b->smem[BS_BP_SYM]) b->smem[BS_BP_SYM] = smo;
         const size_t smr = 2 * (size_t)rpc * p->n * sizeof(float2), smc = 2 * (size_t)cw * (p->n + 1) * sizeof(float2);
         if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
         if (smr > b->smem[BS_FFT_ROWS]) b->smem[BS_FFT_ROWS] = smr;
@@ -1066,7 +1070,7 @@ ctr_status batch_prepare(ctr_batch *b)
     }
     for (int stg = 0; stg < BS_COUNT; ++stg) b->blocks[stg] = pre[(size_t)stg * (ns + 1) + ns];
     CTR_CUDA(cudaMemcpy(b->d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
-    ctr_status st = configure_batch_radon(b->smem[BS_BP]);
+    ctr_status st = configure_batch_radon(b->smem[BS_BP], b->smem[BS_BP_SYM]);
     if (st == CTR_OK) st = configure_batch_fft(b->smem[BS_FFT_ROWS], b->smem[BS_FFT_COLS]);
     return st;
 }
