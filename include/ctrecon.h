@@ -206,9 +206,11 @@ ctr_status tv_pd_vjp_step(ctr_plan *plan, const void *f_dev, const uint8_t *meta
                           double delta, const ctr_params *params, const ctr_state *s0, const ctr_state *s1,
                           void *bu, void *b1, void *b2, void *gf, double *galpha_dev, void *stream);
 
-/* Tuning hook: split the backprojection's angles into `groups` groups whose partial
- * images are summed (more CTAs for small images).  1 <= groups <= the capacity the
- * plan allocated (up to 8 for n <= 1024), else CTR_EINVAL.  No allocation. */
+/* Tuning hook: split the backprojection's angles (on the symmetric path: its jobs, see
+ * ctr_plan_symmetric_jobs) into `groups` groups whose partial images are summed (more
+ * CTAs for small images).  1 <= groups <= the capacity the plan allocated (up to 8 for
+ * n <= 1024), else CTR_EINVAL.  No allocation.  ctr_plan_get_bp_groups returns the
+ * split of the path the plan takes. */
 ctr_status ctr_plan_set_bp_groups(ctr_plan *plan, int groups);
 int ctr_plan_get_bp_groups(const ctr_plan *plan);
 

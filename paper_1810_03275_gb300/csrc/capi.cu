@@ -144,14 +144,18 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     p->d_jobs = (OrbitJob *)tmp;
     if ((st = alloc(p, &p->ubar, sizeof(float4) * (size_t)n * n)) != CTR_OK) return st;
     // (the orbit image holds FP32 records; a BF16 plan's bfloat16 records use its first half)
-    // the symmetric backprojection: job groups so that tiles x groups fills the GPU
-    // (~8 CTAs of 4 warps per SM on 152 SMs), at least 8 jobs per group
+    // the symmetric backprojection: job groups so that tiles x groups is about 1024 CTAs
+    // (~1.7 waves of 4 eight-warp CTAs per SM on 152 SMs; measured best at n = 512 among
+    // 2..8), at least 8 jobs per group; room for up to MAX_BP_GROUPS groups at n <= 1024
+    // so that ctr_plan_set_bp_groups can change the split later
     const int tiles = ((n + 31) / 32) * ((n + 31) / 32);
-    int G = (1216 + tiles - 1) / tiles;
+    int G = (1024 + tiles / 2) / tiles;
     if (G > MAX_BP_GROUPS) G = MAX_BP_GROUPS;
     const int gmax = (int)jobs.size() / 8 > 1 ? (int)jobs.size() / 8 : 1;
     p->obp_groups = G > gmax ? gmax : (G < 1 ? 1 : G);
-    if ((st = alloc(p, &p->obp_part, sizeof(float) * 4 * (size_t)p->obp_groups * n * n)) != CTR_OK) return st;
+    p->obp_cap = n <= 1024 ? (gmax < MAX_BP_GROUPS ? gmax : MAX_BP_GROUPS) : p->obp_groups;
+    if (p->obp_cap < p->obp_groups) p->obp_cap = p->obp_groups;
+    if ((st = alloc(p, &p->obp_part, sizeof(float) * 4 * (size_t)p->obp_cap * n * n)) != CTR_OK) return st;
     CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
     p->n_jobs = (int)jobs.size();
     p->orbit = true;
@@ -623,13 +627,19 @@ ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, doubl
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)
 {
     if (!p) return fail(CTR_EINVAL, "plan is NULL");
+    if (p->orbit) {
+        if (groups < 1 || groups > p->obp_cap)
+            return fail(CTR_EINVAL, "groups must be in [1, " + std::to_string(p->obp_cap) + "]");
+        p->obp_groups = groups;
+        return CTR_OK;
+    }
     if (groups < 1 || groups > p->bp_cap || groups > p->N)
         return fail(CTR_EINVAL, "groups must be in [1, " + std::to_string(p->bp_cap < p->N ? p->bp_cap : p->N) + "]");
     p->bp_groups = groups;
     return CTR_OK;
 }
 
-int ctr_plan_get_bp_groups(const ctr_plan *p) { return p ? p->bp_groups : 0; }
+int ctr_plan_get_bp_groups(const ctr_plan *p) { return p ? (p->orbit ? p->obp_groups : p->bp_groups) : 0; }
 
 void ctr_batch_destroy(ctr_batch *b)
 {

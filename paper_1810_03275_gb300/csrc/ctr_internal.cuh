@@ -225,6 +225,7 @@ struct ctr_plan {
     ctr::OrbitJob *d_jobs = nullptr;
     void *ubar = nullptr;                // n*n float4 orbit image
     int obp_groups = 1;                  // job groups of the symmetric backprojection
+    int obp_cap = 1;                     // groups the partial-plane workspace has room for
     void *obp_part = nullptr;            // obp_groups * 4 * n*n partial planes
     void *d_twiddle = nullptr;  // n complex exp(-2 pi i t/n)
 

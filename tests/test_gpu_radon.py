@@ -99,6 +99,34 @@ def test_symmetric_path_angle_sets(ct, case):
     assert rel_l2(got_b, oracle.rh_adjoint(g, geo)) < TOL["f32"]
 
 
+@pytest.mark.parametrize("geom", [(64, 90, 95), (96, 60, 137)])
+def test_backprojection_group_splits_agree(ct, geom):
+    """Every group split the plan allows (symmetric path: jobs, per-angle path: angles)
+    gives the same R_h^* up to FP32 summation order, and the oracle's."""
+    n, N, M = geom
+    th = np.arange(N) * (np.pi / N)
+    geo = oracle.Geometry(n, N, M, theta=th)
+    g = np.random.default_rng(N).standard_normal((N, M))
+    ref = oracle.rh_adjoint(g, geo)
+    for th_set in (th, th[:-1]):                           # even count: symmetric; odd: per angle
+        plan = ct.Plan(n, th_set.shape[0], M, angles=th_set)
+        gg = to_dev(g[:th_set.shape[0]], plan.torch_dtype)
+        r = ref if th_set is th else oracle.rh_adjoint(g[:-1], oracle.Geometry(n, N - 1, M, theta=th_set))
+        got = {}
+        for G in range(1, 9):
+            try:
+                plan.set_bp_groups(G)
+            except Exception:
+                continue
+            assert plan.bp_groups == G
+            got[G] = to_np(plan.rh_adjoint(gg))
+            assert rel_l2(got[G], r) < TOL["f32"], G
+        assert len(got) >= 2
+        first = next(iter(got.values()))
+        for v in got.values():
+            assert rel_l2(v, first) < 1e-6
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_adjoint_identity_on_gpu(ct, dtype):
     """<R u, g> = <u, R^* g> for the GPU pair (exact transpose: same integer weights)."""
