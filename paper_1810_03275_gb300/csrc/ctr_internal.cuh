@@ -307,6 +307,8 @@ size_t bp_smem_bytes(int wstride);
 size_t obp_smem_bytes(int wstride);   // the symmetric backprojection's dynamic shared memory
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
+size_t fft_rows_smem(int n, size_t esize);   // dynamic shared memory of the row passes
+size_t fft_cols_smem(int n, size_t esize);   // ... and of the column pass
 int fft_cols_per_cta(int n, size_t esize);
 ctr_status configure_batch_radon(size_t bp_smem, size_t obp_smem_max);
 ctr_status configure_batch_fft(size_t rows_smem, size_t cols_smem);

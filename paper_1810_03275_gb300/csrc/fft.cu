@@ -30,7 +30,7 @@ ctr_status fft_radices(int n, std::vector<int> &out)
 namespace {
 
 #ifndef CTR_FFT_THREADS
-#define CTR_FFT_THREADS 128
+#define CTR_FFT_THREADS 256
 #endif
 #ifndef CTR_FFT_POINTS
 #define CTR_FFT_POINTS 1024
@@ -76,7 +76,7 @@ __device__ __forceinline__ void dft4(T2 &x0, T2 &x1, T2 &x2, T2 &x3, T s)
 
 // One Stockham pass of radix R over `cnt` transforms of length n stored with
 // leading dimension ld.  Ns = product of the radices already applied.
-// sign = -1 forward, +1 inverse.  tw[t] = exp(-2 pi i t / n).
+// sign = -1 forward, +1 inverse.  tw[t] = exp(-2 pi i t / n), staged in shared memory.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_pass(const typename C2<T>::type *src, typename C2<T>::type *dst,
                                               int n, int cnt, int ld, int Ns, int sign,
@@ -100,7 +100,7 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::type *src, t
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                T2 w = __ldg(tw + r * k * stride_tw);   // r k stride_tw < R Ns n/(Ns R) = n
+                T2 w = tw[r * k * stride_tw];           // r k stride_tw < R Ns n/(Ns R) = n
                 if (sign > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -201,6 +201,13 @@ __device__ __forceinline__ void staged_copy(int total, L load, W store)
     }
 }
 
+// The twiddle table copied into shared memory (read by every pass of the CTA).
+template <typename T2>
+__device__ __forceinline__ void stage_twiddles(T2 *stw, const T2 *__restrict__ tw, int n)
+{
+    for (int t = threadIdx.x; t < n; t += blockDim.x) stw[t] = tw[t];
+}
+
 // Input of the forward row pass.  part != null: the angle-group partial images of
 // the backprojection, summed in group order and passed through the backprojection
 // epilogue (this fuses the group reduction into the pass); else in_real != null: a
@@ -224,6 +231,8 @@ __device__ __forceinline__ void fft_rows_fwd_body(const RowsInput<T> &src, typen
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)rows_per_cta * n;
+    T2 *stw = b + (size_t)rows_per_cta * n;
+    stage_twiddles(stw, tw, n);
     const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
     const size_t g0 = (size_t)r0 * n;
@@ -260,7 +269,7 @@ __device__ __forceinline__ void fft_rows_fwd_body(const RowsInput<T> &src, typen
         staged_copy(cnt * n, [&](int e) { return cbuf[g0 + e]; }, put);
     }
     __syncthreads();
-    T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, -1, tw);
+    T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, -1, stw);
     staged_copy(cnt * n, [&](int e) { return res[e]; }, [&](int e, T2 v) { cbuf[g0 + e] = v; });
 }
 
@@ -283,6 +292,8 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
     const int ld = n + 1;
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)cw * ld;
+    T2 *stw = b + (size_t)cw * ld;
+    stage_twiddles(stw, tw, n);
     const int c0 = bx * cw;
     const int cnt = min(cw, n - c0);
     const unsigned mc = div_magic(cnt);
@@ -295,7 +306,7 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
         a[(size_t)(e - row * cnt) * ld + row] = v;
     });
     __syncthreads();
-    T2 *res = fft_smem<T>(a, b, n, cnt, ld, fp, -1, tw);
+    T2 *res = fft_smem<T>(a, b, n, cnt, ld, fp, -1, stw);
     staged_copy(cnt * n, [&](int e) {
         const int row = fast_div(e, cnt, mc);
         return sym[(size_t)row * n + c0 + (e - row * cnt)];
@@ -307,7 +318,7 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
     });
     __syncthreads();
     T2 *other = (res == a) ? b : a;
-    T2 *res2 = fft_smem<T>(res, other, n, cnt, ld, fp, +1, tw);
+    T2 *res2 = fft_smem<T>(res, other, n, cnt, ld, fp, +1, stw);
     staged_copy(cnt * n, [&](int e) {
         const int row = fast_div(e, cnt, mc);
         return res2[(size_t)(e - row * cnt) * ld + row];
@@ -339,12 +350,14 @@ __device__ __forceinline__ void fft_rows_inv_body(const typename C2<T>::type *__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)rows_per_cta * n;
+    T2 *stw = b + (size_t)rows_per_cta * n;
+    stage_twiddles(stw, tw, n);
     const int r0 = bx * rows_per_cta;
     const int cnt = min(rows_per_cta, n - r0);
     const size_t g0 = (size_t)r0 * n;
     staged_copy(cnt * n, [&](int e) { return cbuf[g0 + e]; }, [&](int e, T2 v) { a[e] = v; });
     __syncthreads();
-    T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, +1, tw);
+    T2 *res = fft_smem<T>(a, b, n, cnt, n, fp, +1, stw);
     // row-major outputs
     staged_copy(cnt * n, [&](int e) { return mode == 1 ? out[g0 + e] : T(0); }, [&](int e, T prev) {
         const T v = res[e].x;
@@ -457,9 +470,7 @@ int cols_per_cta(const ctr_plan *p) { return fft_cols_per_cta(p->n, p->esize); }
 
 size_t fft_smem_bytes(const ctr_plan *p, int which)
 {
-    const size_t c2 = 2 * p->esize;
-    if (which == 0) return 2 * (size_t)rows_per_cta(p) * p->n * c2;
-    return 2 * (size_t)cols_per_cta(p) * (p->n + 1) * c2;
+    return which == 0 ? fft_rows_smem(p->n, p->esize) : fft_cols_smem(p->n, p->esize);
 }
 
 template <typename T>
@@ -550,6 +561,16 @@ ctr_status launch_batch_fft(int stage, const SliceDesc *sd, const int *prefix, i
 
 // Work split of the FFT passes: about 1024 points per CTA of 128 threads, so that an
 // n = 512 image gives 256 CTAs per pass.
+// Shared memory of the passes: two ping-pong buffers plus the twiddle table.
+size_t fft_rows_smem(int n, size_t esize)
+{
+    return (2 * (size_t)fft_rows_per_cta(n) * n + n) * 2 * esize;
+}
+size_t fft_cols_smem(int n, size_t esize)
+{
+    return (2 * (size_t)fft_cols_per_cta(n, esize) * (n + 1) + n) * 2 * esize;
+}
+
 int fft_rows_per_cta(int n)
 {
     const int r = CTR_FFT_POINTS / n;
@@ -614,8 +635,9 @@ ctr_status static_setup(int dev)
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.cbuf, g_static_cbuf));
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.sym, g_static_sym));
     CTR_CUDA(cudaGetSymbolAddress((void **)&s.tw, g_static_tw));
-    // n <= 1024: rows_per_cta * n <= 1024 and cols_per_cta * (n + 1) <= 1024 + 8 points
-    const int smax = 2 * (1024 + 8) * (int)sizeof(float2);
+    // n <= 1024: rows_per_cta * n <= 1024 and cols_per_cta * (n + 1) <= 1024 + 8 points, plus
+    // the twiddle table
+    const int smax = (2 * (1024 + 8) + STATIC_MAX_N) * (int)sizeof(float2);
     ctr_status st = raise_smem_limit(k_fft_cols<float>, smax);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_fwd<float>, smax);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv<float>, smax);
@@ -661,7 +683,7 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     if (blocks > 4096) blocks = 4096;
     k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps);
     const int rpc = fft_rows_per_cta(n), cw = fft_cols_per_cta(n, sizeof(float));
-    const size_t smr = 2 * (size_t)rpc * n * sizeof(float2), smc = 2 * (size_t)cw * (n + 1) * sizeof(float2);
+    const size_t smr = fft_rows_smem(n, sizeof(float)), smc = fft_cols_smem(n, sizeof(float));
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
     RowsInput<float> src{};
     src.in_real = y_dev;

@@ -1062,7 +1062,7 @@ ctr_status batch_prepare(ctr_batch *b)
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
         const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride) : 0;
         if (smo > b->smem[BS_BP_SYM]) b->smem[BS_BP_SYM] = smo;
-        const size_t smr = 2 * (size_t)rpc * p->n * sizeof(float2), smc = 2 * (size_t)cw * (p->n + 1) * sizeof(float2);
+        const size_t smr = fft_rows_smem(p->n, sizeof(float)), smc = fft_cols_smem(p->n, sizeof(float));
         if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
         if (smr > b->smem[BS_FFT_ROWS]) b->smem[BS_FFT_ROWS] = smr;
         if (smr > b->smem[BS_FFT_ROWS_INV]) b->smem[BS_FFT_ROWS_INV] = smr;
