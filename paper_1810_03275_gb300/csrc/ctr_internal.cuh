@@ -304,7 +304,7 @@ int fwd_grid_y(int N);         // forward-projector grid: angle groups
 
 // batched stages (one launch per stage over all slices of a batch)
 size_t bp_smem_bytes(int wstride);
-size_t obp_smem_bytes(int wstride);   // the symmetric backprojection's dynamic shared memory
+size_t obp_smem_bytes(int wstride, int jobs_per_group);   // the symmetric backprojection's dynamic shared memory
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
 size_t fft_rows_smem(int n, size_t esize);   // dynamic shared memory of the row passes

@@ -19,6 +19,8 @@
 //    No atomics; each output bin is written once.
 // Both kernels derive each weight from the same integer P (see ctr_internal.cuh),
 // so they are transposes of one matrix, bit for bit in the weights.
+#include <algorithm>
+
 #include "ctr_internal.cuh"
 
 namespace ctr {
@@ -720,16 +722,116 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
 #endif
 constexpr int OBP_TY = CTR_OBP_TY;     // warps of a symmetric-backprojection CTA (32 x 32 tile)
 constexpr int OBP_R = CTR_OBP_R;       // pixels per thread (rows i0 + ty + OBP_TY r)
+#ifndef CTR_OBP_ASYNC
+#define CTR_OBP_ASYNC 1
+#endif
+constexpr bool OBP_ASYNC = CTR_OBP_ASYNC;
 #ifndef CTR_OBP_JCH
 #define CTR_OBP_JCH 8
 #endif
-constexpr int OBP_JCH = CTR_OBP_JCH;   // jobs per staged chunk
+constexpr int OBP_JCH = CTR_OBP_JCH;   // jobs per staged chunk (synchronous staging)
+#ifndef CTR_OBP_AJCH
+#define CTR_OBP_AJCH 24
+#endif
+constexpr int OBP_AJCH = CTR_OBP_AJCH; // jobs per staged chunk (asynchronous staging, two buffers)
 
-size_t obp_smem(int wstride)
+size_t obp_smem(int wstride, int jobs_per_group)
 {
+    // staged pairs + chunk tables (bfloat16 operands, synchronous staging) ...
     const size_t stage = sizeof(float4) * 2 * OBP_JCH * wstride + (3 * sizeof(long long) + 5 * sizeof(int)) * OBP_JCH;
+    // ... or two raw chunk buffers + the whole group's tables (FP32, asynchronous staging)
+    const size_t async = sizeof(float4) * 2 * OBP_AJCH * (wstride + 1) +
+                         (3 * sizeof(long long) + 5 * sizeof(int)) * (size_t)jobs_per_group;
     const size_t tr = sizeof(float) * 2 * 32 * 33;
-    return stage > tr ? stage : tr;
+    return std::max(std::max(stage, async), tr);
+}
+
+// cp.async of one 4-byte element into shared memory; src_size 0 stores zero.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The FP32 symmetric backprojection with asynchronous staging: the group's job tables
+// are built once; chunk c + 1's four sinogram rows per job are copied raw into the
+// second of two shared buffers (cp.async, zero-filled outside the detector) while
+// chunk c is computed, so no global-load latency sits between chunks.  Each bin holds
+// the four channels' g as one float4; a (pixel, job) reads bins b and b + 1 and
+// interpolates g_b + f (g_{b+1} - g_b) per channel.
+__device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int n, int M, int wstride,
+                                               int jobs_per_group, int n_jobs, const OrbitJob *__restrict__ jobs,
+                                               float (&acc)[OBP_R][4], int bx, int by, int bz)
+{
+    constexpr int NT = 32 * OBP_TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int WR = wstride + 1;                                           // bins per staged row
+    float4 *raw = reinterpret_cast<float4 *>(smem_raw);                   // [2][JCH][WR], channels in x..w
+    const int la = bz * jobs_per_group;
+    const int nj = max(0, min(n_jobs, la + jobs_per_group) - la);
+    long long *sPb = reinterpret_cast<long long *>(raw + 2 * OBP_AJCH * WR);
+    long long *sC = sPb + jobs_per_group;
+    long long *sS = sC + jobs_per_group;
+    int *sK = reinterpret_cast<int *>(sS + jobs_per_group);
+    int *sL = sK + jobs_per_group;                                        // [job][channel]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i0 = by * 32, j0 = bx * 32;
+    for (int t = threadIdx.x; t < nj; t += NT) {
+        const OrbitJob &jb = jobs[la + t];
+        const long long Cc = jb.am.A, Sc = jb.am.B;
+        const long long P00 = (long long)i0 * Cc + (long long)j0 * Sc + jb.am.Op;
+        const long long kmin = P00 >> 32;                                // Cc, Sc >= 0: the tile's minimum
+        sK[t] = (int)kmin;
+        sPb[t] = P00 - (kmin << 32);
+        sC[t] = Cc;
+        sS[t] = Sc;
+        for (int c = 0; c < 4; ++c) sL[4 * t + c] = jb.l[c];
+    }
+    __syncthreads();
+    const int nch = (nj + OBP_AJCH - 1) / OBP_AJCH;
+    auto prefetch = [&](int ch) {
+        const int a0 = ch * OBP_AJCH, na = min(OBP_AJCH, nj - a0);
+        float *dst = reinterpret_cast<float *>(raw + (size_t)(ch & 1) * OBP_AJCH * WR);
+        for (int e = threadIdx.x; e < na * WR * 4; e += NT) {
+            const int c = e & 3, rest = e >> 2;
+            const int a = rest / WR, w = rest - a * WR;
+            const int k = sK[a0 + a] + w, l = sL[4 * (a0 + a) + c];
+            const bool ok = l >= 0 && k >= 0 && k < M;
+            cp_async4(dst + (size_t)rest * 4 + c, ok ? g + (size_t)l * M + k : g, ok);
+        }
+    };
+    if (nch > 0) prefetch(0);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) prefetch(ch + 1);
+        cp_async_commit();
+        cp_async_wait<1>();                                               // this thread's copies of chunk ch
+        __syncthreads();                                                  // everyone's
+        const int a0 = ch * OBP_AJCH, na = min(OBP_AJCH, nj - a0);
+        const float4 *buf = raw + (size_t)(ch & 1) * OBP_AJCH * WR;
+#pragma unroll 2
+        for (int a = 0; a < na; ++a) {
+            const long long C = sC[a0 + a];
+            long long P = sPb[a0 + a] + (long long)ty * C + (long long)tx * sS[a0 + a];
+            const long long D = C * OBP_TY;
+            const float4 *row = buf + a * WR;
+#pragma unroll
+            for (int r = 0; r < OBP_R; ++r) {
+                const int b = (int)(P >> 32);
+                const float f = one_plus_frac32(P) - 1.f;                 // exact: the 23 fraction bits
+                const float4 lo = row[b], hi = row[b + 1];
+                acc[r][0] += fmaf(f, hi.x - lo.x, lo.x);
+                acc[r][1] += fmaf(f, hi.y - lo.y, lo.y);
+                acc[r][2] += fmaf(f, hi.z - lo.z, lo.z);
+                acc[r][3] += fmaf(f, hi.w - lo.w, lo.w);
+                P += D;
+            }
+        }
+        __syncthreads();                                                  // buffer ch & 1 is refilled next
+    }
+    cp_async_wait<0>();
 }
 
 template <typename S>
@@ -755,6 +857,9 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
 #pragma unroll
     for (int r = 0; r < OBP_R; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
 
+    if constexpr (sizeof(S) == 4 && OBP_ASYNC)
+        obp_body_async(g, n, M, wstride, jobs_per_group, n_jobs, jobs, acc, bx, by, bz);
+    else
     for (int c0 = la; c0 < lb; c0 += OBP_JCH) {
         const int na = min(OBP_JCH, lb - c0);
         __syncthreads();
@@ -956,8 +1061,9 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
             dim3 grid((p->n + BP_TJ - 1) / BP_TJ, (p->n + BP_TI - 1) / BP_TI, G);
             float *part = (float *)p->obp_part;
             p->launches++;
-            k_backproject_orbit<S><<<grid, 32 * OBP_TY, obp_smem(p->wstride), s>>>(
-                g, p->n, p->M, p->wstride, (p->n_jobs + G - 1) / G, p->n_jobs, p->d_jobs, part);
+            const int jpg = (p->n_jobs + G - 1) / G;
+            k_backproject_orbit<S><<<grid, 32 * OBP_TY, obp_smem(p->wstride, jpg), s>>>(
+                g, p->n, p->M, p->wstride, jpg, p->n_jobs, p->d_jobs, part);
             CTR_CHECK_LAUNCH("k_backproject_orbit");
             if (!defer_reduce) {
                 const size_t nn = (size_t)p->n * p->n;
@@ -1031,8 +1137,9 @@ ctr_status configure_radon(const ctr_plan *p)
 {
     const size_t smem = bp_smem<T>(p);
     ctr_status st = raise_smem_limit(k_backproject<T, T>, smem);
-    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float>, obp_smem(p->wstride));
-    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, obp_smem(p->wstride));
+    const size_t osm = p->orbit ? obp_smem(p->wstride, p->n_jobs) : 0;   // any group split
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float>, osm);
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, osm);
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
     return st;
@@ -1086,7 +1193,7 @@ template bool bp_deferred<double>(const ctr_plan *);
 int fwd_grid_x(int M) { return (M + 30) / 31; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
 
-size_t obp_smem_bytes(int wstride) { return obp_smem(wstride); }
+size_t obp_smem_bytes(int wstride, int jobs_per_group) { return obp_smem(wstride, jobs_per_group); }
 
 size_t bp_smem_bytes(int wstride)
 {

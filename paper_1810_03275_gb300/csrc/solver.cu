@@ -1060,7 +1060,7 @@ ctr_status batch_prepare(ctr_batch *b)
         cnt[BS_FWD_SYM] = p->orbit ? fwd_grid_x(p->M) * ((p->n_jobs + 3) / 4) : 0;
         cnt[BS_TV] = grid_for(nn, 256, 1024);
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
-        const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride) : 0;
+        const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride, (p->n_jobs + p->obp_groups - 1) / p->obp_groups) : 0;
         if (smo > b->smem[BS_BP_SYM]) b->smem[BS_BP_SYM] = smo;
         const size_t smr = fft_rows_smem(p->n, sizeof(float)), smc = fft_cols_smem(p->n, sizeof(float));
         if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
