@@ -300,6 +300,7 @@ template <typename T> bool bp_deferred(const ctr_plan *p);
 // orbit image): callers may then skip making the transposed copy uT
 template <typename T> inline bool fwd_needs_transpose(const ctr_plan *p) { return !(sizeof(T) == 4 && p->orbit); }
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
+int orbit_fwd_grid_y(int n_jobs);   // symmetric forward projector: job groups per bin chunk
 int fwd_grid_y(int N);         // forward-projector grid: angle groups
 
 // batched stages (one launch per stage over all slices of a batch)

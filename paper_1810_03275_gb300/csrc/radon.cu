@@ -621,7 +621,11 @@ __device__ __forceinline__ void orbit_out(const ForwardEpi<float> &epi, int l, i
 #define CTR_ORBIT_SEGS 4
 #endif
 constexpr int ORBIT_SEGS = CTR_ORBIT_SEGS;    // row segments of a job's rays (one warp each)
-constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
+#ifndef CTR_ORBIT_SLOTS
+#define CTR_ORBIT_SLOTS 4
+#endif
+constexpr int ORBIT_SLOTS = CTR_ORBIT_SLOTS;  // adjacent jobs per CTA (they share image rows in L1)
+constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 #ifndef CTR_ORBIT_MINB
 #define CTR_ORBIT_MINB 2
 #endif
@@ -629,8 +633,8 @@ constexpr int ORBIT_THREADS = 128 * ORBIT_SEGS;
 #define CTR_OBP_MINB 4
 #endif
 
-// Warp w of the CTA takes job by*4 + (w & 3), bins bx*31 + [0, 31) and the
-// (w >> 2)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
+// Warp w of the CTA takes job by*ORBIT_SLOTS + w % ORBIT_SLOTS, bins bx*31 + [0, 31) and
+// the (w / ORBIT_SLOTS)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
 template <typename S>
 __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
@@ -639,8 +643,8 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
 {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int slot = warp & 3, seg = warp >> 2;
-    const int jb = by * 4 + slot;
+    const int slot = warp % ORBIT_SLOTS, seg = warp / ORBIT_SLOTS;
+    const int jb = by * ORBIT_SLOTS + slot;
     const int kb = bx * 31;
     const int k = kb + lane - 1;
     const bool active = jb < n_jobs && kb < M;        // warp-uniform
@@ -675,7 +679,7 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
         }
     }
     if constexpr (ORBIT_SEGS > 1) {
-        __shared__ float4 s_part[ORBIT_SEGS > 1 ? ORBIT_SEGS - 1 : 1][2][4][32];
+        __shared__ float4 s_part[ORBIT_SEGS > 1 ? ORBIT_SEGS - 1 : 1][2][ORBIT_SLOTS][32];
         if (seg > 0) {
             s_part[seg - 1][0][slot][lane] = Su;
             s_part[seg - 1][1][slot][lane] = Sf;
@@ -1107,7 +1111,8 @@ ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi
             k_orbit_image<S><<<dim3((p->n + 31) / 32, (p->n + 31) / 32), 256, 0, s>>>(u, ub, p->n);
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
-            k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + 3) / 4), ORBIT_THREADS, 0, s>>>(
+            k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS), ORBIT_THREADS,
+                                 0, s>>>(
                 ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
             CTR_CHECK_LAUNCH("k_forward_orbit");
             return CTR_OK;
@@ -1191,6 +1196,7 @@ template bool bp_deferred<float>(const ctr_plan *);
 template bool bp_deferred<double>(const ctr_plan *);
 
 int fwd_grid_x(int M) { return (M + 30) / 31; }
+int orbit_fwd_grid_y(int n_jobs) { return (n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
 
 size_t obp_smem_bytes(int wstride, int jobs_per_group) { return obp_smem(wstride, jobs_per_group); }

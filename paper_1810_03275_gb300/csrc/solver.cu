@@ -1057,7 +1057,7 @@ ctr_status batch_prepare(ctr_batch *b)
         cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
         cnt[BS_ORBIT] = p->orbit ? t32 * t32 : 0;
         cnt[BS_FWD] = p->orbit ? 0 : fwd_grid_x(p->M) * fwd_grid_y(p->N);
-        cnt[BS_FWD_SYM] = p->orbit ? fwd_grid_x(p->M) * ((p->n_jobs + 3) / 4) : 0;
+        cnt[BS_FWD_SYM] = p->orbit ? fwd_grid_x(p->M) * orbit_fwd_grid_y(p->n_jobs) : 0;
         cnt[BS_TV] = grid_for(nn, 256, 1024);
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
         const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride, (p->n_jobs + p->obp_groups - 1) / p->obp_groups) : 0;
