@@ -19,6 +19,7 @@ from .pdrq_ref import (
     lap_symbol,
     freq_norm,
     precond_symbol,
+    precond_symbol_nonneg,
     precond_apply,
     prox_dual,
     tv_project,
@@ -28,6 +29,7 @@ from .pdrq_ref import (
     power_c,
     power_start,
     PDRQState,
+    pdrq5_solve,
     pdrq_solve,
     cp_solve,
     diagnostics,

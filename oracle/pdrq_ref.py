@@ -1,6 +1,7 @@
 """FP64 numpy oracle for everything around R_h: the discrete gradient and
 divergence, the pointwise resolvents, the inverse-norm Fourier preconditioner,
-the power iterations, Alg. 4 (PDRQS1) and Alg. 1 (Chambolle-Pock).
+the power iterations, Alg. 4 (PDRQS1), Alg. 5 (PDRQS1 with u >= 0) and Alg. 1
+(Chambolle-Pock).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows
 the thesis step by step, with library primitives (numpy FFT) as single steps;
@@ -84,6 +85,16 @@ def precond_symbol(n: int, sigma: float, tau: float, c: float, eps: float) -> np
     nrm = freq_norm(n, eps)
     L = lap_symbol(n)
     return nrm / (sigma * sigma * c + (sigma * tau) ** 2 * L * nrm)
+
+
+def precond_symbol_nonneg(n: int, sigma: float, tau: float, c: float, eps: float) -> np.ndarray:
+    """Fourier multiplier of M^{-1} in Alg. 5 (non-negativity, Sec. "Non-negativity
+    constraints"): there T = id + sigma^2 K^*K, so M = id + c sigma^2 F^{-1}(1/||xi||) F
+    - (sigma tau)^2 Delta_p and M^{-1} multiplies by
+    ||xi|| / (||xi|| + sigma^2 c + (sigma tau)^2 F(kappa_Delta) ||xi||)."""
+    nrm = freq_norm(n, eps)
+    L = lap_symbol(n)
+    return nrm / (nrm + sigma * sigma * c + (sigma * tau) ** 2 * L * nrm)
 
 
 def precond_apply(y: np.ndarray, symbol: np.ndarray) -> np.ndarray:
@@ -226,6 +237,7 @@ class PDRQState:
     t2x: Optional[np.ndarray] = None
     t2y: Optional[np.ndarray] = None
     k: int = 0
+    ub: Optional[np.ndarray] = None   # bar u of Alg. 5 (non-negativity); None for Alg. 4
 
     @staticmethod
     def zeros(geo: Geometry) -> "PDRQState":
@@ -236,7 +248,7 @@ class PDRQState:
     def copy(self) -> "PDRQState":
         c = lambda a: None if a is None else a.copy()
         return PDRQState(self.u.copy(), self.Ru.copy(), self.v1b.copy(), self.v2bx.copy(),
-                         self.v2by.copy(), c(self.t1), c(self.t2x), c(self.t2y), self.k)
+                         self.v2by.copy(), c(self.t1), c(self.t2x), c(self.t2y), self.k, c(self.ub))
 
 
 def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, tau: float,
@@ -285,13 +297,62 @@ def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, t
     return st
 
 
+def pdrq5_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, tau: float,
+                eps: float, beta: float, c: float, state: Optional[PDRQState] = None,
+                callback=None) -> PDRQState:
+    """Run ``iters`` iterations of Alg. 5 (PDRQS1 with u >= 0, Sec. "Non-negativity
+    constraints") on the problem scaled by beta.  The added term I_{u >= 0} is the
+    primal function F of the splitting, with resolvent max(., 0) (Lemma
+    lem_resolv_non_neg, d = 0); its effect enters through bar u.  One iteration, in the
+    order of Alg. 5:
+        u_tmp = bar u - u - sigma ( Rt^*(v1b + sigma Rt u) - tau div(v2b + sigma tau grad u) )
+        u_new = u + F^{-1}( F(u_tmp) * m5 ),  m5 = ||xi|| / (||xi|| + sigma^2 c + (sigma tau)^2 L ||xi||)
+        v1, v2, t1, t2, v1b, v2b as in Alg. 4
+        bar u += max(2 u_new - bar u, 0) - u_new ;  u = u_new
+    The data term is the per-bin (w, a, lo, hi) of make_descriptors, as in pdrq_solve."""
+    h = geo.h
+    w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
+    at, lot, hit = a / beta, lo / beta, hi / beta
+    lam = alpha / (beta * beta)
+    m = precond_symbol_nonneg(geo.n, sigma, tau, c, eps)
+    st = PDRQState.zeros(geo) if state is None else state.copy()
+    if st.ub is None:
+        st.ub = np.zeros_like(st.u)
+    for _ in range(iters):
+        y1 = st.v1b + sigma * st.Ru
+        gx, gy = grad(st.u, h)
+        y2x = st.v2bx + sigma * tau * gx
+        y2y = st.v2by + sigma * tau * gy
+        u_tmp = st.ub - st.u - sigma * (rh_adjoint(y1, geo) / beta - tau * div(y2x, y2y, h))
+        u_new = st.u + precond_apply(u_tmp, m)
+        Ru_new = rh_forward(u_new, geo) / beta
+        v1 = st.v1b + sigma * Ru_new
+        gx, gy = grad(u_new, h)
+        v2x = st.v2bx + sigma * tau * gx
+        v2y = st.v2by + sigma * tau * gy
+        t1 = prox_dual(2.0 * v1 - st.v1b, sigma, w, at, lot, hit)
+        st.v1b = st.v1b + t1 - v1
+        t2x, t2y = tv_project(2.0 * v2x - st.v2bx, 2.0 * v2y - st.v2by, lam, tau)
+        st.v2bx = st.v2bx + t2x - v2x
+        st.v2by = st.v2by + t2y - v2y
+        st.ub = st.ub + np.maximum(2.0 * u_new - st.ub, 0.0) - u_new
+        st.u, st.Ru = u_new, Ru_new
+        st.t1, st.t2x, st.t2y = t1, t2x, t2y
+        st.k += 1
+        if callback is not None:
+            callback(st)
+    return st
+
+
 def cp_solve(geo: Geometry, desc, alpha: float, iters: int, *, beta: float,
              sigma: Optional[float] = None, tau: Optional[float] = None,
-             u0: Optional[np.ndarray] = None) -> np.ndarray:
+             u0: Optional[np.ndarray] = None, nonneg: bool = False) -> np.ndarray:
     """Alg. 1 (Chambolle-Pock) for problem (C_h) on the same beta-scaled problem,
     used only as an independent minimiser: (C_h) has a unique solution when R_h
     is injective (Sec. 3.2), so Alg. 1 and Alg. 4 must agree there.  Notation of
-    Alg. 1: tau is the dual and sigma the primal step, sigma tau (||Rt||^2 + 8/h^2) < 1."""
+    Alg. 1: tau is the dual and sigma the primal step, sigma tau (||Rt||^2 + 8/h^2) < 1.
+    nonneg: the primal step ends with the projection onto u >= 0 (the resolvent of
+    I_{u >= 0}), giving the minimiser of the problem Alg. 5 solves."""
     h = geo.h
     w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
     at, lot, hit = a / beta, lo / beta, hi / beta
@@ -312,6 +373,8 @@ def cp_solve(geo: Geometry, desc, alpha: float, iters: int, *, beta: float,
         wx, wy = tv_project(wbx, wby, lam, 1.0)
         v = prox_dual(vb, tau, w, at, lot, hit)
         u_new = u + sigma * div(wx, wy, h) - sigma * rh_adjoint(v, geo) / beta
+        if nonneg:
+            u_new = np.maximum(u_new, 0.0)
         ub = 2.0 * u_new - u
         u = u_new
     return u
