@@ -53,7 +53,8 @@ typedef struct {
 
 typedef struct ctr_plan ctr_plan;   /* opaque: geometry tables + all device workspace */
 
-/* Solver parameters of Alg. 4 (PDRQS1).  ctr_default_params fills the defaults. */
+/* Solver parameters of Alg. 4 (PDRQS1), and of Alg. 5 (PDRQS1 with u >= 0) when
+ * nonneg = 1.  ctr_default_params fills the defaults. */
 typedef struct {
     double sigma;        /* step sigma > 0 (default 1) */
     double tau;          /* gradient scaling tau > 0 (default 1/sqrt(8)) */
@@ -65,6 +66,12 @@ typedef struct {
     double trace_ratio;  /* metal-trace threshold C = trace_ratio * f (default 0.8, Sec. 5.2) */
     int check_every;     /* diagnostics cadence; 0 = only after the last iteration */
     int graph_block;     /* iterations per captured CUDA graph; 0 = plain launches (default 25) */
+    int nonneg;          /* 1: Alg. 5, the non-negativity constraint u >= 0 added to (C_h) (Sec.
+                          * "Non-negativity constraints"): the preconditioner symbol gains the
+                          * identity, ||xi|| / (||xi|| + sigma^2 c + (sigma tau)^2 L ||xi||), the
+                          * first step adds bar u - u and bar u += max(2 u - bar u, 0) - u after
+                          * each update.  0 (default): Alg. 4.  Also selects the symbol that
+                          * precond_apply applies. */
 } ctr_params;
 
 /* Diagnostics after the solve (original, unscaled problem unless noted). */
@@ -83,12 +90,13 @@ typedef struct {
 
 /* Iterate state of Alg. 4 for warm start / checkpoint-resume; device buffers of the
  * plan's dtype: u (n*n), Ru = R_h u / beta (N*M), v1b (N*M), v2b (2*n*n: x plane then
- * y plane). */
+ * y plane), ub = bar u of Alg. 5 (n*n; needed with params->nonneg, ignored otherwise). */
 typedef struct {
     void *u;
     void *Ru;
     void *v1b;
     void *v2b;
+    void *ub;
 } ctr_state;
 
 /* Create a plan for `geo` computing in `dtype` (CTR_F32 or CTR_F64; CTR_BF16 stores

@@ -247,6 +247,7 @@ ctr_status check_params(const ctr_params &q)
     if (!(q.c_margin >= 1.0)) return fail(CTR_EINVAL, "c_margin must be >= 1");
     if (!std::isfinite(q.trace_ratio)) return fail(CTR_EINVAL, "trace_ratio must be finite");
     if (q.graph_block < 0 || q.check_every < 0) return fail(CTR_EINVAL, "graph_block and check_every must be >= 0");
+    if (q.nonneg != 0 && q.nonneg != 1) return fail(CTR_EINVAL, "nonneg must be 0 or 1");
     return CTR_OK;
 }
 
@@ -311,11 +312,13 @@ ctr_status solve_impl(ctr_plan *p, const void *f, const uint8_t *mask, const voi
         CTR_CUDA(cudaMemcpyAsync(p->Ru, state->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
         CTR_CUDA(cudaMemcpyAsync(p->v1b, state->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
         CTR_CUDA(cudaMemcpyAsync(p->v2b, state->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if (q.nonneg) CTR_CUDA(cudaMemcpyAsync(p->ubar_u, state->ub, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
     } else {
         CTR_CUDA(cudaMemsetAsync(p->u, 0, nn * sizeof(T), s));
         CTR_CUDA(cudaMemsetAsync(p->Ru, 0, nm * sizeof(T), s));
         CTR_CUDA(cudaMemsetAsync(p->v1b, 0, nm * sizeof(T), s));
         CTR_CUDA(cudaMemsetAsync(p->v2b, 0, 2 * nn * sizeof(T), s));
+        if (q.nonneg) CTR_CUDA(cudaMemsetAsync(p->ubar_u, 0, nn * sizeof(T), s));
     }
     ctr_diag local{};
     if ((st = pdrq_loop<T>(p, alpha, iters, q, beta, c, diag ? &local : nullptr, s)) != CTR_OK) return st;
@@ -324,6 +327,7 @@ ctr_status solve_impl(ctr_plan *p, const void *f, const uint8_t *mask, const voi
         CTR_CUDA(cudaMemcpyAsync(state->Ru, p->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
         CTR_CUDA(cudaMemcpyAsync(state->v1b, p->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
         CTR_CUDA(cudaMemcpyAsync(state->v2b, p->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if (q.nonneg) CTR_CUDA(cudaMemcpyAsync(state->ub, p->ubar_u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
     if (u_out) CTR_CUDA(cudaMemcpyAsync(u_out, p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (diag) {
@@ -356,6 +360,7 @@ void ctr_default_params(ctr_params *q)
     q->trace_ratio = 0.8;
     q->check_every = 0;
     q->graph_block = 25;
+    q->nonneg = 0;
 }
 
 size_t ctr_plan_device_bytes(const ctr_plan *p) { return p ? p->bytes : 0; }
@@ -429,6 +434,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->Ru, es * nm);
     ALLOC(p->v1b, es * nm);
     ALLOC(p->t1, es * nm);
+    ALLOC(p->ubar_u, es * nn);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
     if (p->bf16) {
@@ -539,10 +545,10 @@ ctr_status precond_apply(ctr_plan *p, const ctr_params *prm, const void *y, void
     if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
     cudaStream_t s = (cudaStream_t)stream;
     if (p->dtype == CTR_F64) {
-        if ((st = launch_symbols<double>(p, q.sigma, q.tau, q.c, q.eps, s)) != CTR_OK) return st;
+        if ((st = launch_symbols<double>(p, q.sigma, q.tau, q.c, q.eps, s, q.nonneg != 0)) != CTR_OK) return st;
         return launch_circulant<double>(p, (const double *)y, false, (const double *)p->sym, (double *)x, 0, nullptr, nullptr, s);
     }
-    if ((st = launch_symbols<float>(p, q.sigma, q.tau, q.c, q.eps, s)) != CTR_OK) return st;
+    if ((st = launch_symbols<float>(p, q.sigma, q.tau, q.c, q.eps, s, q.nonneg != 0)) != CTR_OK) return st;
     return launch_circulant<float>(p, (const float *)y, false, (const float *)p->sym, (float *)x, 0, nullptr, nullptr, s);
 }
 
@@ -577,6 +583,7 @@ ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, 
     if (!state && !u_out) return fail(CTR_EINVAL, "state and u_out are both NULL");
     if (state && (!state->u || !state->Ru || !state->v1b || !state->v2b)) return fail(CTR_EINVAL, "state has a NULL buffer");
     ctr_params q = resolve(p, prm);
+    if (state && q.nonneg && !state->ub) return fail(CTR_EINVAL, "nonneg: state->ub (bar u) must be given");
     ctr_status st = validate_solve(p, alpha, iters, q);
     if (st != CTR_OK) return st;
     return CTR_DISPATCH(p,
@@ -593,6 +600,7 @@ ctr_status tv_pd_solve_state(ctr_plan *p, const void *f, const uint8_t *mask, do
     if (std::isnan(delta)) return fail(CTR_EINVAL, "delta is NaN");
     if (p->bf16) return fail(CTR_EUNSUPPORTED, "state-carrying solves need an FP32 or FP64 plan");
     ctr_params q = resolve(p, prm);
+    if (q.nonneg && !state->ub) return fail(CTR_EINVAL, "nonneg: state->ub (bar u) must be given");
     ctr_status st = validate_solve(p, alpha, iters, q);
     if (st != CTR_OK) return st;
     return CTR_DISPATCH(p,
@@ -609,6 +617,7 @@ ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, doubl
     if (!s0->u || !s0->v1b || !s0->v2b || !s1->u || !s1->Ru) return fail(CTR_EINVAL, "state buffer missing");
     if (p->bf16) return fail(CTR_EUNSUPPORTED, "the reverse mode needs an FP32 or FP64 plan");
     ctr_params q = resolve(p, prm);
+    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "the reverse mode covers Alg. 4 only (nonneg = 0)");
     ctr_status st = validate_solve(p, alpha, 1, q);
     if (st != CTR_OK) return st;
     if (!(q.beta > 0) || !(q.c > 0)) return fail(CTR_EINVAL, "the reverse mode needs beta and c given (> 0)");
@@ -731,6 +740,7 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
     if (!(qc.eps > 0)) qc.eps = 1.0;     // validated per slice (pi/n when unset)
     ctr_status st = check_params(qc);
     if (st != CTR_OK) return st;
+    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "batched solves cover Alg. 4 only (nonneg = 0)");
     CTR_CUDA(cudaEventRecord(b->ev_in, (cudaStream_t)stream));
     CTR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
     st = batch_solve(b, (const float *const *)f_devs, masks, alphas, deltas, iters, q, betas, cs,

@@ -99,6 +99,7 @@ struct BackprojEpi {
     T divtau;          // coefficient of div p (value = scale*R^*g - divtau*div p)
     T outscale;        // final multiplier
     T inv_h;
+    const T *ub, *uu;  // optional (Alg. 5): value += ub - uu (bar u - u) after the multiplier
 };
 
 // div_h p at pixel (i, j): (d1 + d2)/h, backward differences with Dirichlet ends
@@ -120,13 +121,18 @@ __device__ __forceinline__ T div_at(const T *__restrict__ px, int n, int i, int 
 }
 
 // The backprojection epilogue at pixel (i, j) for the sum acc:
-// outscale (scale acc - divtau div p).
+// outscale (scale acc - divtau div p) [+ ub - uu].
 template <typename T>
 __device__ __forceinline__ T bp_epilogue_value(const BackprojEpi<T> &epi, int n, int i, int j, T acc)
 {
     T v = acc * epi.scale;
     if (epi.px) v -= epi.divtau * div_at(epi.px, n, i, j, epi.inv_h);
-    return v * epi.outscale;
+    v *= epi.outscale;
+    if (epi.ub) {
+        const size_t e = (size_t)i * n + j;
+        v += epi.ub[e] - epi.uu[e];
+    }
+    return v;
 }
 
 // The fold of the symmetric backprojection (OrbitJob path): its partial planes
@@ -246,6 +252,7 @@ struct ctr_plan {
     void *Ru = nullptr;        // N*M
     void *v1b = nullptr;       // N*M
     void *t1 = nullptr;        // N*M
+    void *ubar_u = nullptr;    // n*n bar u of Alg. 5 (non-negativity)
     void *gs = nullptr;        // N*M scratch sinogram
     void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
     double *d_red = nullptr;   // reduction partials
@@ -287,7 +294,8 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
                             int mode, T *outT, T *dout, cudaStream_t s, __nv_bfloat16 *outh = nullptr,
                             __nv_bfloat16 *outTh = nullptr, const BackprojEpi<T> *bp_in = nullptr);
 template <typename T>
-ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s);
+ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s,
+                          bool nonneg = false);
 
 template <typename T> ctr_status configure_radon(const ctr_plan *p);   // smem attributes, at plan creation
 template <typename T> ctr_status configure_fft(const ctr_plan *p);

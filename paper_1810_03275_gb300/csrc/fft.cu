@@ -437,7 +437,7 @@ k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 //   sym  = ||xi||_eps / (sigma^2 c + (sigma tau)^2 L ||xi||_eps) / n^2
 //   symh = sqrt(||xi||_eps) / n^2
 template <typename T>
-__global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, double c, double eps)
+__global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, double c, double eps, int nonneg)
 {
     const size_t total = (size_t)n * n;
     const double pi = 3.14159265358979323846;
@@ -450,7 +450,8 @@ __global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, doub
         const double nrm = sqrt(xi * xi + xj * xj + eps * eps);
         const double si = sin(pi * i / n), sj = sin(pi * j / n);
         const double L = 4.0 * si * si + 4.0 * sj * sj;
-        sym[e] = (T)(nrm / (sigma * sigma * c + (sigma * tau) * (sigma * tau) * L * nrm) * inv_n2);
+        const double id = nonneg ? nrm : 0.0;   // Alg. 5: M = id + c sigma^2 F^{-1}(1/||xi||)F - (sigma tau)^2 Delta
+        sym[e] = (T)(nrm / (id + sigma * sigma * c + (sigma * tau) * (sigma * tau) * L * nrm) * inv_n2);
         if (symh) symh[e] = (T)(sqrt(nrm) * inv_n2);
     }
 }
@@ -519,13 +520,14 @@ ctr_status configure_fft(const ctr_plan *p)
 }
 
 template <typename T>
-ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s)
+ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s,
+                          bool nonneg)
 {
     const size_t total = (size_t)p->n * p->n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     p->launches++;
-    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps);
+    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0);
     CTR_CHECK_LAUNCH("k_symbols");
     return CTR_OK;
 }
@@ -587,8 +589,8 @@ int fft_cols_per_cta(int n, size_t esize)
 
 template ctr_status configure_fft<float>(const ctr_plan *);
 template ctr_status configure_fft<double>(const ctr_plan *);
-template ctr_status launch_symbols<float>(const ctr_plan *, double, double, double, double, cudaStream_t);
-template ctr_status launch_symbols<double>(const ctr_plan *, double, double, double, double, cudaStream_t);
+template ctr_status launch_symbols<float>(const ctr_plan *, double, double, double, double, cudaStream_t, bool);
+template ctr_status launch_symbols<double>(const ctr_plan *, double, double, double, double, cudaStream_t, bool);
 
 // ------------------------------------------------------------------------------
 // precond_apply_static: the FP32 preconditioner without any device allocation.
@@ -681,7 +683,7 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     const size_t nn = (size_t)n * n;
     int blocks = (int)((nn + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps);
+    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps, 0);
     const int rpc = fft_rows_per_cta(n), cw = fft_cols_per_cta(n, sizeof(float));
     const size_t smr = fft_rows_smem(n, sizeof(float)), smc = fft_cols_smem(n, sizeof(float));
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;

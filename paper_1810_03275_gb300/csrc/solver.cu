@@ -121,9 +121,10 @@ __global__ void k_init_y2(const T *__restrict__ u, const T *__restrict__ v2b, in
 }
 
 // Step D of Alg. 4: TV dual update with the projection onto the ball of radius lam/tau.
+// ub (Alg. 5 only): bar u += max(2 u - bar u, 0) - u, the resolvent of I_{u >= 0}.
 template <typename T>
 __device__ __forceinline__ void tv_dual_body(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b,
-                                             T *y2, T *t2, int b, int nb)
+                                             T *y2, T *t2, T *ub, int b, int nb)
 {
     const size_t nn = (size_t)n * n;
     const T st = sigma * tau;
@@ -148,14 +149,18 @@ __device__ __forceinline__ void tv_dual_body(const T *__restrict__ u, int n, T s
             t2[e] = tx;
             t2[e + nn] = ty;
         }
+        if (ub) {
+            const T uc = u[e], b0 = ub[e];
+            ub[e] = b0 + fmax(T(2) * uc - b0, T(0)) - uc;
+        }
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b, T *y2, T *t2)
+k_tv_dual(const T *__restrict__ u, int n, T sigma, T tau, T lam, T inv_h, T *v2b, T *y2, T *t2, T *ub)
 {
-    tv_dual_body<T>(u, n, sigma, tau, lam, inv_h, v2b, y2, t2, blockIdx.x, gridDim.x);
+    tv_dual_body<T>(u, n, sigma, tau, lam, inv_h, v2b, y2, t2, ub, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256)
@@ -168,7 +173,7 @@ k_tv_dual_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix
         else hi = mid - 1;
     }
     const SliceDesc &d = sd[lo];
-    tv_dual_body<float>(d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, blockIdx.x - prefix[lo],
+    tv_dual_body<float>(d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, nullptr, blockIdx.x - prefix[lo],
                         prefix[lo + 1] - prefix[lo]);
 }
 
@@ -472,6 +477,7 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
 template <typename T>
 struct IterArgs {
     T sigma, tau, lam, inv_beta, inv_h;
+    bool nonneg = false;   // Alg. 5 (u >= 0)
 };
 
 // One iteration of Alg. 4 (steps A-D).  diag: also keep du, t1, t2 for diagnostics.
@@ -490,6 +496,10 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     ea.divtau = a.tau;
     ea.outscale = -a.sigma;
     ea.inv_h = a.inv_h;
+    if (a.nonneg) {                              // Alg. 5: u_tmp = bar u - u - sigma (...)
+        ea.ub = (const T *)p->ubar_u;
+        ea.uu = (const T *)p->u;
+    }
     const bool h = sizeof(T) == 4 && p->bf16;   // projector operands in bfloat16
     const bool fuse = bp_deferred<T>(p);        // partial-image sum and epilogue inside the first FFT pass
     if (h) {
@@ -531,7 +541,8 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     const size_t nn = (size_t)n * n;
     p->launches++;
     k_tv_dual<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, n, a.sigma, a.tau, a.lam, a.inv_h,
-                                                        (T *)p->v2b, (T *)p->y2, diag ? (T *)p->t2 : nullptr);
+                                                        (T *)p->v2b, (T *)p->y2, diag ? (T *)p->t2 : nullptr,
+                                                        a.nonneg ? (T *)p->ubar_u : nullptr);
     CTR_CHECK_LAUNCH("k_tv_dual");
     return CTR_OK;
 }
@@ -600,8 +611,9 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
     a.lam = (T)(alpha / (beta * beta));
     a.inv_beta = (T)(1.0 / beta);
     a.inv_h = (T)(1.0 / p->h);
+    a.nonneg = prm.nonneg != 0;
     ctr_status st;
-    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s)) != CTR_OK) return st;
+    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s, a.nonneg)) != CTR_OK) return st;
     // y1 = v1b + sigma Ru ; y2 = v2b + sigma tau grad u
     p->launches++;
     k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->v1b, (const T *)p->Ru, a.sigma, nm, (T *)p->y1);
@@ -655,7 +667,10 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
     for (; done < body; ++done)
         if ((st = pdrq_iteration<T>(p, a, false, s)) != CTR_OK) return st;
     if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
-    if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, iters, diag, s);
+    if (diag) {
+        if ((st = compute_diag<T>(p, alpha, beta, prm.tau, c, iters, diag, s)) != CTR_OK) return st;
+        if (a.nonneg) diag->gap = diag->dual_residual = nan("");   // defined for Alg. 4's saddle problem only
+    }
     return CTR_OK;
 }
 

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("eps", ctypes.c_double),
                 ("c", ctypes.c_double), ("beta", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("c_margin", ctypes.c_double), ("trace_ratio", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int), ("nonneg", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
@@ -56,7 +56,8 @@ class Diag(ctypes.Structure):
 
 
 class State(ctypes.Structure):
-    _fields_ = [("u", ctypes.c_void_p), ("Ru", ctypes.c_void_p), ("v1b", ctypes.c_void_p), ("v2b", ctypes.c_void_p)]
+    _fields_ = [("u", ctypes.c_void_p), ("Ru", ctypes.c_void_p), ("v1b", ctypes.c_void_p), ("v2b", ctypes.c_void_p),
+                ("ub", ctypes.c_void_p)]
 
 
 EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_last_error", "ctr_plan_device_bytes",
@@ -314,8 +315,9 @@ class Plan:
 
     def _state(self, st):
         sino = (self.n_angles, self.n_bins)
+        ub = self._t(st["ub"], (self.n, self.n), "ub").value if st.get("ub") is not None else None
         return State(self._t(st["u"], (self.n, self.n), "u").value, self._t(st["Ru"], sino, "Ru").value,
-                     self._t(st["v1b"], sino, "v1b").value, self._t(st["v2b"], (2, self.n, self.n), "v2b").value)
+                     self._t(st["v1b"], sino, "v1b").value, self._t(st["v2b"], (2, self.n, self.n), "v2b").value, ub)
 
     def _mask(self, metal_mask):
         import torch
@@ -354,7 +356,8 @@ class Plan:
         import torch
         z = dict(device="cuda", dtype=self.torch_dtype)
         return {"u": torch.zeros((self.n, self.n), **z), "Ru": torch.zeros((self.n_angles, self.n_bins), **z),
-                "v1b": torch.zeros((self.n_angles, self.n_bins), **z), "v2b": torch.zeros((2, self.n, self.n), **z)}
+                "v1b": torch.zeros((self.n_angles, self.n_bins), **z), "v2b": torch.zeros((2, self.n, self.n), **z),
+                "ub": torch.zeros((self.n, self.n), **z)}
 
     def tv_pd_run(self, w, a, lo, hi, alpha: float, iters: int, params: Optional[Params] = None, state=None,
                   u_out=None, want_diag: bool = True, stream=None):
@@ -362,9 +365,7 @@ class Plan:
         sino = (self.n_angles, self.n_bins)
         st = None
         if state is not None:
-            st = State(self._t(state["u"], (self.n, self.n), "u").value, self._t(state["Ru"], sino, "Ru").value,
-                       self._t(state["v1b"], sino, "v1b").value,
-                       self._t(state["v2b"], (2, self.n, self.n), "v2b").value)
+            st = self._state(state)
         if state is None and u_out is None:
             u_out = self.empty_image()
         diag = Diag()
