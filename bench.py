@@ -143,6 +143,29 @@ def cpu_oracle_rate(problem, budget_s: float = 12.0, max_iters: int = 40):
     return k / dt, k, dt, oracle.num_threads()
 
 
+def measure_nonneg(plan, f, mask, pr, iters: int = 200):
+    """Alg. 5 (u >= 0) against Alg. 4 on the benchmark plan and data: iterations/s at
+    fixed (beta, c), CUDA events on the torch stream, and the most negative pixel of each."""
+    import numpy as np
+    import torch
+    from paper_1810_03275_gb300 import ctrecon as ct
+    beta = plan.power_beta(20)
+    c = 1.05 * plan.power_lambda(beta, np.pi / pr.n, 20)
+    out = {}
+    for name, nn in (("alg4", 0), ("alg5_nonneg", 1)):
+        prm = ct.default_params(beta=beta, c=c, nonneg=nn)
+        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, 5, params=prm)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        u, _ = plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = {"iters_per_s": iters / (a.elapsed_time(b) / 1e3), "min_u": float(u.min())}
+    out["workload"] = f"512x512/720/729 MAR data, {iters} iterations per timing (beta, c fixed)"
+    return out
+
+
 def measure_forms(iters: int = 30):
     """The BF16 form against the plain FP32 path on the 2048 x 2048 / 2048 views /
     2897 bins geometry: iterations/s of Alg. 4 (fixed beta and c, so only the
@@ -376,7 +399,8 @@ def main():
 
     forms = None
     if rank == 0 and not args.no_forms:
-        forms = {"bf16": measure_forms(), "batched": measure_batched()}
+        forms = {"bf16": measure_forms(), "batched": measure_batched(),
+                 "nonneg": measure_nonneg(plan, f, mask, pr)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

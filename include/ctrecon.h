@@ -185,6 +185,21 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
                        double alpha, double delta, int iters, const ctr_params *params,
                        void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* Alg. 1 (Chambolle-Pock, Sec. 3.2) for the same problem as tv_pd_solve, from u = 0:
+ * the unpreconditioned primal-dual baseline against which the thesis measures Alg. 4.
+ * Runs on the beta-scaled problem (R_h / beta, so its norm is about 1) with primal step
+ * sigma_p and dual step tau_d, sigma_p tau_d (1 + 8/h^2) < 1; sigma_p <= 0 or tau_d <= 0
+ * selects 0.99 / sqrt(1.02 (1 + 8/h^2)) for both.  Per iteration: v = prox(v + tau_d R u_bar)
+ * (in the forward projector's epilogue), w = P_lambda(w + tau_d grad u_bar), u_new = u +
+ * sigma_p div w - sigma_p R^* v and u_bar = 2 u_new - u (in the backprojection's epilogue).
+ * params: beta, power_iters, trace_ratio and graph_block are used (NULL = defaults);
+ * params->tau only scales the reported dual (t2 = w / tau) so that diag_out's gap and
+ * dual residual are those of tv_pd_solve's saddle problem.  FP32 and FP64 plans
+ * (CTR_EUNSUPPORTED for BF16), any n (no FFT); errors as tv_pd_solve. */
+ctr_status tv_cp_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_mask_dev, double alpha,
+                       double delta, int iters, double sigma_p, double tau_d, const ctr_params *params,
+                       void *u_out_dev, ctr_diag *diag_out, void *stream);
+
 /* General form: per-bin data term g_r(z) = w_r/2 (z - a_r)^2 + I_[lo_r, hi_r](z) given
  * by four device arrays of N*M (original scale, +-inf allowed in lo/hi), which covers
  * every resolvent variant of Sec. 3.3-3.5.  `state` (may be NULL) holds the start on

@@ -48,6 +48,8 @@ template <typename T> ctr_status power_lambda(ctr_plan *, double, double, int, d
 template <typename T>
 ctr_status pdrq_loop(ctr_plan *, double, int, const ctr_params &, double, double, ctr_diag *, cudaStream_t);
 template <typename T>
+ctr_status cp_loop(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *, cudaStream_t);
+template <typename T>
 ctr_status build_desc_from_data(ctr_plan *, const T *, const uint8_t *, double, double, double, cudaStream_t);
 template <typename T>
 ctr_status build_desc_from_arrays(ctr_plan *, const T *, const T *, const T *, const T *, double, cudaStream_t);
@@ -338,6 +340,36 @@ ctr_status solve_impl(ctr_plan *p, const void *f, const uint8_t *mask, const voi
     return CTR_OK;
 }
 
+template <typename T>
+ctr_status cp_impl(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters, double sp,
+                   double sd, const ctr_params &q, void *u_out, ctr_diag *diag, void *stream)
+{
+    StreamJoin sj(p, stream);
+    ctr_status st = sj.begin();
+    if (st != CTR_OK) return st;
+    cudaStream_t s = p->stream;
+    double beta = q.beta;
+    if (!(beta > 0)) {
+        if ((st = power_beta<T>(p, q.power_iters, &beta, s)) != CTR_OK) return st;
+        if (!(beta > 0)) return fail(CTR_ENUMERIC, "power iteration gave ||R_h|| = 0");
+    }
+    if ((st = build_desc_from_data<T>(p, (const T *)f, mask, delta, q.trace_ratio, beta, s)) != CTR_OK) return st;
+    if (!(sp > 0) || !(sd > 0)) {
+        // sigma tau (||Rt||^2 + 8/h^2) < 1 with ||Rt|| = 1 up to the power-iteration estimate
+        const double step = 0.99 / std::sqrt(1.02 * (1.0 + 8.0 / (p->h * p->h)));
+        sp = sd = step;
+    }
+    ctr_diag local{};
+    if ((st = cp_loop<T>(p, alpha, iters, q, beta, sp, sd, diag ? &local : nullptr, s)) != CTR_OK) return st;
+    CTR_CUDA(cudaMemcpyAsync(u_out, p->u, (size_t)p->n * p->n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (diag) {
+        *diag = local;
+        diag->beta = beta;
+        diag->c = 0.0;
+    }
+    return CTR_OK;
+}
+
 }  // namespace
 }  // namespace ctr
 
@@ -559,6 +591,24 @@ static ctr_status validate_solve(ctr_plan *p, double alpha, int iters, const ctr
     if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
     (void)p;
     return check_params(q);
+}
+
+ctr_status tv_cp_solve(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,
+                       double sigma_p, double tau_d, const ctr_params *prm, void *u_out, ctr_diag *diag,
+                       void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
+    if (std::isnan(delta) || std::isnan(sigma_p) || std::isnan(tau_d)) return fail(CTR_EINVAL, "NaN argument");
+    if (p->bf16) return fail(CTR_EUNSUPPORTED, "Alg. 1 runs on FP32 and FP64 plans");
+    ctr_params q = resolve(p, prm);
+    // no preconditioner: any n (validate_solve's FFT-size rule does not apply)
+    if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(CTR_EINVAL, "alpha must be finite and >= 0");
+    if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
+    ctr_status st = check_params(q);
+    if (st != CTR_OK) return st;
+    return CTR_DISPATCH(p, cp_impl<float>(p, f, mask, alpha, delta, iters, sigma_p, tau_d, q, u_out, diag, stream),
+                        cp_impl<double>(p, f, mask, alpha, delta, iters, sigma_p, tau_d, q, u_out, diag, stream));
 }
 
 ctr_status tv_pd_solve(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,

@@ -99,7 +99,8 @@ struct BackprojEpi {
     T divtau;          // coefficient of div p (value = scale*R^*g - divtau*div p)
     T outscale;        // final multiplier
     T inv_h;
-    const T *ub, *uu;  // optional (Alg. 5): value += ub - uu (bar u - u) after the multiplier
+    const T *ub, *uu;  // optional: value += ub - uu (Alg. 5: bar u - u), or += ub when uu is null
+    T *bar_out;        // optional (Alg. 1): bar_out = 2 value - ub (the extrapolated iterate)
 };
 
 // div_h p at pixel (i, j): (d1 + d2)/h, backward differences with Dirichlet ends
@@ -130,7 +131,7 @@ __device__ __forceinline__ T bp_epilogue_value(const BackprojEpi<T> &epi, int n,
     v *= epi.outscale;
     if (epi.ub) {
         const size_t e = (size_t)i * n + j;
-        v += epi.ub[e] - epi.uu[e];
+        v += epi.ub[e] - (epi.uu ? epi.uu[e] : T(0));
     }
     return v;
 }
@@ -151,7 +152,7 @@ __device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int 
 
 template <typename T>
 struct ForwardEpi {
-    int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4)
+    int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4); 2: CP dual step (Alg. 1)
     T *g;              // mode 0 output
     T scale;
     // mode 1

@@ -105,8 +105,10 @@ __device__ __forceinline__ double interp(double acc, double2 pr, long long P, in
 template <typename T>
 __device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, int i, int j, T acc)
 {
-    const T v = bp_epilogue_value(epi, n, i, j, acc);
     const size_t o = (size_t)i * n + j;
+    const T old = epi.bar_out ? epi.ub[o] : T(0);      // read before out (may alias ub) is written
+    const T v = bp_epilogue_value(epi, n, i, j, acc);
+    if (epi.bar_out) epi.bar_out[o] = T(2) * v - old;
     if (epi.complex_out) {
         epi.out[2 * o] = v;
         epi.out[2 * o + 1] = T(0);
@@ -244,11 +246,27 @@ __device__ __forceinline__ void acc_sample(double &Su, double &Sf, double v, lon
     Sf = fma((double)((unsigned long long)P & mask) * inv2F, v, Sf);   // sum frac u
 }
 
+// The data resolvent (id + s dg_r^*)^{-1}(z) = z - s clip(q, lo, hi), q = (z + w a)/(s + w),
+// written as w (z - s a)/(s + w) + s (q - clip(q)): for w = 0 and q inside the box it is
+// exactly 0 (the one-sided trace constraint then keeps its dual in the conjugate's domain).
+template <typename T>
+__device__ __forceinline__ T data_resolvent(T z, T s, T w, T a, T lo, T hi)
+{
+    const T q = (z + w * a) / (s + w);
+    return w * (z - s * a) / (s + w) + s * (q - fmin(fmax(q, lo), hi));
+}
+
 template <typename T>
 __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_t r, T val)
 {
     if (epi.mode == 0) {
         epi.g[r] = val * epi.scale;
+        return;
+    }
+    if (epi.mode == 2) {
+        // Alg. 1: v = (id + tau dG1^*)^{-1}(v + tau Rt u_bar), tau carried in epi.sigma
+        const T z = epi.v1b[r] + epi.sigma * (val * epi.scale);
+        epi.v1b[r] = data_resolvent(z, epi.sigma, epi.dw[r], epi.da[r], epi.dlo[r], epi.dhi[r]);
         return;
     }
     // Alg. 4: v1 = v1b + sigma Rt u_new; t = (id + sigma dG1^*)^{-1}(2 v1 - v1b);
@@ -258,10 +276,7 @@ __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_
     const T vb = epi.v1b[r];
     const T v1 = vb + sigma * Ru;
     const T z = T(2) * v1 - vb;
-    const T w = epi.dw[r];
-    T zz = (z + w * epi.da[r]) / (sigma + w);
-    zz = fmin(fmax(zz, epi.dlo[r]), epi.dhi[r]);
-    const T t = z - sigma * zz;
+    const T t = data_resolvent(z, sigma, epi.dw[r], epi.da[r], epi.dlo[r], epi.dhi[r]);
     const T vbn = vb + t - v1;
     epi.Ru[r] = Ru;
     epi.v1b[r] = vbn;

@@ -177,6 +177,27 @@ k_tv_dual_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix
                         prefix[lo + 1] - prefix[lo]);
 }
 
+// Alg. 1, TV dual: w = P_lambda(w + tau grad u_bar) (ball of radius lambda).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cp_tv(const T *__restrict__ ub, int n, T tau, T lam, T inv_h, T *w)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T gx, gy;
+        grad_at(ub, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        const T zx = w[e] + tau * gx, zy = w[e + nn] + tau * gy;
+        T tx = T(0), ty = T(0);
+        if (lam > T(0)) {
+            const T den = fmax(T(1), sqrt(zx * zx + zy * zy) / lam);
+            tx = zx / den;
+            ty = zy / den;
+        }
+        w[e] = tx;
+        w[e + nn] = ty;
+    }
+}
+
 __global__ void k_to_bf16(const float *__restrict__ x, size_t len, __nv_bfloat16 *y)
 {
     for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
@@ -595,6 +616,99 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     if (!std::isfinite(out->objective) || !std::isfinite(out->tv))
         return fail(CTR_ENUMERIC, "non-finite objective after the solve");
     return CTR_OK;
+}
+
+// Alg. 1 (Chambolle-Pock) on the beta-scaled (C_h), from zero: the unpreconditioned
+// baseline.  State: u (p->u), u_bar (p->ubar_u), v (p->v1b), w (p->v2b).  One iteration:
+//   v = prox_{tau g*}(v + tau Rt u_bar)          forward projection of u_bar + epilogue (mode 2)
+//   w = P_lambda(w + tau grad u_bar)             k_cp_tv
+//   u_new = u + sigma div w - sigma Rt^* v,  u_bar = 2 u_new - u   backprojection + epilogue
+// sp = sigma (primal step), sd = tau (dual step) in the notation of Alg. 1.  tau4 is the
+// tau of Alg. 4's saddle form used to report the diagnostics (t2 = w / tau4).
+template <typename T>
+ctr_status cp_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm, double beta, double sp, double sd,
+                   ctr_diag *diag, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    const T lam = (T)(alpha / (beta * beta)), inv_h = (T)(1.0 / p->h);
+    T *u = (T *)p->u, *ub = (T *)p->ubar_u, *v = (T *)p->v1b, *w = (T *)p->v2b;
+    const T *d = (const T *)p->desc;
+    CTR_CUDA(cudaMemsetAsync(u, 0, nn * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(ub, 0, nn * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(v, 0, nm * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(w, 0, 2 * nn * sizeof(T), s));
+    auto one = [&]() -> ctr_status {
+        ctr_status st;
+        ForwardEpi<T> ec{};
+        ec.mode = 2;
+        ec.scale = (T)(1.0 / beta);
+        ec.sigma = (T)sd;
+        ec.v1b = v;
+        ec.dw = d;
+        ec.da = d + nm;
+        ec.dlo = d + 2 * nm;
+        ec.dhi = d + 3 * nm;
+        if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, ub, (T *)p->uT, s)) != CTR_OK) return st;
+        if ((st = launch_forward<T>(p, ub, (const T *)p->uT, ec, s)) != CTR_OK) return st;
+        p->launches++;
+        k_cp_tv<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(ub, n, (T)sd, lam, inv_h, w);
+        CTR_CHECK_LAUNCH("k_cp_tv");
+        BackprojEpi<T> eb{};
+        eb.out = u;
+        eb.scale = (T)(1.0 / beta);
+        eb.px = w;
+        eb.divtau = T(1);
+        eb.outscale = (T)(-sp);
+        eb.inv_h = inv_h;
+        eb.ub = u;              // + u (old)
+        eb.bar_out = ub;        // u_bar = 2 u_new - u
+        return launch_backproject<T>(p, v, eb, s);
+    };
+    ctr_status st;
+    const int blk = prm.graph_block > 0 ? prm.graph_block : 0;
+    int done = 0;
+    if (blk > 0 && iters >= blk) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long before = p->launches;
+        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = CTR_OK;
+        for (int k = 0; k < blk && st == CTR_OK; ++k) st = one();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const unsigned long long per_graph = p->launches - before;
+        p->launches = before;
+        if (st != CTR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        for (; done + blk <= iters; done += blk) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(ce, "cudaGraphLaunch");
+            }
+            p->launches += per_graph;
+        }
+        cudaGraphExecDestroy(exec);
+    }
+    for (; done < iters; ++done)
+        if ((st = one()) != CTR_OK) return st;
+    if (!diag) return CTR_OK;
+    // diagnostics of the saddle problem of Alg. 4 at (u; t1 = v, t2 = w / tau4); du = u - u_prev
+    const T tau4 = (T)prm.tau;
+    p->launches += 3;
+    k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(ub, u, T(-1), nn, (T *)p->du);   // u_bar - u = u - u_prev
+    k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(v, v, T(0), nm, (T *)p->t1);
+    k_axpy<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(w, w, T(1) / tau4 - T(1), 2 * nn, (T *)p->t2);
+    CTR_CHECK_LAUNCH("cp diagnostics set-up");
+    if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, u, (T *)p->uT, s)) != CTR_OK) return st;
+    if ((st = op_forward<T>(p, u, (const T *)p->uT, (T *)p->Ru, 1.0 / beta, s)) != CTR_OK) return st;
+    return compute_diag<T>(p, alpha, beta, prm.tau, 0.0, iters, diag, s);
 }
 
 // Full solve on the plan's internal stream.  desc must already hold the
@@ -1100,6 +1214,8 @@ ctr_status batch_prepare(ctr_batch *b)
     template ctr_status power_lambda<T>(ctr_plan *, double, double, int, double *, cudaStream_t);                     \
     template ctr_status pdrq_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, ctr_diag *,         \
                                      cudaStream_t);                                                                   \
+    template ctr_status cp_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *,   \
+                                   cudaStream_t);                                                                     \
     template ctr_status build_desc_from_data<T>(ctr_plan *, const T *, const uint8_t *, double, double, double,       \
                                                 cudaStream_t);                                                        \
     template ctr_status build_desc_from_arrays<T>(ctr_plan *, const T *, const T *, const T *, const T *, double,     \

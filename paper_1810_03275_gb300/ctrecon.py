@@ -64,7 +64,8 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_plan_launch_count", "ctr_plan_symmetric_jobs", "rh_forward", "rh_forward_t", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run", "ctr_power_beta",
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
-           "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step"]
+           "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
+           "tv_cp_solve"]
 
 
 def load(path: str = LIB_PATH):
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
                                     P(Diag), vp]
         lib.tv_pd_run.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, P(Params), P(State), vp,
                                   P(Diag), vp]
+        lib.tv_cp_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, P(Params), vp, P(Diag), vp]
         lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
         lib.ctr_power_lambda.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(ctypes.c_double), vp]
         lib.precond_apply_static.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -311,6 +314,18 @@ class Plan:
         _check(load().tv_pd_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), mptr, float(alpha),
                                   float(delta), int(iters), ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"),
                                   ctypes.byref(diag), _stream(stream)))
+        return u_out, diag.as_dict()
+
+    def tv_cp_solve(self, f, metal_mask, alpha: float, delta: float, iters: int, sigma_p: float = 0.0,
+                    tau_d: float = 0.0, params: Optional[Params] = None, u_out=None, stream=None):
+        """Alg. 1 (Chambolle-Pock) from u = 0 on problem (C_h); returns (u, diag dict)."""
+        u_out = self.empty_image() if u_out is None else u_out
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_cp_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), self._mask(metal_mask),
+                                  float(alpha), float(delta), int(iters), float(sigma_p), float(tau_d),
+                                  ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag),
+                                  _stream(stream)))
         return u_out, diag.as_dict()
 
     def _state(self, st):
