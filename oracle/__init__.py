@@ -20,6 +20,8 @@ from .pdrq_ref import (
     freq_norm,
     precond_symbol,
     precond_symbol_nonneg,
+    precond_symbol_from,
+    impulse_response_kernel_dft,
     precond_apply,
     prox_dual,
     tv_project,

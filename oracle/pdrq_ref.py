@@ -97,6 +97,34 @@ def precond_symbol_nonneg(n: int, sigma: float, tau: float, c: float, eps: float
     return nrm / (nrm + sigma * sigma * c + (sigma * tau) ** 2 * L * nrm)
 
 
+def impulse_response_kernel_dft(geo: Geometry, floor: float = 1e-3) -> np.ndarray:
+    """Sec. "Impulse response preconditioners": the DFT of the point-symmetrised impulse
+    response of R_h^* R_h, the approximation s of R_h^* R_h used in place of 1/||xi||.
+    Readings: the impulse sits at (n//2, n//2) (for even n the lower right of the middle
+    four pixels, as printed; the middle pixel for odd n); "symmetric" is taken as point
+    symmetry about it, k(x) = (k~(x) + k~(-x))/2 after moving the impulse to the origin,
+    which makes the convolution self-adjoint and the DFT real; the DFT is bounded below by
+    floor * its maximum (the thesis is silent on signs; R_h^* R_h is positive
+    semidefinite, and its discrete impulse response has small negative DFT values at the
+    highest frequencies)."""
+    n = geo.n
+    c = n // 2
+    d = np.zeros((n, n))
+    d[c, c] = 1.0
+    kt = np.roll(rh_adjoint(rh_forward(d, geo), geo), (-c, -c), axis=(0, 1))
+    k = 0.5 * (kt + np.roll(kt[::-1, ::-1], (1, 1), axis=(0, 1)))      # k(x) and k(-x mod n)
+    F = np.real(np.fft.fft2(k))
+    return np.maximum(F, floor * F.max())
+
+
+def precond_symbol_from(n: int, sigma: float, tau: float, c: float, s: np.ndarray, nonneg: bool = False) -> np.ndarray:
+    """Fourier multiplier of M^{-1} for M = sigma^2 c S - (sigma tau)^2 Delta_p (+ id for Alg.
+    5), S the convolution whose DFT is s: s = 1/||xi||_eps gives precond_symbol /
+    precond_symbol_nonneg, s = impulse_response_kernel_dft the impulse-response preconditioner."""
+    L = lap_symbol(n)
+    return 1.0 / ((1.0 if nonneg else 0.0) + sigma * sigma * c * s + (sigma * tau) ** 2 * L)
+
+
 def precond_apply(y: np.ndarray, symbol: np.ndarray) -> np.ndarray:
     """x = F^{-1}(F(y) * symbol) with the 2-D DFT (numpy FFT as one step)."""
     return np.real(np.fft.ifft2(np.fft.fft2(np.asarray(y, dtype=np.float64)) * symbol))
@@ -203,9 +231,12 @@ def power_beta(geo: Geometry, iters: int = 50) -> float:
     return float(np.sqrt(max(lam, 0.0)))
 
 
-def power_c(geo: Geometry, beta: float, eps: float, iters: int = 50, margin: float = 1.05) -> float:
+def power_c(geo: Geometry, beta: float, eps: float, iters: int = 50, margin: float = 1.05,
+            s: Optional[np.ndarray] = None) -> float:
+    """c = margin x the largest eigenvalue of S^{-1/2} Rt^* Rt S^{-1/2} (S the convolution
+    with DFT s; default s = 1/||xi||_eps, Sec. 4.3.1), by power iteration from the R2 start."""
     n = geo.n
-    half = np.sqrt(freq_norm(n, eps))
+    half = np.sqrt(freq_norm(n, eps)) if s is None else 1.0 / np.sqrt(s)
 
     def mhalf(x):
         return np.real(np.fft.ifft2(np.fft.fft2(x) * half))
@@ -253,7 +284,7 @@ class PDRQState:
 
 def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, tau: float,
                eps: float, beta: float, c: float, state: Optional[PDRQState] = None,
-               callback=None) -> PDRQState:
+               callback=None, symbol: Optional[np.ndarray] = None) -> PDRQState:
     """Run ``iters`` iterations of Alg. 4 on the problem scaled by beta (Sec. 5.1).
 
     desc = (w, a, lo, hi) per bin in the original scale (see make_descriptors).
@@ -270,7 +301,7 @@ def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, t
     w, a, lo, hi = (np.asarray(x, dtype=np.float64) for x in desc)
     at, lot, hit = a / beta, lo / beta, hi / beta
     lam = alpha / (beta * beta)
-    m = precond_symbol(geo.n, sigma, tau, c, eps)
+    m = precond_symbol(geo.n, sigma, tau, c, eps) if symbol is None else symbol
     st = PDRQState.zeros(geo) if state is None else state.copy()
     for _ in range(iters):
         y1 = st.v1b + sigma * st.Ru
