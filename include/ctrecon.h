@@ -72,6 +72,14 @@ typedef struct {
                           * first step adds bar u - u and bar u += max(2 u - bar u, 0) - u after
                           * each update.  0 (default): Alg. 4.  Also selects the symbol that
                           * precond_apply applies. */
+    int precond;         /* 0 (default): inverse-norm preconditioner, S = F^{-1}(1/||xi||_eps)F
+                          * (Sec. 4.3.1).  1: impulse response (Sec. "Impulse response
+                          * preconditioners"): S = convolution with k = R_h^* R_h delta, the
+                          * response to the impulse at (n/2, n/2) made point-symmetric, its DFT
+                          * bounded below by 1e-3 of its maximum; built on the plan's first use
+                          * (a few kernel launches, no allocation).  Either way M = sigma^2 c S +
+                          * (sigma tau)^2 (-Delta_p) and c is from the power iteration on
+                          * S^{-1/2} R^*R S^{-1/2}.  Batched solves take 0 only. */
 } ctr_params;
 
 /* Diagnostics after the solve (original, unscaled problem unless noted). */

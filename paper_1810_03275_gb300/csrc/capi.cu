@@ -49,6 +49,16 @@ template <typename T>
 ctr_status pdrq_loop(ctr_plan *, double, int, const ctr_params &, double, double, ctr_diag *, cudaStream_t);
 template <typename T>
 ctr_status cp_loop(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *, cudaStream_t);
+template <typename T> ctr_status prepare_impulse_symbol(ctr_plan *, cudaStream_t);
+
+// The preconditioner that params select (inverse norm, or the impulse response of
+// R_h^* R_h, built on the first use of the plan).
+template <typename T>
+ctr_status select_precond(ctr_plan *p, const ctr_params &q, cudaStream_t s)
+{
+    p->precond_kind = q.precond;
+    return q.precond == 1 ? prepare_impulse_symbol<T>(p, s) : CTR_OK;
+}
 template <typename T>
 ctr_status build_desc_from_data(ctr_plan *, const T *, const uint8_t *, double, double, double, cudaStream_t);
 template <typename T>
@@ -250,6 +260,7 @@ ctr_status check_params(const ctr_params &q)
     if (!std::isfinite(q.trace_ratio)) return fail(CTR_EINVAL, "trace_ratio must be finite");
     if (q.graph_block < 0 || q.check_every < 0) return fail(CTR_EINVAL, "graph_block and check_every must be >= 0");
     if (q.nonneg != 0 && q.nonneg != 1) return fail(CTR_EINVAL, "nonneg must be 0 or 1");
+    if (q.precond != 0 && q.precond != 1) return fail(CTR_EINVAL, "precond must be 0 or 1");
     return CTR_OK;
 }
 
@@ -293,6 +304,7 @@ ctr_status solve_impl(ctr_plan *p, const void *f, const uint8_t *mask, const voi
     ctr_status st = sj.begin();
     if (st != CTR_OK) return st;
     cudaStream_t s = p->stream;
+    if ((st = select_precond<T>(p, q, s)) != CTR_OK) return st;
     double beta = q.beta;
     if (!(beta > 0)) {
         if ((st = power_beta<T>(p, q.power_iters, &beta, s)) != CTR_OK) return st;
@@ -393,6 +405,7 @@ void ctr_default_params(ctr_params *q)
     q->check_every = 0;
     q->graph_block = 25;
     q->nonneg = 0;
+    q->precond = 0;
 }
 
 size_t ctr_plan_device_bytes(const ctr_plan *p) { return p ? p->bytes : 0; }
@@ -467,6 +480,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->v1b, es * nm);
     ALLOC(p->t1, es * nm);
     ALLOC(p->ubar_u, es * nn);
+    ALLOC(p->pk_s, es * nn);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
     if (p->bf16) {
@@ -577,9 +591,11 @@ ctr_status precond_apply(ctr_plan *p, const ctr_params *prm, const void *y, void
     if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
     cudaStream_t s = (cudaStream_t)stream;
     if (p->dtype == CTR_F64) {
+        if ((st = select_precond<double>(p, q, s)) != CTR_OK) return st;
         if ((st = launch_symbols<double>(p, q.sigma, q.tau, q.c, q.eps, s, q.nonneg != 0)) != CTR_OK) return st;
         return launch_circulant<double>(p, (const double *)y, false, (const double *)p->sym, (double *)x, 0, nullptr, nullptr, s);
     }
+    if ((st = select_precond<float>(p, q, s)) != CTR_OK) return st;
     if ((st = launch_symbols<float>(p, q.sigma, q.tau, q.c, q.eps, s, q.nonneg != 0)) != CTR_OK) return st;
     return launch_circulant<float>(p, (const float *)y, false, (const float *)p->sym, (float *)x, 0, nullptr, nullptr, s);
 }
@@ -672,6 +688,8 @@ ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, doubl
     if (st != CTR_OK) return st;
     if (!(q.beta > 0) || !(q.c > 0)) return fail(CTR_EINVAL, "the reverse mode needs beta and c given (> 0)");
     cudaStream_t s = (cudaStream_t)stream;
+    st = p->dtype == CTR_F64 ? select_precond<double>(p, q, s) : select_precond<float>(p, q, s);
+    if (st != CTR_OK) return st;
     if (p->dtype == CTR_F64)
         return pdrq_vjp_step<double>(p, (const double *)s0->u, (const double *)s0->v1b, (const double *)s0->v2b,
                                      (const double *)s1->u, (const double *)s1->Ru, (const double *)f, mask, delta,
@@ -791,6 +809,7 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
     ctr_status st = check_params(qc);
     if (st != CTR_OK) return st;
     if (q.nonneg) return fail(CTR_EUNSUPPORTED, "batched solves cover Alg. 4 only (nonneg = 0)");
+    if (q.precond) return fail(CTR_EUNSUPPORTED, "batched solves use the inverse-norm preconditioner (precond = 0)");
     CTR_CUDA(cudaEventRecord(b->ev_in, (cudaStream_t)stream));
     CTR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
     st = batch_solve(b, (const float *const *)f_devs, masks, alphas, deltas, iters, q, betas, cs,
@@ -818,6 +837,7 @@ ctr_status ctr_power_lambda(ctr_plan *p, double beta, double eps, int iters, dou
     StreamJoin sj(p, stream);
     ctr_status st = sj.begin();
     if (st != CTR_OK) return st;
+    p->precond_kind = 0;   // this entry point is the inverse-norm form; solves choose their own
     return CTR_DISPATCH(p, power_lambda<float>(p, beta, eps, iters, lam, p->stream),
                         power_lambda<double>(p, beta, eps, iters, lam, p->stream));
 }

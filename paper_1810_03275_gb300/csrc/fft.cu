@@ -281,7 +281,8 @@ k_fft_rows_fwd(RowsInput<T> src, typename C2<T>::type *cbuf, int n, int rows_per
     fft_rows_fwd_body<T>(src, cbuf, n, rows_per_cta, fp, tw, blockIdx.x);
 }
 
-// Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf).
+// Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf);
+// sym == null: the forward column FFT only.
 template <typename T>
 __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
                                               const FftPasses &fp, const typename C2<T>::type *__restrict__ tw,
@@ -307,6 +308,16 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
     });
     __syncthreads();
     T2 *res = fft_smem<T>(a, b, n, cnt, ld, fp, -1, stw);
+    if (!sym) {                                   // forward transform only: write F back
+        staged_copy(cnt * n, [&](int e) {
+            const int row = fast_div(e, cnt, mc);
+            return res[(size_t)(e - row * cnt) * ld + row];
+        }, [&](int e, T2 v) {
+            const int row = fast_div(e, cnt, mc);
+            cbuf[(size_t)row * n + c0 + (e - row * cnt)] = v;
+        });
+        return;
+    }
     staged_copy(cnt * n, [&](int e) {
         const int row = fast_div(e, cnt, mc);
         return sym[(size_t)row * n + c0 + (e - row * cnt)];
@@ -437,7 +448,8 @@ k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 //   sym  = ||xi||_eps / (sigma^2 c + (sigma tau)^2 L ||xi||_eps) / n^2
 //   symh = sqrt(||xi||_eps) / n^2
 template <typename T>
-__global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, double c, double eps, int nonneg)
+__global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, double c, double eps, int nonneg,
+                          const T *__restrict__ s_arr)
 {
     const size_t total = (size_t)n * n;
     const double pi = 3.14159265358979323846;
@@ -450,6 +462,13 @@ __global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, doub
         const double nrm = sqrt(xi * xi + xj * xj + eps * eps);
         const double si = sin(pi * i / n), sj = sin(pi * j / n);
         const double L = 4.0 * si * si + 4.0 * sj * sj;
+        if (s_arr) {
+            // M = sigma^2 c S - (sigma tau)^2 Delta_p (+ id), S the convolution with DFT s
+            const double sv = (double)s_arr[e];
+            sym[e] = (T)(inv_n2 / ((nonneg ? 1.0 : 0.0) + sigma * sigma * c * sv + (sigma * tau) * (sigma * tau) * L));
+            if (symh) symh[e] = (T)(inv_n2 / sqrt(sv));
+            continue;
+        }
         const double id = nonneg ? nrm : 0.0;   // Alg. 5: M = id + c sigma^2 F^{-1}(1/||xi||)F - (sigma tau)^2 Delta
         sym[e] = (T)(nrm / (id + sigma * sigma * c + (sigma * tau) * (sigma * tau) * L * nrm) * inv_n2);
         if (symh) symh[e] = (T)(sqrt(nrm) * inv_n2);
@@ -509,6 +528,29 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
     return CTR_OK;
 }
 
+// cbuf = F2(in_real), the plain 2-D forward DFT (row pass, then the column pass alone).
+template <typename T>
+ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t s)
+{
+    using T2 = typename C2<T>::type;
+    const int n = p->n;
+    const FftPasses fp = make_passes(p);
+    const T2 *tw = reinterpret_cast<const T2 *>(p->d_twiddle);
+    T2 *cb = reinterpret_cast<T2 *>(p->cbuf);
+    const int rpc = rows_per_cta(p), cw = cols_per_cta(p);
+    RowsInput<T> src{};
+    src.in_real = in_real;
+    p->launches++;
+    k_fft_rows_fwd<T><<<(n + rpc - 1) / rpc, FFT_THREADS, fft_smem_bytes(p, 0), s>>>(src, cb, n, rpc, fp, tw);
+    CTR_CHECK_LAUNCH("k_fft_rows_fwd");
+    p->launches++;
+    k_fft_cols<T><<<(n + cw - 1) / cw, FFT_THREADS, fft_smem_bytes(p, 1), s>>>(cb, nullptr, n, cw, fp, tw);
+    CTR_CHECK_LAUNCH("k_fft_cols");
+    return CTR_OK;
+}
+template ctr_status launch_fft2_forward<float>(const ctr_plan *, const float *, cudaStream_t);
+template ctr_status launch_fft2_forward<double>(const ctr_plan *, const double *, cudaStream_t);
+
 template <typename T>
 ctr_status configure_fft(const ctr_plan *p)
 {
@@ -527,7 +569,8 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     p->launches++;
-    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0);
+    const T *s_arr = p->precond_kind == 1 ? (const T *)p->pk_s : nullptr;   // impulse response
+    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0, s_arr);
     CTR_CHECK_LAUNCH("k_symbols");
     return CTR_OK;
 }
@@ -683,7 +726,7 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     const size_t nn = (size_t)n * n;
     int blocks = (int)((nn + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps, 0);
+    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps, 0, nullptr);
     const int rpc = fft_rows_per_cta(n), cw = fft_cols_per_cta(n, sizeof(float));
     const size_t smr = fft_rows_smem(n, sizeof(float)), smc = fft_cols_smem(n, sizeof(float));
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;

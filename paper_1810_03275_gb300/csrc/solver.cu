@@ -198,6 +198,45 @@ k_cp_tv(const T *__restrict__ ub, int n, T tau, T lam, T inv_h, T *w)
     }
 }
 
+// Impulse-response preconditioner set-up -------------------------------------------
+template <typename T>
+__global__ void k_set_one(T *x) { *x = T(1); }
+
+// k(i, j) = (kt(i, j) + kt(-i, -j)) / 2 with kt the impulse response y moved from
+// (c, c) to the origin (indices mod n): the point-symmetric kernel.
+template <typename T>
+__global__ void k_kernel_sym(const T *__restrict__ y, int n, int c, T *k)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const int ia = (i + c) % n, ja = (j + c) % n;
+        const int ib = ((c - i) % n + n) % n, jb = ((c - j) % n + n) % n;
+        k[e] = T(0.5) * (y[(size_t)ia * n + ja] + y[(size_t)ib * n + jb]);
+    }
+}
+
+// max over the real parts (the maximum is positive: it is at least the DC value, the
+// sum of the kernel); positive doubles order like their bit patterns
+template <typename T2>
+__global__ void k_real_max(const T2 *__restrict__ F, size_t len, unsigned long long *mx)
+{
+    double m = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, (double)F[e].x);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T, typename T2>
+__global__ void k_real_floor(const T2 *__restrict__ F, size_t len, const unsigned long long *__restrict__ mx,
+                             double floor_frac, T *s)
+{
+    const double lo = floor_frac * __longlong_as_double((long long)*mx);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+        s[e] = (T)fmax((double)F[e].x, lo);
+}
+
 __global__ void k_to_bf16(const float *__restrict__ x, size_t len, __nv_bfloat16 *y)
 {
     for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
@@ -615,6 +654,40 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     out->iters_done = iters_done;
     if (!std::isfinite(out->objective) || !std::isfinite(out->tv))
         return fail(CTR_ENUMERIC, "non-finite objective after the solve");
+    return CTR_OK;
+}
+
+// The impulse-response preconditioner's DFT s (Sec. "Impulse response preconditioners"),
+// built once per plan: the response of R_h^* R_h to the impulse at (n/2, n/2), made
+// point-symmetric about it and moved to the origin, transformed by the 2-D DFT (real by
+// the symmetry), bounded below by 1e-3 of its maximum.  Leaves it in p->pk_s.
+template <typename T>
+ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
+{
+    if (p->pk_ready) return CTR_OK;
+    using T2 = typename Cplx<T>::type;
+    const int n = p->n, c = n / 2;
+    const size_t nn = (size_t)n * n;
+    T *x = (T *)p->x, *xt = (T *)p->xt, *y = (T *)p->du, *g = (T *)p->gs;
+    ctr_status st;
+    CTR_CUDA(cudaMemsetAsync(x, 0, nn * sizeof(T), s));
+    p->launches++;
+    k_set_one<T><<<1, 1, 0, s>>>(x + (size_t)c * n + c);
+    CTR_CHECK_LAUNCH("k_set_one");
+    if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return st;
+    if ((st = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return st;
+    if ((st = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return st;
+    p->launches++;
+    k_kernel_sym<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(y, n, c, xt);
+    CTR_CHECK_LAUNCH("k_kernel_sym");
+    if ((st = launch_fft2_forward<T>(p, xt, s)) != CTR_OK) return st;
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(p->d_red);
+    CTR_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+    p->launches += 2;
+    k_real_max<T2><<<grid_for(nn, 256, 1024), 256, 0, s>>>((const T2 *)p->cbuf, nn, mx);
+    k_real_floor<T, T2><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T2 *)p->cbuf, nn, mx, 1e-3, (T *)p->pk_s);
+    CTR_CHECK_LAUNCH("impulse symbol");
+    p->pk_ready = true;
     return CTR_OK;
 }
 
@@ -1216,6 +1289,7 @@ ctr_status batch_prepare(ctr_batch *b)
                                      cudaStream_t);                                                                   \
     template ctr_status cp_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *,   \
                                    cudaStream_t);                                                                     \
+    template ctr_status prepare_impulse_symbol<T>(ctr_plan *, cudaStream_t);                                          \
     template ctr_status build_desc_from_data<T>(ctr_plan *, const T *, const uint8_t *, double, double, double,       \
                                                 cudaStream_t);                                                        \
     template ctr_status build_desc_from_arrays<T>(ctr_plan *, const T *, const T *, const T *, const T *, double,     \

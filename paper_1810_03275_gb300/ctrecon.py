@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("eps", ctypes.c_double),
                 ("c", ctypes.c_double), ("beta", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("c_margin", ctypes.c_double), ("trace_ratio", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int), ("nonneg", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int), ("nonneg", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class Diag(ctypes.Structure):
