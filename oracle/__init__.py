@@ -23,6 +23,14 @@ from .pdrq_ref import (
     precond_symbol_from,
     impulse_response_kernel_dft,
     precond_apply,
+    flatten,
+    unflatten,
+    circulant_first_column,
+    circulant_kernel_dft,
+    circulant_laplace_dft,
+    precond_symbol_circulant,
+    precond_apply_circulant,
+    richardson_m,
     prox_dual,
     tv_project,
     conj_data_term,

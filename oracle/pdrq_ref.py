@@ -1,7 +1,7 @@
 """FP64 numpy oracle for everything around R_h: the discrete gradient and
 divergence, the pointwise resolvents, the inverse-norm Fourier preconditioner,
-the power iterations, Alg. 4 (PDRQS1), Alg. 5 (PDRQS1 with u >= 0) and Alg. 1
-(Chambolle-Pock).
+the impulse-response, circulant and Richardson preconditioners, the power
+iterations, Alg. 4 (PDRQS1), Alg. 5 (PDRQS1 with u >= 0) and Alg. 1 (Chambolle-Pock).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows
 the thesis step by step, with library primitives (numpy FFT) as single steps;
@@ -131,6 +131,77 @@ def precond_apply(y: np.ndarray, symbol: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Sec. "Circulant matrix preconditioner": R_h^* R_h and -Delta_h approximated by
+# circulant matrices acting on the image flattened to a vector of n^2 entries, and
+# inverted with the 1-D DFT F_{h,1} of length n^2.
+# Readings: the image u[i, j] is flattened with the first index running fastest,
+# t = i + n j (column-major, the order of the thesis's MATLAB arrays); the impulse is
+# the same point function as in the impulse-response section, at (n//2, n//2), flat
+# index p = n//2 + n (n//2); its response is moved to index 0 (the first column of the
+# circulant is the response to the first unit vector) and then symmetrised as
+# printed, k_t = (k~_t + k~_{(n^2 - t) mod n^2}) / 2; the Laplace kernel comes from
+# -Delta_h delta = -div_h grad_h delta by the same steps; the DFT of k is bounded
+# below by 1e-3 of its maximum, as for the impulse-response preconditioner.
+# ----------------------------------------------------------------------------
+def flatten(u: np.ndarray) -> np.ndarray:
+    """Image -> vector, t = i + n j."""
+    return np.asarray(u).reshape(-1, order="F")
+
+
+def unflatten(x: np.ndarray, n: int) -> np.ndarray:
+    return np.asarray(x).reshape((n, n), order="F")
+
+
+def circulant_first_column(response: np.ndarray) -> np.ndarray:
+    """The symmetrised first column k of the circulant from the response (n x n) to the
+    impulse at (n//2, n//2)."""
+    n = response.shape[0]
+    p = n // 2 + n * (n // 2)
+    kt = np.roll(flatten(response), -p)                    # impulse moved to index 0
+    return 0.5 * (kt + kt[(-np.arange(n * n)) % (n * n)])
+
+
+def circulant_kernel_dft(geo: Geometry, floor: float = 1e-3) -> np.ndarray:
+    """F_{h,1}(k), k the symmetrised circulant column of R_h^* R_h (length n^2, real by
+    the symmetry), bounded below by floor * its maximum."""
+    n = geo.n
+    d = np.zeros((n, n))
+    d[n // 2, n // 2] = 1.0
+    k = circulant_first_column(rh_adjoint(rh_forward(d, geo), geo))
+    F = np.real(np.fft.fft(k))
+    return np.maximum(F, floor * F.max())
+
+
+def circulant_laplace_dft(n: int, h: float = 1.0) -> np.ndarray:
+    """F_{h,1}(kappa_Delta), kappa_Delta the symmetrised circulant column of -Delta_h."""
+    d = np.zeros((n, n))
+    d[n // 2, n // 2] = 1.0
+    return np.real(np.fft.fft(circulant_first_column(-div(*grad(d, h), h))))
+
+
+def precond_symbol_circulant(n: int, sigma: float, tau: float, c: float, s1: np.ndarray, lap1: np.ndarray,
+                             nonneg: bool = False) -> np.ndarray:
+    """1-D multiplier of M^{-1}, M = sigma^2 c C_k + (sigma tau)^2 C_Delta (+ id for Alg. 5)."""
+    return 1.0 / ((1.0 if nonneg else 0.0) + sigma * sigma * c * s1 + (sigma * tau) ** 2 * lap1)
+
+
+def precond_apply_circulant(y: np.ndarray, symbol1: np.ndarray) -> np.ndarray:
+    """x = F_{h,1}^{-1}(F_{h,1}(y) * symbol1) on the flattened image."""
+    y = np.asarray(y, dtype=np.float64)
+    return unflatten(np.real(np.fft.ifft(np.fft.fft(flatten(y)) * symbol1)), y.shape[0])
+
+
+# ----------------------------------------------------------------------------
+# Sec. "Suitable Preconditioners": Richardson, M = m id with m >= ||T||.
+# Reading: with T = sigma^2 Rt^* Rt + (sigma tau)^2 (-Delta_h) the constant is taken
+# as m = sigma^2 c + (sigma tau)^2 8 / h^2, c >= ||Rt^* Rt|| from the power iteration
+# (with S = id) and 8 / h^2 >= ||-Delta_h||, so M - T >= 0 holds term by term.
+# ----------------------------------------------------------------------------
+def richardson_m(sigma: float, tau: float, c: float, h: float = 1.0, nonneg: bool = False) -> float:
+    return (1.0 if nonneg else 0.0) + sigma * sigma * c + (sigma * tau) ** 2 * 8.0 / (h * h)
+
+
+# ----------------------------------------------------------------------------
 # Sec. 3.3 / 3.5: pointwise resolvents.
 # Per-bin data term g_r(z) = (w_r/2)(z - a_r)^2 + I_[lo_r, hi_r](z).  By
 # Lemma lem_loc the resolvent of sigma*G1^* acts per bin, and by the Moreau
@@ -232,13 +303,16 @@ def power_beta(geo: Geometry, iters: int = 50) -> float:
 
 
 def power_c(geo: Geometry, beta: float, eps: float, iters: int = 50, margin: float = 1.05,
-            s: Optional[np.ndarray] = None) -> float:
+            s: Optional[np.ndarray] = None, circulant: bool = False) -> float:
     """c = margin x the largest eigenvalue of S^{-1/2} Rt^* Rt S^{-1/2} (S the convolution
-    with DFT s; default s = 1/||xi||_eps, Sec. 4.3.1), by power iteration from the R2 start."""
+    with 2-D DFT s; default s = 1/||xi||_eps, Sec. 4.3.1; with circulant=True, S the
+    circulant with 1-D DFT s on the flattened image), by power iteration from the R2 start."""
     n = geo.n
     half = np.sqrt(freq_norm(n, eps)) if s is None else 1.0 / np.sqrt(s)
 
     def mhalf(x):
+        if circulant:
+            return precond_apply_circulant(x, half)
         return np.real(np.fft.ifft2(np.fft.fft2(x) * half))
 
     z = power_start(n)
@@ -284,8 +358,10 @@ class PDRQState:
 
 def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, tau: float,
                eps: float, beta: float, c: float, state: Optional[PDRQState] = None,
-               callback=None, symbol: Optional[np.ndarray] = None) -> PDRQState:
+               callback=None, symbol: Optional[np.ndarray] = None, circulant: bool = False) -> PDRQState:
     """Run ``iters`` iterations of Alg. 4 on the problem scaled by beta (Sec. 5.1).
+    symbol: the multiplier of M^{-1} (default: the inverse-norm one); circulant=True
+    applies it with the 1-D DFT of the flattened image (circulant preconditioner).
 
     desc = (w, a, lo, hi) per bin in the original scale (see make_descriptors).
     One iteration, in the order of Alg. 4:
@@ -309,7 +385,7 @@ def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, t
         y2x = st.v2bx + sigma * tau * gx
         y2y = st.v2by + sigma * tau * gy
         u_tmp = -sigma * (rh_adjoint(y1, geo) / beta - tau * div(y2x, y2y, h))
-        u_new = st.u + precond_apply(u_tmp, m)
+        u_new = st.u + (precond_apply_circulant(u_tmp, m) if circulant else precond_apply(u_tmp, m))
         Ru_new = rh_forward(u_new, geo) / beta
         v1 = st.v1b + sigma * Ru_new
         gx, gy = grad(u_new, h)
