@@ -76,10 +76,17 @@ typedef struct {
                           * (Sec. 4.3.1).  1: impulse response (Sec. "Impulse response
                           * preconditioners"): S = convolution with k = R_h^* R_h delta, the
                           * response to the impulse at (n/2, n/2) made point-symmetric, its DFT
-                          * bounded below by 1e-3 of its maximum; built on the plan's first use
-                          * (a few kernel launches, no allocation).  Either way M = sigma^2 c S +
-                          * (sigma tau)^2 (-Delta_p) and c is from the power iteration on
-                          * S^{-1/2} R^*R S^{-1/2}.  Batched solves take 0 only. */
+                          * bounded below by 1e-3 of its maximum.  2: circulant (Sec.
+                          * "Circulant matrix preconditioner"): the same response on the image
+                          * flattened as t = i + n j, rolled to t = 0 and symmetrised, S its
+                          * circulant matrix, inverted with the 1-D DFT of length n^2 (the
+                          * Laplacian term likewise the circulant of -Delta_h).  3: Richardson
+                          * (Sec. "Suitable Preconditioners"): S = id and the Laplacian term
+                          * replaced by its bound 8/h^2, M = (sigma^2 c + 8 (sigma tau)^2/h^2) id.
+                          * Kinds 1 and 2 build their kernel DFT on the plan's first use (a few
+                          * kernel launches, no allocation).  In all kinds M = sigma^2 c S +
+                          * (sigma tau)^2 Lap (+ id with nonneg) and c is from the power
+                          * iteration on S^{-1/2} R^*R S^{-1/2}.  Batched solves take 0 only. */
 } ctr_params;
 
 /* Diagnostics after the solve (original, unscaled problem unless noted). */

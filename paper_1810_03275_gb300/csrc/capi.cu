@@ -51,13 +51,14 @@ template <typename T>
 ctr_status cp_loop(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *, cudaStream_t);
 template <typename T> ctr_status prepare_impulse_symbol(ctr_plan *, cudaStream_t);
 
-// The preconditioner that params select (inverse norm, or the impulse response of
-// R_h^* R_h, built on the first use of the plan).
+// The preconditioner that params select (inverse norm, impulse response, circulant or
+// Richardson); the DFTs of the impulse-response and circulant kernels are built on their
+// first use by the plan.
 template <typename T>
 ctr_status select_precond(ctr_plan *p, const ctr_params &q, cudaStream_t s)
 {
     p->precond_kind = q.precond;
-    return q.precond == 1 ? prepare_impulse_symbol<T>(p, s) : CTR_OK;
+    return (q.precond == 1 || q.precond == 2) ? prepare_impulse_symbol<T>(p, s) : CTR_OK;
 }
 template <typename T>
 ctr_status build_desc_from_data(ctr_plan *, const T *, const uint8_t *, double, double, double, cudaStream_t);
@@ -260,7 +261,7 @@ ctr_status check_params(const ctr_params &q)
     if (!std::isfinite(q.trace_ratio)) return fail(CTR_EINVAL, "trace_ratio must be finite");
     if (q.graph_block < 0 || q.check_every < 0) return fail(CTR_EINVAL, "graph_block and check_every must be >= 0");
     if (q.nonneg != 0 && q.nonneg != 1) return fail(CTR_EINVAL, "nonneg must be 0 or 1");
-    if (q.precond != 0 && q.precond != 1) return fail(CTR_EINVAL, "precond must be 0 or 1");
+    if (q.precond < 0 || q.precond > 3) return fail(CTR_EINVAL, "precond must be 0, 1, 2 or 3");
     return CTR_OK;
 }
 

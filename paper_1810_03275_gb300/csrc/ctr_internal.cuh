@@ -254,9 +254,10 @@ struct ctr_plan {
     void *v1b = nullptr;       // N*M
     void *t1 = nullptr;        // N*M
     void *ubar_u = nullptr;    // n*n bar u of Alg. 5 (non-negativity)
-    int precond_kind = 0;      // 0: inverse norm (Sec. 4.3.1); 1: impulse response (symbol from pk_s)
-    void *pk_s = nullptr;      // n*n DFT of the symmetrised impulse response of R_h^* R_h (lazily built)
-    bool pk_ready = false;
+    int precond_kind = 0;      // 0: inverse norm (Sec. 4.3.1); 1: impulse response; 2: circulant; 3: Richardson
+    void *pk_s = nullptr;      // n*n DFT (2-D for kind 1, 1-D of the flattened image for kind 2) of the
+                               // symmetrised impulse response of R_h^* R_h (built on first use)
+    int pk_kind = 0;           // the kind pk_s currently holds (0: none)
     void *gs = nullptr;        // N*M scratch sinogram
     void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
     double *d_red = nullptr;   // reduction partials
@@ -302,7 +303,7 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
                           bool nonneg = false);
 // cbuf = the 2-D forward DFT of the real n x n image in_real
 template <typename T>
-ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t s);
+ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t s, bool twist = false);
 
 template <typename T> ctr_status configure_radon(const ctr_plan *p);   // smem attributes, at plan creation
 template <typename T> ctr_status configure_fft(const ctr_plan *p);

@@ -51,6 +51,21 @@ template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
     return r;
 }
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { a.x += b.x; a.y += b.y; return a; }
+
+// exp(-2 pi i r / N) for the twisted column pass (0 <= r < N <= 2^24, so r and N are
+// exact in FP32)
+__device__ __forceinline__ float2 twist_factor(float, int r, int N)
+{
+    float sn, cs;
+    sincospif(2.0f * (float)r / (float)N, &sn, &cs);
+    return make_float2(cs, -sn);
+}
+__device__ __forceinline__ double2 twist_factor(double, int r, int N)
+{
+    double sn, cs;
+    sincospi(2.0 * (double)r / (double)N, &sn, &cs);
+    return make_double2(cs, -sn);
+}
 template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { a.x -= b.x; a.y -= b.y; return a; }
 
 // x / d for 0 <= x, x d < 2^32 through a multiply-high: m = floor(2^32 / d) + 1
@@ -283,10 +298,16 @@ k_fft_rows_fwd(RowsInput<T> src, typename C2<T>::type *cbuf, int n, int rows_per
 
 // Column FFT, multiply by the real symbol, inverse column FFT (in place on cbuf);
 // sym == null: the forward column FFT only.
+// twist: the 1-D DFT of length N = n^2 of the image flattened as t = i + n j (the
+// circulant preconditioner) instead of the 2-D DFT.  With k = kB + n kA,
+//   sum_t x_t e^{-2 pi i t k / N} = sum_i e^{-2 pi i i kA / n} [ e^{-2 pi i i kB / N} sum_j x_ij e^{-2 pi i j kB / n} ],
+// so the row pass is unchanged, the column pass multiplies element (i, kB) by
+// e^{-2 pi i i kB / N} before its forward transform (and by the conjugate after the
+// inverse one), and F_1(x)_k lands at (kA, kB), i.e. at flat position k.
 template <typename T>
 __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
                                               const FftPasses &fp, const typename C2<T>::type *__restrict__ tw,
-                                              int bx)
+                                              int bx, int twist = 0)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -304,6 +325,7 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
         return cbuf[(size_t)row * n + c0 + (e - row * cnt)];
     }, [&](int e, T2 v) {
         const int row = fast_div(e, cnt, mc);
+        if (twist) v = cmul(v, twist_factor(T(0), row * (c0 + e - row * cnt), n * n));
         a[(size_t)(e - row * cnt) * ld + row] = v;
     });
     __syncthreads();
@@ -335,6 +357,11 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
         return res2[(size_t)(e - row * cnt) * ld + row];
     }, [&](int e, T2 v) {
         const int row = fast_div(e, cnt, mc);
+        if (twist) {
+            T2 w = twist_factor(T(0), row * (c0 + e - row * cnt), n * n);
+            w.y = -w.y;
+            v = cmul(v, w);
+        }
         cbuf[(size_t)row * n + c0 + (e - row * cnt)] = v;
     });
 }
@@ -342,9 +369,9 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
 template <typename T>
 __global__ void __launch_bounds__(FFT_THREADS)
 k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw, FftPasses fp,
-           const typename C2<T>::type *__restrict__ tw)
+           const typename C2<T>::type *__restrict__ tw, int twist)
 {
-    fft_cols_body<T>(cbuf, sym, n, cw, fp, tw, blockIdx.x);
+    fft_cols_body<T>(cbuf, sym, n, cw, fp, tw, blockIdx.x, twist);
 }
 
 // Inverse row FFTs and the epilogue on the real part v:
@@ -449,7 +476,7 @@ k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 //   symh = sqrt(||xi||_eps) / n^2
 template <typename T>
 __global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, double c, double eps, int nonneg,
-                          const T *__restrict__ s_arr)
+                          int kind, double inv_h2, const T *__restrict__ s_arr)
 {
     const size_t total = (size_t)n * n;
     const double pi = 3.14159265358979323846;
@@ -462,10 +489,25 @@ __global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, doub
         const double nrm = sqrt(xi * xi + xj * xj + eps * eps);
         const double si = sin(pi * i / n), sj = sin(pi * j / n);
         const double L = 4.0 * si * si + 4.0 * sj * sj;
-        if (s_arr) {
-            // M = sigma^2 c S - (sigma tau)^2 Delta_p (+ id), S the convolution with DFT s
+        const double st2 = (sigma * tau) * (sigma * tau), id1 = nonneg ? 1.0 : 0.0;
+        if (kind == 3) {
+            // Richardson: M = (sigma^2 c + (sigma tau)^2 8 / h^2) id (+ id), S = id
+            sym[e] = (T)(inv_n2 / (id1 + sigma * sigma * c + st2 * 8.0 * inv_h2));
+            if (symh) symh[e] = (T)inv_n2;
+            continue;
+        }
+        if (kind == 1 || kind == 2) {
+            // M = sigma^2 c S + (sigma tau)^2 Lap (+ id), S the convolution (kind 1, 2-D DFT s)
+            // or the circulant (kind 2, 1-D DFT s of the flattened image, position e = flat
+            // frequency k) with Lap = -Delta_p resp. the circulant of -Delta_h, whose
+            // 1-D DFT is (4 - 2 cos(2 pi k / n^2) - 2 cos(2 pi k / n)) / h^2
             const double sv = (double)s_arr[e];
-            sym[e] = (T)(inv_n2 / ((nonneg ? 1.0 : 0.0) + sigma * sigma * c * sv + (sigma * tau) * (sigma * tau) * L));
+            double Lk = L;
+            if (kind == 2) {
+                const double nn2 = (double)n * (double)n;
+                Lk = (4.0 - 2.0 * cospi(2.0 * (double)e / nn2) - 2.0 * cospi(2.0 * (double)j / n)) * inv_h2;
+            }
+            sym[e] = (T)(inv_n2 / (id1 + sigma * sigma * c * sv + st2 * Lk));
             if (symh) symh[e] = (T)(inv_n2 / sqrt(sv));
             continue;
         }
@@ -520,7 +562,7 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
     k_fft_rows_fwd<T><<<gr, FFT_THREADS, smr, s>>>(src, cb, n, rpc, fp, tw);
     CTR_CHECK_LAUNCH("k_fft_rows_fwd");
     p->launches++;
-    k_fft_cols<T><<<gc, FFT_THREADS, smc, s>>>(cb, sym, n, cw, fp, tw);
+    k_fft_cols<T><<<gc, FFT_THREADS, smc, s>>>(cb, sym, n, cw, fp, tw, p->precond_kind == 2 ? 1 : 0);
     CTR_CHECK_LAUNCH("k_fft_cols");
     p->launches++;
     k_fft_rows_inv<T><<<gr, FFT_THREADS, smr, s>>>(cb, n, rpc, fp, tw, out, mode, outT, dout, outh, outTh);
@@ -530,7 +572,7 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
 
 // cbuf = F2(in_real), the plain 2-D forward DFT (row pass, then the column pass alone).
 template <typename T>
-ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t s)
+ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t s, bool twist)
 {
     using T2 = typename C2<T>::type;
     const int n = p->n;
@@ -544,12 +586,13 @@ ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t
     k_fft_rows_fwd<T><<<(n + rpc - 1) / rpc, FFT_THREADS, fft_smem_bytes(p, 0), s>>>(src, cb, n, rpc, fp, tw);
     CTR_CHECK_LAUNCH("k_fft_rows_fwd");
     p->launches++;
-    k_fft_cols<T><<<(n + cw - 1) / cw, FFT_THREADS, fft_smem_bytes(p, 1), s>>>(cb, nullptr, n, cw, fp, tw);
+    k_fft_cols<T><<<(n + cw - 1) / cw, FFT_THREADS, fft_smem_bytes(p, 1), s>>>(cb, nullptr, n, cw, fp, tw,
+                                                                              twist ? 1 : 0);
     CTR_CHECK_LAUNCH("k_fft_cols");
     return CTR_OK;
 }
-template ctr_status launch_fft2_forward<float>(const ctr_plan *, const float *, cudaStream_t);
-template ctr_status launch_fft2_forward<double>(const ctr_plan *, const double *, cudaStream_t);
+template ctr_status launch_fft2_forward<float>(const ctr_plan *, const float *, cudaStream_t, bool);
+template ctr_status launch_fft2_forward<double>(const ctr_plan *, const double *, cudaStream_t, bool);
 
 template <typename T>
 ctr_status configure_fft(const ctr_plan *p)
@@ -569,8 +612,8 @@ ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c,
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     p->launches++;
-    const T *s_arr = p->precond_kind == 1 ? (const T *)p->pk_s : nullptr;   // impulse response
-    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0, s_arr);
+    k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0,
+                                        p->precond_kind, 1.0 / (p->h * p->h), (const T *)p->pk_s);
     CTR_CHECK_LAUNCH("k_symbols");
     return CTR_OK;
 }
@@ -726,14 +769,14 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     const size_t nn = (size_t)n * n;
     int blocks = (int)((nn + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps, 0, nullptr);
+    k_symbols<float><<<blocks, 256, 0, str>>>(s.sym, nullptr, n, sigma, tau, c, eps, 0, 0, 1.0, nullptr);
     const int rpc = fft_rows_per_cta(n), cw = fft_cols_per_cta(n, sizeof(float));
     const size_t smr = fft_rows_smem(n, sizeof(float)), smc = fft_cols_smem(n, sizeof(float));
     const int gr = (n + rpc - 1) / rpc, gc = (n + cw - 1) / cw;
     RowsInput<float> src{};
     src.in_real = y_dev;
     k_fft_rows_fwd<float><<<gr, FFT_THREADS, smr, str>>>(src, s.cbuf, n, rpc, fp, s.tw);
-    k_fft_cols<float><<<gc, FFT_THREADS, smc, str>>>(s.cbuf, s.sym, n, cw, fp, s.tw);
+    k_fft_cols<float><<<gc, FFT_THREADS, smc, str>>>(s.cbuf, s.sym, n, cw, fp, s.tw, 0);
     k_fft_rows_inv<float><<<gr, FFT_THREADS, smr, str>>>(s.cbuf, n, rpc, fp, s.tw, x_dev, 0, nullptr, nullptr,
                                                          nullptr, nullptr);
     cudaError_t e = cudaGetLastError();

@@ -204,12 +204,22 @@ __global__ void k_set_one(T *x) { *x = T(1); }
 
 // k(i, j) = (kt(i, j) + kt(-i, -j)) / 2 with kt the impulse response y moved from
 // (c, c) to the origin (indices mod n): the point-symmetric kernel.
+// flat != 0 (circulant preconditioner): the same on the image flattened as t = i + n j,
+// k_t = (y_{(t + p) mod n^2} + y_{(p - t) mod n^2}) / 2 with p = c + n c, written back at
+// the pixel (i, j) of t.
 template <typename T>
-__global__ void k_kernel_sym(const T *__restrict__ y, int n, int c, T *k)
+__global__ void k_kernel_sym(const T *__restrict__ y, int n, int c, int flat, T *k)
 {
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / n), j = (int)(e % n);
+        if (flat) {
+            const long long N = (long long)nn, t = i + (long long)n * j, pc = c + (long long)n * c;
+            const long long ta = (t + pc) % N, tb = ((pc - t) % N + N) % N;
+            const int ia = (int)(ta % n), ja = (int)(ta / n), ib = (int)(tb % n), jb = (int)(tb / n);
+            k[e] = T(0.5) * (y[(size_t)ia * n + ja] + y[(size_t)ib * n + jb]);
+            continue;
+        }
         const int ia = (i + c) % n, ja = (j + c) % n;
         const int ib = ((c - i) % n + n) % n, jb = ((c - j) % n + n) % n;
         k[e] = T(0.5) * (y[(size_t)ia * n + ja] + y[(size_t)ib * n + jb]);
@@ -657,14 +667,17 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     return CTR_OK;
 }
 
-// The impulse-response preconditioner's DFT s (Sec. "Impulse response preconditioners"),
-// built once per plan: the response of R_h^* R_h to the impulse at (n/2, n/2), made
-// point-symmetric about it and moved to the origin, transformed by the 2-D DFT (real by
-// the symmetry), bounded below by 1e-3 of its maximum.  Leaves it in p->pk_s.
+// The DFT s of the impulse-response preconditioner (kind 1, Sec. "Impulse response
+// preconditioners") or of the circulant one (kind 2, Sec. "Circulant matrix
+// preconditioner"): the response of R_h^* R_h to the impulse at (n/2, n/2), moved to the
+// origin and made point-symmetric, on the image (kind 1) or on the image flattened as
+// t = i + n j (kind 2), transformed by the 2-D DFT resp. the 1-D DFT of length n^2 (real
+// by the symmetry), bounded below by 1e-3 of its maximum.  Leaves it in p->pk_s.
 template <typename T>
 ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
 {
-    if (p->pk_ready) return CTR_OK;
+    const int kind = p->precond_kind;
+    if (p->pk_kind == kind) return CTR_OK;
     using T2 = typename Cplx<T>::type;
     const int n = p->n, c = n / 2;
     const size_t nn = (size_t)n * n;
@@ -678,16 +691,16 @@ ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
     if ((st = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return st;
     if ((st = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return st;
     p->launches++;
-    k_kernel_sym<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(y, n, c, xt);
+    k_kernel_sym<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(y, n, c, kind == 2 ? 1 : 0, xt);
     CTR_CHECK_LAUNCH("k_kernel_sym");
-    if ((st = launch_fft2_forward<T>(p, xt, s)) != CTR_OK) return st;
+    if ((st = launch_fft2_forward<T>(p, xt, s, kind == 2)) != CTR_OK) return st;
     unsigned long long *mx = reinterpret_cast<unsigned long long *>(p->d_red);
     CTR_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
     p->launches += 2;
     k_real_max<T2><<<grid_for(nn, 256, 1024), 256, 0, s>>>((const T2 *)p->cbuf, nn, mx);
     k_real_floor<T, T2><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T2 *)p->cbuf, nn, mx, 1e-3, (T *)p->pk_s);
     CTR_CHECK_LAUNCH("impulse symbol");
-    p->pk_ready = true;
+    p->pk_kind = kind;
     return CTR_OK;
 }
 
