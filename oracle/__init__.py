@@ -40,6 +40,7 @@ from .pdrq_ref import (
     power_start,
     PDRQState,
     pdrq5_solve,
+    pdrq2_solve,
     pdrq_solve,
     cp_solve,
     diagnostics,

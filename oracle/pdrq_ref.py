@@ -1,7 +1,8 @@
 """FP64 numpy oracle for everything around R_h: the discrete gradient and
 divergence, the pointwise resolvents, the inverse-norm Fourier preconditioner,
 the impulse-response, circulant and Richardson preconditioners, the power
-iterations, Alg. 4 (PDRQS1), Alg. 5 (PDRQS1 with u >= 0) and Alg. 1 (Chambolle-Pock).
+iterations, Alg. 4 (PDRQS1), Alg. 3 (PDRQS2, unconstrained), Alg. 5 (PDRQS1 with
+u >= 0) and Alg. 1 (Chambolle-Pock).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows
 the thesis step by step, with library primitives (numpy FFT) as single steps;
@@ -401,6 +402,47 @@ def pdrq_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, t
         st.k += 1
         if callback is not None:
             callback(st)
+    return st
+
+
+def pdrq2_solve(geo: Geometry, f, alpha: float, iters: int, *, sigma: float, tau: float, eps: float,
+                beta: float, c: float, state: Optional[PDRQState] = None, symbol: Optional[np.ndarray] = None,
+                circulant: bool = False) -> PDRQState:
+    """Run ``iters`` iterations of Alg. 3 (PDRQS2) for the unconstrained problem (U_h),
+    min 1/2 ||R_h u - f||^2 + alpha ||grad_h u||_1, on the problem scaled by beta.  Only
+    the TV term is dualised; the data term stays in the quadratic part, so
+    T = sigma Rt^* Rt + (sigma tau)^2 (-Delta_h) and the multiplier of M^{-1} is
+    ||xi|| / (sigma c + (sigma tau)^2 L ||xi||).  One iteration, in the order of Alg. 3:
+        u_tmp = sigma tau div v2b + sigma Rt^*(ft - Rt u) + (sigma tau)^2 div grad u
+        u_new = u + F^{-1}( F(u_tmp) * m )
+        v2 = v2b + sigma tau grad u_new
+        t2 = P_{lambda/tau}(2 v2 - v2b) ;  v2b += t2 - v2 ;  u = u_new
+    Reading: the printed quadratic part carries -(sigma tau)^2 Delta_h u with the
+    Laplacian taken as the positive semidefinite -div_h grad_h (so that T >= 0), i.e.
+    +(sigma tau)^2 div_h grad_h u here.  symbol / circulant as in pdrq_solve, where the
+    symbol passed must already hold sigma c in place of sigma^2 c.  The state's Ru is
+    Rt u and t1 = Rt u - ft (the data term's gradient, its optimal dual), so that
+    diagnostics() applies with the unconstrained descriptors."""
+    h = geo.h
+    ft = np.asarray(f, dtype=np.float64) / beta
+    lam = alpha / (beta * beta)
+    m = precond_symbol(geo.n, sigma, tau, c / sigma, eps) if symbol is None else symbol
+    st = PDRQState.zeros(geo) if state is None else state.copy()
+    for _ in range(iters):
+        gx, gy = grad(st.u, h)
+        u_tmp = (sigma * tau * div(st.v2bx, st.v2by, h) + sigma * rh_adjoint(ft - st.Ru, geo) / beta
+                 + (sigma * tau) ** 2 * div(gx, gy, h))
+        u_new = st.u + (precond_apply_circulant(u_tmp, m) if circulant else precond_apply(u_tmp, m))
+        gx, gy = grad(u_new, h)
+        v2x = st.v2bx + sigma * tau * gx
+        v2y = st.v2by + sigma * tau * gy
+        t2x, t2y = tv_project(2.0 * v2x - st.v2bx, 2.0 * v2y - st.v2by, lam, tau)
+        st.v2bx = st.v2bx + t2x - v2x
+        st.v2by = st.v2by + t2y - v2y
+        st.u = u_new
+        st.Ru = rh_forward(u_new, geo) / beta
+        st.t1, st.t2x, st.t2y = st.Ru - ft, t2x, t2y
+        st.k += 1
     return st
 
 
