@@ -200,6 +200,19 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
                        double alpha, double delta, int iters, const ctr_params *params,
                        void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* Alg. 3 (PDRQS2, Sec. "Suitable Preconditioners") for the unconstrained problem (U_h),
+ *   min_u  1/2 ||R_h u - f||^2 + alpha ||grad_h u||_1,
+ * from u = 0: the data term stays in the quadratic part (only the TV term is
+ * dualised), so T = sigma Rt^* Rt + (sigma tau)^2 (-Delta_h) and M carries sigma c where
+ * Alg. 4's carries sigma^2 c; c, beta and the preconditioner kind as in tv_pd_solve
+ * (params->nonneg must be 0: CTR_EUNSUPPORTED).  Per iteration: one backprojection of
+ * the residual R_h u/beta - f/beta (with the divergence and Laplacian terms in its
+ * epilogue), the preconditioner, one forward projection writing the next residual,
+ * and the TV dual step.  diag_out's gap and dual residual use t1 = R_h u/beta - f/beta,
+ * the data term's gradient.  FP32, FP64 and BF16 plans; errors as tv_pd_solve. */
+ctr_status tv_pdrq2_solve(ctr_plan *plan, const void *f_dev, double alpha, int iters, const ctr_params *params,
+                          void *u_out_dev, ctr_diag *diag_out, void *stream);
+
 /* Alg. 1 (Chambolle-Pock, Sec. 3.2) for the same problem as tv_pd_solve, from u = 0:
  * the unpreconditioned primal-dual baseline against which the thesis measures Alg. 4.
  * Runs on the beta-scaled problem (R_h / beta, so its norm is about 1) with primal step

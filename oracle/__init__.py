@@ -35,6 +35,8 @@ from .pdrq_ref import (
     tv_project,
     conj_data_term,
     make_descriptors,
+    dilate_disk,
+    metal_trace_estimate,
     power_beta,
     power_c,
     power_start,

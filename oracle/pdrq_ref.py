@@ -270,6 +270,39 @@ def make_descriptors(f, metal_mask, delta: float, trace_ratio: float = 0.8):
 
 
 # ----------------------------------------------------------------------------
+# Sec. "Real metal artifacts": estimating the metal trace D_0 from a reconstruction.
+# The pixels whose reconstructed value exceeds a threshold are marked, the marks are
+# dilated (by 5 px in the thesis's experiment), and the sinogram bins that the marked
+# pixels project onto form the trace.  Readings: the thesis says "back projection" for
+# the image-to-sinogram step, which is R_h (the forward projection); the dilation uses
+# the disk {di^2 + dj^2 <= r^2}; a bin belongs to the trace when R_h of the 0/1 image of
+# marked pixels exceeds proj_tol (a bin that no marked pixel touches gets exactly 0).
+# ----------------------------------------------------------------------------
+def dilate_disk(marked: np.ndarray, radius: int) -> np.ndarray:
+    """Binary dilation of a 0/1 image by the disk of the given radius (in pixels)."""
+    marked = np.asarray(marked).astype(bool)
+    n0, n1 = marked.shape
+    out = np.zeros_like(marked)
+    r = int(radius)
+    for di in range(-r, r + 1):
+        for dj in range(-r, r + 1):
+            if di * di + dj * dj > r * r:
+                continue
+            # out[i, j] |= marked[i + di, j + dj] where that pixel exists
+            src = marked[max(di, 0):n0 + min(di, 0), max(dj, 0):n1 + min(dj, 0)]
+            out[max(-di, 0):n0 + min(-di, 0), max(-dj, 0):n1 + min(-dj, 0)] |= src
+    return out
+
+
+def metal_trace_estimate(u: np.ndarray, geo: Geometry, threshold: float, radius: int = 5,
+                         proj_tol: float = 1e-6):
+    """(marked image, sinogram trace mask) from a reconstruction u."""
+    marked = dilate_disk(np.asarray(u) > threshold, radius)
+    trace = rh_forward(marked.astype(np.float64), geo) > proj_tol
+    return marked.astype(np.uint8), trace.astype(np.uint8)
+
+
+# ----------------------------------------------------------------------------
 # Sec. 4.3 / 5.1: power iterations.
 # beta ~ ||R_h|| (the problem is solved with R_h/beta, f/beta, lambda/beta^2,
 # Sec. 5.1); c ~ 1.05 lambda_max(Mt^{-1} Rt^* Rt) with Mt = F^{-1}(1/||xi||_eps) F

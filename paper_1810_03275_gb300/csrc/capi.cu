@@ -642,6 +642,26 @@ ctr_status tv_pd_solve(ctr_plan *p, const void *f, const uint8_t *mask, double a
                         solve_impl<double>(p, f, mask, nullptr, nullptr, nullptr, nullptr, alpha, delta, iters, q, nullptr, u_out, diag, stream));
 }
 
+ctr_status tv_pdrq2_solve(ctr_plan *p, const void *f, double alpha, int iters, const ctr_params *prm, void *u_out,
+                          ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, iters, q);
+    if (st != CTR_OK) return st;
+    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "Alg. 3 has no non-negativity variant (nonneg = 0)");
+    struct Alg3Scope {
+        ctr_plan *p;
+        explicit Alg3Scope(ctr_plan *pp) : p(pp) { p->alg3 = true; }
+        ~Alg3Scope() { p->alg3 = false; }
+    } scope(p);
+    // (U_h): no metal trace, no data tolerance
+    return CTR_DISPATCH(p,
+                        solve_impl<float>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream),
+                        solve_impl<double>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream));
+}
+
 ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, const void *hi, double alpha, int iters,
                      const ctr_params *prm, ctr_state *state, void *u_out, ctr_diag *diag, void *stream)
 {

@@ -152,7 +152,8 @@ __device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int 
 
 template <typename T>
 struct ForwardEpi {
-    int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4); 2: CP dual step (Alg. 1)
+    int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4); 2: CP dual step (Alg. 1);
+                       // 3: Alg. 3 residual y1 = Rt u - a (and t1 = y1), Ru kept
     T *g;              // mode 0 output
     T scale;
     // mode 1
@@ -258,6 +259,7 @@ struct ctr_plan {
     void *pk_s = nullptr;      // n*n DFT (2-D for kind 1, 1-D of the flattened image for kind 2) of the
                                // symmetrised impulse response of R_h^* R_h (built on first use)
     int pk_kind = 0;           // the kind pk_s currently holds (0: none)
+    bool alg3 = false;         // the iteration is Alg. 3 (set for the duration of tv_pdrq2_solve)
     void *gs = nullptr;        // N*M scratch sinogram
     void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
     double *d_red = nullptr;   // reduction partials

@@ -269,6 +269,20 @@ __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_
         epi.v1b[r] = data_resolvent(z, epi.sigma, epi.dw[r], epi.da[r], epi.dlo[r], epi.dhi[r]);
         return;
     }
+    if (epi.mode == 3) {
+        // Alg. 3: the next iteration backprojects the residual Rt u_new - ft
+        const T Ru = val * epi.scale;
+        const T y = Ru - epi.da[r];
+        epi.Ru[r] = Ru;
+        if constexpr (sizeof(T) == 4) {
+            if (epi.y1h) epi.y1h[r] = __float2bfloat16_rn(y);
+            else epi.y1[r] = y;
+        } else {
+            epi.y1[r] = y;
+        }
+        if (epi.t1) epi.t1[r] = y;
+        return;
+    }
     // Alg. 4: v1 = v1b + sigma Rt u_new; t = (id + sigma dG1^*)^{-1}(2 v1 - v1b);
     // v1b <- v1b + t - v1; and the next iteration's y1 = v1b + sigma Rt u_new.
     const T sigma = epi.sigma;

@@ -548,6 +548,7 @@ template <typename T>
 struct IterArgs {
     T sigma, tau, lam, inv_beta, inv_h;
     bool nonneg = false;   // Alg. 5 (u >= 0)
+    bool alg3 = false;     // Alg. 3: data term in the quadratic part, only the TV term dualised
 };
 
 // One iteration of Alg. 4 (steps A-D).  diag: also keep du, t1, t2 for diagnostics.
@@ -587,7 +588,7 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
         return st;
     // C: ray-driven Rt u with the data-dual step
     ForwardEpi<T> ec{};
-    ec.mode = 1;
+    ec.mode = a.alg3 ? 3 : 1;
     ec.scale = a.inv_beta;
     ec.sigma = a.sigma;
     ec.Ru = (T *)p->Ru;
@@ -812,11 +813,19 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
     a.inv_beta = (T)(1.0 / beta);
     a.inv_h = (T)(1.0 / p->h);
     a.nonneg = prm.nonneg != 0;
+    a.alg3 = p->alg3;
     ctr_status st;
-    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s, a.nonneg)) != CTR_OK) return st;
-    // y1 = v1b + sigma Ru ; y2 = v2b + sigma tau grad u
+    // Alg. 3's M carries sigma c where Alg. 4's carries sigma^2 c
+    const double c_sym = a.alg3 ? c / prm.sigma : c;
+    if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c_sym, prm.eps, s, a.nonneg)) != CTR_OK) return st;
+    // y1 = v1b + sigma Ru (Alg. 3: the residual Ru - ft) ; y2 = v2b + sigma tau grad u
     p->launches++;
-    k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->v1b, (const T *)p->Ru, a.sigma, nm, (T *)p->y1);
+    if (a.alg3)
+        k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->Ru, (const T *)p->desc + nm, T(-1), nm,
+                                                          (T *)p->y1);
+    else
+        k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const T *)p->v1b, (const T *)p->Ru, a.sigma, nm,
+                                                          (T *)p->y1);
     p->launches++;
     k_init_y2<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, (const T *)p->v2b, n, a.sigma * a.tau, a.inv_h, (T *)p->y2);
     if (sizeof(T) == 4 && p->bf16) {

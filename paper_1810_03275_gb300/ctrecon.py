@@ -66,7 +66,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
-           "tv_cp_solve"]
+           "tv_cp_solve", "tv_pdrq2_solve"]
 
 
 def load(path: str = LIB_PATH):
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
                                   P(Diag), vp]
         lib.tv_cp_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, P(Params), vp, P(Diag), vp]
+        lib.tv_pdrq2_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, P(Params), vp, P(Diag), vp]
         lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
         lib.ctr_power_lambda.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(ctypes.c_double), vp]
         lib.precond_apply_static.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -327,6 +328,17 @@ class Plan:
                                   float(alpha), float(delta), int(iters), float(sigma_p), float(tau_d),
                                   ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag),
                                   _stream(stream)))
+        return u_out, diag.as_dict()
+
+    def tv_pdrq2_solve(self, f, alpha: float, iters: int, params: Optional[Params] = None, u_out=None,
+                       stream=None):
+        """Alg. 3 (PDRQS2) from u = 0 on the unconstrained problem (U_h); returns (u, diag dict)."""
+        u_out = self.empty_image() if u_out is None else u_out
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_pdrq2_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), float(alpha),
+                                     int(iters), ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"),
+                                     ctypes.byref(diag), _stream(stream)))
         return u_out, diag.as_dict()
 
     def _state(self, st):
