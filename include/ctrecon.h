@@ -200,6 +200,27 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
                        double alpha, double delta, int iters, const ctr_params *params,
                        void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* Metal-trace estimation (Sec. "Real metal artifacts"): the pixels of u_dev (n*n, the
+ * plan's real type: float for FP32 and BF16 plans, double for FP64) whose value exceeds
+ * `threshold` (compared in FP64) are marked, the marks dilated by the disk
+ * {di^2 + dj^2 <= radius^2} (0 <= radius <= 64; the thesis dilates by 5 px), and
+ * trace_dev[r] (N*M bytes) = 1 where R_h of the 0/1 image of marks exceeds proj_tol >= 0,
+ * else 0 (bins that no mark touches get exactly 0).  marked_dev (n*n bytes) receives the
+ * dilated marks, or may be NULL.  The result is the metal_mask argument of tv_pd_solve.
+ * Uses the plan's scratch (not reentrant per plan); asynchronous on `stream`. */
+ctr_status ctr_metal_trace(ctr_plan *plan, const void *u_dev, double threshold, int radius, double proj_tol,
+                           uint8_t *marked_dev, uint8_t *trace_dev, void *stream);
+
+/* The metal-artifact pipeline of Sec. "Real metal artifacts": iters_pre iterations of
+ * Alg. 3 on the unconstrained problem give a first reconstruction (into u_out_dev),
+ * ctr_metal_trace(threshold, radius, proj_tol) turns it into the trace (trace_out_dev,
+ * N*M bytes), and tv_pd_solve(f, trace, alpha, delta, iters) solves (C_h) with it into
+ * u_out_dev, reusing the first stage's beta and c.  params as for tv_pd_solve (nonneg
+ * applies to the second stage only); diag_out describes the second stage. */
+ctr_status tv_mar_solve(ctr_plan *plan, const void *f_dev, double alpha, double delta, double threshold,
+                        int radius, double proj_tol, int iters_pre, int iters, const ctr_params *params,
+                        uint8_t *trace_out_dev, void *u_out_dev, ctr_diag *diag_out, void *stream);
+
 /* Alg. 3 (PDRQS2, Sec. "Suitable Preconditioners") for the unconstrained problem (U_h),
  *   min_u  1/2 ||R_h u - f||^2 + alpha ||grad_h u||_1,
  * from u = 0: the data term stays in the quadratic part (only the TV term is

@@ -50,6 +50,8 @@ ctr_status pdrq_loop(ctr_plan *, double, int, const ctr_params &, double, double
 template <typename T>
 ctr_status cp_loop(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *, cudaStream_t);
 template <typename T> ctr_status prepare_impulse_symbol(ctr_plan *, cudaStream_t);
+template <typename T>
+ctr_status metal_trace(ctr_plan *, const T *, double, int, double, uint8_t *, uint8_t *, cudaStream_t);
 
 // The preconditioner that params select (inverse norm, impulse response, circulant or
 // Richardson); the DFTs of the impulse-response and circulant kernels are built on their
@@ -558,6 +560,19 @@ ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
     return op_forward<float>(p, (const float *)u, (const float *)p->uT, (float *)g, 1.0, s);
 }
 
+ctr_status ctr_metal_trace(ctr_plan *p, const void *u, double threshold, int radius, double proj_tol,
+                           uint8_t *marked, uint8_t *trace, void *stream)
+{
+    CTR_GUARD(p);
+    if (!u || !trace) return fail(CTR_EINVAL, "u and trace must not be NULL");
+    if (!std::isfinite(threshold)) return fail(CTR_EINVAL, "threshold must be finite");
+    if (radius < 0 || radius > 64) return fail(CTR_EINVAL, "radius must be in [0, 64]");
+    if (!(proj_tol >= 0) || !std::isfinite(proj_tol)) return fail(CTR_EINVAL, "proj_tol must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, metal_trace<float>(p, (const float *)u, threshold, radius, proj_tol, marked, trace, s),
+                        metal_trace<double>(p, (const double *)u, threshold, radius, proj_tol, marked, trace, s));
+}
+
 ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, void *stream)
 {
     CTR_GUARD(p);
@@ -660,6 +675,25 @@ ctr_status tv_pdrq2_solve(ctr_plan *p, const void *f, double alpha, int iters, c
     return CTR_DISPATCH(p,
                         solve_impl<float>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream),
                         solve_impl<double>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream));
+}
+
+ctr_status tv_mar_solve(ctr_plan *p, const void *f, double alpha, double delta, double threshold, int radius,
+                        double proj_tol, int iters_pre, int iters, const ctr_params *prm, uint8_t *trace_out,
+                        void *u_out, ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !u_out || !trace_out) return fail(CTR_EINVAL, "f, trace_out and u_out must not be NULL");
+    if (iters_pre < 1) return fail(CTR_EINVAL, "iters_pre must be >= 1");
+    ctr_params q = resolve(p, prm);
+    ctr_params q3 = q;
+    q3.nonneg = 0;
+    ctr_diag d3{};
+    ctr_status st = tv_pdrq2_solve(p, f, alpha, iters_pre, &q3, u_out, &d3, stream);
+    if (st != CTR_OK) return st;
+    if ((st = ctr_metal_trace(p, u_out, threshold, radius, proj_tol, nullptr, trace_out, stream)) != CTR_OK) return st;
+    q.beta = d3.beta;   // the same operator norm and constant c serve the second stage
+    q.c = d3.c;
+    return tv_pd_solve(p, f, trace_out, alpha, delta, iters, &q, u_out, diag, stream);
 }
 
 ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, const void *hi, double alpha, int iters,

@@ -705,6 +705,76 @@ ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
     return CTR_OK;
 }
 
+// Metal-trace estimation (Sec. "Real metal artifacts"): the pixels whose value exceeds
+// the threshold, dilated by the disk {di^2 + dj^2 <= r^2}, as a 0/1 image (in the
+// projector's operand type) and optionally as bytes.  Comparisons in FP64, so that the
+// decision does not depend on the image's storage type.
+template <typename T, typename S>
+__global__ void k_mark_dilate(const T *__restrict__ u, int n, double thr, int r, uint8_t *marked, S *img)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        bool hit = false;
+        for (int di = -r; di <= r && !hit; ++di) {
+            const int ii = i + di;
+            if (ii < 0 || ii >= n) continue;
+            int w = r;
+            while (w * w + di * di > r * r) --w;
+            const int j0 = max(j - w, 0), j1 = min(j + w, n - 1);
+            for (int jj = j0; jj <= j1; ++jj)
+                if ((double)u[(size_t)ii * n + jj] > thr) {
+                    hit = true;
+                    break;
+                }
+        }
+        if (marked) marked[e] = hit ? 1 : 0;
+        img[e] = hit ? S(1.0f) : S(0.0f);
+    }
+}
+
+template <typename T>
+__global__ void k_trace_from_sino(const T *__restrict__ g, size_t len, double tol, uint8_t *trace)
+{
+    for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
+        trace[r] = (double)g[r] > tol ? 1 : 0;
+}
+
+// marks -> R_h of the 0/1 image -> bins above proj_tol.  Scratch: x, uT (or the bfloat16
+// operand copies), gs.
+template <typename T>
+ctr_status metal_trace(ctr_plan *p, const T *u, double thr, int radius, double proj_tol, uint8_t *marked,
+                       uint8_t *trace, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    T *g = (T *)p->gs;
+    ctr_status st;
+    p->launches++;
+    if constexpr (sizeof(T) == 4) {
+        if (p->bf16) {
+            k_mark_dilate<T, __nv_bfloat16><<<grid_for(nn, 256, 4096), 256, 0, s>>>(u, n, thr, radius, marked, p->uh);
+            CTR_CHECK_LAUNCH("k_mark_dilate");
+            if (fwd_needs_transpose<float>(p) && (st = launch_transpose<__nv_bfloat16>(p, p->uh, p->uTh, s)) != CTR_OK)
+                return st;
+            if ((st = op_forward_bf16(p, p->uh, p->uTh, (float *)g, s)) != CTR_OK) return st;
+            p->launches++;
+            k_trace_from_sino<float><<<grid_for(nm, 256, 4096), 256, 0, s>>>((const float *)g, nm, proj_tol, trace);
+            CTR_CHECK_LAUNCH("k_trace_from_sino");
+            return CTR_OK;
+        }
+    }
+    T *x = (T *)p->x;
+    k_mark_dilate<T, T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(u, n, thr, radius, marked, x);
+    CTR_CHECK_LAUNCH("k_mark_dilate");
+    if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, x, (T *)p->uT, s)) != CTR_OK) return st;
+    if ((st = op_forward<T>(p, x, (const T *)p->uT, g, 1.0, s)) != CTR_OK) return st;
+    p->launches++;
+    k_trace_from_sino<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(g, nm, proj_tol, trace);
+    CTR_CHECK_LAUNCH("k_trace_from_sino");
+    return CTR_OK;
+}
+
 // Alg. 1 (Chambolle-Pock) on the beta-scaled (C_h), from zero: the unpreconditioned
 // baseline.  State: u (p->u), u_bar (p->ubar_u), v (p->v1b), w (p->v2b).  One iteration:
 //   v = prox_{tau g*}(v + tau Rt u_bar)          forward projection of u_bar + epilogue (mode 2)
@@ -1312,6 +1382,7 @@ ctr_status batch_prepare(ctr_batch *b)
     template ctr_status cp_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *,   \
                                    cudaStream_t);                                                                     \
     template ctr_status prepare_impulse_symbol<T>(ctr_plan *, cudaStream_t);                                          \
+    template ctr_status metal_trace<T>(ctr_plan *, const T *, double, int, double, uint8_t *, uint8_t *, cudaStream_t); \
     template ctr_status build_desc_from_data<T>(ctr_plan *, const T *, const uint8_t *, double, double, double,       \
                                                 cudaStream_t);                                                        \
     template ctr_status build_desc_from_arrays<T>(ctr_plan *, const T *, const T *, const T *, const T *, double,     \

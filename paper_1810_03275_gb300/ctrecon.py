@@ -66,7 +66,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
-           "tv_cp_solve", "tv_pdrq2_solve"]
+           "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve"]
 
 
 def load(path: str = LIB_PATH):
@@ -103,6 +103,9 @@ def load(path: str = LIB_PATH):
         lib.tv_cp_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, P(Params), vp, P(Diag), vp]
         lib.tv_pdrq2_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, P(Params), vp, P(Diag), vp]
+        lib.ctr_metal_trace.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, vp, vp, vp]
+        lib.tv_mar_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, P(Params), vp, vp, P(Diag), vp]
         lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
         lib.ctr_power_lambda.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, P(ctypes.c_double), vp]
         lib.precond_apply_static.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -329,6 +332,35 @@ class Plan:
                                   ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag),
                                   _stream(stream)))
         return u_out, diag.as_dict()
+
+    def metal_trace(self, u, threshold: float, radius: int = 5, proj_tol: float = 1e-6, want_marks: bool = False,
+                    stream=None):
+        """Metal-trace estimate from a reconstruction u: the sinogram mask (uint8, N x M) of
+        the bins that the marks (u > threshold, dilated by a disk of `radius` px) project
+        onto; with want_marks also the dilated marks (uint8, n x n)."""
+        import torch
+        trace = torch.empty((self.n_angles, self.n_bins), dtype=torch.uint8, device="cuda")
+        marks = torch.empty((self.n, self.n), dtype=torch.uint8, device="cuda") if want_marks else None
+        u_p = self._t(u, (self.n, self.n), "u")
+        _check(load().ctr_metal_trace(self._h, u_p, float(threshold), int(radius),
+                                      float(proj_tol), ctypes.c_void_p(marks.data_ptr() if marks is not None else 0),
+                                      ctypes.c_void_p(trace.data_ptr()), _stream(stream)))
+        return (trace, marks) if want_marks else trace
+
+    def tv_mar_solve(self, f, alpha: float, delta: float, threshold: float, iters_pre: int, iters: int,
+                     radius: int = 5, proj_tol: float = 1e-6, params: Optional[Params] = None, u_out=None,
+                     stream=None):
+        """Alg. 3 pre-reconstruction -> metal trace -> Alg. 4 on (C_h); returns (u, trace, diag dict)."""
+        import torch
+        u_out = self.empty_image() if u_out is None else u_out
+        trace = torch.empty((self.n_angles, self.n_bins), dtype=torch.uint8, device="cuda")
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_mar_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), float(alpha),
+                                   float(delta), float(threshold), int(radius), float(proj_tol), int(iters_pre),
+                                   int(iters), ctypes.byref(prm), ctypes.c_void_p(trace.data_ptr()),
+                                   self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag), _stream(stream)))
+        return u_out, trace, diag.as_dict()
 
     def tv_pdrq2_solve(self, f, alpha: float, iters: int, params: Optional[Params] = None, u_out=None,
                        stream=None):
