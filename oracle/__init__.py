@@ -43,6 +43,10 @@ from .pdrq_ref import (
     PDRQState,
     pdrq5_solve,
     pdrq2_solve,
+    ADMMState,
+    pcg,
+    soft_threshold2,
+    admm_solve,
     pdrq_solve,
     cp_solve,
     diagnostics,

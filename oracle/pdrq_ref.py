@@ -2,7 +2,7 @@
 divergence, the pointwise resolvents, the inverse-norm Fourier preconditioner,
 the impulse-response, circulant and Richardson preconditioners, the power
 iterations, Alg. 4 (PDRQS1), Alg. 3 (PDRQS2, unconstrained), Alg. 5 (PDRQS1 with
-u >= 0) and Alg. 1 (Chambolle-Pock).
+u >= 0), Alg. 1 (Chambolle-Pock), ADMM with PCG, and the metal-trace estimation.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function follows
 the thesis step by step, with library primitives (numpy FFT) as single steps;
@@ -523,6 +523,107 @@ def pdrq5_solve(geo: Geometry, desc, alpha: float, iters: int, *, sigma: float, 
         st.k += 1
         if callback is not None:
             callback(st)
+    return st
+
+
+# ----------------------------------------------------------------------------
+# Sec. "Alternating Direction Method of Multipliers" (ADMM with PCG inner solves) for
+# the unconstrained problem, on the beta-scaled problem: z = (w, v) = K u with
+# K = [Rt; grad_h], f(z) = 1/2 ||w - ft||^2 + lambda ||v||_1, weighting
+# Lambda = diag(I, tau I), scaled multiplier eta = (eta_w, eta_v).
+# ----------------------------------------------------------------------------
+@dataclass
+class ADMMState:
+    u: np.ndarray
+    Ru: np.ndarray      # Rt u
+    w: np.ndarray       # z_w (sinogram)
+    vx: np.ndarray      # z_v (two image planes)
+    vy: np.ndarray
+    ew: np.ndarray      # eta_w
+    evx: np.ndarray     # eta_v
+    evy: np.ndarray
+    k: int = 0
+
+    @staticmethod
+    def zeros(geo: Geometry) -> "ADMMState":
+        n = geo.n
+        z = lambda: np.zeros((n, n))
+        return ADMMState(z(), np.zeros(geo.sino_shape), np.zeros(geo.sino_shape), z(), z(),
+                         np.zeros(geo.sino_shape), z(), z())
+
+    def copy(self) -> "ADMMState":
+        return ADMMState(*(getattr(self, f).copy() for f in ("u", "Ru", "w", "vx", "vy", "ew", "evx", "evy")),
+                         k=self.k)
+
+
+def pcg(apply_A, b: np.ndarray, x0: np.ndarray, iters: int, apply_Minv) -> np.ndarray:
+    """`iters` steps of the preconditioned conjugate gradient method for A x = b from x0
+    (A symmetric positive definite, M^{-1} symmetric positive definite), textbook form;
+    stops early only when the preconditioned residual vanishes exactly."""
+    x = np.array(x0, dtype=np.float64)
+    r = b - apply_A(x)
+    z = apply_Minv(r)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    for _ in range(iters):
+        if rz == 0.0:
+            break
+        Ap = apply_A(p)
+        alpha = rz / float(np.sum(p * Ap))
+        x = x + alpha * p
+        r = r - alpha * Ap
+        z = apply_Minv(r)
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x
+
+
+def soft_threshold2(ux, uy, t: float):
+    """argmin_x 1/2 ||x - u||^2 + t ||x|| per pixel (Lemma lem_soft_thres2d): 0 if
+    ||u|| <= t, else (1 - t/||u||) u."""
+    nrm = np.sqrt(ux * ux + uy * uy)
+    fac = np.where(nrm > t, 1.0 - t / np.where(nrm > 0, nrm, 1.0), 0.0)
+    return fac * ux, fac * uy
+
+
+def admm_solve(geo: Geometry, f, alpha: float, iters: int, *, mu: float, tau: float, cg_iters: int,
+               beta: float, minv_symbol: np.ndarray, circulant: bool = False,
+               state: Optional[ADMMState] = None) -> ADMMState:
+    """``iters`` ADMM iterations for min 1/2 ||R_h u - f||^2 + alpha ||grad_h u||_1 (scaled by
+    beta).  One iteration, in the thesis's order:
+        u   = PCG_{cg_iters}( Rt^* Rt + tau^2 (-Delta_h),  Rt^*(w - eta_w) - tau^2 div_h(v - eta_v) ),
+              warm-started at the current u, preconditioned by the multiplier minv_symbol
+              (2-D DFT, or the 1-D DFT of the flattened image with circulant=True)
+        w   = (ft + mu (Rt u + eta_w)) / (1 + mu)
+        v   = soft_threshold(grad_h u + eta_v, lambda / (mu tau^2))
+        eta_w -= w - Rt u ;  eta_v -= v - grad_h u
+    Readings: the multiplier is the scaled one with step 1 (the printed factor mu belongs
+    to the unscaled multiplier); the v-step's weight "mu nu" is mu tau^2, from
+    Lambda = diag(I, tau I)."""
+    h = geo.h
+    ft = np.asarray(f, dtype=np.float64) / beta
+    lam = alpha / (beta * beta)
+    st = ADMMState.zeros(geo) if state is None else state.copy()
+    t2 = tau * tau
+
+    def apply_A(x):
+        return rh_adjoint(rh_forward(x, geo) / beta, geo) / beta - t2 * div(*grad(x, h), h)
+
+    def apply_Minv(y):
+        return precond_apply_circulant(y, minv_symbol) if circulant else precond_apply(y, minv_symbol)
+
+    for _ in range(iters):
+        b = rh_adjoint(st.w - st.ew, geo) / beta - t2 * div(st.vx - st.evx, st.vy - st.evy, h)
+        st.u = pcg(apply_A, b, st.u, cg_iters, apply_Minv)
+        st.Ru = rh_forward(st.u, geo) / beta
+        gx, gy = grad(st.u, h)
+        st.w = (ft + mu * (st.Ru + st.ew)) / (1.0 + mu)
+        st.vx, st.vy = soft_threshold2(gx + st.evx, gy + st.evy, lam / (mu * t2))
+        st.ew = st.ew - (st.w - st.Ru)
+        st.evx = st.evx - (st.vx - gx)
+        st.evy = st.evy - (st.vy - gy)
+        st.k += 1
     return st
 
 
