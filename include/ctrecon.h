@@ -211,6 +211,21 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
 ctr_status ctr_metal_trace(ctr_plan *plan, const void *u_dev, double threshold, int radius, double proj_tol,
                            uint8_t *marked_dev, uint8_t *trace_dev, void *stream);
 
+/* ADMM with PCG inner solves (Sec. "Alternating Direction Method of Multipliers") for the
+ * unconstrained problem (U_h), from u = 0, on the beta-scaled problem: z = (w, v) = K u,
+ * K = [R_h/beta; grad_h], weighting diag(I, tau I) (tau = params->tau), penalty mu > 0.
+ * Per iteration: cg_iters (1..64) steps of preconditioned CG, warm-started, on
+ * (Rt^* Rt - tau^2 Delta_h) u = Rt^*(w - eta_w) - tau^2 div_h(v - eta_v), preconditioned by
+ * M = c S + tau^2 Lap of the kind params->precond selects (c, beta from power iterations
+ * unless given); then w = (f/beta + mu (Rt u + eta_w))/(1 + mu), v = soft-threshold of
+ * grad u + eta_v at lambda/(mu tau^2), eta -= z - K u.  Rt u is carried through the CG
+ * updates (no extra projection).  Everything runs on the device (CG scalars in device
+ * memory, no host round trip); graph_block iterations per CUDA graph.  diag_out's gap and
+ * dual residual use t1 = Rt u - f/beta and t2 = mu tau eta_v.  FP32 and FP64 plans
+ * (CTR_EUNSUPPORTED for BF16 or nonneg = 1); errors as tv_pd_solve. */
+ctr_status tv_admm_solve(ctr_plan *plan, const void *f_dev, double alpha, int iters, double mu, int cg_iters,
+                         const ctr_params *params, void *u_out_dev, ctr_diag *diag_out, void *stream);
+
 /* The metal-artifact pipeline of Sec. "Real metal artifacts": iters_pre iterations of
  * Alg. 3 on the unconstrained problem give a first reconstruction (into u_out_dev),
  * ctr_metal_trace(threshold, radius, proj_tol) turns it into the trace (trace_out_dev,

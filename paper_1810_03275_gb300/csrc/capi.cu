@@ -51,6 +51,9 @@ template <typename T>
 ctr_status cp_loop(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *, cudaStream_t);
 template <typename T> ctr_status prepare_impulse_symbol(ctr_plan *, cudaStream_t);
 template <typename T>
+ctr_status admm_loop(ctr_plan *, double, int, int, double, const ctr_params &, double, double, ctr_diag *,
+                     cudaStream_t);
+template <typename T>
 ctr_status metal_trace(ctr_plan *, const T *, double, int, double, uint8_t *, uint8_t *, cudaStream_t);
 
 // The preconditioner that params select (inverse norm, impulse response, circulant or
@@ -484,6 +487,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->t1, es * nm);
     ALLOC(p->ubar_u, es * nn);
     ALLOC(p->pk_s, es * nn);
+    ALLOC(p->aux, es * nn);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
     if (p->bf16) {
@@ -675,6 +679,52 @@ ctr_status tv_pdrq2_solve(ctr_plan *p, const void *f, double alpha, int iters, c
     return CTR_DISPATCH(p,
                         solve_impl<float>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream),
                         solve_impl<double>(p, f, nullptr, nullptr, nullptr, nullptr, nullptr, alpha, -1.0, iters, q, nullptr, u_out, diag, stream));
+}
+
+ctr_status tv_admm_solve(ctr_plan *p, const void *f, double alpha, int iters, double mu, int cg_iters,
+                         const ctr_params *prm, void *u_out, ctr_diag *diag, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
+    if (!(mu > 0) || !std::isfinite(mu)) return fail(CTR_EINVAL, "mu must be finite and > 0");
+    if (cg_iters < 1 || cg_iters > 64) return fail(CTR_EINVAL, "cg_iters must be in [1, 64]");
+    if (p->bf16) return fail(CTR_EUNSUPPORTED, "ADMM runs on FP32 and FP64 plans");
+    ctr_params q = resolve(p, prm);
+    ctr_status st = validate_solve(p, alpha, iters, q);
+    if (st != CTR_OK) return st;
+    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "ADMM solves the unconstrained problem (nonneg = 0)");
+    auto run = [&](auto tag) -> ctr_status {
+        using T = decltype(tag);
+        StreamJoin sj(p, stream);
+        ctr_status s2 = sj.begin();
+        if (s2 != CTR_OK) return s2;
+        cudaStream_t s = p->stream;
+        if ((s2 = select_precond<T>(p, q, s)) != CTR_OK) return s2;
+        double beta = q.beta;
+        if (!(beta > 0)) {
+            if ((s2 = power_beta<T>(p, q.power_iters, &beta, s)) != CTR_OK) return s2;
+            if (!(beta > 0)) return fail(CTR_ENUMERIC, "power iteration gave ||R_h|| = 0");
+        }
+        double c = q.c;
+        if (!(c > 0)) {
+            double lam = 0;
+            if ((s2 = power_lambda<T>(p, beta, q.eps, q.power_iters, &lam, s)) != CTR_OK) return s2;
+            c = q.c_margin * lam;
+            if (!(c > 0)) return fail(CTR_ENUMERIC, "power iteration gave c <= 0");
+        }
+        if ((s2 = build_desc_from_data<T>(p, (const T *)f, nullptr, -1.0, q.trace_ratio, beta, s)) != CTR_OK) return s2;
+        ctr_diag local{};
+        if ((s2 = admm_loop<T>(p, alpha, iters, cg_iters, mu, q, beta, c, diag ? &local : nullptr, s)) != CTR_OK)
+            return s2;
+        CTR_CUDA(cudaMemcpyAsync(u_out, p->u, (size_t)p->n * p->n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if (diag) {
+            *diag = local;
+            diag->beta = beta;
+            diag->c = c;
+        }
+        return CTR_OK;
+    };
+    return p->dtype == CTR_F64 ? run(double{}) : run(float{});
 }
 
 ctr_status tv_mar_solve(ctr_plan *p, const void *f, double alpha, double delta, double threshold, int radius,

@@ -260,6 +260,7 @@ struct ctr_plan {
                                // symmetrised impulse response of R_h^* R_h (built on first use)
     int pk_kind = 0;           // the kind pk_s currently holds (0: none)
     bool alg3 = false;         // the iteration is Alg. 3 (set for the duration of tv_pdrq2_solve)
+    void *aux = nullptr;       // n*n image scratch (ADMM: the iterate before the last iteration)
     void *gs = nullptr;        // N*M scratch sinogram
     void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
     double *d_red = nullptr;   // reduction partials

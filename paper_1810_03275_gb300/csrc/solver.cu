@@ -705,6 +705,245 @@ ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
     return CTR_OK;
 }
 
+// `count` calls of step() on stream s, blk at a time replayed from one captured CUDA
+// graph (blk <= 0 or count < blk: plain launches).  step() must enqueue the same work on
+// every call.
+template <typename F>
+ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s)
+{
+    ctr_status st = CTR_OK;
+    int done = 0;
+    if (blk > 0 && count >= blk) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long before = p->launches;
+        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < blk && st == CTR_OK; ++k) st = step();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
+        p->launches = before;
+        if (st != CTR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        for (; done + blk <= count; done += blk) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(ce, "cudaGraphLaunch");
+            }
+            p->launches += per_graph;
+        }
+        cudaGraphExecDestroy(exec);
+    }
+    for (; done < count; ++done)
+        if ((st = step()) != CTR_OK) return st;
+    return CTR_OK;
+}
+
+// ADMM with PCG inner solves (Sec. "Alternating Direction Method of Multipliers") ----
+// Device scalars of the conjugate gradient: rz in two alternating slots, p.Ap in a third
+// (dot2 writes two doubles per slot: the product and the second operand's square).
+constexpr int CG_SLOT_RZ0 = 32, CG_SLOT_RZ1 = 34, CG_SLOT_PAP = 36;
+
+// y = w - eta_w - Rt u (sinogram) and q = v - eta_v - grad u (image): the right-hand side
+// Rt^*(w - eta_w) - tau^2 div(v - eta_v) minus A u, A = Rt^* Rt - tau^2 div grad, comes out
+// of one backprojection of y with the divergence of q in its epilogue.
+template <typename T>
+__global__ void k_admm_resid(const T *__restrict__ w, const T *__restrict__ ew, const T *__restrict__ Ru, size_t nm,
+                             const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ ev, int n,
+                             T inv_h, T *y, T *q)
+{
+    const size_t nn = (size_t)n * n, total = nm > nn ? nm : nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < nm) y[e] = w[e] - ew[e] - Ru[e];
+        if (e < nn) {
+            T gx, gy;
+            grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+            q[e] = v[e] - ev[e] - gx;
+            q[e + nn] = v[e + nn] - ev[e + nn] - gy;
+        }
+    }
+}
+
+// alpha = rz / pAp;  u += alpha p;  r -= alpha Ap (image);  Ru += alpha Rp (sinogram)
+template <typename T>
+__global__ void k_cg_step(T *u, T *r, const T *__restrict__ pd, const T *__restrict__ Ap, size_t nn, T *Ru,
+                          const T *__restrict__ Rp, size_t nm, const double *__restrict__ sc, int slot_rz)
+{
+    const double pap = sc[CG_SLOT_PAP];
+    const T alpha = (T)(pap != 0.0 ? sc[slot_rz] / pap : 0.0);
+    const size_t total = nm > nn ? nm : nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < nn) {
+            u[e] += alpha * pd[e];
+            r[e] -= alpha * Ap[e];
+        }
+        if (e < nm) Ru[e] += alpha * Rp[e];
+    }
+}
+
+// p = z + (rz_new / rz_old) p
+template <typename T>
+__global__ void k_cg_dir(const T *__restrict__ z, T *pd, size_t nn, const double *__restrict__ sc, int slot_old,
+                         int slot_new)
+{
+    const double old = sc[slot_old];
+    const T b = (T)(old != 0.0 ? sc[slot_new] / old : 0.0);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x)
+        pd[e] = z[e] + b * pd[e];
+}
+
+// w = (ft + mu (Ru + eta_w)) / (1 + mu);  eta_w -= w - Ru;  y = w - eta_w - Ru (next right-hand side)
+template <typename T>
+__global__ void k_admm_sino(const T *__restrict__ Ru, const T *__restrict__ ft, T *w, T *ew, size_t nm, T mu,
+                            T *y)
+{
+    const T inv = T(1) / (T(1) + mu);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nm; e += (size_t)gridDim.x * blockDim.x) {
+        const T ru = Ru[e];
+        const T wn = (ft[e] + mu * (ru + ew[e])) * inv;
+        const T en = ew[e] - (wn - ru);
+        w[e] = wn;
+        ew[e] = en;
+        y[e] = wn - en - ru;
+    }
+}
+
+// g = grad u;  v = shrink(g + eta_v, thr);  eta_v -= v - g;  q = v - eta_v - g
+template <typename T>
+__global__ void k_admm_img(const T *__restrict__ u, int n, T inv_h, T thr, T *v, T *ev, T *q)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        T gx, gy;
+        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        const T ax = gx + ev[e], ay = gy + ev[e + nn];
+        const T nrm = sqrt(ax * ax + ay * ay);
+        const T fac = nrm > thr ? T(1) - thr / nrm : T(0);
+        const T vx = fac * ax, vy = fac * ay;
+        const T ex = ev[e] - (vx - gx), ey = ev[e + nn] - (vy - gy);
+        v[e] = vx;
+        v[e + nn] = vy;
+        ev[e] = ex;
+        ev[e + nn] = ey;
+        q[e] = vx - ex - gx;
+        q[e + nn] = vy - ey - gy;
+    }
+}
+
+// Dual certificates of the saddle problem for the diagnostics: t1 = Rt u - ft,
+// t2 = mu tau eta_v; du = u - u_prev.
+template <typename T>
+__global__ void k_admm_diag(const T *__restrict__ Ru, const T *__restrict__ ft, size_t nm, const T *__restrict__ ev,
+                            const T *__restrict__ u, const T *__restrict__ uprev, size_t nn, T mutau, T *t1, T *t2,
+                            T *du)
+{
+    const size_t total = nm > 2 * nn ? nm : 2 * nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < nm) t1[e] = Ru[e] - ft[e];
+        if (e < 2 * nn) t2[e] = mutau * ev[e];
+        if (e < nn) du[e] = u[e] - uprev[e];
+    }
+}
+
+// One ADMM iteration.  Buffers: u = p->u, Rt u = p->Ru (kept up to date through the CG
+// updates, Rt(u + alpha p) = Rt u + alpha Rt p), w = p->v1b, eta_w = p->y1, v = p->v2b,
+// eta_v = p->y2; y (sinogram) in p->gs and q (image pair) in p->t2 on entry; CG
+// scratch: r = p->du, z = p->x, p = p->ubar_u, A p = p->xt, grad p = p->t2, Rt p = p->gs.
+template <typename T>
+ctr_status admm_iteration(ctr_plan *p, int cg_iters, T tau, T mu, T lam, T inv_beta, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    const T inv_h = (T)(1.0 / p->h), tau2 = tau * tau;
+    T *u = (T *)p->u, *Ru = (T *)p->Ru, *r = (T *)p->du, *z = (T *)p->x, *pd = (T *)p->ubar_u, *Ap = (T *)p->xt;
+    T *gs = (T *)p->gs, *t2 = (T *)p->t2;
+    double *sc = p->d_scal;
+    ctr_status st;
+    BackprojEpi<T> eb{};
+    eb.complex_out = 0;
+    eb.scale = inv_beta;
+    eb.px = t2;
+    eb.divtau = tau2;
+    eb.outscale = T(1);
+    eb.inv_h = inv_h;
+    // r = b - A u;  z = M^{-1} r (p = z as a second output);  rz = r.z
+    eb.out = r;
+    if ((st = launch_backproject<T>(p, gs, eb, s)) != CTR_OK) return st;
+    if ((st = launch_circulant<T>(p, r, false, (const T *)p->sym, z, 0, nullptr, pd, s)) != CTR_OK) return st;
+    if ((st = dot2<T>(p, r, z, nn, sc + CG_SLOT_RZ0, s)) != CTR_OK) return st;
+    for (int k = 0; k < cg_iters; ++k) {
+        const int so = (k & 1) ? CG_SLOT_RZ1 : CG_SLOT_RZ0, sn = (k & 1) ? CG_SLOT_RZ0 : CG_SLOT_RZ1;
+        if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, pd, (T *)p->uT, s)) != CTR_OK) return st;
+        if ((st = op_forward<T>(p, pd, (const T *)p->uT, gs, (double)inv_beta, s)) != CTR_OK) return st;
+        if ((st = op_grad<T>(p, pd, t2, s)) != CTR_OK) return st;
+        eb.out = Ap;
+        if ((st = launch_backproject<T>(p, gs, eb, s)) != CTR_OK) return st;
+        if ((st = dot2<T>(p, pd, Ap, nn, sc + CG_SLOT_PAP, s)) != CTR_OK) return st;
+        p->launches++;
+        k_cg_step<T><<<grid_for(nm > nn ? nm : nn, 256, 4096), 256, 0, s>>>(u, r, pd, Ap, nn, Ru, gs, nm, sc, so);
+        CTR_CHECK_LAUNCH("k_cg_step");
+        if (k + 1 == cg_iters) break;   // the last direction would not be used
+        if ((st = launch_circulant<T>(p, r, false, (const T *)p->sym, z, 0, nullptr, nullptr, s)) != CTR_OK) return st;
+        if ((st = dot2<T>(p, r, z, nn, sc + sn, s)) != CTR_OK) return st;
+        p->launches++;
+        k_cg_dir<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(z, pd, nn, sc, so, sn);
+        CTR_CHECK_LAUNCH("k_cg_dir");
+    }
+    p->launches += 2;
+    k_admm_sino<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(Ru, (const T *)p->desc + nm, (T *)p->v1b, (T *)p->y1, nm,
+                                                          mu, gs);
+    k_admm_img<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(u, n, inv_h, lam / (mu * tau2), (T *)p->v2b, (T *)p->y2,
+                                                         t2);
+    CTR_CHECK_LAUNCH("admm updates");
+    return CTR_OK;
+}
+
+// ADMM from zero on the beta-scaled unconstrained problem; desc holds (1, ft, -inf, +inf).
+template <typename T>
+ctr_status admm_loop(ctr_plan *p, double alpha, int iters, int cg_iters, double mu, const ctr_params &prm,
+                     double beta, double c, ctr_diag *diag, cudaStream_t s)
+{
+    const int n = p->n;
+    const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
+    ctr_status st;
+    // PCG preconditioner for Rt^* Rt + tau^2 (-Delta_h): M = c S + tau^2 Lap (sigma = 1)
+    if ((st = launch_symbols<T>(p, 1.0, prm.tau, c, prm.eps, s, false)) != CTR_OK) return st;
+    CTR_CUDA(cudaMemsetAsync(p->u, 0, nn * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(p->Ru, 0, nm * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(p->v1b, 0, nm * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(p->y1, 0, nm * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(p->v2b, 0, 2 * nn * sizeof(T), s));
+    CTR_CUDA(cudaMemsetAsync(p->y2, 0, 2 * nn * sizeof(T), s));
+    p->launches++;
+    k_admm_resid<T><<<grid_for(nm > nn ? nm : nn, 256, 4096), 256, 0, s>>>(
+        (const T *)p->v1b, (const T *)p->y1, (const T *)p->Ru, nm, (const T *)p->u, (const T *)p->v2b,
+        (const T *)p->y2, n, (T)(1.0 / p->h), (T *)p->gs, (T *)p->t2);
+    CTR_CHECK_LAUNCH("k_admm_resid");
+    const T tau = (T)prm.tau, mu_t = (T)mu, lam = (T)(alpha / (beta * beta)), inv_beta = (T)(1.0 / beta);
+    auto one = [&]() { return admm_iteration<T>(p, cg_iters, tau, mu_t, lam, inv_beta, s); };
+    const int body = iters > 0 ? iters - 1 : 0;
+    if ((st = run_graphed(p, body, prm.graph_block, one, s)) != CTR_OK) return st;
+    if (iters > 0) {
+        CTR_CUDA(cudaMemcpyAsync(p->aux, p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if ((st = one()) != CTR_OK) return st;
+    } else {
+        CTR_CUDA(cudaMemsetAsync(p->aux, 0, nn * sizeof(T), s));
+    }
+    if (!diag) return CTR_OK;
+    p->launches++;
+    k_admm_diag<T><<<grid_for(nm > 2 * nn ? nm : 2 * nn, 256, 4096), 256, 0, s>>>(
+        (const T *)p->Ru, (const T *)p->desc + nm, nm, (const T *)p->y2, (const T *)p->u, (const T *)p->aux, nn,
+        (T)(mu * prm.tau), (T *)p->t1, (T *)p->t2, (T *)p->du);
+    CTR_CHECK_LAUNCH("k_admm_diag");
+    return compute_diag<T>(p, alpha, beta, prm.tau, c, iters, diag, s);
+}
+
 // Metal-trace estimation (Sec. "Real metal artifacts"): the pixels whose value exceeds
 // the threshold, dilated by the disk {di^2 + dj^2 <= r^2}, as a 0/1 image (in the
 // projector's operand type) and optionally as bytes.  Comparisons in FP64, so that the
@@ -1382,6 +1621,8 @@ ctr_status batch_prepare(ctr_batch *b)
     template ctr_status cp_loop<T>(ctr_plan *, double, int, const ctr_params &, double, double, double, ctr_diag *,   \
                                    cudaStream_t);                                                                     \
     template ctr_status prepare_impulse_symbol<T>(ctr_plan *, cudaStream_t);                                          \
+    template ctr_status admm_loop<T>(ctr_plan *, double, int, int, double, const ctr_params &, double, double,        \
+                                     ctr_diag *, cudaStream_t);                                                       \
     template ctr_status metal_trace<T>(ctr_plan *, const T *, double, int, double, uint8_t *, uint8_t *, cudaStream_t); \
     template ctr_status build_desc_from_data<T>(ctr_plan *, const T *, const uint8_t *, double, double, double,       \
                                                 cudaStream_t);                                                        \

@@ -66,7 +66,8 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_power_lambda", "ctr_grad", "ctr_div", "precond_apply_static", "ctr_plan_set_bp_groups",
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
-           "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve"]
+           "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
+           "tv_admm_solve"]
 
 
 def load(path: str = LIB_PATH):
@@ -104,6 +105,8 @@ def load(path: str = LIB_PATH):
                                     ctypes.c_double, P(Params), vp, P(Diag), vp]
         lib.tv_pdrq2_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, P(Params), vp, P(Diag), vp]
         lib.ctr_metal_trace.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, vp, vp, vp]
+        lib.tv_admm_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      P(Params), vp, P(Diag), vp]
         lib.tv_mar_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, P(Params), vp, vp, P(Diag), vp]
         lib.ctr_power_beta.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), vp]
@@ -346,6 +349,17 @@ class Plan:
                                       float(proj_tol), ctypes.c_void_p(marks.data_ptr() if marks is not None else 0),
                                       ctypes.c_void_p(trace.data_ptr()), _stream(stream)))
         return (trace, marks) if want_marks else trace
+
+    def tv_admm_solve(self, f, alpha: float, iters: int, mu: float = 1.0, cg_iters: int = 2,
+                      params: Optional[Params] = None, u_out=None, stream=None):
+        """ADMM with PCG inner solves from u = 0 on the unconstrained problem; returns (u, diag dict)."""
+        u_out = self.empty_image() if u_out is None else u_out
+        diag = Diag()
+        prm = params if params is not None else default_params()
+        _check(load().tv_admm_solve(self._h, self._t(f, (self.n_angles, self.n_bins), "f"), float(alpha), int(iters),
+                                    float(mu), int(cg_iters), ctypes.byref(prm),
+                                    self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag), _stream(stream)))
+        return u_out, diag.as_dict()
 
     def tv_mar_solve(self, f, alpha: float, delta: float, threshold: float, iters_pre: int, iters: int,
                      radius: int = 5, proj_tol: float = 1e-6, params: Optional[Params] = None, u_out=None,

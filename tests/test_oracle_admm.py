@@ -1,7 +1,8 @@
 """Pins of the oracle's ADMM with PCG inner solves (Sec. "Alternating Direction Method of
 Multipliers"): PCG against a dense LAPACK solve and the one-step steepest-descent closed
 form, the soft-thresholding lemma against numerical minimisation, and ADMM reaching the
-minimiser that Alg. 1 finds with z = K u at the limit."""
+minimiser that Alg. 1 finds with z = K u at the limit and its multipliers closing the
+saddle problem's gap."""
 import numpy as np
 import pytest
 import scipy.optimize
@@ -64,3 +65,7 @@ def test_admm_reaches_the_cp_minimiser():
     assert np.linalg.norm(st.u - u_cp) / np.linalg.norm(u_cp) < 2e-6
     gx, gy = oracle.grad(st.u)
     assert np.abs(st.w - st.Ru).max() < 1e-8 and np.abs(st.vx - gx).max() < 1e-6
+    # the multipliers are the saddle problem's duals: t1 = Rt u - ft, t2 = mu tau eta_v
+    d = oracle.diagnostics(geo, desc, alpha, st.u, beta=beta, tau=tau, t1=st.Ru - f / beta,
+                           t2x=tau * st.evx, t2y=tau * st.evy)
+    assert abs(d["gap"]) < 1e-7 * d["objective"] and d["dual_residual"] < 1e-7
