@@ -35,6 +35,9 @@ from .pdrq_ref import (
     tv_project,
     conj_data_term,
     make_descriptors,
+    ramlak_kernel,
+    ramp_filter,
+    fbp,
     dilate_disk,
     metal_trace_estimate,
     power_beta,

@@ -270,6 +270,38 @@ def make_descriptors(f, metal_mask, delta: float, trace_ratio: float = 0.8):
 
 
 # ----------------------------------------------------------------------------
+# Sec. 2 (filtered backprojection): the detector-axis ramp filter F_1^{-1} |omega| F_1
+# (the Ram-Lak filter) and the filtered backprojection that inverts the Radon transform.
+# Readings: the filter is the band-limited ramp sampled in space (the classical Ram-Lak
+# kernel k(0) = 1/(4 ds^2), k(m) = -1/(pi^2 m^2 ds^2) for odd m, 0 for even m != 0),
+# applied per view as the linear (not circular) convolution ds sum_m k(m) g(k - m) over
+# the detector; the backprojection integral over [0, pi) becomes (pi / N) R_h^* (angles
+# taken as uniform; the data are line integrals, the thesis's R_h with h = ds = 1).
+# ----------------------------------------------------------------------------
+def ramlak_kernel(M: int, ds: float = 1.0) -> np.ndarray:
+    """k(m) for m = -(M-1) .. M-1 (index m + M - 1)."""
+    m = np.arange(-(M - 1), M)
+    k = np.zeros(2 * M - 1)
+    k[M - 1] = 1.0 / (4.0 * ds * ds)
+    odd = (m % 2) != 0
+    k[odd] = -1.0 / (np.pi ** 2 * m[odd].astype(np.float64) ** 2 * ds * ds)
+    return k
+
+
+def ramp_filter(g: np.ndarray, ds: float = 1.0) -> np.ndarray:
+    """Per view: y(k) = ds sum_{k'} k_RL(k - k') g(k'), k = 0..M-1 (linear convolution)."""
+    g = np.asarray(g, dtype=np.float64)
+    M = g.shape[1]
+    ker = ramlak_kernel(M, ds)
+    return np.stack([ds * np.convolve(row, ker)[M - 1:2 * M - 1] for row in g])
+
+
+def fbp(g: np.ndarray, geo: Geometry) -> np.ndarray:
+    """Filtered backprojection (pi / N) R_h^*(ramp_filter(g))."""
+    return (np.pi / geo.n_angles) * rh_adjoint(ramp_filter(g, geo.ds), geo)
+
+
+# ----------------------------------------------------------------------------
 # Sec. "Real metal artifacts": estimating the metal trace D_0 from a reconstruction.
 # The pixels whose reconstructed value exceeds a threshold are marked, the marks are
 # dilated (by 5 px in the thesis's experiment), and the sinogram bins that the marked
