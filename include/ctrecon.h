@@ -200,6 +200,20 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
                        double alpha, double delta, int iters, const ctr_params *params,
                        void *u_out_dev, ctr_diag *diag_out, void *stream);
 
+/* Detector-axis ramp filter F_1^{-1}|omega|F_1 of the filtered backprojection (Sec. 2),
+ * the Ram-Lak kernel k(0) = 1/(4 ds^2), k(m) = -1/(pi^2 m^2 ds^2) (odd m), 0 (even m != 0)
+ * applied per view as the linear convolution y(k) = ds sum_k' k(k - k') g(k') over the M
+ * bins (an FFT of length L >= 2M - 1 along the bins, one CTA per view).  g_dev, y_dev:
+ * N*M in the plan's real type (float for FP32 and BF16 plans).  The filter tables are
+ * built on the first call (synchronous), later calls are asynchronous on `stream`. */
+ctr_status ctr_ramp_filter(ctr_plan *plan, const void *g_dev, void *y_dev, void *stream);
+
+/* Filtered backprojection u = (pi / N) R_h^*(ramp-filtered g) (Sec. 2, uniform angles over
+ * [0, pi)), the classical reconstruction of the line integrals g_dev (N*M) into u_dev
+ * (n*n).  BF16 plans backproject the filtered views stored in bfloat16.  Uses the
+ * plan's sinogram scratch. */
+ctr_status ctr_fbp(ctr_plan *plan, const void *g_dev, void *u_dev, void *stream);
+
 /* Metal-trace estimation (Sec. "Real metal artifacts"): the pixels of u_dev (n*n, the
  * plan's real type: float for FP32 and BF16 plans, double for FP64) whose value exceeds
  * `threshold` (compared in FP64) are marked, the marks dilated by the disk

@@ -488,6 +488,13 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->ubar_u, es * nn);
     ALLOC(p->pk_s, es * nn);
     ALLOC(p->aux, es * nn);
+    p->ramp_L = ramp_length(p->M);
+    if ((st = fft_radices(p->ramp_L, p->ramp_radices)) != CTR_OK) {
+        destroy(p);
+        return st;
+    }
+    ALLOC(p->d_ramp_tw, 2 * es * p->ramp_L);
+    ALLOC(p->d_ramp_H, es * p->ramp_L);
     ALLOC(p->gs, es * nm);
     ALLOC(p->desc, 4 * es * nm);
     if (p->bf16) {
@@ -575,6 +582,34 @@ ctr_status ctr_metal_trace(ctr_plan *p, const void *u, double threshold, int rad
     cudaStream_t s = (cudaStream_t)stream;
     return CTR_DISPATCH(p, metal_trace<float>(p, (const float *)u, threshold, radius, proj_tol, marked, trace, s),
                         metal_trace<double>(p, (const double *)u, threshold, radius, proj_tol, marked, trace, s));
+}
+
+ctr_status ctr_ramp_filter(ctr_plan *p, const void *g, void *y, void *stream)
+{
+    CTR_GUARD(p);
+    if (!g || !y) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    return CTR_DISPATCH(p, launch_ramp<float>(p, (const float *)g, (float *)y, nullptr, 1.0, s),
+                        launch_ramp<double>(p, (const double *)g, (double *)y, nullptr, 1.0, s));
+}
+
+ctr_status ctr_fbp(ctr_plan *p, const void *g, void *u, void *stream)
+{
+    CTR_GUARD(p);
+    if (!g || !u) return fail(CTR_EINVAL, "null buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double w = 3.14159265358979323846 / p->N;   // the angle integral over [0, pi)
+    ctr_status st;
+    if (p->dtype == CTR_F64) {
+        if ((st = launch_ramp<double>(p, (const double *)g, (double *)p->gs, nullptr, w, s)) != CTR_OK) return st;
+        return op_adjoint<double>(p, (const double *)p->gs, (double *)u, 1.0, s);
+    }
+    if (p->bf16) {
+        if ((st = launch_ramp<float>(p, (const float *)g, nullptr, p->y1h, w, s)) != CTR_OK) return st;
+        return op_adjoint_bf16(p, p->y1h, (float *)u, s);
+    }
+    if ((st = launch_ramp<float>(p, (const float *)g, (float *)p->gs, nullptr, w, s)) != CTR_OK) return st;
+    return op_adjoint<float>(p, (const float *)p->gs, (float *)u, 1.0, s);
 }
 
 ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, void *stream)

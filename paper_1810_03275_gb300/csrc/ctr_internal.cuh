@@ -261,6 +261,13 @@ struct ctr_plan {
     int pk_kind = 0;           // the kind pk_s currently holds (0: none)
     bool alg3 = false;         // the iteration is Alg. 3 (set for the duration of tv_pdrq2_solve)
     void *aux = nullptr;       // n*n image scratch (ADMM: the iterate before the last iteration)
+    // detector-axis ramp filter: FFT length L >= 2M - 1 (2^a 3^b), its radices and
+    // twiddles, and the real multiplier (the Ram-Lak kernel's DFT, times ds / L); the
+    // tables are filled on first use
+    int ramp_L = 0;
+    std::vector<int> ramp_radices;
+    void *d_ramp_tw = nullptr, *d_ramp_H = nullptr;
+    bool ramp_ready = false;
     void *gs = nullptr;        // N*M scratch sinogram
     void *desc = nullptr;      // 4*N*M: w, a, lo, hi (beta-scaled)
     double *d_red = nullptr;   // reduction partials
@@ -311,6 +318,10 @@ ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t
 template <typename T> ctr_status configure_radon(const ctr_plan *p);   // smem attributes, at plan creation
 template <typename T> ctr_status configure_fft(const ctr_plan *p);
 ctr_status fft_radices(int n, std::vector<int> &out);
+int ramp_length(int M);   // smallest 2^a 3^b >= 2M - 1
+// y = (ramp-filtered g) * outscale per view (N x M); yh (optional): the same in bfloat16 instead
+template <typename T>
+ctr_status launch_ramp(ctr_plan *p, const T *g, T *y, __nv_bfloat16 *yh, double outscale, cudaStream_t s);
 size_t fft_smem_bytes(const ctr_plan *p, int which);
 
 int backproject_tile_rows();   // pixel rows of a backprojection tile (its width is 32)

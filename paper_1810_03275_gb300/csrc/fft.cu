@@ -27,6 +27,16 @@ ctr_status fft_radices(int n, std::vector<int> &out)
     return CTR_OK;
 }
 
+int ramp_length(int M)
+{
+    const int need = 2 * (M > 1 ? M : 1) - 1;
+    int best = 0;
+    for (long long p2 = 1; p2 < 4LL * need; p2 *= 2)
+        for (long long v = p2; v < 4LL * need; v *= 3)
+            if (v >= need && (best == 0 || v < best)) best = (int)v;
+    return best;
+}
+
 namespace {
 
 #ifndef CTR_FFT_THREADS
@@ -593,6 +603,99 @@ ctr_status launch_fft2_forward(const ctr_plan *p, const T *in_real, cudaStream_t
 }
 template ctr_status launch_fft2_forward<float>(const ctr_plan *, const float *, cudaStream_t, bool);
 template ctr_status launch_fft2_forward<double>(const ctr_plan *, const double *, cudaStream_t, bool);
+
+// Detector-axis ramp filter (Sec. 2): per view, the bins zero-padded to L, forward FFT,
+// times the real multiplier H (the DFT of the Ram-Lak kernel wrapped onto L points, with
+// ds / L folded in), inverse FFT, the first M outputs times outscale: the linear
+// convolution of each view with the kernel.
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_ramp_filter(const T *__restrict__ g, int N, int M, int L, int rpc, FftPasses fp,
+              const typename C2<T>::type *__restrict__ tw, const T *__restrict__ H, T outscale, T *y,
+              __nv_bfloat16 *yh)
+{
+    using T2 = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *a = reinterpret_cast<T2 *>(smem_raw);
+    T2 *b = a + (size_t)rpc * L;
+    T2 *stw = b + (size_t)rpc * L;
+    stage_twiddles(stw, tw, L);
+    const int l0 = blockIdx.x * rpc;
+    const int cnt = min(rpc, N - l0);
+    for (int e = threadIdx.x; e < cnt * L; e += blockDim.x) {
+        const int r = e / L, k = e - r * L;
+        T2 v;
+        v.x = k < M ? g[(size_t)(l0 + r) * M + k] : T(0);
+        v.y = T(0);
+        a[e] = v;
+    }
+    __syncthreads();
+    T2 *res = fft_smem<T>(a, b, L, cnt, L, fp, -1, stw);
+    for (int e = threadIdx.x; e < cnt * L; e += blockDim.x) {
+        const T m = H[e % L];
+        res[e].x *= m;
+        res[e].y *= m;
+    }
+    __syncthreads();
+    T2 *res2 = fft_smem<T>(res, res == a ? b : a, L, cnt, L, fp, +1, stw);
+    for (int e = threadIdx.x; e < cnt * M; e += blockDim.x) {
+        const int r = e / M, k = e - r * M;
+        const T v = res2[(size_t)r * L + k].x * outscale;
+        const size_t o = (size_t)(l0 + r) * M + k;
+        if (yh) yh[o] = __float2bfloat16_rn((float)v);
+        else y[o] = v;
+    }
+}
+
+size_t ramp_smem(int L, size_t esize) { return (2 * (size_t)fft_rows_per_cta(L) * L + L) * 2 * esize; }
+
+// The ramp tables: twiddles e^{-2 pi i t / L} and H(t) = (ds / L) sum_m k(m) cos(2 pi m t / L)
+// with the Ram-Lak kernel k(0) = 1/(4 ds^2), k(m) = -1/(pi^2 m^2 ds^2) for odd |m| < M.
+template <typename T>
+ctr_status prepare_ramp(ctr_plan *p)
+{
+    if (p->ramp_ready) return CTR_OK;
+    const int L = p->ramp_L, M = p->M;
+    const double pi = 3.14159265358979323846, ds = p->ds;
+    std::vector<T> tw(2 * (size_t)L), H(L);
+    for (int t = 0; t < L; ++t) {
+        tw[2 * t] = (T)cos(2.0 * pi * t / L);
+        tw[2 * t + 1] = (T)(-sin(2.0 * pi * t / L));
+    }
+    for (int t = 0; t < L; ++t) {
+        double acc = 1.0 / (4.0 * ds * ds);
+        for (int m = 1; m < M; m += 2) {
+            const long long r = ((long long)m * t) % L;
+            acc += 2.0 * (-1.0 / (pi * pi * (double)m * m * ds * ds)) * cos(2.0 * pi * (double)r / L);
+        }
+        H[t] = (T)(acc * ds / L);
+    }
+    CTR_CUDA(cudaMemcpy(p->d_ramp_tw, tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice));
+    CTR_CUDA(cudaMemcpy(p->d_ramp_H, H.data(), sizeof(T) * H.size(), cudaMemcpyHostToDevice));
+    ctr_status st = raise_smem_limit(k_ramp_filter<T>, ramp_smem(L, sizeof(T)));
+    if (st != CTR_OK) return st;
+    p->ramp_ready = true;
+    return CTR_OK;
+}
+
+template <typename T>
+ctr_status launch_ramp(ctr_plan *p, const T *g, T *y, __nv_bfloat16 *yh, double outscale, cudaStream_t s)
+{
+    ctr_status st = prepare_ramp<T>(p);
+    if (st != CTR_OK) return st;
+    FftPasses fp;
+    fp.count = (int)p->ramp_radices.size();
+    for (int i = 0; i < fp.count && i < MAX_PASSES; ++i) fp.radix[i] = p->ramp_radices[i];
+    const int L = p->ramp_L, rpc = fft_rows_per_cta(L);
+    p->launches++;
+    k_ramp_filter<T><<<(p->N + rpc - 1) / rpc, FFT_THREADS, ramp_smem(L, sizeof(T)), s>>>(
+        g, p->N, p->M, L, rpc, fp, reinterpret_cast<const typename C2<T>::type *>(p->d_ramp_tw),
+        (const T *)p->d_ramp_H, (T)outscale, y, yh);
+    CTR_CHECK_LAUNCH("k_ramp_filter");
+    return CTR_OK;
+}
+template ctr_status launch_ramp<float>(ctr_plan *, const float *, float *, __nv_bfloat16 *, double, cudaStream_t);
+template ctr_status launch_ramp<double>(ctr_plan *, const double *, double *, __nv_bfloat16 *, double, cudaStream_t);
 
 template <typename T>
 ctr_status configure_fft(const ctr_plan *p)

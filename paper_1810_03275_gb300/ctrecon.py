@@ -67,7 +67,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
-           "tv_admm_solve"]
+           "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp"]
 
 
 def load(path: str = LIB_PATH):
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
                                     ctypes.c_double, P(Params), vp, P(Diag), vp]
         lib.tv_pdrq2_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, P(Params), vp, P(Diag), vp]
         lib.ctr_metal_trace.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, vp, vp, vp]
+        lib.ctr_ramp_filter.argtypes = [vp, vp, vp, vp]
+        lib.ctr_fbp.argtypes = [vp, vp, vp, vp]
         lib.tv_admm_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                       P(Params), vp, P(Diag), vp]
         lib.tv_mar_solve.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -335,6 +337,20 @@ class Plan:
                                   ctypes.byref(prm), self._t(u_out, (self.n, self.n), "u_out"), ctypes.byref(diag),
                                   _stream(stream)))
         return u_out, diag.as_dict()
+
+    def ramp_filter(self, g, y=None, stream=None):
+        """Detector-axis Ram-Lak filter of each view (linear convolution along the bins)."""
+        y = self.empty_sino() if y is None else y
+        sino = (self.n_angles, self.n_bins)
+        _check(load().ctr_ramp_filter(self._h, self._t(g, sino, "g"), self._t(y, sino, "y"), _stream(stream)))
+        return y
+
+    def fbp(self, g, u_out=None, stream=None):
+        """Filtered backprojection (pi / N) R_h^*(ramp-filtered g)."""
+        u_out = self.empty_image() if u_out is None else u_out
+        _check(load().ctr_fbp(self._h, self._t(g, (self.n_angles, self.n_bins), "g"),
+                              self._t(u_out, (self.n, self.n), "u_out"), _stream(stream)))
+        return u_out
 
     def metal_trace(self, u, threshold: float, radius: int = 5, proj_tol: float = 1e-6, want_marks: bool = False,
                     stream=None):
