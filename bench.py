@@ -143,25 +143,41 @@ def cpu_oracle_rate(problem, budget_s: float = 12.0, max_iters: int = 40):
     return k / dt, k, dt, oracle.num_threads()
 
 
-def measure_nonneg(plan, f, mask, pr, iters: int = 200):
-    """Alg. 5 (u >= 0) against Alg. 4 on the benchmark plan and data: iterations/s at
-    fixed (beta, c), CUDA events on the torch stream, and the most negative pixel of each."""
+def measure_algorithms(plan, f, mask, pr, iters: int = 200):
+    """Every solver and preconditioner kind on the benchmark plan and data: iterations/s
+    at fixed (beta, c), CUDA events on the torch stream.  Alg. 4 with each preconditioner
+    kind (0 inverse norm, 1 impulse response, 2 circulant, 3 Richardson), Alg. 5 (u >= 0,
+    with its most negative pixel), Alg. 3 and ADMM (2 CG steps) on the unconstrained
+    problem, Alg. 1 (Chambolle-Pock) on (C_h)."""
     import numpy as np
     import torch
     from paper_1810_03275_gb300 import ctrecon as ct
     beta = plan.power_beta(20)
     c = 1.05 * plan.power_lambda(beta, np.pi / pr.n, 20)
-    out = {}
-    for name, nn in (("alg4", 0), ("alg5_nonneg", 1)):
-        prm = ct.default_params(beta=beta, c=c, nonneg=nn)
-        plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, 5, params=prm)
+
+    def timed(fn):
+        fn(5)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        u, _ = plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm)
+        u = fn(iters)
         b.record()
         torch.cuda.synchronize()
-        out[name] = {"iters_per_s": iters / (a.elapsed_time(b) / 1e3), "min_u": float(u.min())}
+        return {"iters_per_s": iters / (a.elapsed_time(b) / 1e3), "min_u": float(u.min())}
+
+    out = {}
+    for kind in (0, 1, 2, 3):
+        ck = c if kind == 0 else plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, 1, params=ct.default_params(
+            beta=beta, precond=kind, power_iters=20))[1]["c"]          # c of this kind's own power iteration
+        prm = ct.default_params(beta=beta, c=ck, precond=kind)
+        out[f"alg4_precond{kind}"] = timed(lambda k: plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, k, params=prm)[0])
+    prm = ct.default_params(beta=beta, c=c)
+    out["alg5_nonneg"] = timed(lambda k: plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, k,
+                                                          params=ct.default_params(beta=beta, c=c, nonneg=1))[0])
+    out["alg3_unconstrained"] = timed(lambda k: plan.tv_pdrq2_solve(f, pr.alpha, k, params=prm)[0])
+    out["admm_cg2_unconstrained"] = timed(lambda k: plan.tv_admm_solve(f, pr.alpha, k, mu=1.0, cg_iters=2,
+                                                                       params=prm)[0])
+    out["alg1_cp"] = timed(lambda k: plan.tv_cp_solve(f, mask, pr.alpha, pr.delta, k, params=prm)[0])
     out["workload"] = f"512x512/720/729 MAR data, {iters} iterations per timing (beta, c fixed)"
     return out
 
@@ -400,7 +416,7 @@ def main():
     forms = None
     if rank == 0 and not args.no_forms:
         forms = {"bf16": measure_forms(), "batched": measure_batched(),
-                 "nonneg": measure_nonneg(plan, f, mask, pr)}
+                 "algorithms": measure_algorithms(plan, f, mask, pr)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
