@@ -206,6 +206,7 @@ enum BatchStage { BS_BP = 0, BS_BP_SYM, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_IN
 // ---------------------------------------------------------------------------
 // The plan.
 // ---------------------------------------------------------------------------
+constexpr int SYM_KEY_LEN = 8;   // sigma, tau, c, eps, nonneg, kind, kernel held, 1/h^2
 struct ctr_plan {
     int n = 0, N = 0, M = 0;
     double h = 1.0, ds = 1.0;
@@ -260,6 +261,9 @@ struct ctr_plan {
                                // symmetrised impulse response of R_h^* R_h (built on first use)
     int pk_kind = 0;           // the kind pk_s currently holds (0: none)
     bool alg3 = false;         // the iteration is Alg. 3 (set for the duration of tv_pdrq2_solve)
+    // the arguments sym / symh were last computed for (launch_symbols skips a repeat)
+    mutable double sym_key[SYM_KEY_LEN] = {};
+    mutable bool sym_valid = false;
     void *aux = nullptr;       // n*n image scratch (ADMM: the iterate before the last iteration)
     // detector-axis ramp filter: FFT length L >= 2M - 1 (2^a 3^b), its radices and
     // twiddles, and the real multiplier (the Ram-Lak kernel's DFT, times ds / L); the

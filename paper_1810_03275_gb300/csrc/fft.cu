@@ -9,6 +9,7 @@
 //   rows   : inverse FFT of every row, then the epilogue (write, or add to the
 //            iterate and also write its transpose for the ray-driven projector).
 #include <cmath>
+#include <cstring>
 
 #include "ctr_internal.cuh"
 
@@ -246,6 +247,83 @@ struct RowsInput {
     BackprojEpi<T> epi;
 };
 
+// The real input of the forward row pass at (row, col) for the part / in_real sources.
+template <typename T>
+__device__ __forceinline__ T rows_input_value(const RowsInput<T> &src, int n, int row, int col)
+{
+    const size_t e = (size_t)row * n + col;
+    if (!src.part) return src.in_real[e];
+    T acc;
+    if constexpr (sizeof(T) == 4) {
+        if (src.orbit) acc = orbit_fold(src.part, src.groups, n, row, col);
+    }
+    if (!(sizeof(T) == 4 && src.orbit)) {
+        const size_t nn = (size_t)n * n;
+        const T *pp = src.part + e;
+        acc = pp[0];
+#pragma unroll
+        for (int z = 1; z < MAX_BP_GROUPS; ++z)
+            if (z < src.groups) acc += pp[(size_t)z * nn];
+    }
+    return bp_epilogue_value(src.epi, n, row, col, acc);
+}
+
+// Real-input form of the forward row pass (for real images and real even symbols):
+// rows 2c and 2c + 1 of the CTA's rows go through one complex FFT as z = x_a + i x_b,
+// and X_a(k) = (Z(k) + conj Z(n-k)) / 2, X_b(k) = (Z(k) - conj Z(n-k)) / (2i) are kept for
+// k = 0 .. n/2 only (the rest is their conjugate mirror): cbuf holds n rows of
+// H = n/2 + 1 coefficients.  Inputs: the part or in_real sources (never cbuf itself,
+// whose rows the packed output would overwrite).
+template <typename T>
+__device__ __forceinline__ void fft_rows_fwd_packed_body(const RowsInput<T> &src, typename C2<T>::type *cbuf, int n,
+                                                         int rows_per_cta, const FftPasses &fp,
+                                                         const typename C2<T>::type *__restrict__ tw, int bx)
+{
+    using T2 = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cmax = rows_per_cta / 2;
+    T2 *a = reinterpret_cast<T2 *>(smem_raw);
+    T2 *b = a + (size_t)cmax * n;
+    T2 *stw = b + (size_t)cmax * n;
+    stage_twiddles(stw, tw, n);
+    const int r0 = bx * rows_per_cta;
+    const int cnt = min(rows_per_cta, n - r0);
+    const int cc = (cnt + 1) / 2;
+    const int H = n / 2 + 1;
+    const unsigned mn = div_magic(n);
+    staged_copy(cc * n, [&](int e) {
+        const int c = fast_div(e, n, mn), j = e - c * n;
+        const int ra = r0 + 2 * c;
+        T2 v;
+        v.x = rows_input_value(src, n, ra, j);
+        v.y = ra + 1 < r0 + cnt ? rows_input_value(src, n, ra + 1, j) : T(0);
+        return v;
+    }, [&](int e, T2 v) { a[e] = v; });
+    __syncthreads();
+    T2 *res = fft_smem<T>(a, b, n, cc, n, fp, -1, stw);
+    const unsigned mh = div_magic(H);
+    for (int e = threadIdx.x; e < cc * H; e += blockDim.x) {
+        const int c = fast_div(e, H, mh), k = e - c * H;
+        const T2 z = res[(size_t)c * n + k], zm = res[(size_t)c * n + (k == 0 ? 0 : n - k)];
+        const int ra = r0 + 2 * c;
+        T2 xa, xb;
+        xa.x = T(0.5) * (z.x + zm.x);
+        xa.y = T(0.5) * (z.y - zm.y);
+        xb.x = T(0.5) * (z.y + zm.y);
+        xb.y = T(0.5) * (zm.x - z.x);
+        cbuf[(size_t)ra * H + k] = xa;
+        if (ra + 1 < r0 + cnt) cbuf[(size_t)(ra + 1) * H + k] = xb;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_rows_fwd_packed(RowsInput<T> src, typename C2<T>::type *cbuf, int n, int rows_per_cta, FftPasses fp,
+                      const typename C2<T>::type *__restrict__ tw)
+{
+    fft_rows_fwd_packed_body<T>(src, cbuf, n, rows_per_cta, fp, tw, blockIdx.x);
+}
+
 // Forward row FFTs (in place on cbuf).
 template <typename T>
 __device__ __forceinline__ void fft_rows_fwd_body(const RowsInput<T> &src, typename C2<T>::type *cbuf, int n,
@@ -314,25 +392,29 @@ k_fft_rows_fwd(RowsInput<T> src, typename C2<T>::type *cbuf, int n, int rows_per
 // so the row pass is unchanged, the column pass multiplies element (i, kB) by
 // e^{-2 pi i i kB / N} before its forward transform (and by the conjugate after the
 // inverse one), and F_1(x)_k lands at (kA, kB), i.e. at flat position k.
+// ncols / ldg: the columns present and the row stride of cbuf (n and n, or H = n/2 + 1
+// for both in the real-input form; the symbol keeps its n x n layout).
 template <typename T>
 __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
                                               const FftPasses &fp, const typename C2<T>::type *__restrict__ tw,
-                                              int bx, int twist = 0)
+                                              int bx, int twist = 0, int ncols = 0, int ldg = 0)
 {
     using T2 = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ld = n + 1;
+    if (ncols <= 0) ncols = n;
+    if (ldg <= 0) ldg = n;
     T2 *a = reinterpret_cast<T2 *>(smem_raw);
     T2 *b = a + (size_t)cw * ld;
     T2 *stw = b + (size_t)cw * ld;
     stage_twiddles(stw, tw, n);
     const int c0 = bx * cw;
-    const int cnt = min(cw, n - c0);
+    const int cnt = min(cw, ncols - c0);
     const unsigned mc = div_magic(cnt);
     // element e: row e / cnt, column c0 + e % cnt (consecutive threads: consecutive columns)
     staged_copy(cnt * n, [&](int e) {
         const int row = fast_div(e, cnt, mc);
-        return cbuf[(size_t)row * n + c0 + (e - row * cnt)];
+        return cbuf[(size_t)row * ldg + c0 + (e - row * cnt)];
     }, [&](int e, T2 v) {
         const int row = fast_div(e, cnt, mc);
         if (twist) v = cmul(v, twist_factor(T(0), row * (c0 + e - row * cnt), n * n));
@@ -346,7 +428,7 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
             return res[(size_t)(e - row * cnt) * ld + row];
         }, [&](int e, T2 v) {
             const int row = fast_div(e, cnt, mc);
-            cbuf[(size_t)row * n + c0 + (e - row * cnt)] = v;
+            cbuf[(size_t)row * ldg + c0 + (e - row * cnt)] = v;
         });
         return;
     }
@@ -372,7 +454,7 @@ __device__ __forceinline__ void fft_cols_body(typename C2<T>::type *cbuf, const 
             w.y = -w.y;
             v = cmul(v, w);
         }
-        cbuf[(size_t)row * n + c0 + (e - row * cnt)] = v;
+        cbuf[(size_t)row * ldg + c0 + (e - row * cnt)] = v;
     });
 }
 
@@ -382,6 +464,93 @@ k_fft_cols(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw,
            const typename C2<T>::type *__restrict__ tw, int twist)
 {
     fft_cols_body<T>(cbuf, sym, n, cw, fp, tw, blockIdx.x, twist);
+}
+
+// The column pass of the real-input form: the H = n/2 + 1 stored columns.
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_cols_packed(typename C2<T>::type *cbuf, const T *__restrict__ sym, int n, int cw, FftPasses fp,
+                  const typename C2<T>::type *__restrict__ tw)
+{
+    fft_cols_body<T>(cbuf, sym, n, cw, fp, tw, blockIdx.x, 0, n / 2 + 1, n / 2 + 1);
+}
+
+// Inverse of the real-input form: rows 2c and 2c + 1 rebuilt from their H stored
+// coefficients (X(k) = conj X(n-k) beyond n/2), transformed together as
+// Z = X_a + i X_b, real part -> row 2c, imaginary part -> row 2c + 1; then the same
+// epilogue as fft_rows_inv_body (the final values staged in the spare buffer for the
+// transposed writes).
+template <typename T>
+__device__ __forceinline__ void fft_rows_inv_packed_body(const typename C2<T>::type *__restrict__ cbuf, int n,
+                                                         int rows_per_cta, const FftPasses &fp,
+                                                         const typename C2<T>::type *__restrict__ tw, T *out,
+                                                         int mode, T *outT, T *dout, __nv_bfloat16 *outh,
+                                                         __nv_bfloat16 *outTh, int bx)
+{
+    using T2 = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int cmax = rows_per_cta / 2;
+    T2 *a = reinterpret_cast<T2 *>(smem_raw);
+    T2 *b = a + (size_t)cmax * n;
+    T2 *stw = b + (size_t)cmax * n;
+    stage_twiddles(stw, tw, n);
+    const int r0 = bx * rows_per_cta;
+    const int cnt = min(rows_per_cta, n - r0);
+    const int cc = (cnt + 1) / 2;
+    const int H = n / 2 + 1, half = n / 2;
+    const unsigned mn = div_magic(n);
+    staged_copy(cc * n, [&](int e) {
+        const int c = fast_div(e, n, mn), k = e - c * n;
+        const int ra = r0 + 2 * c;
+        const bool lo = k <= half;
+        const int kk = lo ? k : n - k;
+        T2 xa = cbuf[(size_t)ra * H + kk];
+        T2 xb;
+        xb.x = T(0);
+        xb.y = T(0);
+        if (ra + 1 < r0 + cnt) xb = cbuf[(size_t)(ra + 1) * H + kk];
+        if (!lo) {
+            xa.y = -xa.y;
+            xb.y = -xb.y;
+        }
+        T2 z;
+        z.x = xa.x - xb.y;
+        z.y = xa.y + xb.x;
+        return z;
+    }, [&](int e, T2 v) { a[e] = v; });
+    __syncthreads();
+    T2 *res = fft_smem<T>(a, b, n, cc, n, fp, +1, stw);
+    T *fin = reinterpret_cast<T *>(res == a ? b : a);              // final values, [local row][col]
+    const size_t g0 = (size_t)r0 * n;
+    staged_copy(cnt * n, [&](int e) { return mode == 1 ? out[g0 + e] : T(0); }, [&](int e, T prev) {
+        const int rl = fast_div(e, n, mn), j = e - rl * n;
+        const T2 z = res[(size_t)(rl >> 1) * n + j];
+        const T v = (rl & 1) ? z.y : z.x;
+        if (dout) dout[g0 + e] = v;
+        const T o = v + prev;
+        out[g0 + e] = o;
+        if (outh) outh[g0 + e] = __float2bfloat16_rn((float)o);
+        fin[e] = o;
+    });
+    if (outT || outTh) {
+        __syncthreads();
+        const unsigned mc = div_magic(cnt);
+        for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+            const int col = fast_div(e, cnt, mc), r = e - col * cnt;
+            const T o = fin[(size_t)r * n + col];
+            if (outT) outT[(size_t)col * n + r0 + r] = o;
+            if (outTh) outTh[(size_t)col * n + r0 + r] = __float2bfloat16_rn((float)o);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_fft_rows_inv_packed(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_per_cta, FftPasses fp,
+                      const typename C2<T>::type *__restrict__ tw, T *out, int mode, T *outT, T *dout,
+                      __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
+{
+    fft_rows_inv_packed_body<T>(cbuf, n, rows_per_cta, fp, tw, out, mode, outT, dout, outh, outTh, blockIdx.x);
 }
 
 // Inverse row FFTs and the epilogue on the real part v:
@@ -537,6 +706,26 @@ FftPasses make_passes(const ctr_plan *p)
 
 int rows_per_cta(const ctr_plan *p) { return fft_rows_per_cta(p->n); }
 int cols_per_cta(const ctr_plan *p) { return fft_cols_per_cta(p->n, p->esize); }
+// real-input form: an even number of rows per CTA (pairs share a complex FFT), about the
+// same points per CTA as the complex form; columns: half as many per CTA (half remain)
+#ifndef CTR_PACK_ROWS_MUL
+#define CTR_PACK_ROWS_MUL 1
+#endif
+#ifndef CTR_PACK_COLS_MUL
+#define CTR_PACK_COLS_MUL 1
+#endif
+int packed_rows_per_cta(const ctr_plan *p)
+{
+    return 2 * CTR_PACK_ROWS_MUL * (fft_rows_per_cta(p->n) > 1 ? fft_rows_per_cta(p->n) / 2 : 1);
+}
+int packed_cols_per_cta(const ctr_plan *p)
+{
+    int c = CTR_PACK_COLS_MUL * (cols_per_cta(p) > 1 ? cols_per_cta(p) / 2 : 1);
+    while (c > 1 && 2 * (size_t)c * (p->n + 1) * 2 * p->esize > 160 * 1024) c /= 2;
+    return c;
+}
+size_t packed_rows_smem(const ctr_plan *p) { return (2 * (size_t)(packed_rows_per_cta(p) / 2) * p->n + p->n) * 2 * p->esize; }
+size_t packed_cols_smem(const ctr_plan *p) { return (2 * (size_t)packed_cols_per_cta(p) * (p->n + 1) + p->n) * 2 * p->esize; }
 
 }  // namespace
 
@@ -568,6 +757,24 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
         src.epi = *bp_in;
     } else if (!in_is_cbuf) {
         src.in_real = in_real;
+    }
+    // Real-input form: real image in, real image out and a real even symbol (every kind
+    // but the circulant one, whose 1-D transform is not the 2-D DFT); its packed rows
+    // would overwrite unread input rows if the input were cbuf itself.
+    if (p->precond_kind != 2 && (bp_in || !in_is_cbuf)) {
+        const int prp = packed_rows_per_cta(p), pcw = packed_cols_per_cta(p);
+        const int pgr = (n + prp - 1) / prp, pgc = (n / 2 + 1 + pcw - 1) / pcw;
+        const size_t psr = packed_rows_smem(p), psc = packed_cols_smem(p);
+        k_fft_rows_fwd_packed<T><<<pgr, FFT_THREADS, psr, s>>>(src, cb, n, prp, fp, tw);
+        CTR_CHECK_LAUNCH("k_fft_rows_fwd_packed");
+        p->launches++;
+        k_fft_cols_packed<T><<<pgc, FFT_THREADS, psc, s>>>(cb, sym, n, pcw, fp, tw);
+        CTR_CHECK_LAUNCH("k_fft_cols_packed");
+        p->launches++;
+        k_fft_rows_inv_packed<T><<<pgr, FFT_THREADS, psr, s>>>(cb, n, prp, fp, tw, out, mode, outT, dout, outh,
+                                                               outTh);
+        CTR_CHECK_LAUNCH("k_fft_rows_inv_packed");
+        return CTR_OK;
     }
     k_fft_rows_fwd<T><<<gr, FFT_THREADS, smr, s>>>(src, cb, n, rpc, fp, tw);
     CTR_CHECK_LAUNCH("k_fft_rows_fwd");
@@ -704,6 +911,9 @@ ctr_status configure_fft(const ctr_plan *p)
     ctr_status st = raise_smem_limit(k_fft_rows_fwd<T>, smr);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv<T>, smr);
     if (st == CTR_OK) st = raise_smem_limit(k_fft_cols<T>, smc);
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_fwd_packed<T>, packed_rows_smem(p));
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_rows_inv_packed<T>, packed_rows_smem(p));
+    if (st == CTR_OK) st = raise_smem_limit(k_fft_cols_packed<T>, packed_cols_smem(p));
     return st;
 }
 
@@ -711,10 +921,16 @@ template <typename T>
 ctr_status launch_symbols(const ctr_plan *p, double sigma, double tau, double c, double eps, cudaStream_t s,
                           bool nonneg)
 {
+    // the symbols of the last call are still in place if nothing they depend on changed
+    const double key[SYM_KEY_LEN] = {sigma, tau, c, eps, nonneg ? 1.0 : 0.0, (double)p->precond_kind,
+                                     (double)p->pk_kind, 1.0 / (p->h * p->h)};
+    if (p->sym_valid && std::memcmp(key, p->sym_key, sizeof(key)) == 0) return CTR_OK;
     const size_t total = (size_t)p->n * p->n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     p->launches++;
+    std::memcpy(p->sym_key, key, sizeof(key));
+    p->sym_valid = true;
     k_symbols<T><<<blocks, 256, 0, s>>>((T *)p->sym, (T *)p->symh, p->n, sigma, tau, c, eps, nonneg ? 1 : 0,
                                         p->precond_kind, 1.0 / (p->h * p->h), (const T *)p->pk_s);
     CTR_CHECK_LAUNCH("k_symbols");

@@ -30,9 +30,11 @@ def test_grad_div(ct, n, h, dtype):
 
 
 @pytest.mark.parametrize("dtype,n", [("f64", 64), ("f32", 64), ("f32", 48), ("f32", 384), ("f32", 512),
-                                     ("f64", 27), ("f32", 1), ("f32", 2048)])
+                                     ("f64", 27), ("f32", 1), ("f32", 2048), ("f32", 81), ("f64", 3),
+                                     ("f32", 6), ("f64", 1024)])
 def test_precond_apply(ct, n, dtype):
-    """M^{-1} y of Alg. 4 vs numpy's FFT on the oracle's symbol (radix 2, 3, 4 paths)."""
+    """M^{-1} y of Alg. 4 vs numpy's FFT on the oracle's symbol (radix 2, 3, 4 paths; the
+    real-input form with paired rows and n/2 + 1 columns, odd n included)."""
     plan = ct.Plan(n, 4, 5, dtype=dtype)
     sigma, tau, c, eps = 1.3, 0.35, 0.7, np.pi / n
     prm = ct.default_params(sigma=sigma, tau=tau, c=c, eps=eps)
