@@ -157,13 +157,16 @@ def measure_algorithms(plan, f, mask, pr, iters: int = 200):
 
     def timed(fn):
         fn(5)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record()
-        u = fn(iters)
-        b.record()
-        torch.cuda.synchronize()
-        return {"iters_per_s": iters / (a.elapsed_time(b) / 1e3), "min_u": float(u.min())}
+        best = 0.0
+        for _ in range(2):                      # the better of two timings
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            u = fn(iters)
+            b.record()
+            torch.cuda.synchronize()
+            best = max(best, iters / (a.elapsed_time(b) / 1e3))
+        return {"iters_per_s": best, "min_u": float(u.min())}
 
     out = {}
     for kind in (0, 1, 2, 3):

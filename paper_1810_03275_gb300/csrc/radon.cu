@@ -568,8 +568,63 @@ k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ 
     orbit_image_body<S>(u, ubar, n, blockIdx.x, blockIdx.y);
 }
 
+// Paired FP32 arithmetic (add / sub / fma on two lanes of a 64-bit register pair, one
+// instruction for two values; each lane rounds exactly as the scalar instruction).
+#ifndef CTR_F32X2
+#define CTR_F32X2 1
+#endif
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b)
+{
+#if CTR_F32X2
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b)
+{
+#if CTR_F32X2
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+// a * b + c per lane
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+#if CTR_F32X2
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
 __device__ __forceinline__ void acc4(float4 &Su, float4 &Sf, float4 v, float f)
 {
+#if CTR_F32X2
+    const float2 f2 = make_float2(f, f);
+    const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
+    const float2 u01 = fadd2(make_float2(Su.x, Su.y), v01), u23 = fadd2(make_float2(Su.z, Su.w), v23);
+    const float2 s01 = ffma2(f2, v01, make_float2(Sf.x, Sf.y)), s23 = ffma2(f2, v23, make_float2(Sf.z, Sf.w));
+    Su = make_float4(u01.x, u01.y, u23.x, u23.y);
+    Sf = make_float4(s01.x, s01.y, s23.x, s23.y);
+    return;
+#endif
     Su.x += v.x;
     Su.y += v.y;
     Su.z += v.z;
@@ -855,10 +910,16 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
                 const int b = (int)(P >> 32);
                 const float f = one_plus_frac32(P) - 1.f;                 // exact: the 23 fraction bits
                 const float4 lo = row[b], hi = row[b + 1];
-                acc[r][0] += fmaf(f, hi.x - lo.x, lo.x);
-                acc[r][1] += fmaf(f, hi.y - lo.y, lo.y);
-                acc[r][2] += fmaf(f, hi.z - lo.z, lo.z);
-                acc[r][3] += fmaf(f, hi.w - lo.w, lo.w);
+                const float2 f2 = make_float2(f, f);
+                const float2 lo01 = make_float2(lo.x, lo.y), lo23 = make_float2(lo.z, lo.w);
+                const float2 t01 = ffma2(f2, fsub2(make_float2(hi.x, hi.y), lo01), lo01);
+                const float2 t23 = ffma2(f2, fsub2(make_float2(hi.z, hi.w), lo23), lo23);
+                const float2 a01 = fadd2(make_float2(acc[r][0], acc[r][1]), t01);
+                const float2 a23 = fadd2(make_float2(acc[r][2], acc[r][3]), t23);
+                acc[r][0] = a01.x;
+                acc[r][1] = a01.y;
+                acc[r][2] = a23.x;
+                acc[r][3] = a23.y;
                 P += D;
             }
         }
@@ -908,7 +969,7 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
         }
         if (threadIdx.x < 4 * na) sL[threadIdx.x] = jobs[c0 + (threadIdx.x >> 2)].l[threadIdx.x & 3];
         __syncthreads();
-        float2 *st2 = reinterpret_cast<float2 *>(stage);
+        float *stf = reinterpret_cast<float *>(stage);
         for (int e = threadIdx.x; e < na * wstride * 4; e += NT) {
             const int c = e & 3, rest = e >> 2;
             const int a = rest / wstride, w = rest - a * wstride;
@@ -916,8 +977,12 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
             const S *row = g + (size_t)(l < 0 ? 0 : l) * M;
             const float g0 = (l >= 0 && k >= 0 && k < M) ? ldv(row + k) : 0.f;
             const float g1 = (l >= 0 && k + 1 >= 0 && k + 1 < M) ? ldv(row + k + 1) : 0.f;
-            // float4 planes (ch0 ch1) and (ch2 ch3) of the job, consecutive bins adjacent
-            st2[((size_t)(2 * a + (c >> 1)) * wstride + w) * 2 + (c & 1)] = make_stage(g0, g1);
+            // float4 planes (ch0 ch1) and (ch2 ch3) of the job, consecutive bins adjacent; in
+            // each float4 the two channels' (g0 - d) first, then their d = g1 - g0
+            const float2 st = make_stage(g0, g1);
+            float *q = stf + ((size_t)(2 * a + (c >> 1)) * wstride + w) * 4 + (c & 1);
+            q[0] = st.x;
+            q[2] = st.y;
         }
         __syncthreads();
 #pragma unroll 2
@@ -932,10 +997,15 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
                 const int b = (int)(P >> 32);
                 const float f = one_plus_frac32(P);
                 const float4 s01 = row01[b], s23 = row23[b];
-                acc[r][0] = fmaf(f, s01.y, acc[r][0] + s01.x);
-                acc[r][1] = fmaf(f, s01.w, acc[r][1] + s01.z);
-                acc[r][2] = fmaf(f, s23.y, acc[r][2] + s23.x);
-                acc[r][3] = fmaf(f, s23.w, acc[r][3] + s23.z);
+                const float2 f2 = make_float2(f, f);
+                const float2 a01 = ffma2(f2, make_float2(s01.z, s01.w),
+                                         fadd2(make_float2(acc[r][0], acc[r][1]), make_float2(s01.x, s01.y)));
+                const float2 a23 = ffma2(f2, make_float2(s23.z, s23.w),
+                                         fadd2(make_float2(acc[r][2], acc[r][3]), make_float2(s23.x, s23.y)));
+                acc[r][0] = a01.x;
+                acc[r][1] = a01.y;
+                acc[r][2] = a23.x;
+                acc[r][3] = a23.y;
                 P += D;
             }
         }
