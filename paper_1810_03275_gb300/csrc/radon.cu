@@ -706,12 +706,14 @@ __device__ __forceinline__ void orbit_out(const ForwardEpi<float> &epi, int l, i
 #endif
 constexpr int ORBIT_SEGS = CTR_ORBIT_SEGS;    // row segments of a job's rays (one warp each)
 #ifndef CTR_ORBIT_SLOTS
-#define CTR_ORBIT_SLOTS 4
+#define CTR_ORBIT_SLOTS 1
 #endif
-constexpr int ORBIT_SLOTS = CTR_ORBIT_SLOTS;  // adjacent jobs per CTA (they share image rows in L1)
+// adjacent jobs per CTA; 1 (128-thread CTAs, 8 per SM) measured fastest: co-resident CTAs of
+// adjacent jobs share the SM's L1 anyway, and small CTAs retire and refill sooner
+constexpr int ORBIT_SLOTS = CTR_ORBIT_SLOTS;
 constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 #ifndef CTR_ORBIT_MINB
-#define CTR_ORBIT_MINB 2
+#define CTR_ORBIT_MINB 8
 #endif
 #ifndef CTR_OBP_MINB
 #define CTR_OBP_MINB 4
