@@ -185,6 +185,52 @@ def measure_algorithms(plan, f, mask, pr, iters: int = 200):
     return out
 
 
+def measure_autograd(slices: int = 16, K: int = 20, ckpt: int = 5):
+    """The differentiable form: `slices` phantoms of 256 x 256 (360 views, 363 bins, FP32),
+    K unrolled iterations of Alg. 4 with checkpoints every `ckpt`, gradient of
+    ||u_K - u_true||^2 w.r.t. f and alpha per slice; CUDA events on the torch stream around
+    all slices' forward + backward (beta and c fixed once per plan)."""
+    import torch
+    from paper_1810_03275_gb300 import autograd as ag
+    from paper_1810_03275_gb300 import ctrecon as ct
+    from paper_1810_03275_gb300 import phantom
+    n, N, M = 256, 360, 363
+    probs = [phantom.make_problem(f"ad{i}", n, N, M, seed=40 + i, n_ellipses=4, n_metal=1, noise="poisson",
+                                  alpha=0.3) for i in range(slices)]
+    plan = ct.Plan(n, N, M, angles=probs[0].theta)
+    prm = ag.fixed_scaling(plan)
+    data = [(torch.as_tensor(p.f, dtype=torch.float32, device="cuda"), torch.as_tensor(p.mask, device="cuda"),
+             torch.as_tensor(p.truth, dtype=torch.float32, device="cuda"), p.alpha, p.delta) for p in probs]
+
+    def run(ds):
+        for f0, mask, truth, alpha0, delta in ds:
+            f = f0.clone().requires_grad_(True)
+            alpha = torch.tensor(alpha0, dtype=torch.float64, requires_grad=True)
+            u = ag.unrolled_pdrq(f, alpha, plan, mask, delta, iters=K, ckpt=ckpt, params=prm)
+            ((u - truth) ** 2).sum().backward()
+
+    run(data[:2])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    run(data)
+    b.record()
+    torch.cuda.synchronize()
+    secs = a.elapsed_time(b) / 1e3
+    fwd_only = 0.0
+    a.record()
+    for f0, mask, truth, alpha0, delta in data:
+        ag.unrolled_pdrq(f0, torch.tensor(alpha0, dtype=torch.float64), plan, mask, delta, iters=K, ckpt=ckpt,
+                         params=prm)
+    b.record()
+    torch.cuda.synchronize()
+    fwd_only = a.elapsed_time(b) / 1e3
+    return {"slices": slices, "K": K, "ckpt": ckpt,
+            "unrolled_iters_per_s_fwd_bwd": slices * K / secs, "ms_per_slice_fwd_bwd": 1e3 * secs / slices,
+            "ms_per_slice_fwd": 1e3 * fwd_only / slices,
+            "workload": "16 x 256^2 phantoms, 360 views, 363 bins, FP32, gradient w.r.t. f and alpha"}
+
+
 def measure_forms(iters: int = 30):
     """The BF16 form against the plain FP32 path on the 2048 x 2048 / 2048 views /
     2897 bins geometry: iterations/s of Alg. 4 (fixed beta and c, so only the
@@ -419,7 +465,7 @@ def main():
     forms = None
     if rank == 0 and not args.no_forms:
         forms = {"bf16": measure_forms(), "batched": measure_batched(),
-                 "algorithms": measure_algorithms(plan, f, mask, pr)}
+                 "algorithms": measure_algorithms(plan, f, mask, pr), "autograd": measure_autograd()}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
