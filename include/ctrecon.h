@@ -307,6 +307,19 @@ ctr_status tv_pd_vjp_step(ctr_plan *plan, const void *f_dev, const uint8_t *meta
                           double delta, const ctr_params *params, const ctr_state *s0, const ctr_state *s1,
                           void *bu, void *b1, void *b2, void *gf, double *galpha_dev, void *stream);
 
+/* Reverse mode of `length` (>= 1) consecutive iterations of Alg. 4 starting from the
+ * checkpoint s_start: the iterations are replayed on the device (state k stored in
+ * workspace_dev), then reversed newest first with the same kernels as tv_pd_vjp_step,
+ * all on `stream` without host synchronisation.  workspace_dev: (length + 1) states of
+ * n*n + 2*N*M + 2*n*n elements of the plan's real type, caller-owned (state k at offset
+ * k * (3*n*n + 2*N*M): u, Ru, v1b, v2b).  bu, b1, b2, gf, galpha_dev as tv_pd_vjp_step
+ * (the cotangents of the state after the last iteration in, of s_start out).  Equal to
+ * replaying with tv_pd_solve_state and calling tv_pd_vjp_step per iteration. */
+ctr_status tv_pd_vjp_segment(ctr_plan *plan, const void *f_dev, const uint8_t *metal_mask_dev, double alpha,
+                             double delta, const ctr_params *params, const ctr_state *s_start, int length,
+                             void *workspace_dev, void *bu, void *b1, void *b2, void *gf, double *galpha_dev,
+                             void *stream);
+
 /* Tuning hook: split the backprojection's angles (on the symmetric path: its jobs, see
  * ctr_plan_symmetric_jobs) into `groups` groups whose partial images are summed (more
  * CTAs for small images).  1 <= groups <= the capacity the plan allocated (up to 8 for

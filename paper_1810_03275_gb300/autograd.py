@@ -5,8 +5,8 @@ the data f and of alpha, with checkpoints every few iterates.
 Forward: the iterations run through tv_pd_solve_state in segments of `ckpt`
 iterations; the state (u, R u, v1b, v2b) at the start of each segment is kept.
 Backward: each segment is replayed one iteration at a time from its checkpoint and
-then reversed with tv_pd_vjp_step (the library's reverse-mode kernels), newest
-segment first.  beta and c are fixed per plan (they depend on the geometry only).
+then reversed (tv_pd_vjp_segment: the library's reverse-mode kernels, the states kept in
+a device workspace), newest segment first.  beta and c are fixed per plan (they depend on the geometry only).
 """
 from __future__ import annotations
 
@@ -87,16 +87,11 @@ class UnrolledPDRQ(torch.autograd.Function):
         gf = torch.zeros((N, M), dtype=dt, device="cuda")
         galpha = torch.zeros(1, dtype=torch.float64, device="cuda")
         bounds = [k for k, _ in ctx.ckpts] + [ctx.iters]
-        for seg in reversed(range(len(ctx.ckpts))):
+        ws = plan.vjp_workspace(max(bounds[i + 1] - bounds[i] for i in range(len(ctx.ckpts))))
+        for seg in reversed(range(len(ctx.ckpts))):      # each segment replayed and reversed on the device
             start, st0 = ctx.ckpts[seg]
-            length = bounds[seg + 1] - start
-            states = [st0]
-            cur = _clone(st0)
-            for _ in range(length):                      # replay the segment
-                plan.tv_pd_solve_state(f, mask, a, delta, 1, params, cur)
-                states.append(_clone(cur))
-            for k in reversed(range(length)):            # and reverse it
-                plan.tv_pd_vjp_step(f, mask, a, delta, params, states[k], states[k + 1], bu, b1, b2, gf, galpha)
+            plan.tv_pd_vjp_segment(f, mask, a, delta, params, st0, bounds[seg + 1] - start, ws, bu, b1, b2, gf,
+                                   galpha)
         ga = galpha.to(torch.float64) if ctx.alpha_is_tensor else None
         if ga is not None:
             ga = ga.reshape(()).to(dtype=torch.float64)

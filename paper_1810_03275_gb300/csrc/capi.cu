@@ -841,6 +841,58 @@ ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, doubl
                                 (float *)gf, galpha_dev, s);
 }
 
+ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta,
+                             const ctr_params *prm, const ctr_state *s_start, int length, void *workspace, void *bu,
+                             void *b1, void *b2, void *gf, double *galpha_dev, void *stream)
+{
+    CTR_GUARD(p);
+    if (!f || !s_start || !workspace || !bu || !b1 || !b2 || !gf || !galpha_dev) return fail(CTR_EINVAL, "null argument");
+    if (!s_start->u || !s_start->Ru || !s_start->v1b || !s_start->v2b) return fail(CTR_EINVAL, "state buffer missing");
+    if (length < 1) return fail(CTR_EINVAL, "length must be >= 1");
+    if (p->bf16) return fail(CTR_EUNSUPPORTED, "the reverse mode needs an FP32 or FP64 plan");
+    ctr_params q = resolve(p, prm);
+    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "the reverse mode covers Alg. 4 only (nonneg = 0)");
+    ctr_status st = validate_solve(p, alpha, 1, q);
+    if (st != CTR_OK) return st;
+    if (!(q.beta > 0) || !(q.c > 0)) return fail(CTR_EINVAL, "the reverse mode needs beta and c given (> 0)");
+    auto run = [&](auto tag) -> ctr_status {
+        using T = decltype(tag);
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t nn = (size_t)p->n * p->n, nm = (size_t)p->N * p->M, per = 3 * nn + 2 * nm;
+        T *ws = (T *)workspace;
+        auto slot = [&](int k, int part) -> T * {   // 0: u, 1: Ru, 2: v1b, 3: v2b
+            T *b = ws + (size_t)k * per;
+            return part == 0 ? b : part == 1 ? b + nn : part == 2 ? b + nn + nm : b + nn + 2 * nm;
+        };
+        ctr_status s2;
+        if ((s2 = select_precond<T>(p, q, s)) != CTR_OK) return s2;
+        if ((s2 = build_desc_from_data<T>(p, (const T *)f, mask, delta, q.trace_ratio, q.beta, s)) != CTR_OK) return s2;
+        CTR_CUDA(cudaMemcpyAsync(p->u, s_start->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->Ru, s_start->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->v1b, s_start->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CTR_CUDA(cudaMemcpyAsync(p->v2b, s_start->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        auto save = [&](int k) -> ctr_status {
+            CTR_CUDA(cudaMemcpyAsync(slot(k, 0), p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            CTR_CUDA(cudaMemcpyAsync(slot(k, 1), p->Ru, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            CTR_CUDA(cudaMemcpyAsync(slot(k, 2), p->v1b, nm * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            CTR_CUDA(cudaMemcpyAsync(slot(k, 3), p->v2b, 2 * nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            return CTR_OK;
+        };
+        if ((s2 = save(0)) != CTR_OK) return s2;
+        for (int k = 0; k < length; ++k) {           // replay, keeping every state
+            if ((s2 = pdrq_loop<T>(p, alpha, 1, q, q.beta, q.c, nullptr, s)) != CTR_OK) return s2;
+            if ((s2 = save(k + 1)) != CTR_OK) return s2;
+        }
+        for (int k = length - 1; k >= 0; --k)        // and reverse it, newest first
+            if ((s2 = pdrq_vjp_step<T>(p, slot(k, 0), slot(k, 2), slot(k, 3), slot(k + 1, 0), slot(k + 1, 1),
+                                       (const T *)f, mask, delta, q.trace_ratio, alpha, q.beta, q.c, q, (T *)bu,
+                                       (T *)b1, (T *)b2, (T *)gf, galpha_dev, s)) != CTR_OK)
+                return s2;
+        return CTR_OK;
+    };
+    return p->dtype == CTR_F64 ? run(double{}) : run(float{});
+}
+
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)
 {
     if (!p) return fail(CTR_EINVAL, "plan is NULL");

@@ -67,7 +67,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
-           "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp"]
+           "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment"]
 
 
 def load(path: str = LIB_PATH):
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH):
         lib.tv_pd_vjp_step.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, P(Params), P(State), P(State),
                                        vp, vp, vp, vp, vp, vp]
         lib.tv_pd_vjp_step.restype = ctypes.c_int
+        lib.tv_pd_vjp_segment.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, P(Params), P(State),
+                                          ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
         lib.ctr_div.argtypes = [vp, vp, vp, vp]
         for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
@@ -441,6 +443,32 @@ class Plan:
                                      self._t(bu, (self.n, self.n), "bu"), self._t(b1, sino, "b1"),
                                      self._t(b2, (2, self.n, self.n), "b2"), self._t(gf, sino, "gf"),
                                      ctypes.c_void_p(galpha.data_ptr()), _stream(stream)))
+
+    def vjp_workspace(self, length: int):
+        """Device workspace for tv_pd_vjp_segment of up to `length` iterations."""
+        import torch
+        per = 3 * self.n * self.n + 2 * self.n_angles * self.n_bins
+        return torch.empty((length + 1) * per, dtype=self.torch_dtype, device="cuda")
+
+    def tv_pd_vjp_segment(self, f, metal_mask, alpha: float, delta: float, params: Params, s_start, length: int,
+                          workspace, bu, b1, b2, gf, galpha, stream=None):
+        """Reverse mode of `length` iterations from the checkpoint s_start, replayed and
+        reversed on the device (cotangents as tv_pd_vjp_step)."""
+        import torch
+        if galpha.dtype != torch.float64 or not galpha.is_cuda:
+            raise TypeError("galpha must be a float64 CUDA tensor")
+        per = 3 * self.n * self.n + 2 * self.n_angles * self.n_bins
+        if workspace.dtype != self.torch_dtype or not workspace.is_cuda or workspace.numel() < (length + 1) * per \
+                or not workspace.is_contiguous():
+            raise ValueError("workspace too small (see vjp_workspace)")
+        a = self._state(s_start)
+        sino = (self.n_angles, self.n_bins)
+        _check(load().tv_pd_vjp_segment(self._h, self._t(f, sino, "f"), self._mask(metal_mask), float(alpha),
+                                        float(delta), ctypes.byref(params), ctypes.byref(a), int(length),
+                                        ctypes.c_void_p(workspace.data_ptr()), self._t(bu, (self.n, self.n), "bu"),
+                                        self._t(b1, sino, "b1"), self._t(b2, (2, self.n, self.n), "b2"),
+                                        self._t(gf, sino, "gf"), ctypes.c_void_p(galpha.data_ptr()),
+                                        _stream(stream)))
 
     def new_state(self):
         import torch

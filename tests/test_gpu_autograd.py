@@ -135,3 +135,42 @@ def test_differentiation_configuration(mods):
     df64, _ = oracle.pdrq_grad(geo, p.f, p.mask, p.delta, p.alpha, K, 2.0 * (to_np(u) - p.truth), **kw)
     assert rel_l2(to_np(f.grad), df64) < 1e-8
     assert float(alpha.grad) == pytest.approx(dalpha, rel=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_vjp_segment_equals_step_by_step(mods, dtype):
+    """tv_pd_vjp_segment (replay and reverse on the device) gives the same cotangents as
+    replaying with tv_pd_solve_state and calling tv_pd_vjp_step per iteration."""
+    import torch
+    ct, ag = mods
+    pr = phantom.make_problem("seg", 64, 90, 95, seed=8, n_ellipses=4, n_metal=1, noise="gaussian", alpha=0.05)
+    plan = ct.Plan(64, 90, 95, angles=pr.theta, dtype=dtype)
+    prm = ag.fixed_scaling(plan, power_iters=20)
+    dt = plan.torch_dtype
+    f = to_dev(pr.f, dt)
+    mask = torch.as_tensor(pr.mask, device="cuda")
+    st0 = plan.new_state()
+    plan.tv_pd_solve_state(f, mask, pr.alpha, pr.delta, 3, prm, st0)      # a non-zero checkpoint
+    L = 4
+    rng = np.random.default_rng(1)
+    seeds = [to_dev(rng.standard_normal(s), dt) for s in ((64, 64), (90, 95), (2, 64, 64))]
+    outs = []
+    for mode in ("step", "segment"):
+        bu, b1, b2 = (x.clone() for x in seeds)
+        gf = torch.zeros((90, 95), dtype=dt, device="cuda")
+        ga = torch.zeros(1, dtype=torch.float64, device="cuda")
+        if mode == "step":
+            states = [{k: v.clone() for k, v in st0.items()}]
+            for _ in range(L):
+                nxt = {k: v.clone() for k, v in states[-1].items()}
+                plan.tv_pd_solve_state(f, mask, pr.alpha, pr.delta, 1, prm, nxt)
+                states.append(nxt)
+            for k in reversed(range(L)):
+                plan.tv_pd_vjp_step(f, mask, pr.alpha, pr.delta, prm, states[k], states[k + 1], bu, b1, b2, gf, ga)
+        else:
+            plan.tv_pd_vjp_segment(f, mask, pr.alpha, pr.delta, prm, st0, L, plan.vjp_workspace(L), bu, b1, b2, gf,
+                                   ga)
+        outs.append([to_np(x) for x in (bu, b1, b2, gf)] + [float(ga)])
+    for a, b in zip(outs[0][:4], outs[1][:4]):
+        np.testing.assert_array_equal(a, b)
+    assert outs[0][4] == outs[1][4]
