@@ -150,6 +150,58 @@ __device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int 
     return s;
 }
 
+// grad_h u at pixel (i, j): forward differences with Neumann boundary (Sec. 3.1)
+template <typename T>
+__device__ __forceinline__ void grad_at(const T *__restrict__ u, int n, int i, int j, T inv_h, T &gx, T &gy)
+{
+    const size_t e = (size_t)i * n + j;
+    const T c = u[e];
+    gx = (i < n - 1) ? (u[e + n] - c) * inv_h : T(0);
+    gy = (j < n - 1) ? (u[e + 1] - c) * inv_h : T(0);
+}
+
+// Step D of Alg. 4 at one pixel: TV dual update with the projection onto the ball of
+// radius lam/tau, the next y2 = v2b + sigma tau grad u, optionally the certificate t2
+// and (Alg. 5) bar u += max(2 u - bar u, 0) - u, the resolvent of I_{u >= 0}.
+template <typename T>
+struct TvDualJob {
+    const T *u;
+    int n;
+    T sigma, tau, lam, inv_h;
+    T *v2b, *y2, *t2, *ub;
+};
+
+template <typename T>
+__device__ __forceinline__ void tv_dual_at(const TvDualJob<T> &t, int i, int j)
+{
+    const size_t nn = (size_t)t.n * t.n, e = (size_t)i * t.n + j;
+    const T st = t.sigma * t.tau;
+    T gx, gy;
+    grad_at(t.u, t.n, i, j, t.inv_h, gx, gy);
+    const T bx = t.v2b[e], by = t.v2b[e + nn];
+    const T vx = bx + st * gx, vy = by + st * gy;
+    const T zx = T(2) * vx - bx, zy = T(2) * vy - by;
+    T tx = T(0), ty = T(0);
+    if (t.lam > T(0)) {
+        const T den = fmax(T(1), t.tau * sqrt(zx * zx + zy * zy) / t.lam);
+        tx = zx / den;
+        ty = zy / den;
+    }
+    const T nbx = bx + tx - vx, nby = by + ty - vy;
+    t.v2b[e] = nbx;
+    t.v2b[e + nn] = nby;
+    t.y2[e] = nbx + st * gx;
+    t.y2[e + nn] = nby + st * gy;
+    if (t.t2) {
+        t.t2[e] = tx;
+        t.t2[e + nn] = ty;
+    }
+    if (t.ub) {
+        const T uc = t.u[e], b0 = t.ub[e];
+        t.ub[e] = b0 + fmax(T(2) * uc - b0, T(0)) - uc;
+    }
+}
+
 template <typename T>
 struct ForwardEpi {
     int mode;          // 0: plain g = scale*sum; 1: PDRQ dual step (Alg. 4); 2: CP dual step (Alg. 1);
@@ -296,8 +348,11 @@ ctr_status launch_backproject_bf16(const ctr_plan *p, const __nv_bfloat16 *g, co
 // the forward projector with the image operands stored in bfloat16 (FP32 accumulation)
 ctr_status launch_forward_bf16(const ctr_plan *p, const __nv_bfloat16 *u, const __nv_bfloat16 *uT,
                                const ForwardEpi<float> &epi, cudaStream_t s);
+// tv (optional, FP32 symmetric path only): the TV dual step of Alg. 4 fused into the
+// kernel that builds the orbit image (both read u once)
 template <typename T>
-ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s);
+ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s,
+                          const TvDualJob<T> *tv = nullptr);
 template <typename T>
 ctr_status launch_transpose(const ctr_plan *p, const T *in, T *out, cudaStream_t s);
 

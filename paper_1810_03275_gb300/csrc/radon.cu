@@ -20,6 +20,7 @@
 // Both kernels derive each weight from the same integer P (see ctr_internal.cuh),
 // so they are transposes of one matrix, bit for bit in the weights.
 #include <algorithm>
+#include <type_traits>
 
 #include "ctr_internal.cuh"
 
@@ -566,6 +567,19 @@ __global__ void __launch_bounds__(256)
 k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar, int n)
 {
     orbit_image_body<S>(u, ubar, n, blockIdx.x, blockIdx.y);
+}
+
+// The orbit image and, for the pixels (m, q) of the CTA's tile, the TV dual step of
+// Alg. 4 (both read u; each pixel's TV step runs exactly once over the grid).
+__global__ void __launch_bounds__(256)
+k_orbit_image_tv(const float *__restrict__ u, OrbitRec<float>::type *__restrict__ ubar, int n, TvDualJob<float> tv)
+{
+    orbit_image_body<float>(u, ubar, n, blockIdx.x, blockIdx.y);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int m = blockIdx.y * 32 + r, q = blockIdx.x * 32 + tx;
+        if (m < n && q < n) tv_dual_at(tv, m, q);
+    }
 }
 
 // Paired FP32 arithmetic (add / sub / fma on two lanes of a 64-bit register pair, one
@@ -1201,7 +1215,8 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
 }
 
 template <typename T, typename S>
-ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi<T> &epi, cudaStream_t s,
+                    const TvDualJob<T> *tv = nullptr)
 {
     const bool exact1 = p->h <= p->ds;
     if constexpr (sizeof(T) == 4) {
@@ -1209,7 +1224,13 @@ ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi
             using R = typename OrbitRec<S>::type;
             R *ub = (R *)p->ubar;
             p->launches++;
-            k_orbit_image<S><<<dim3((p->n + 31) / 32, (p->n + 31) / 32), 256, 0, s>>>(u, ub, p->n);
+            const dim3 og((p->n + 31) / 32, (p->n + 31) / 32);
+            if constexpr (std::is_same<S, float>::value) {
+                if (tv) k_orbit_image_tv<<<og, 256, 0, s>>>(u, ub, p->n, *tv);
+                else k_orbit_image<S><<<og, 256, 0, s>>>(u, ub, p->n);
+            } else {
+                k_orbit_image<S><<<og, 256, 0, s>>>(u, ub, p->n);
+            }
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
             k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS), ORBIT_THREADS,
@@ -1271,9 +1292,10 @@ ctr_status launch_backproject(const ctr_plan *p, const T *g, const BackprojEpi<T
 }
 
 template <typename T>
-ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s)
+ctr_status launch_forward(const ctr_plan *p, const T *u, const T *uT, const ForwardEpi<T> &epi, cudaStream_t s,
+                          const TvDualJob<T> *tv)
 {
-    return fwd_impl<T, T>(p, u, uT, epi, s);
+    return fwd_impl<T, T>(p, u, uT, epi, s, tv);
 }
 
 template <typename T>
@@ -1341,8 +1363,10 @@ template ctr_status launch_backproject<float>(const ctr_plan *, const float *, c
                                              bool);
 template ctr_status launch_backproject<double>(const ctr_plan *, const double *, const BackprojEpi<double> &,
                                               cudaStream_t, bool);
-template ctr_status launch_forward<float>(const ctr_plan *, const float *, const float *, const ForwardEpi<float> &, cudaStream_t);
-template ctr_status launch_forward<double>(const ctr_plan *, const double *, const double *, const ForwardEpi<double> &, cudaStream_t);
+template ctr_status launch_forward<float>(const ctr_plan *, const float *, const float *, const ForwardEpi<float> &,
+                                         cudaStream_t, const TvDualJob<float> *);
+template ctr_status launch_forward<double>(const ctr_plan *, const double *, const double *,
+                                          const ForwardEpi<double> &, cudaStream_t, const TvDualJob<double> *);
 template ctr_status configure_radon<float>(const ctr_plan *);
 template ctr_status configure_radon<double>(const ctr_plan *);
 template ctr_status launch_transpose<float>(const ctr_plan *, const float *, float *, cudaStream_t);

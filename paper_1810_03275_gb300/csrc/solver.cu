@@ -70,16 +70,6 @@ __global__ void k_axpy(const T *__restrict__ a, const T *__restrict__ b, T s, si
 }
 
 template <typename T>
-__device__ __forceinline__ void grad_at(const T *__restrict__ u, int n, int i, int j, T inv_h, T &gx, T &gy)
-{
-    // forward differences with Neumann boundary (Sec. 3.1)
-    const size_t e = (size_t)i * n + j;
-    const T c = u[e];
-    gx = (i < n - 1) ? (u[e + n] - c) * inv_h : T(0);
-    gy = (j < n - 1) ? (u[e + 1] - c) * inv_h : T(0);
-}
-
-template <typename T>
 __global__ void k_grad(const T *__restrict__ u, int n, T inv_h, T *px)
 {
     const size_t nn = (size_t)n * n;
@@ -127,33 +117,9 @@ __device__ __forceinline__ void tv_dual_body(const T *__restrict__ u, int n, T s
                                              T *y2, T *t2, T *ub, int b, int nb)
 {
     const size_t nn = (size_t)n * n;
-    const T st = sigma * tau;
-    for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x) {
-        T gx, gy;
-        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
-        const T bx = v2b[e], by = v2b[e + nn];
-        const T vx = bx + st * gx, vy = by + st * gy;
-        const T zx = T(2) * vx - bx, zy = T(2) * vy - by;
-        T tx = T(0), ty = T(0);
-        if (lam > T(0)) {
-            const T den = fmax(T(1), tau * sqrt(zx * zx + zy * zy) / lam);
-            tx = zx / den;
-            ty = zy / den;
-        }
-        const T nbx = bx + tx - vx, nby = by + ty - vy;
-        v2b[e] = nbx;
-        v2b[e + nn] = nby;
-        y2[e] = nbx + st * gx;
-        y2[e + nn] = nby + st * gy;
-        if (t2) {
-            t2[e] = tx;
-            t2[e + nn] = ty;
-        }
-        if (ub) {
-            const T uc = u[e], b0 = ub[e];
-            ub[e] = b0 + fmax(T(2) * uc - b0, T(0)) - uc;
-        }
-    }
+    const TvDualJob<T> job{u, n, sigma, tau, lam, inv_h, v2b, y2, t2, ub};
+    for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x)
+        tv_dual_at(job, (int)(e / n), (int)(e % n));
 }
 
 template <typename T>
@@ -600,15 +566,20 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     ec.da = d + nm;
     ec.dlo = d + 2 * nm;
     ec.dhi = d + 3 * nm;
+    const bool tv_fused = !h && sizeof(T) == 4 && p->orbit;
+    const TvDualJob<T> tvj{(const T *)p->u, n, a.sigma, a.tau, a.lam, a.inv_h, (T *)p->v2b, (T *)p->y2,
+                           diag ? (T *)p->t2 : nullptr, a.nonneg ? (T *)p->ubar_u : nullptr};
     if (h) {
         if constexpr (sizeof(T) == 4) {
             ec.y1h = p->y1h;
             if ((st = launch_forward_bf16(p, p->uh, p->uTh, ec, s)) != CTR_OK) return st;
         }
-    } else if ((st = launch_forward<T>(p, (const T *)p->u, (const T *)p->uT, ec, s)) != CTR_OK) {
+    } else if ((st = launch_forward<T>(p, (const T *)p->u, (const T *)p->uT, ec, s, tv_fused ? &tvj : nullptr)) !=
+               CTR_OK) {
         return st;
     }
-    // D: TV dual step
+    // D: TV dual step (fused into the orbit-image kernel of step C on the FP32 symmetric path)
+    if (tv_fused) return CTR_OK;
     const size_t nn = (size_t)n * n;
     p->launches++;
     k_tv_dual<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T *)p->u, n, a.sigma, a.tau, a.lam, a.inv_h,
