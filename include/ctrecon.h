@@ -205,7 +205,9 @@ ctr_status tv_pd_solve(ctr_plan *plan, const void *f_dev, const uint8_t *metal_m
  * applied per view as the linear convolution y(k) = ds sum_k' k(k - k') g(k') over the M
  * bins (an FFT of length L >= 2M - 1 along the bins, one CTA per view).  g_dev, y_dev:
  * N*M in the plan's real type (float for FP32 and BF16 plans).  The filter tables are
- * built on the first call (synchronous), later calls are asynchronous on `stream`. */
+ * built on the first call (synchronous), later calls are asynchronous on `stream`.
+ * CTR_EUNSUPPORTED when one padded view does not fit a CTA's shared memory (FP64 plans
+ * with more than about 1600 bins, FP32 beyond about 4600). */
 ctr_status ctr_ramp_filter(ctr_plan *plan, const void *g_dev, void *y_dev, void *stream);
 
 /* Filtered backprojection u = (pi / N) R_h^*(ramp-filtered g) (Sec. 2, uniform angles over

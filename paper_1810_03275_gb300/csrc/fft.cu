@@ -863,6 +863,9 @@ ctr_status prepare_ramp(ctr_plan *p)
 {
     if (p->ramp_ready) return CTR_OK;
     const int L = p->ramp_L, M = p->M;
+    if (ramp_smem(L, sizeof(T)) > 227 * 1024)
+        return fail(CTR_EUNSUPPORTED, "detector too long for the shared-memory ramp filter in this precision "
+                                      "(one view of 2M - 1 padded points must fit one CTA)");
     const double pi = 3.14159265358979323846, ds = p->ds;
     std::vector<T> tw(2 * (size_t)L), H(L);
     for (int t = 0; t < L; ++t) {

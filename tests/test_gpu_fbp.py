@@ -51,3 +51,15 @@ def test_benchmark_geometry_disk_and_bf16(ct):
     p16 = ct.Plan(pr.n, pr.n_angles, pr.n_bins, angles=pr.theta, dtype="bf16")
     u16 = to_np(p16.fbp(to_dev(chord, torch.float32)))
     assert rel_l2(u16, u) < 1e-2
+
+
+def test_over_long_detector_is_refused(ct):
+    """One padded FP64 view of 2 * 3000 - 1 points does not fit a CTA: CTR_EUNSUPPORTED,
+    and the plan stays usable."""
+    import torch
+    plan = ct.Plan(32, 4, 3000, dtype="f64")
+    g = torch.zeros((4, 3000), dtype=torch.float64, device="cuda")
+    with pytest.raises(ct.CtrError) as e:
+        plan.ramp_filter(g)
+    assert e.value.status == -6
+    assert float(plan.rh_adjoint(g).abs().max()) == 0.0
