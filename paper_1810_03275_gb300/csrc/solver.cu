@@ -444,6 +444,51 @@ ctr_status op_adjoint_bf16(ctr_plan *p, const __nv_bfloat16 *g, float *u, cudaSt
     return launch_backproject_bf16(p, g, e, s);
 }
 
+// `count` calls of step() on stream s, blk at a time replayed from one captured CUDA
+// graph (blk <= 0 or count < blk: plain launches).  step() must enqueue the same work on
+// every call.
+template <typename F>
+ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s)
+{
+    ctr_status st = CTR_OK;
+    int done = 0;
+    if (blk > 0 && count >= blk) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const unsigned long long before = p->launches;
+        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < blk && st == CTR_OK; ++k) st = step();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
+        p->launches = before;
+        if (st != CTR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        for (; done + blk <= count; done += blk) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return cuda_fail(ce, "cudaGraphLaunch");
+            }
+            p->launches += per_graph;
+        }
+        cudaGraphExecDestroy(exec);
+    }
+    for (; done < count; ++done)
+        if ((st = step()) != CTR_OK) return st;
+    return CTR_OK;
+}
+
+#ifndef CTR_POWER_GRAPH_BLOCK
+#define CTR_POWER_GRAPH_BLOCK 25
+#endif
+constexpr int POWER_GRAPH_BLOCK = CTR_POWER_GRAPH_BLOCK;   // power-iteration steps per CUDA graph
+
 // Power iteration for beta ~ ||R_h||: x <- R^*R x / ||R^*R x|| from the R2 start.
 template <typename T>
 ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
@@ -457,14 +502,17 @@ ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
     p->launches++;
     k_normalize<T><<<grid_for(nn), 256, 0, s>>>(x, nn, p->d_scal, 1, x);
     CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
-    for (int it = 0; it < iters; ++it) {
-        if (fwd_needs_transpose<T>(p) && (st = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return st;
-        if ((st = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return st;
-        if ((st = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return st;
-        if ((st = dot2<T>(p, x, y, nn, p->d_scal, s)) != CTR_OK) return st;
+    auto step = [&]() -> ctr_status {
+        ctr_status s2;
+        if (fwd_needs_transpose<T>(p) && (s2 = launch_transpose<T>(p, x, xt, s)) != CTR_OK) return s2;
+        if ((s2 = op_forward<T>(p, x, xt, g, 1.0, s)) != CTR_OK) return s2;
+        if ((s2 = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return s2;
+        if ((s2 = dot2<T>(p, x, y, nn, p->d_scal, s)) != CTR_OK) return s2;
         p->launches++;
         k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, x);
-    }
+        return CTR_OK;
+    };
+    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s)) != CTR_OK) return st;
     CTR_CHECK_LAUNCH("power_beta");
     double h[2];
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -490,17 +538,20 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
     k_normalize<T><<<grid_for(nn), 256, 0, s>>>(z, nn, p->d_scal, 1, z);
     CTR_CUDA(cudaMemsetAsync(p->d_scal, 0, 2 * sizeof(double), s));
     const double ib = 1.0 / beta;
-    for (int it = 0; it < iters; ++it) {
-        if ((st = launch_circulant<T>(p, z, false, (const T *)p->symh, x, 0, fwd_needs_transpose<T>(p) ? xt : nullptr,
+    auto step = [&]() -> ctr_status {
+        ctr_status s2;
+        if ((s2 = launch_circulant<T>(p, z, false, (const T *)p->symh, x, 0, fwd_needs_transpose<T>(p) ? xt : nullptr,
                                       nullptr, s)) != CTR_OK)
-            return st;
-        if ((st = op_forward<T>(p, x, xt, g, ib, s)) != CTR_OK) return st;
-        if ((st = op_adjoint<T>(p, g, yp, ib, s)) != CTR_OK) return st;
-        if ((st = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s)) != CTR_OK) return st;
-        if ((st = dot2<T>(p, z, y, nn, p->d_scal, s)) != CTR_OK) return st;
+            return s2;
+        if ((s2 = op_forward<T>(p, x, xt, g, ib, s)) != CTR_OK) return s2;
+        if ((s2 = op_adjoint<T>(p, g, yp, ib, s)) != CTR_OK) return s2;
+        if ((s2 = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s)) != CTR_OK) return s2;
+        if ((s2 = dot2<T>(p, z, y, nn, p->d_scal, s)) != CTR_OK) return s2;
         p->launches++;
         k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, z);
-    }
+        return CTR_OK;
+    };
+    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s)) != CTR_OK) return st;
     CTR_CHECK_LAUNCH("power_lambda");
     double h[2];
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -673,46 +724,6 @@ ctr_status prepare_impulse_symbol(ctr_plan *p, cudaStream_t s)
     k_real_floor<T, T2><<<grid_for(nn, 256, 4096), 256, 0, s>>>((const T2 *)p->cbuf, nn, mx, 1e-3, (T *)p->pk_s);
     CTR_CHECK_LAUNCH("impulse symbol");
     p->pk_kind = kind;
-    return CTR_OK;
-}
-
-// `count` calls of step() on stream s, blk at a time replayed from one captured CUDA
-// graph (blk <= 0 or count < blk: plain launches).  step() must enqueue the same work on
-// every call.
-template <typename F>
-ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s)
-{
-    ctr_status st = CTR_OK;
-    int done = 0;
-    if (blk > 0 && count >= blk) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        const unsigned long long before = p->launches;
-        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < blk && st == CTR_OK; ++k) st = step();
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
-        p->launches = before;
-        if (st != CTR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        for (; done + blk <= count; done += blk) {
-            ce = cudaGraphLaunch(exec, s);
-            if (ce != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
-                return cuda_fail(ce, "cudaGraphLaunch");
-            }
-            p->launches += per_graph;
-        }
-        cudaGraphExecDestroy(exec);
-    }
-    for (; done < count; ++done)
-        if ((st = step()) != CTR_OK) return st;
     return CTR_OK;
 }
 
