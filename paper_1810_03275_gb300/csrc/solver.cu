@@ -544,8 +544,18 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
                                       nullptr, s)) != CTR_OK)
             return s2;
         if ((s2 = op_forward<T>(p, x, xt, g, ib, s)) != CTR_OK) return s2;
-        if ((s2 = op_adjoint<T>(p, g, yp, ib, s)) != CTR_OK) return s2;
-        if ((s2 = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s)) != CTR_OK) return s2;
+        // Rt^* g; where the backprojection leaves partial images, their sum and the scale
+        // run inside the preconditioner's first pass (as in the solver's step A)
+        BackprojEpi<T> e{};
+        e.out = yp;
+        e.scale = (T)ib;
+        e.outscale = T(1);
+        e.inv_h = (T)(1.0 / p->h);
+        const bool fuse = bp_deferred<T>(p);
+        if ((s2 = launch_backproject<T>(p, g, e, s, fuse)) != CTR_OK) return s2;
+        if ((s2 = launch_circulant<T>(p, yp, false, (const T *)p->symh, y, 0, nullptr, nullptr, s, nullptr, nullptr,
+                                      fuse ? &e : nullptr)) != CTR_OK)
+            return s2;
         if ((s2 = dot2<T>(p, z, y, nn, p->d_scal, s)) != CTR_OK) return s2;
         p->launches++;
         k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, z);
