@@ -38,7 +38,8 @@ def _oracle_precond(geo, kind, sigma, tau, c, nonneg=False):
 
 @pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("n,N,M,h,dtype,tol", [(64, 90, 95, 1.0, "f64", 1e-10), (48, 37, 71, 1.0, "f32", 2e-5),
-                                               (96, 120, 137, 0.8, "f32", 2e-5)])
+                                               (96, 120, 137, 0.8, "f32", 2e-5), (27, 30, 41, 1.0, "f64", 1e-10),
+                                               (81, 44, 117, 1.0, "f32", 2e-5)])
 def test_symbol_through_precond_apply(ct, kind, n, N, M, h, dtype, tol):
     """M^{-1} y for a random y against the oracle's preconditioner of the same kind, with
     and without the identity of Alg. 5; precond = 0 is unchanged afterwards."""
