@@ -86,7 +86,7 @@ typedef struct {
                           * Kinds 1 and 2 build their kernel DFT on the plan's first use (a few
                           * kernel launches, no allocation).  In all kinds M = sigma^2 c S +
                           * (sigma tau)^2 Lap (+ id with nonneg) and c is from the power
-                          * iteration on S^{-1/2} R^*R S^{-1/2}.  Batched solves take 0 only. */
+                          * iteration on S^{-1/2} R^*R S^{-1/2}.  Batched solves take every kind. */
 } ctr_params;
 
 /* Diagnostics after the solve (original, unscaled problem unless noted). */

@@ -638,7 +638,7 @@ k_fft_cols_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefi
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, blockIdx.x - prefix[s]);
+    fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, blockIdx.x - prefix[s], d.twist);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS)

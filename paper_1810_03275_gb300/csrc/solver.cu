@@ -1403,6 +1403,8 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
     for (int i = 0; i < ns; ++i) {
         ctr_plan *p = b->plans[i];
         const unsigned long long l0 = p->launches;
+        p->precond_kind = prm.precond;                 // the preconditioner kind (its kernel built once per plan)
+        if ((prm.precond == 1 || prm.precond == 2) && (st = prepare_impulse_symbol<float>(p, s)) != CTR_OK) return st;
         beta[i] = betas ? betas[i] : 0.0;
         if (!(beta[i] > 0)) {
             if ((st = power_beta<float>(p, prm.power_iters, &beta[i], s)) != CTR_OK) return st;
@@ -1441,6 +1443,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.M = p->M;
         d.wstride = p->wstride;
         d.orbit = p->orbit ? 1 : 0;
+        d.twist = prm.precond == 2 ? 1 : 0;
         d.n_jobs = p->n_jobs;
         d.jobs = p->d_jobs;
         d.ubar = (float4 *)p->ubar;

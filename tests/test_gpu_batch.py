@@ -106,3 +106,38 @@ def test_batch_rejects_bad_input(ct):
         ct.Batch([dict(n=10, n_angles=8, n_bins=15)])            # n not 2^a 3^b
     with pytest.raises(ct.CtrError):
         ct.Batch([dict(n=16, n_angles=8, n_bins=23, h=1.0, ds=2.0)])
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_batch_with_other_preconditioners(ct, kind):
+    """params.precond = 1 (impulse response), 2 (circulant, twisted column pass in the
+    batched stage), 3 (Richardson): each slice equals the same slice solved alone with
+    that kind (β, c from the slices' own power iterations, which read the kind), and the
+    oracle's Alg. 4 with that kind's multiplier."""
+    import torch
+    probs = _slices()[:4]
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    iters = 25
+    prm = ct.default_params(graph_block=8, precond=kind, power_iters=25)
+    us, diags = batch.solve(fs, ms, [p.alpha for p in probs], [p.delta for p in probs], iters, params=prm)
+    for i, p in enumerate(probs):
+        plan = ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta)
+        plan.set_bp_groups(batch.plans[i].bp_groups)
+        u1, d1 = plan.tv_pd_solve(fs[i], ms[i], p.alpha, p.delta, iters, params=prm)
+        assert diags[i]["c"] == pytest.approx(d1["c"], rel=1e-6) and diags[i]["beta"] == pytest.approx(d1["beta"], rel=1e-6)
+        assert rel_l2(to_np(us[i]), to_np(u1)) < 2e-6, i
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        tau, c = 1 / np.sqrt(8), d1["c"]
+        if kind == 1:
+            sym, circ = oracle.precond_symbol_from(p.n, 1.0, tau, c, oracle.impulse_response_kernel_dft(geo)), False
+        elif kind == 2:
+            sym = oracle.precond_symbol_circulant(p.n, 1.0, tau, c, oracle.circulant_kernel_dft(geo),
+                                                  oracle.circulant_laplace_dft(p.n))
+            circ = True
+        else:
+            sym, circ = np.full((p.n, p.n), 1.0 / oracle.richardson_m(1.0, tau, c)), False
+        ref = oracle.pdrq_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, iters, sigma=1.0,
+                                tau=tau, eps=np.pi / p.n, beta=d1["beta"], c=c, symbol=sym, circulant=circ)
+        assert rel_l2(to_np(us[i]), ref.u) < 1e-5, i

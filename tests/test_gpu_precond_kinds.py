@@ -3,7 +3,7 @@
 preconditioner", 1-D DFT of length n^2 on the flattened image), 3 = Richardson (Sec.
 "Suitable Preconditioners"), with the oracle: the multiplier through precond_apply, c from
 the solve's own power iteration, Alg. 4 iterates at fixed (beta, c), the FP32 benchmark
-geometry, and the refusals."""
+geometry, and the refusals (batches with the kinds: tests/test_gpu_batch.py)."""
 import numpy as np
 import pytest
 
@@ -115,4 +115,4 @@ def test_refusals(ct):
     batch = ct.Batch([dict(n=32, n_angles=20, n_bins=47)])
     with pytest.raises(Exception, match="precond"):
         batch.solve([torch.zeros((20, 47), device="cuda")], [None], [0.1], [-1.0], 2,
-                    params=ct.default_params(precond=1))
+                    params=ct.default_params(precond=5))
