@@ -344,9 +344,10 @@ ctr_plan *ctr_batch_plan(ctr_batch *batch, int index);
 ctr_status ctr_batch_retune(ctr_batch *batch);
 unsigned long long ctr_batch_launch_count(const ctr_batch *batch);
 /* tv_pd_solve for every slice i: f_devs[i] (N_i*M_i floats), masks[i] (bytes or NULL;
- * masks may be NULL), alphas[i], deltas[i], shared iters and params; betas/cs (may
- * be NULL, or entries <= 0) select power iterations per slice; u_outs[i] (n_i^2
- * floats); diags (NULL or count entries, host) filled after an internal sync. */
+ * masks may be NULL), alphas[i], deltas[i], shared iters and params (every
+ * preconditioner kind; nonneg = 1 runs Alg. 5 on all slices); betas/cs (may be NULL,
+ * or entries <= 0) select power iterations per slice; u_outs[i] (n_i^2 floats); diags
+ * (NULL or count entries, host) filled after an internal sync. */
 ctr_status tv_pd_solve_batched(ctr_batch *batch, const void *const *f_devs, const uint8_t *const *masks,
                                const double *alphas, const double *deltas, int iters, const ctr_params *params,
                                const double *betas, const double *cs, void *const *u_outs, ctr_diag *diags,

@@ -1000,7 +1000,6 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
     if (!(qc.eps > 0)) qc.eps = 1.0;     // validated per slice (pi/n when unset)
     ctr_status st = check_params(qc);
     if (st != CTR_OK) return st;
-    if (q.nonneg) return fail(CTR_EUNSUPPORTED, "batched solves cover Alg. 4 only (nonneg = 0)");
     CTR_CUDA(cudaEventRecord(b->ev_in, (cudaStream_t)stream));
     CTR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
     st = batch_solve(b, (const float *const *)f_devs, masks, alphas, deltas, iters, q, betas, cs,

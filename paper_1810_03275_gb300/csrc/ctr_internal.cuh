@@ -239,6 +239,7 @@ struct SliceDesc {
     float *u, *uT, *y1, *y2, *v2b, *bp_part;   // bp_part: angle-group images, or the symmetric planes
     int orbit;                    // symmetric projector path (per_group, bp_groups count jobs)
     int twist;                    // the circulant preconditioner's 1-D transform in the column pass
+    float *ub;                    // Alg. 5: bar u (updated by the TV stage); null for Alg. 4
     int n_jobs;
     const OrbitJob *jobs;
     float4 *ubar;

@@ -139,7 +139,7 @@ k_tv_dual_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefix
         else hi = mid - 1;
     }
     const SliceDesc &d = sd[lo];
-    tv_dual_body<float>(d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, nullptr, blockIdx.x - prefix[lo],
+    tv_dual_body<float>(d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, d.ub, blockIdx.x - prefix[lo],
                         prefix[lo + 1] - prefix[lo]);
 }
 
@@ -1424,8 +1424,11 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         CTR_CUDA(cudaMemsetAsync(p->Ru, 0, nm * sizeof(float), s));
         CTR_CUDA(cudaMemsetAsync(p->v1b, 0, nm * sizeof(float), s));
         CTR_CUDA(cudaMemsetAsync(p->v2b, 0, 2 * nn * sizeof(float), s));
-        if ((st = launch_symbols<float>(p, prm.sigma, prm.tau, c[i], eps, s)) != CTR_OK) return st;
+        const bool nonneg = prm.nonneg != 0;                 // Alg. 5
+        if (nonneg) CTR_CUDA(cudaMemsetAsync(p->ubar_u, 0, nn * sizeof(float), s));
+        if ((st = launch_symbols<float>(p, prm.sigma, prm.tau, c[i], eps, s, nonneg)) != CTR_OK) return st;
         IterArgs<float> &a = args[i];
+        a.nonneg = nonneg;
         a.sigma = (float)prm.sigma;
         a.tau = (float)prm.tau;
         a.lam = (float)(alpha[i] / (beta[i] * beta[i]));
@@ -1475,6 +1478,11 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.bpe.divtau = a.tau;
         d.bpe.outscale = -a.sigma;
         d.bpe.inv_h = a.inv_h;
+        d.ub = nonneg ? (float *)p->ubar_u : nullptr;
+        if (nonneg) {                                       // u_tmp = bar u - u - sigma (...)
+            d.bpe.ub = (const float *)p->ubar_u;
+            d.bpe.uu = (const float *)p->u;
+        }
         d.fwe = ForwardEpi<float>{};
         d.fwe.mode = 1;
         d.fwe.scale = a.inv_beta;
@@ -1556,6 +1564,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
             }
             if ((st = compute_diag<float>(p, alpha[i], beta[i], prm.tau, c[i], iters, &diags[i], s)) != CTR_OK)
                 return st;
+            if (prm.nonneg) diags[i].gap = diags[i].dual_residual = nan("");   // Alg. 4's saddle problem only
         }
         if (u_out && u_out[i])
             CTR_CUDA(cudaMemcpyAsync(u_out[i], p->u, sizeof(float) * p->n * p->n, cudaMemcpyDeviceToDevice, s));

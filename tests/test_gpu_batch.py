@@ -141,3 +141,27 @@ def test_batch_with_other_preconditioners(ct, kind):
         ref = oracle.pdrq_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, iters, sigma=1.0,
                                 tau=tau, eps=np.pi / p.n, beta=d1["beta"], c=c, symbol=sym, circulant=circ)
         assert rel_l2(to_np(us[i]), ref.u) < 1e-5, i
+
+
+def test_batch_alg5(ct):
+    """params.nonneg = 1 in a batch (symmetric and per-angle slices): each slice equals
+    the same slice solved alone by Alg. 5 and the oracle's Alg. 5; gap and dual residual
+    are NaN as for single solves."""
+    import torch
+    probs = _slices()[:4]
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    iters = 30
+    prm = ct.default_params(graph_block=8, nonneg=1, power_iters=25)
+    us, diags = batch.solve(fs, ms, [p.alpha for p in probs], [p.delta for p in probs], iters, params=prm)
+    for i, p in enumerate(probs):
+        plan = ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta)
+        plan.set_bp_groups(batch.plans[i].bp_groups)
+        u1, d1 = plan.tv_pd_solve(fs[i], ms[i], p.alpha, p.delta, iters, params=prm)
+        assert rel_l2(to_np(us[i]), to_np(u1)) < 2e-6, i
+        assert np.isnan(diags[i]["gap"]) and np.isfinite(diags[i]["objective"])
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        ref = oracle.pdrq5_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, iters, sigma=1.0,
+                                 tau=1 / np.sqrt(8), eps=np.pi / p.n, beta=d1["beta"], c=d1["c"])
+        assert rel_l2(to_np(us[i]), ref.u) < 1e-5, i

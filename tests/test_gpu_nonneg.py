@@ -131,4 +131,4 @@ def test_alg5_refused_where_not_covered(ct):
     batch = ct.Batch([dict(n=32, n_angles=20, n_bins=47)])
     with pytest.raises(Exception, match="nonneg"):
         batch.solve([torch.zeros((20, 47), device="cuda")], [None], [0.1], [-1.0], 2,
-                    params=ct.default_params(nonneg=1))
+                    params=ct.default_params(nonneg=3))
