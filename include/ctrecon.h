@@ -65,7 +65,7 @@ typedef struct {
     double c_margin;     /* c = c_margin * lambda_max estimate (default 1.05) */
     double trace_ratio;  /* metal-trace threshold C = trace_ratio * f (default 0.8, Sec. 5.2) */
     int check_every;     /* diagnostics cadence; 0 = only after the last iteration */
-    int graph_block;     /* iterations per captured CUDA graph; 0 = plain launches (default 25) */
+    int graph_block;     /* iterations per captured CUDA graph; 0 = plain launches (default 10) */
     int nonneg;          /* 1: Alg. 5, the non-negativity constraint u >= 0 added to (C_h) (Sec.
                           * "Non-negativity constraints"): the preconditioner symbol gains the
                           * identity, ||xi|| / (||xi|| + sigma^2 c + (sigma tau)^2 L ||xi||), the
