@@ -64,3 +64,18 @@ def test_plan_create_rejects_bad_geometry_before_touching_the_device(lib):
                 ctrecon.Geometry(8, 4, 5, 1.0, 1.0, None)]:
         assert ctrecon.load().ctr_plan_create(ctypes.byref(bad), 0, ctypes.byref(out)) == -1
         assert out.value is None
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with the library absent the binding raises instead of computing."""
+    from paper_1810_03275_gb300 import ctrecon
+    monkeypatch.setattr(ctrecon, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        ctrecon.load(str(tmp_path / "missing" / "libctrecon.so"))
+
+
+def test_binding_declares_every_exported_symbol():
+    """The Python binding lists every entry point the header declares (argument
+    marshalling only; nothing is computed in Python)."""
+    from paper_1810_03275_gb300 import ctrecon
+    assert set(declared_functions()) <= set(ctrecon.EXPORTS)
