@@ -1315,7 +1315,6 @@ ctr_status pdrq_vjp_step(ctr_plan *p, const T *u0, const T *v1b0, const T *v2b0,
     T *du1 = (T *)p->du;            // n^2
     T *dr = (T *)p->x;              // n^2
     T *drT = (T *)p->xt;            // n^2
-    T *tmp = (T *)p->u;             // n^2
     ctr_status st;
     if ((st = launch_symbols<T>(p, prm.sigma, prm.tau, c, prm.eps, s)) != CTR_OK) return st;
     // data and TV pointwise steps
@@ -1326,7 +1325,7 @@ ctr_status pdrq_vjp_step(ctr_plan *p, const T *u0, const T *v1b0, const T *v2b0,
     k_finalize<1><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 0u, p->d_scal + 20);
     k_accum_scalar<<<1, 32, 0, s>>>(p->d_scal + 20, ib * ib, galpha);
     CTR_CHECK_LAUNCH("vjp pointwise");
-    // du' = bu + Rt^* dRu - div(dg)
+    // du' = bu + Rt^* dRu - div(dg)   (bu added in the backprojection's epilogue)
     BackprojEpi<T> e{};
     e.out = du1;
     e.scale = (T)ib;
@@ -1334,32 +1333,28 @@ ctr_status pdrq_vjp_step(ctr_plan *p, const T *u0, const T *v1b0, const T *v2b0,
     e.divtau = T(1);
     e.outscale = T(1);
     e.inv_h = inv_h;
+    e.ub = bu;
     if ((st = launch_backproject<T>(p, dRu, e, s)) != CTR_OK) return st;
-    p->launches += 1;
-    k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(du1, bu, T(1), nn, du1);
-    // dr = -sigma P(du')
+    // dr = -sigma P(du'): P(du') is kept unscaled and -sigma goes into the two consumers
     const bool tr = fwd_needs_transpose<T>(p);
     if ((st = launch_circulant<T>(p, du1, false, (const T *)p->sym, dr, 0, tr ? drT : nullptr, nullptr, s)) != CTR_OK)
         return st;
-    p->launches += tr ? 2 : 1;
-    k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(dr, -sigma, nn, dr);
-    if (tr) k_scal<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(drT, -sigma, nn, drT);
-    // dy1 = Rt dr ; dy2 = tau grad dr
-    if ((st = op_forward<T>(p, dr, drT, dy1, ib, s)) != CTR_OK) return st;
+    // dy1 = Rt dr = -sigma Rt P(du') ; dy2 = tau grad dr = -sigma tau grad P(du')
+    if ((st = op_forward<T>(p, dr, drT, dy1, -prm.sigma * ib, s)) != CTR_OK) return st;
     if ((st = op_grad<T>(p, dr, dy2, s)) != CTR_OK) return st;
     p->launches += 1;
-    k_scal<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(dy2, tau, 2 * nn, dy2);
-    // du = du' + sigma Rt^* dy1 - sigma tau div(dy2)
+    k_scal<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(dy2, -sigma * tau, 2 * nn, dy2);
+    // du = du' + sigma Rt^* dy1 - sigma tau div(dy2)   (du' added in the epilogue, into bu)
     BackprojEpi<T> e2{};
-    e2.out = tmp;
+    e2.out = bu;
     e2.scale = (T)(prm.sigma * ib);
     e2.px = dy2;
     e2.divtau = sigma * tau;
     e2.outscale = T(1);
     e2.inv_h = inv_h;
+    e2.ub = du1;
     if ((st = launch_backproject<T>(p, dy1, e2, s)) != CTR_OK) return st;
-    p->launches += 3;
-    k_axpy<T><<<grid_for(nn, 256, 4096), 256, 0, s>>>(du1, tmp, T(1), nn, bu);
+    p->launches += 2;
     // dv1b = dz1 + dy1 ; dv2b = dz2 + dy2
     k_axpy<T><<<grid_for(nm, 256, 4096), 256, 0, s>>>(b1, dy1, T(1), nm, b1);
     k_axpy<T><<<grid_for(2 * nn, 256, 4096), 256, 0, s>>>(b2, dy2, T(1), 2 * nn, b2);
