@@ -63,8 +63,9 @@ template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b)
 }
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { a.x += b.x; a.y += b.y; return a; }
 
-// exp(-2 pi i r / N) for the twisted column pass (0 <= r < N <= 2^24, so r and N are
-// exact in FP32)
+// exp(-2 pi i r / N) for the twisted column pass, 0 <= r < N = n^2 (r and N are exact
+// in FP32 up to n = 4096; beyond, their rounding moves the phase by at most about
+// 2 pi 2^-24, the FP32 rounding of the factor itself)
 __device__ __forceinline__ float2 twist_factor(float, int r, int N)
 {
     float sn, cs;
