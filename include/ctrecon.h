@@ -64,7 +64,15 @@ typedef struct {
     int power_iters;     /* power-iteration steps for beta and c (default 50) */
     double c_margin;     /* c = c_margin * lambda_max estimate (default 1.05) */
     double trace_ratio;  /* metal-trace threshold C = trace_ratio * f (default 0.8, Sec. 5.2) */
-    int check_every;     /* diagnostics cadence; 0 = only after the last iteration */
+    int check_every;     /* diagnostics cadence of Alg. 4, 5 and 3 solves (tv_pd_solve, tv_pd_run,
+                          * tv_pd_solve_state, tv_pdrq2_solve, tv_mar_solve's second stage): k > 0
+                          * computes the diagnostics of ctr_diag on the device after every k-th
+                          * iteration (one extra R_h^* each, no host synchronisation unless
+                          * stop_tol > 0) and keeps them as a history that ctr_plan_history
+                          * returns -- the convergence record of Sec. 5 (objective against the
+                          * iteration count).  At most 4096 checks per solve (iters / k > 4096:
+                          * CTR_EINVAL).  0 (default): diagnostics only after the last
+                          * iteration.  Alg. 1, ADMM and batches: CTR_EUNSUPPORTED for k > 0. */
     int graph_block;     /* iterations per captured CUDA graph; 0 = plain launches (default 10) */
     int nonneg;          /* 1: Alg. 5, the non-negativity constraint u >= 0 added to (C_h) (Sec.
                           * "Non-negativity constraints"): the preconditioner symbol gains the
@@ -87,6 +95,10 @@ typedef struct {
                           * kernel launches, no allocation).  In all kinds M = sigma^2 c S +
                           * (sigma tau)^2 Lap (+ id with nonneg) and c is from the power
                           * iteration on S^{-1/2} R^*R S^{-1/2}.  Batched solves take every kind. */
+    double stop_tol;     /* > 0 (needs check_every > 0): stop at the first check whose rel_change
+                          * ||u_k - u_{k-1}|| / ||u_k|| is <= stop_tol; diag_out->iters_done then
+                          * tells how many iterations ran.  Each check synchronises the stream to
+                          * read rel_change.  0 (default): run all iterations. */
 } ctr_params;
 
 /* Diagnostics after the solve (original, unscaled problem unless noted). */
@@ -97,7 +109,10 @@ typedef struct {
     double data_fit;
     double tv;             /* ||grad_h u||_1, isotropic */
     double violation;      /* max_r max(lo_r - (R u)_r, (R u)_r - hi_r, 0) */
-    double gap;            /* Fenchel-Young gap G(Ku)+G*(t)-<Ku,t> of the beta-scaled problem (boxes excluded) */
+    double gap;            /* Fenchel-Young gap G(Ku)+G*(t)-<Ku,t> of the beta-scaled problem with the box
+                            * indicators left out (they appear as `violation`): a certificate of
+                            * optimality only at a feasible iterate (violation = 0); while the
+                            * iterate violates a box the value can be negative */
     double dual_residual;  /* ||K^* t||_2 of the beta-scaled problem */
     double rel_change;     /* ||u_k - u_{k-1}|| / ||u_k|| */
     int iters_done;
@@ -131,6 +146,13 @@ void ctr_default_params(ctr_params *p);
 const char *ctr_last_error(void);
 /* Bytes of device memory the plan holds. */
 size_t ctr_plan_device_bytes(const ctr_plan *plan);
+/* The diagnostics history of the plan's last solve (params->check_every > 0; Sec. 5's
+ * convergence record): *count receives the number of checks it made, and the first
+ * min(capacity, *count) records are copied to out_host in order (record r describes the
+ * iterate after (r + 1) * check_every iterations; iters_done says which).  A solve with
+ * check_every = 0 leaves 0 records.  Synchronises the plan's internal stream; out_host may
+ * be NULL when capacity = 0.  CTR_EINVAL for a NULL plan or count or capacity < 0. */
+ctr_status ctr_plan_history(ctr_plan *plan, ctr_diag *out_host, int capacity, int *count);
 /* Number of this library's kernels the plan has launched so far (kernels replayed
  * inside CUDA graphs included). */
 unsigned long long ctr_plan_launch_count(const ctr_plan *plan);
@@ -360,6 +382,13 @@ ctr_status tv_pd_solve_batched(ctr_batch *batch, const void *const *f_devs, cons
 ctr_status ctr_power_beta(ctr_plan *plan, int iters, double *beta_out, void *stream);
 ctr_status ctr_power_lambda(ctr_plan *plan, double beta, double eps, int iters,
                             double *lambda_out, void *stream);
+
+/* Measured FP32 FMA ceiling of the current device (FMA/s): independent FMA chains in
+ * registers, scalar and paired (.f32x2) forms, 8 CTAs of 256 threads per SM; the faster
+ * form after a warm-up launch.  The denominator of the projectors' roofline (they do two
+ * FMAs per (pixel, angle) sample, Sec. 3.1, on operands staged on chip).  No counterpart
+ * in the thesis: a measurement utility.  Synchronises `stream`; no allocation. */
+ctr_status ctr_fp32_fma_rate(double *fma_per_s, void *stream);
 
 /* grad_h (forward differences, Neumann; Sec. 3.1): u (n*n) -> p (2*n*n, x then y). */
 ctr_status ctr_grad(ctr_plan *plan, const void *u_dev, void *p_dev, void *stream);

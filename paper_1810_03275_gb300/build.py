@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libctrecon.so")
 ROOT = os.path.dirname(HERE)
 HEADERS = [os.path.join(ROOT, "include", "ctrecon.h"), os.path.join(SRC, "ctr_internal.cuh")]
-UNITS = ["radon.cu", "fft.cu", "solver.cu", "capi.cu"]
+UNITS = ["radon.cu", "fft.cu", "solver.cu", "capi.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -265,6 +265,8 @@ ctr_status check_params(const ctr_params &q)
     if (!(q.c_margin >= 1.0)) return fail(CTR_EINVAL, "c_margin must be >= 1");
     if (!std::isfinite(q.trace_ratio)) return fail(CTR_EINVAL, "trace_ratio must be finite");
     if (q.graph_block < 0 || q.check_every < 0) return fail(CTR_EINVAL, "graph_block and check_every must be >= 0");
+    if (!(q.stop_tol >= 0) || !std::isfinite(q.stop_tol)) return fail(CTR_EINVAL, "stop_tol must be finite and >= 0");
+    if (q.stop_tol > 0 && q.check_every < 1) return fail(CTR_EINVAL, "stop_tol > 0 needs check_every >= 1");
     if (q.nonneg != 0 && q.nonneg != 1) return fail(CTR_EINVAL, "nonneg must be 0 or 1");
     if (q.precond < 0 || q.precond > 3) return fail(CTR_EINVAL, "precond must be 0, 1, 2 or 3");
     return CTR_OK;
@@ -409,12 +411,42 @@ void ctr_default_params(ctr_params *q)
     q->c_margin = 1.05;
     q->trace_ratio = 0.8;
     q->check_every = 0;
+    q->stop_tol = 0.0;
     q->graph_block = 10;   // measured: 10 to 30 within 0.5 %, smaller graphs instantiate faster
     q->nonneg = 0;
     q->precond = 0;
 }
 
 size_t ctr_plan_device_bytes(const ctr_plan *p) { return p ? p->bytes : 0; }
+
+ctr_status ctr_plan_history(ctr_plan *p, ctr_diag *out, int capacity, int *count)
+{
+    if (!p || !count) return fail(CTR_EINVAL, "plan and count must not be NULL");
+    if (capacity < 0 || (capacity > 0 && !out)) return fail(CTR_EINVAL, "capacity must be >= 0 (out given when > 0)");
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(CTR_ECUDA, "cannot select the plan's device");
+    *count = p->hist_count;
+    const int k = capacity < p->hist_count ? capacity : p->hist_count;
+    if (k <= 0) return CTR_OK;
+    std::vector<double> h((size_t)k * HIST_FIELDS);
+    CTR_CUDA(cudaMemcpyAsync(h.data(), p->d_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CTR_CUDA(cudaStreamSynchronize(p->stream));
+    for (int r = 0; r < k; ++r) {
+        const double *v = &h[(size_t)r * HIST_FIELDS];
+        ctr_diag &d = out[r];
+        d.beta = v[0];
+        d.c = v[1];
+        d.objective = v[2];
+        d.data_fit = v[3];
+        d.tv = v[4];
+        d.violation = v[5];
+        d.gap = v[6];
+        d.dual_residual = v[7];
+        d.rel_change = v[8];
+        d.iters_done = (int)v[9];
+    }
+    return CTR_OK;
+}
 
 ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **out)
 {
@@ -519,6 +551,7 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     }
     ALLOC(p->d_red, sizeof(double) * 8 * p->red_blocks);
     ALLOC(p->d_scal, sizeof(double) * 64);
+    ALLOC(p->d_hist, sizeof(double) * HIST_FIELDS * MAX_CHECKS);
 #undef ALLOC
     if ((st = build_tables(p)) != CTR_OK) { destroy(p); return st; }
     st = (dtype == CTR_F64) ? build_twiddles<double>(p) : build_twiddles<float>(p);
@@ -660,6 +693,9 @@ static ctr_status validate_solve(ctr_plan *p, double alpha, int iters, const ctr
     if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");
     if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(CTR_EINVAL, "alpha must be finite and >= 0");
     if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
+    if (q.check_every > 0 && iters / q.check_every > MAX_CHECKS)
+        return fail(CTR_EINVAL, "iters / check_every exceeds the " + std::to_string(MAX_CHECKS) +
+                                    " diagnostics records a plan holds");
     (void)p;
     return check_params(q);
 }
@@ -678,6 +714,7 @@ ctr_status tv_cp_solve(ctr_plan *p, const void *f, const uint8_t *mask, double a
     if (iters < 0) return fail(CTR_EINVAL, "iters must be >= 0");
     ctr_status st = check_params(q);
     if (st != CTR_OK) return st;
+    if (q.check_every > 0) return fail(CTR_EUNSUPPORTED, "check_every is implemented for Alg. 4, 5 and 3 solves");
     return CTR_DISPATCH(p, cp_impl<float>(p, f, mask, alpha, delta, iters, sigma_p, tau_d, q, u_out, diag, stream),
                         cp_impl<double>(p, f, mask, alpha, delta, iters, sigma_p, tau_d, q, u_out, diag, stream));
 }
@@ -728,6 +765,7 @@ ctr_status tv_admm_solve(ctr_plan *p, const void *f, double alpha, int iters, do
     ctr_status st = validate_solve(p, alpha, iters, q);
     if (st != CTR_OK) return st;
     if (q.nonneg) return fail(CTR_EUNSUPPORTED, "ADMM solves the unconstrained problem (nonneg = 0)");
+    if (q.check_every > 0) return fail(CTR_EUNSUPPORTED, "check_every is implemented for Alg. 4, 5 and 3 solves");
     auto run = [&](auto tag) -> ctr_status {
         using T = decltype(tag);
         StreamJoin sj(p, stream);
@@ -855,6 +893,8 @@ ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, do
     ctr_status st = validate_solve(p, alpha, 1, q);
     if (st != CTR_OK) return st;
     if (!(q.beta > 0) || !(q.c > 0)) return fail(CTR_EINVAL, "the reverse mode needs beta and c given (> 0)");
+    q.check_every = 0;   // the replay keeps no diagnostics history
+    q.stop_tol = 0.0;
     auto run = [&](auto tag) -> ctr_status {
         using T = decltype(tag);
         cudaStream_t s = (cudaStream_t)stream;
@@ -1000,6 +1040,7 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
     if (!(qc.eps > 0)) qc.eps = 1.0;     // validated per slice (pi/n when unset)
     ctr_status st = check_params(qc);
     if (st != CTR_OK) return st;
+    if (q.check_every > 0) return fail(CTR_EUNSUPPORTED, "check_every is implemented for single-plan solves");
     CTR_CUDA(cudaEventRecord(b->ev_in, (cudaStream_t)stream));
     CTR_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
     st = batch_solve(b, (const float *const *)f_devs, masks, alphas, deltas, iters, q, betas, cs,

@@ -255,6 +255,39 @@ struct SliceDesc {
 enum BatchStage { BS_BP = 0, BS_BP_SYM, BS_FFT_ROWS, BS_FFT_COLS, BS_FFT_ROWS_INV, BS_ORBIT, BS_FWD, BS_FWD_SYM,
                   BS_TV, BS_COUNT };
 
+// Instantiated CUDA graphs kept across calls, keyed by everything the captured launches
+// depend on (a tag for the loop, the block length, the scalar kernel arguments and the
+// plan state that selects kernels); the buffers the kernels touch belong to the plan, so
+// a replay with an equal key enqueues exactly the work a fresh capture would.  Least
+// recently used entries are dropped beyond CAP.
+struct GraphCache {
+    struct Entry {
+        std::vector<double> key;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long per_graph = 0;   // library kernels one replay launches
+        unsigned long long last_use = 0;
+    };
+    static constexpr size_t CAP = 12;
+    std::vector<Entry> entries;
+    unsigned long long clock = 0;
+    GraphCache() = default;
+    GraphCache(const GraphCache &) = delete;
+    GraphCache &operator=(const GraphCache &) = delete;
+    ~GraphCache() { clear(); }
+    void clear()
+    {
+        for (auto &e : entries)
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+        entries.clear();
+    }
+};
+
+// Diagnostics history of a solve with check_every > 0: one record of HIST_FIELDS doubles
+// per check (beta, c, objective, data_fit, tv, violation, gap, dual_residual, rel_change,
+// iters_done), at most MAX_CHECKS records per solve.
+constexpr int HIST_FIELDS = 10;
+constexpr int MAX_CHECKS = 4096;
+
 }  // namespace ctr
 
 // ---------------------------------------------------------------------------
@@ -333,6 +366,9 @@ struct ctr_plan {
     int red_blocks = 0;
     cudaStream_t stream = nullptr;       // internal stream (graph capture)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    double *d_hist = nullptr;            // MAX_CHECKS x HIST_FIELDS diagnostics records
+    int hist_count = 0;                  // records the last solve wrote
+    ctr::GraphCache graphs;              // instantiated iteration graphs, reused across calls
 };
 
 namespace ctr {
@@ -424,4 +460,5 @@ struct ctr_batch {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     unsigned long long launches = 0;
+    ctr::GraphCache graphs;
 };

@@ -1083,6 +1083,19 @@ extern "C" ctr_status precond_apply_static(int n, double sigma, double tau, doub
     int dev = -1;
     CTR_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= STATIC_MAX_DEVICES) return fail(CTR_EUNSUPPORTED, "precond_apply_static: device index too large");
+    // both buffers must be device (or managed) memory of the current device; the
+    // attribute query allocates nothing
+    for (const void *p : {(const void *)y_dev, (const void *)x_dev}) {
+        cudaPointerAttributes attr{};
+        cudaError_t pe = cudaPointerGetAttributes(&attr, p);
+        if (pe != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(CTR_EINVAL, "precond_apply_static: a buffer is not a CUDA pointer");
+        }
+        if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != dev)
+            return fail(CTR_EINVAL, "precond_apply_static: y_dev and x_dev must be device memory of the current "
+                                    "device (cuda:" + std::to_string(dev) + ")");
+    }
     ctr_status st = static_setup(dev);
     if (st != CTR_OK) return st;
     const StaticScratch &s = g_scratch[dev];

@@ -446,42 +446,92 @@ ctr_status op_adjoint_bf16(ctr_plan *p, const __nv_bfloat16 *g, float *u, cudaSt
 
 // `count` calls of step() on stream s, blk at a time replayed from one captured CUDA
 // graph (blk <= 0 or count < blk: plain launches).  step() must enqueue the same work on
-// every call.
+// every call.  With a key the instantiated graph stays in `cache` and later calls with an
+// equal key replay it without capturing again (the key must hold every argument of the
+// captured launches that can change between calls; buffers are fixed per plan).
+// `launches` counts this library's kernels (graph replays included).
 template <typename F>
-ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s)
+ctr_status run_graphed_in(GraphCache &cache, unsigned long long &launches, int count, int blk, F &&step,
+                          cudaStream_t s, const std::vector<double> *key)
 {
     ctr_status st = CTR_OK;
     int done = 0;
     if (blk > 0 && count >= blk) {
-        cudaGraph_t graph = nullptr;
+        GraphCache::Entry *hit = nullptr;
+        if (key)
+            for (auto &e : cache.entries)
+                if (e.key == *key) {
+                    hit = &e;
+                    break;
+                }
         cudaGraphExec_t exec = nullptr;
-        const unsigned long long before = p->launches;
-        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < blk && st == CTR_OK; ++k) st = step();
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
-        p->launches = before;
-        if (st != CTR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
+        unsigned long long per_graph = 0;
+        if (hit) {
+            exec = hit->exec;
+            per_graph = hit->per_graph;
+            hit->last_use = ++cache.clock;
+        } else {
+            cudaGraph_t graph = nullptr;
+            const unsigned long long before = launches;
+            CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < blk && st == CTR_OK; ++k) st = step();
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            per_graph = launches - before;   // captured, not yet run
+            launches = before;
+            if (st != CTR_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+            if (key) {
+                if (cache.entries.size() >= GraphCache::CAP) {   // drop the least recently used
+                    size_t lru = 0;
+                    for (size_t i = 1; i < cache.entries.size(); ++i)
+                        if (cache.entries[i].last_use < cache.entries[lru].last_use) lru = i;
+                    cudaGraphExecDestroy(cache.entries[lru].exec);
+                    cache.entries.erase(cache.entries.begin() + (long)lru);
+                }
+                GraphCache::Entry e;
+                e.key = *key;
+                e.exec = exec;
+                e.per_graph = per_graph;
+                e.last_use = ++cache.clock;
+                cache.entries.push_back(std::move(e));
+            }
         }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
         for (; done + blk <= count; done += blk) {
-            ce = cudaGraphLaunch(exec, s);
+            cudaError_t ce = cudaGraphLaunch(exec, s);
             if (ce != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
+                if (!key) cudaGraphExecDestroy(exec);
                 return cuda_fail(ce, "cudaGraphLaunch");
             }
-            p->launches += per_graph;
+            launches += per_graph;
         }
-        cudaGraphExecDestroy(exec);
+        if (!key) cudaGraphExecDestroy(exec);
     }
     for (; done < count; ++done)
         if ((st = step()) != CTR_OK) return st;
     return CTR_OK;
+}
+
+template <typename F>
+ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s,
+                       const std::vector<double> *key = nullptr)
+{
+    return run_graphed_in(p->graphs, p->launches, count, blk, step, s, key);
+}
+
+// The plan state that decides which kernels (and shapes) the projector and FFT
+// launches use, for graph keys.
+inline void plan_state_key(const ctr_plan *p, std::vector<double> &k)
+{
+    k.push_back((double)p->bp_groups);
+    k.push_back((double)p->obp_groups);
+    k.push_back((double)p->precond_kind);
+    k.push_back((double)p->alg3);
 }
 
 #ifndef CTR_POWER_GRAPH_BLOCK
@@ -512,7 +562,9 @@ ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
         k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, x);
         return CTR_OK;
     };
-    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s)) != CTR_OK) return st;
+    std::vector<double> key = {3.0, (double)POWER_GRAPH_BLOCK};
+    plan_state_key(p, key);
+    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s, &key)) != CTR_OK) return st;
     CTR_CHECK_LAUNCH("power_beta");
     double h[2];
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -561,7 +613,9 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
         k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, z);
         return CTR_OK;
     };
-    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s)) != CTR_OK) return st;
+    std::vector<double> key = {4.0, (double)POWER_GRAPH_BLOCK, ib};
+    plan_state_key(p, key);
+    if ((st = run_graphed(p, iters, POWER_GRAPH_BLOCK, step, s, &key)) != CTR_OK) return st;
     CTR_CHECK_LAUNCH("power_lambda");
     double h[2];
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -650,9 +704,11 @@ ctr_status pdrq_iteration(ctr_plan *p, const IterArgs<T> &a, bool diag, cudaStre
     return CTR_OK;
 }
 
+// Enqueue the diagnostics reductions of the current state (u, Ru, du, t1, t2) into the
+// device scalars: sc[4..6] data fit / 2, max violation, data part of the gap (beta-scaled);
+// sc[8..11] TV, TV part of the gap, ||du||^2, ||u||^2; sc[13] ||K^* t||^2.
 template <typename T>
-ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, double c, int iters_done,
-                        ctr_diag *out, cudaStream_t s)
+ctr_status enqueue_diag(ctr_plan *p, double alpha, double beta, double tau, cudaStream_t s)
 {
     const int n = p->n;
     const size_t nm = (size_t)p->N * p->M, nn = (size_t)n * n;
@@ -681,19 +737,51 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     e.inv_h = (T)(1.0 / p->h);
     ctr_status st;
     if ((st = launch_backproject<T>(p, (const T *)p->t1, e, s)) != CTR_OK) return st;
-    if ((st = dot2<T>(p, (const T *)p->x, (const T *)p->x, nn, sc + 12, s)) != CTR_OK) return st;
-    double h[16];
-    CTR_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    return dot2<T>(p, (const T *)p->x, (const T *)p->x, nn, sc + 12, s);
+}
+
+// The reported values from the device scalars of enqueue_diag (one formula for the
+// host result and the device history record).
+__host__ __device__ inline void diag_values(const double *h, double alpha, double beta, double c, int iters_done,
+                                            bool nonneg, double *v)
+{
+    v[0] = beta;
+    v[1] = c;
+    v[3] = h[4] * beta * beta;                   // data fit
+    v[4] = h[8];                                 // TV
+    v[2] = v[3] + alpha * v[4];                  // objective
+    v[5] = h[5] > 0 ? h[5] * beta : 0.0;         // violation
+    v[6] = nonneg ? nan("") : h[6] + h[9];       // gap (Alg. 4's saddle problem only)
+    v[7] = nonneg ? nan("") : sqrt(h[13]);       // dual residual
+    v[8] = h[11] > 0 ? sqrt(h[10] / h[11]) : 0.0;
+    v[9] = (double)iters_done;
+}
+
+__global__ void k_diag_record(const double *__restrict__ sc, double alpha, double beta, double c, int iters_done,
+                              int nonneg, double *rec)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) diag_values(sc, alpha, beta, c, iters_done, nonneg != 0, rec);
+}
+
+template <typename T>
+ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, double c, int iters_done,
+                        ctr_diag *out, cudaStream_t s, bool nonneg = false)
+{
+    ctr_status st;
+    if ((st = enqueue_diag<T>(p, alpha, beta, tau, s)) != CTR_OK) return st;
+    double h[16], v[HIST_FIELDS];
+    CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
     CTR_CUDA(cudaStreamSynchronize(s));
-    out->beta = beta;
-    out->c = c;
-    out->data_fit = h[4] * beta * beta;
-    out->violation = h[5] > 0 ? h[5] * beta : 0.0;
-    out->tv = h[8];
-    out->objective = out->data_fit + alpha * out->tv;
-    out->gap = h[6] + h[9];
-    out->dual_residual = std::sqrt(h[13]);
-    out->rel_change = h[11] > 0 ? std::sqrt(h[10] / h[11]) : 0.0;
+    diag_values(h, alpha, beta, c, iters_done, nonneg, v);
+    out->beta = v[0];
+    out->c = v[1];
+    out->objective = v[2];
+    out->data_fit = v[3];
+    out->tv = v[4];
+    out->violation = v[5];
+    out->gap = v[6];
+    out->dual_residual = v[7];
+    out->rel_change = v[8];
     out->iters_done = iters_done;
     if (!std::isfinite(out->objective) || !std::isfinite(out->tv))
         return fail(CTR_ENUMERIC, "non-finite objective after the solve");
@@ -920,7 +1008,11 @@ ctr_status admm_loop(ctr_plan *p, double alpha, int iters, int cg_iters, double 
     const T tau = (T)prm.tau, mu_t = (T)mu, lam = (T)(alpha / (beta * beta)), inv_beta = (T)(1.0 / beta);
     auto one = [&]() { return admm_iteration<T>(p, cg_iters, tau, mu_t, lam, inv_beta, s); };
     const int body = iters > 0 ? iters - 1 : 0;
-    if ((st = run_graphed(p, body, prm.graph_block, one, s)) != CTR_OK) return st;
+    std::vector<double> key = {5.0, (double)prm.graph_block, (double)cg_iters, (double)tau, (double)mu_t, (double)lam,
+                               (double)inv_beta};
+    plan_state_key(p, key);
+    p->hist_count = 0;
+    if ((st = run_graphed(p, body, prm.graph_block, one, s, &key)) != CTR_OK) return st;
     if (iters > 0) {
         CTR_CUDA(cudaMemcpyAsync(p->aux, p->u, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
         if ((st = one()) != CTR_OK) return st;
@@ -1055,37 +1147,10 @@ ctr_status cp_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm, 
     };
     ctr_status st;
     const int blk = prm.graph_block > 0 ? prm.graph_block : 0;
-    int done = 0;
-    if (blk > 0 && iters >= blk) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        const unsigned long long before = p->launches;
-        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = CTR_OK;
-        for (int k = 0; k < blk && st == CTR_OK; ++k) st = one();
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        const unsigned long long per_graph = p->launches - before;
-        p->launches = before;
-        if (st != CTR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        for (; done + blk <= iters; done += blk) {
-            ce = cudaGraphLaunch(exec, s);
-            if (ce != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
-                return cuda_fail(ce, "cudaGraphLaunch");
-            }
-            p->launches += per_graph;
-        }
-        cudaGraphExecDestroy(exec);
-    }
-    for (; done < iters; ++done)
-        if ((st = one()) != CTR_OK) return st;
+    std::vector<double> key = {2.0, (double)blk, (double)lam, sp, sd, beta, (double)inv_h};
+    plan_state_key(p, key);
+    p->hist_count = 0;
+    if ((st = run_graphed(p, iters, blk, one, s, &key)) != CTR_OK) return st;
     if (!diag) return CTR_OK;
     // diagnostics of the saddle problem of Alg. 4 at (u; t1 = v, t2 = w / tau4); du = u - u_prev
     const T tau4 = (T)prm.tau;
@@ -1138,49 +1203,49 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
         CTR_CUDA(cudaMemsetAsync(p->du, 0, nn * sizeof(T), s));
         CTR_CUDA(cudaMemsetAsync(p->t1, 0, nm * sizeof(T), s));
         CTR_CUDA(cudaMemsetAsync(p->t2, 0, 2 * nn * sizeof(T), s));
-        if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, 0, diag, s);
+        p->hist_count = 0;
+        if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, 0, diag, s, a.nonneg);
         return CTR_OK;
     }
-    const int body = iters - 1;     // the last iteration also keeps du, t1, t2
+    // graphs of plain iterations, reused across calls while the key holds
     const int blk = prm.graph_block > 0 ? prm.graph_block : 0;
+    std::vector<double> key = {1.0, (double)blk, (double)a.sigma, (double)a.tau, (double)a.lam, (double)a.inv_beta,
+                               (double)a.inv_h, (double)a.nonneg};
+    plan_state_key(p, key);
+    auto plain = [&]() { return pdrq_iteration<T>(p, a, false, s); };
+    p->hist_count = 0;
     int done = 0;
-    if (blk > 0 && body >= blk) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        const unsigned long long before = p->launches;
-        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < blk; ++k) {
-            st = pdrq_iteration<T>(p, a, false, s);
-            if (st != CTR_OK) break;
-        }
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        const unsigned long long per_graph = p->launches - before;   // captured, not yet run
-        p->launches = before;
-        if (st != CTR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        for (; done + blk <= body; done += blk) {
-            ce = cudaGraphLaunch(exec, s);
-            if (ce != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
-                return cuda_fail(ce, "cudaGraphLaunch");
+    const int ce = prm.check_every;
+    if (ce > 0) {
+        // a check after every ce iterations: the last iteration of each segment keeps du,
+        // t1, t2, the reductions and one record stay on the device (no host round trip
+        // unless stop_tol asks for rel_change)
+        while (iters - done >= ce) {
+            if ((st = run_graphed(p, ce - 1, blk, plain, s, &key)) != CTR_OK) return st;
+            if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
+            done += ce;
+            if (p->hist_count >= MAX_CHECKS) return fail(CTR_EINVAL, "more diagnostics checks than the plan holds");
+            if ((st = enqueue_diag<T>(p, alpha, beta, prm.tau, s)) != CTR_OK) return st;
+            double *rec = p->d_hist + (size_t)p->hist_count * HIST_FIELDS;
+            p->launches++;
+            k_diag_record<<<1, 32, 0, s>>>(p->d_scal, alpha, beta, c, done, a.nonneg ? 1 : 0, rec);
+            CTR_CHECK_LAUNCH("k_diag_record");
+            ++p->hist_count;
+            if (prm.stop_tol > 0) {
+                double rel = 0;
+                CTR_CUDA(cudaMemcpyAsync(&rel, rec + 8, sizeof(double), cudaMemcpyDeviceToHost, s));
+                CTR_CUDA(cudaStreamSynchronize(s));
+                if (rel <= prm.stop_tol) break;
             }
-            p->launches += per_graph;
+            if (done == iters) break;
         }
-        cudaGraphExecDestroy(exec);
     }
-    for (; done < body; ++done)
-        if ((st = pdrq_iteration<T>(p, a, false, s)) != CTR_OK) return st;
-    if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
-    if (diag) {
-        if ((st = compute_diag<T>(p, alpha, beta, prm.tau, c, iters, diag, s)) != CTR_OK) return st;
-        if (a.nonneg) diag->gap = diag->dual_residual = nan("");   // defined for Alg. 4's saddle problem only
+    if (done < iters) {   // the rest; the last iteration also keeps du, t1, t2
+        if ((st = run_graphed(p, iters - done - 1, blk, plain, s, &key)) != CTR_OK) return st;
+        if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
+        done = iters;
     }
+    if (diag) return compute_diag<T>(p, alpha, beta, prm.tau, c, done, diag, s, a.nonneg);
     return CTR_OK;
 }
 
@@ -1515,38 +1580,13 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         b->launches += nl;
         return CTR_OK;
     };
-    int done = 0;
     const int blk = prm.graph_block;
-    if (blk > 0 && body >= blk) {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        const unsigned long long before = b->launches;
-        CTR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        st = CTR_OK;
-        for (int k = 0; k < blk && st == CTR_OK; ++k) st = one_iteration();
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
-        const unsigned long long per_graph = b->launches - before;
-        b->launches = before;
-        if (st != CTR_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (batch)");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate (batch)");
-        for (; done + blk <= body; done += blk) {
-            ce = cudaGraphLaunch(exec, s);
-            if (ce != cudaSuccess) {
-                cudaGraphExecDestroy(exec);
-                return cuda_fail(ce, "cudaGraphLaunch (batch)");
-            }
-            b->launches += per_graph;
-        }
-        cudaGraphExecDestroy(exec);
+    std::vector<double> key = {6.0, (double)blk, (double)ns};
+    for (int stg = 0; stg < BS_COUNT; ++stg) {
+        key.push_back((double)b->blocks[stg]);
+        key.push_back((double)b->smem[stg]);
     }
-    for (; done < body; ++done)
-        if ((st = one_iteration()) != CTR_OK) return st;
+    if ((st = run_graphed_in(b->graphs, b->launches, body, blk, one_iteration, s, &key)) != CTR_OK) return st;
     for (int i = 0; i < ns; ++i) {
         ctr_plan *p = b->plans[i];
         const unsigned long long l0 = p->launches;

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("c", ctypes.c_double), ("beta", ctypes.c_double), ("power_iters", ctypes.c_int),
                 ("c_margin", ctypes.c_double), ("trace_ratio", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("graph_block", ctypes.c_int), ("nonneg", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("stop_tol", ctypes.c_double)]
 
 
 class Diag(ctypes.Structure):
@@ -67,7 +67,8 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_plan_get_bp_groups", "ctr_batch_create", "ctr_batch_destroy", "ctr_batch_plan", "ctr_batch_retune",
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
-           "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment"]
+           "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment", "ctr_plan_history",
+           "ctr_fp32_fma_rate"]
 
 
 def load(path: str = LIB_PATH):
@@ -141,6 +142,10 @@ def load(path: str = LIB_PATH):
         lib.tv_pd_vjp_step.restype = ctypes.c_int
         lib.tv_pd_vjp_segment.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, P(Params), P(State),
                                           ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+        lib.ctr_plan_history.argtypes = [vp, P(Diag), ctypes.c_int, P(ctypes.c_int)]
+        lib.ctr_plan_history.restype = ctypes.c_int
+        lib.ctr_fp32_fma_rate.argtypes = [P(ctypes.c_double), vp]
+        lib.ctr_fp32_fma_rate.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
         lib.ctr_div.argtypes = [vp, vp, vp, vp]
         for name in ["ctr_plan_create", "rh_forward", "rh_adjoint", "precond_apply", "tv_pd_solve", "tv_pd_run",
@@ -174,9 +179,23 @@ def precond_apply_static(y, sigma: float, tau: float, c: float, eps: float, x=No
             or y.dim() != 2 or y.shape[0] != y.shape[1]:
         raise TypeError("y must be a contiguous square float32 CUDA tensor")
     x = torch.empty_like(y) if x is None else x
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous() \
+            or x.shape != y.shape:
+        raise TypeError("x must be a contiguous float32 CUDA tensor of y's shape")
+    # the C entry runs on the current device: both buffers must live there
+    dev = torch.cuda.current_device()
+    if y.device.index != dev or x.device.index != dev:
+        raise TypeError(f"x and y must be on the current CUDA device (cuda:{dev})")
     _check(load().precond_apply_static(int(y.shape[0]), float(sigma), float(tau), float(c), float(eps),
                                        ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), _stream(stream)))
     return x
+
+
+def fp32_fma_rate(stream=None) -> float:
+    """Measured FP32 FMA ceiling of the current device in FMA/s (ctr_fp32_fma_rate)."""
+    out = ctypes.c_double()
+    _check(load().ctr_fp32_fma_rate(ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def _stream(stream):
@@ -258,6 +277,18 @@ class Plan:
                                    self._t(uT, (self.n, self.n), "uT", self.op_dtype),
                                    self._t(g, (self.n_angles, self.n_bins), "g"), _stream(stream)))
         return g
+
+    def history(self):
+        """Diagnostics records of the last solve with params.check_every > 0 (list of dicts,
+        one per check, in order)."""
+        lib = load()
+        count = ctypes.c_int()
+        _check(lib.ctr_plan_history(self._h, None, 0, ctypes.byref(count)))
+        if count.value == 0:
+            return []
+        recs = (Diag * count.value)()
+        _check(lib.ctr_plan_history(self._h, recs, count.value, ctypes.byref(count)))
+        return [r.as_dict() for r in recs]
 
     @property
     def launch_count(self) -> int:
