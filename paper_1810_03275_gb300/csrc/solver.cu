@@ -770,8 +770,15 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     ctr_status st;
     if ((st = enqueue_diag<T>(p, alpha, beta, tau, s)) != CTR_OK) return st;
     double h[16], v[HIST_FIELDS];
+    int status = 0;
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CTR_CUDA(cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CTR_CUDA(cudaStreamSynchronize(s));
+    if (status != 0) {
+        CTR_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+        return fail(CTR_ETIMEOUT, (status & 1) ? "a staged projector block was not delivered in time (bounded wait ran out)"
+                                               : "a staged projector block exceeded its shared-memory window");
+    }
     diag_values(h, alpha, beta, c, iters_done, nonneg, v);
     out->beta = v[0];
     out->c = v[1];
@@ -1215,6 +1222,7 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
     auto plain = [&]() { return pdrq_iteration<T>(p, a, false, s); };
     p->hist_count = 0;
     int done = 0;
+    bool stopped = false;
     const int ce = prm.check_every;
     if (ce > 0) {
         // a check after every ce iterations: the last iteration of each segment keeps du,
@@ -1235,12 +1243,15 @@ ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm
                 double rel = 0;
                 CTR_CUDA(cudaMemcpyAsync(&rel, rec + 8, sizeof(double), cudaMemcpyDeviceToHost, s));
                 CTR_CUDA(cudaStreamSynchronize(s));
-                if (rel <= prm.stop_tol) break;
+                if (rel <= prm.stop_tol) {
+                    stopped = true;
+                    break;
+                }
             }
             if (done == iters) break;
         }
     }
-    if (done < iters) {   // the rest; the last iteration also keeps du, t1, t2
+    if (!stopped && done < iters) {   // the rest; the last iteration also keeps du, t1, t2
         if ((st = run_graphed(p, iters - done - 1, blk, plain, s, &key)) != CTR_OK) return st;
         if ((st = pdrq_iteration<T>(p, a, true, s)) != CTR_OK) return st;
         done = iters;
