@@ -468,23 +468,6 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         kt[name] = a.elapsed_time(b) / reps / 1e3
-    variants = {}
-    if plan.fwd_variant == 1:                       # the forward projector's L1/L2-gather variant, same timing
-        plan.set_fwd_variant(0)
-        fn = lambda: plan.rh_forward_t(u, uT, g)
-        for _ in range(3):
-            fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        plan.set_fwd_variant(1)
-        variants = {"rh_forward_t staged (k_forward_orbit_tma)": 1e3 * kt["rh_forward_t"],
-                    "rh_forward_t gathered (k_forward_orbit)": a.elapsed_time(b) / reps}
-        call_kernels["rh_forward_t"] = ["k_orbit_image", "k_forward_orbit_tma"]
     dom = max(kt, key=kt.get)
     hbm_peak, peak_kind = peaks()
     nominal = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6                # FMA/s, FP32 lanes x max clock
@@ -541,7 +524,6 @@ def main():
             "gsamples_per_s": ws * samples / t_step / 1e9,
             "roofline": roof,
             "kernels": kernels,
-            "forward_variants_ms": variants,
             "forms": forms,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(f_h.numel() * 4 + m_h.numel()),

@@ -352,15 +352,6 @@ ctr_status tv_pd_vjp_segment(ctr_plan *plan, const void *f_dev, const uint8_t *m
 ctr_status ctr_plan_set_bp_groups(ctr_plan *plan, int groups);
 int ctr_plan_get_bp_groups(const ctr_plan *plan);
 
-/* Tuning hook: the forward projector of the symmetric path.  0: each lane reads the orbit
- * image through L1/L2 as it marches; 1 (default where available): the band of the orbit
- * image that a CTA's rays cross is staged into shared memory by 2-D tensor loads
- * (cp.async.bulk.tensor) a block of rows ahead of the march.  Both give identical results.
- * CTR_EUNSUPPORTED for 1 when the plan is not on the symmetric path or has no tensor map
- * (rows of the orbit image not a multiple of 16 bytes, or no driver entry point).
- * ctr_plan_get_fwd_variant returns the variant in use (-1 off the symmetric path). */
-ctr_status ctr_plan_set_fwd_variant(ctr_plan *plan, int variant);
-int ctr_plan_get_fwd_variant(const ctr_plan *plan);
 
 /* Batches: many independent slices (each its own geometry, image size and view
  * count), FP32, solved together.  Each stage of an iteration of Alg. 4 is ONE kernel

@@ -8,8 +8,6 @@
 #include <new>
 #include <utility>
 
-#include <cudaTypedefs.h>
-
 #include "ctr_internal.cuh"
 
 namespace ctr {
@@ -179,30 +177,6 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
     p->n_jobs = (int)jobs.size();
     p->orbit = true;
-    // the tensor map through which k_forward_orbit_tma stages the orbit image: a 2-D array
-    // of uint64 elements (two per FP32 record, one per bfloat16 record), rows of n records;
-    // without it (no driver entry point, or rows not a multiple of 16 bytes) the plan keeps
-    // the L1/L2 gather kernel
-    p->tf_nbox = 0;
-    const int rec = p->bf16 ? 8 : 16;
-    const int nbox = tf_boxes(jobs, rec);
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult qr{};
-    if (nbox > 0 && ((size_t)n * rec) % 16 == 0 &&
-        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
-        qr == cudaDriverEntryPointSuccess && fn) {
-        auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-        const cuuint64_t dims[2] = {(cuuint64_t)n * (rec / 8), (cuuint64_t)n};
-        const cuuint64_t strides[1] = {(cuuint64_t)n * rec};
-        const cuuint32_t box[2] = {128u, (cuuint32_t)tf_rows()};
-        const cuuint32_t estr[2] = {1u, 1u};
-        const CUresult r = encode(&p->tmap_ubar, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, p->ubar, dims, strides, box, estr,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS) p->tf_nbox = nbox;
-    } else {
-        (void)cudaGetLastError();
-    }
     return CTR_OK;
 }
 
@@ -578,8 +552,6 @@ ctr_status ctr_plan_create(const ctr_geometry *g, ctr_dtype dtype, ctr_plan **ou
     ALLOC(p->d_red, sizeof(double) * 8 * p->red_blocks);
     ALLOC(p->d_scal, sizeof(double) * 64);
     ALLOC(p->d_hist, sizeof(double) * HIST_FIELDS * MAX_CHECKS);
-    ALLOC(p->d_status, sizeof(int));
-    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) { destroy(p); return fail(CTR_ECUDA, "cudaMemset"); }
 #undef ALLOC
     if ((st = build_tables(p)) != CTR_OK) { destroy(p); return st; }
     st = (dtype == CTR_F64) ? build_twiddles<double>(p) : build_twiddles<float>(p);
@@ -959,22 +931,6 @@ ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, do
         return CTR_OK;
     };
     return p->dtype == CTR_F64 ? run(double{}) : run(float{});
-}
-
-ctr_status ctr_plan_set_fwd_variant(ctr_plan *p, int variant)
-{
-    if (!p) return fail(CTR_EINVAL, "plan is NULL");
-    if (variant != 0 && variant != 1) return fail(CTR_EINVAL, "variant must be 0 or 1");
-    if (variant == 1 && (!p->orbit || p->tf_nbox <= 0))
-        return fail(CTR_EUNSUPPORTED, "the staged forward projector needs the symmetric path and a tensor map");
-    p->fwd_variant = variant;
-    return CTR_OK;
-}
-
-int ctr_plan_get_fwd_variant(const ctr_plan *p)
-{
-    if (!p || !p->orbit) return -1;
-    return p->tf_nbox > 0 ? p->fwd_variant : 0;
 }
 
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)

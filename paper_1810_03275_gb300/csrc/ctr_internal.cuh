@@ -1,7 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libctrecon.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -367,12 +366,6 @@ struct ctr_plan {
     int red_blocks = 0;
     cudaStream_t stream = nullptr;       // internal stream (graph capture)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    // the forward projector on the symmetric path: 0 = orbit image read through L1/L2
-    // (k_forward_orbit), 1 = orbit image staged by tensor loads (k_forward_orbit_tma)
-    int fwd_variant = 1;
-    int tf_nbox = 0;                     // boxes per staged block (0: tensor map unavailable)
-    CUtensorMap tmap_ubar{};             // 2-D tensor map of the orbit image (uint64 elements)
-    int *d_status = nullptr;             // device status word: bit 0 a bounded wait ran out
     double *d_hist = nullptr;            // MAX_CHECKS x HIST_FIELDS diagnostics records
     int hist_count = 0;                  // records the last solve wrote
     ctr::GraphCache graphs;              // instantiated iteration graphs, reused across calls
@@ -434,9 +427,6 @@ template <typename T> bool bp_deferred(const ctr_plan *p);
 // orbit image): callers may then skip making the transposed copy uT
 template <typename T> inline bool fwd_needs_transpose(const ctr_plan *p) { return !(sizeof(T) == 4 && p->orbit); }
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
-size_t tf_smem_bytes(int nbox);   // dynamic shared memory of k_forward_orbit_tma
-int tf_rows();                    // rows per staged block (the tensor box height)
-int tf_boxes(const std::vector<OrbitJob> &jobs, int rec_bytes);   // boxes per staged block
 int orbit_fwd_grid_y(int n_jobs);   // symmetric forward projector: job groups per bin chunk
 int fwd_grid_y(int N);         // forward-projector grid: angle groups
 

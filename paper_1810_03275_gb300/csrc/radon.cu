@@ -22,8 +22,6 @@
 #include <algorithm>
 #include <type_traits>
 
-#include <cuda.h>
-
 #include "ctr_internal.cuh"
 
 namespace ctr {
@@ -811,204 +809,6 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric forward projector with the orbit image staged by the tensor memory
-// accelerator.  A CTA of TF_WARPS warps takes one job and TF_BINS = 31 TF_WARPS
-// adjacent detector intervals (each warp 31 bins, as in k_forward_orbit), and all
-// warps march the same rows: the band of the orbit image that the CTA's rays cross
-// in a block of TF_ROWS rows is one parallelogram, copied into shared memory by 2-D
-// tensor loads (cp.async.bulk.tensor, boxes of TF_ROWS rows x 1 KB, zero-filled
-// outside the image, so the march needs no bounds checks) while the previous block is
-// marched.  Each lane then reads its pixels from shared memory instead of L1/L2.
-// The weights, the march and the per-lane sums are those of k_forward_orbit, so the
-// results are bit-identical to it.
-// ---------------------------------------------------------------------------
-#ifndef CTR_TF_WARPS
-#define CTR_TF_WARPS 4
-#endif
-#ifndef CTR_TF_ROWS
-#define CTR_TF_ROWS 8
-#endif
-#ifndef CTR_TF_STAGES
-#define CTR_TF_STAGES 2
-#endif
-constexpr int TF_WARPS = CTR_TF_WARPS;
-constexpr int TF_BINS = 31 * TF_WARPS;
-constexpr int TF_ROWS = CTR_TF_ROWS;          // rows per staged block (the box height)
-constexpr int TF_STAGES = CTR_TF_STAGES;      // staged blocks in flight
-constexpr int TF_ROW_BYTES = 1024;            // one box row: 128 uint64 elements
-constexpr unsigned TF_BOX_BYTES = TF_ROWS * TF_ROW_BYTES;
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase with the given parity; false when it has not completed within
-// about two seconds (the caller records the failure and stops using the buffer).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 0; it < (1u << 26); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) break;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar)
-{
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                 ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
-                 : "memory");
-}
-
-template <typename S>
-__global__ void __launch_bounds__(32 * TF_WARPS)
-k_forward_orbit_tma(const __grid_constant__ CUtensorMap tmap, int n, int M, int nbox_max,
-                    const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi, int *status)
-{
-    using R = typename OrbitRec<S>::type;
-    constexpr int PXB = TF_ROW_BYTES / (int)sizeof(R);      // pixels per box row
-    constexpr int EPP = (int)sizeof(R) / 8;                 // uint64 elements per pixel
-    constexpr int QALIGN = 16 / (int)sizeof(R) > 1 ? 16 / (int)sizeof(R) : 1;   // box x on 16 bytes
-    extern __shared__ __align__(128) unsigned char tf_smem_raw[];
-    // the staged blocks start on a 128-byte boundary (tensor-load destinations)
-    unsigned char *tf_smem = tf_smem_raw + ((128u - (smem_addr(tf_smem_raw) & 127u)) & 127u);
-    __shared__ __align__(8) unsigned long long s_bar[TF_STAGES];
-    __shared__ int s_q0[TF_STAGES];
-    __shared__ int s_mlo, s_mhi;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kb = blockIdx.x * TF_BINS;
-    const int k = kb + warp * 31 + lane - 1;                // this lane's interval [k, k + 1)
-    const OrbitJob &job = jobs[blockIdx.y];
-    const AngleMarch am = job.am;                           // canonical: A >= B >= 0
-    const int4 ls = *reinterpret_cast<const int4 *>(job.l);
-    if (threadIdx.x == 0) {
-        s_mlo = n;
-        s_mhi = -1;
-        for (int b = 0; b < TF_STAGES; ++b) mbar_init(smem_addr(&s_bar[b]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    {   // rows crossed by the CTA's rays on the detector (outer bounds, as k_forward_orbit)
-        int mlo = n, mhi = -1;
-        if (k < M) {
-            const float Q0 = (float)k * am.kA - am.oA;
-            rows_in<true>(Q0, am.binv, -3.f, (float)n + 1.f, n, mlo, mhi);
-        }
-        mlo = __reduce_min_sync(0xffffffffu, mlo);
-        mhi = __reduce_max_sync(0xffffffffu, mhi);
-        if (lane == 0 && mlo <= mhi) {
-            atomicMin(&s_mlo, mlo);
-            atomicMax(&s_mhi, mhi);
-        }
-    }
-    __syncthreads();
-    const int mlo = s_mlo, mhi = s_mhi;
-    const int nst = mlo <= mhi ? (mhi - mlo + TF_ROWS) / TF_ROWS : 0;
-    const long long A = am.A, B = am.B;
-    // Block st covers rows mlo + st TF_ROWS + [0, TF_ROWS); its pixels q lie between the
-    // first pixel of interval kb - 1 on the block's last row and the last pixel of
-    // interval kb + TF_BINS - 1 on its first row (P = q A + m B + Op grows with q and m).
-    auto issue = [&](int st) {
-        const int buf = st % TF_STAGES;
-        const int m_first = mlo + st * TF_ROWS, m_last = min(m_first + TF_ROWS - 1, mhi);
-        const long long Klo = (long long)(kb - 1) * 4294967296ll, Khi = (long long)(kb + TF_BINS - 1) * 4294967296ll;
-        long long qlo = ceil_div_ll(Klo - (long long)m_last * B - am.Op, A);
-        const long long qhi = ceil_div_ll(Khi + 4294967296ll - (long long)m_first * B - am.Op, A) - 1;
-        qlo -= ((qlo % QALIGN) + QALIGN) % QALIGN;           // box x on a 16-byte boundary
-        int nb = (int)((qhi - qlo + PXB) / PXB);
-        if (nb > nbox_max) {                                 // cannot happen for the plan's jobs
-            atomicOr(status, 2);
-            nb = nbox_max;
-        }
-        s_q0[buf] = (int)qlo;
-        const unsigned bar = smem_addr(&s_bar[buf]);
-        mbar_arrive_expect_tx(bar, (unsigned)nb * TF_BOX_BYTES);
-        unsigned char *dst = tf_smem + (size_t)buf * nbox_max * TF_BOX_BYTES;
-        for (int b = 0; b < nb; ++b)
-            tma_load_2d(smem_addr(dst + (size_t)b * TF_BOX_BYTES), &tmap, (int)((qlo + (long long)b * PXB) * EPP),
-                        m_first, bar);
-    };
-    if (threadIdx.x == 0)
-        for (int st = 0; st < TF_STAGES && st < nst; ++st) issue(st);
-    float4 Su = make_float4(0.f, 0.f, 0.f, 0.f), Sf = Su;
-    if (nst > 0) {
-        // the lane's march state at row mlo: q = first pixel with P >= K, r = P - K in [0, A)
-        const long long K = (long long)k * 4294967296ll;
-        const long long qa = ceil_div_ll(K - (long long)mlo * B - am.Op, A);
-        unsigned r = (unsigned)(qa * A + (long long)mlo * B + am.Op - K);
-        int q = (int)qa;
-        const unsigned A32 = (unsigned)A, B32 = (unsigned)B;
-        const unsigned lim = (unsigned)(4294967296ll - A);
-        const unsigned thr = (unsigned)(A - B);
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool ok = true;
-        for (int st = 0; st < nst; ++st) {
-            const int buf = st % TF_STAGES;
-            if (ok && !mbar_wait_bounded(smem_addr(&s_bar[buf]), (unsigned)(st / TF_STAGES) & 1u)) {
-                atomicOr(status, 1);
-                ok = false;
-            }
-            const int rows = min(TF_ROWS, mhi - (mlo + st * TF_ROWS) + 1);
-            if (ok) {
-                const unsigned char *blk = tf_smem + (size_t)buf * nbox_max * TF_BOX_BYTES;
-                int idx = q - s_q0[buf];
-#pragma unroll
-                for (int rr = 0; rr < TF_ROWS; ++rr) {
-                    if (rr < rows) {
-                        const unsigned u1 = (unsigned)idx;
-                        const R *p1 = reinterpret_cast<const R *>(blk + (u1 / PXB) * TF_BOX_BYTES +
-                                                                  rr * TF_ROW_BYTES + (u1 % PXB) * sizeof(R));
-                        const float4 v1 = rec_f32(*p1);
-                        float4 v2 = zero;
-                        if (r < lim) {
-                            const unsigned i2 = (unsigned)idx + 1u;
-                            v2 = rec_f32(*reinterpret_cast<const R *>(blk + (i2 / PXB) * TF_BOX_BYTES +
-                                                                      rr * TF_ROW_BYTES + (i2 % PXB) * sizeof(R)));
-                        }
-                        acc4(Su, Sf, v1, one_plus_frac32u(r));
-                        acc4(Su, Sf, v2, one_plus_frac32u(r + A32));
-                        const bool sdn = r >= thr;           // the first pixel moves one to the left
-                        r += sdn ? B32 - A32 : B32;
-                        idx -= sdn ? 1 : 0;
-                        q -= sdn ? 1 : 0;
-                    }
-                }
-            }
-            __syncthreads();                                // block st is consumed
-            if (threadIdx.x == 0 && ok && st + TF_STAGES < nst) issue(st + TF_STAGES);
-        }
-    }
-    if (kb + warp * 31 >= M) return;                          // warp-uniform
-    orbit_out(epi, ls.x, M, k, lane, Su.x, Sf.x);
-    orbit_out(epi, ls.y, M, k, lane, Su.y, Sf.y);
-    orbit_out(epi, ls.z, M, k, lane, Su.z, Sf.z);
-    orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
-}
-
-// ---------------------------------------------------------------------------
 // Symmetric backprojection (OrbitJob): a CTA owns a 32 x 32 tile of canonical
 // pixels x and a group of jobs; per job it stages the four channels' sinogram rows
 // side by side, so one fixed-point P(x) and one pair of 16-byte shared loads serve
@@ -1433,13 +1233,6 @@ ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi
             }
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
-            if (p->fwd_variant == 1 && p->tf_nbox > 0) {
-                k_forward_orbit_tma<S><<<dim3((p->M + TF_BINS - 1) / TF_BINS, p->n_jobs), 32 * TF_WARPS,
-                                         tf_smem_bytes(p->tf_nbox), s>>>(p->tmap_ubar, p->n, p->M, p->tf_nbox,
-                                                                         p->d_jobs, epi, p->d_status);
-                CTR_CHECK_LAUNCH("k_forward_orbit_tma");
-                return CTR_OK;
-            }
             k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS), ORBIT_THREADS,
                                  0, s>>>(
                 ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
@@ -1476,10 +1269,6 @@ ctr_status configure_radon(const ctr_plan *p)
     if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, osm);
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
-    if (st == CTR_OK && p->tf_nbox > 0) {
-        st = raise_smem_limit(k_forward_orbit_tma<float>, tf_smem_bytes(p->tf_nbox));
-        if (st == CTR_OK) st = raise_smem_limit(k_forward_orbit_tma<__nv_bfloat16>, tf_smem_bytes(p->tf_nbox));
-    }
     return st;
 }
 
@@ -1531,24 +1320,6 @@ template bool bp_deferred<double>(const ctr_plan *);
 
 int fwd_grid_x(int M) { return (M + 30) / 31; }
 
-size_t tf_smem_bytes(int nbox) { return (size_t)TF_STAGES * nbox * TF_BOX_BYTES + 128; }
-int tf_rows() { return TF_ROWS; }
-
-// Boxes of 1 KB rows a staged block needs for the widest job: the pixels between the
-// first of interval kb - 1 on a block's last row and the last of interval kb + TF_BINS - 1
-// on its first row, plus the rounding of both ends and of the box start to 16 bytes.
-int tf_boxes(const std::vector<OrbitJob> &jobs, int rec_bytes)
-{
-    const int pxb = TF_ROW_BYTES / rec_bytes;
-    long long wmax = 0;
-    for (const OrbitJob &j : jobs) {
-        if (j.am.A <= 0) return 0;
-        const __int128 span = (__int128)(TF_BINS + 1) * ((__int128)1 << 32) + (__int128)(TF_ROWS - 1) * j.am.B;
-        const long long w = (long long)(span / j.am.A) + 4 + 16 / rec_bytes;
-        wmax = std::max(wmax, w);
-    }
-    return (int)((wmax + pxb - 1) / pxb);
-}
 int orbit_fwd_grid_y(int n_jobs) { return (n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }
 

@@ -770,15 +770,8 @@ ctr_status compute_diag(ctr_plan *p, double alpha, double beta, double tau, doub
     ctr_status st;
     if ((st = enqueue_diag<T>(p, alpha, beta, tau, s)) != CTR_OK) return st;
     double h[16], v[HIST_FIELDS];
-    int status = 0;
     CTR_CUDA(cudaMemcpyAsync(h, p->d_scal, sizeof(h), cudaMemcpyDeviceToHost, s));
-    CTR_CUDA(cudaMemcpyAsync(&status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CTR_CUDA(cudaStreamSynchronize(s));
-    if (status != 0) {
-        CTR_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
-        return fail(CTR_ETIMEOUT, (status & 1) ? "a staged projector block was not delivered in time (bounded wait ran out)"
-                                               : "a staged projector block exceeded its shared-memory window");
-    }
     diag_values(h, alpha, beta, c, iters_done, nonneg, v);
     out->beta = v[0];
     out->c = v[1];

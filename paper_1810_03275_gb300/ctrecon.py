@@ -68,7 +68,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
            "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment", "ctr_plan_history",
-           "ctr_fp32_fma_rate", "ctr_plan_set_fwd_variant", "ctr_plan_get_fwd_variant"]
+           "ctr_fp32_fma_rate"]
 
 
 def load(path: str = LIB_PATH):
@@ -144,10 +144,6 @@ def load(path: str = LIB_PATH):
                                           ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.ctr_plan_history.argtypes = [vp, P(Diag), ctypes.c_int, P(ctypes.c_int)]
         lib.ctr_plan_history.restype = ctypes.c_int
-        lib.ctr_plan_set_fwd_variant.argtypes = [vp, ctypes.c_int]
-        lib.ctr_plan_set_fwd_variant.restype = ctypes.c_int
-        lib.ctr_plan_get_fwd_variant.argtypes = [vp]
-        lib.ctr_plan_get_fwd_variant.restype = ctypes.c_int
         lib.ctr_fp32_fma_rate.argtypes = [P(ctypes.c_double), vp]
         lib.ctr_fp32_fma_rate.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
@@ -309,14 +305,6 @@ class Plan:
 
     def set_bp_groups(self, groups: int):
         _check(load().ctr_plan_set_bp_groups(self._h, int(groups)))
-
-    @property
-    def fwd_variant(self) -> int:
-        """Forward projector of the symmetric path: 0 L1/L2 gather, 1 tensor-staged (-1: per-angle path)."""
-        return int(load().ctr_plan_get_fwd_variant(self._h))
-
-    def set_fwd_variant(self, variant: int):
-        _check(load().ctr_plan_set_fwd_variant(self._h, int(variant)))
 
     def rh_adjoint(self, g, u=None, stream=None):
         u = self.empty_image() if u is None else u

@@ -179,41 +179,3 @@ def test_point_projection(ct):
     np.testing.assert_allclose(got.sum(1), 1.0, atol=1e-6)
     np.testing.assert_allclose((got * np.arange(M)).sum(1), pos, atol=2e-5)
 
-
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-@pytest.mark.parametrize("geom", [(8, 12, 13, 1.0), (37, 50, 53, 1.0), (64, 90, 95, 1.0), (48, 40, 70, 0.8),
-                                  (60, 24, 90, 0.9), (130, 8, 60, 1.0), (200, 46, 283, 1.0),
-                                  (512, 720, 729, 1.0)])
-def test_forward_variants_agree(ct, geom, dtype):
-    """The symmetric path's two forward projectors -- the orbit image read through L1/L2
-    and the orbit image staged in shared memory by tensor loads (zero-filled outside the
-    image) -- give the same sinogram bit for bit, and match the oracle."""
-    import torch
-    n, N, M, h = geom
-    th = np.arange(N) * (np.pi / N)
-    plan = ct.Plan(n, N, M, angles=th, h=h, dtype=dtype)
-    assert plan.symmetric_jobs > 0
-    if plan.fwd_variant != 1:
-        pytest.skip("no tensor map for this plan (rows of the orbit image not a multiple of 16 bytes)")
-    rng = np.random.default_rng(n)
-    u = rng.standard_normal((n, n))
-    ud = to_dev(u, torch.float32).to(plan.op_dtype)
-    staged = to_np(plan.rh_forward(ud))
-    plan.set_fwd_variant(0)
-    assert plan.fwd_variant == 0
-    gathered = to_np(plan.rh_forward(ud))
-    plan.set_fwd_variant(1)
-    again = to_np(plan.rh_forward(ud))
-    assert np.array_equal(staged, gathered)
-    assert np.array_equal(staged, again)
-    ref = oracle.rh_forward(ud.double().cpu().numpy(), oracle.Geometry(n, N, M, h=h, theta=th))
-    assert rel_l2(staged, ref) < 1e-5
-
-
-def test_forward_variant_refusals(ct):
-    p64 = ct.Plan(64, 90, 95, dtype="f64")
-    assert p64.fwd_variant == -1
-    with pytest.raises(ct.CtrError):
-        p64.set_fwd_variant(1)
-    with pytest.raises(ct.CtrError):
-        ct.Plan(64, 90, 95).set_fwd_variant(2)
