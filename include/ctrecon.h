@@ -366,6 +366,19 @@ ctr_plan *ctr_batch_plan(ctr_batch *batch, int index);
 /* Rebuild the batch's launch tables after ctr_plan_set_bp_groups on its plans. */
 ctr_status ctr_batch_retune(ctr_batch *batch);
 unsigned long long ctr_batch_launch_count(const ctr_batch *batch);
+/* How a batch runs an iteration of Alg. 4.  mode 0 (default): one kernel launch per stage
+ * over all slices, iterations replayed from CUDA graphs.  mode 1: one persistent
+ * cooperative launch per iteration that runs every stage for every slice (as many CTAs
+ * as are resident at once, the stages separated by grid barriers); results are identical
+ * to mode 0.  Each CTA polls a grid barrier at most spin_limit times (~100 ns per poll)
+ * before it gives up; the launch then ends early and the solve returns CTR_ETIMEOUT
+ * (spin_limit 0 makes every barrier give up at once, which tests that path).
+ * CTR_EUNSUPPORTED for mode 1 when the persistent kernel cannot be resident with the
+ * batch's shared memory.  ctr_batch_persistent_ctas returns the persistent grid size
+ * (0: unavailable). */
+ctr_status ctr_batch_set_mode(ctr_batch *batch, int mode, unsigned long long spin_limit);
+int ctr_batch_get_mode(const ctr_batch *batch);
+int ctr_batch_persistent_ctas(const ctr_batch *batch);
 /* tv_pd_solve for every slice i: f_devs[i] (N_i*M_i floats), masks[i] (bytes or NULL;
  * masks may be NULL), alphas[i], deltas[i], shared iters and params (every
  * preconditioner kind; nonneg = 1 runs Alg. 5 on all slices); betas/cs (may be NULL,

@@ -15,7 +15,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libctrecon.so")
 ROOT = os.path.dirname(HERE)
 HEADERS = [os.path.join(ROOT, "include", "ctrecon.h"), os.path.join(SRC, "ctr_internal.cuh")]
-UNITS = ["radon.cu", "fft.cu", "solver.cu", "capi.cu", "peak.cu"]
+# kernels.cu includes radon.cu and fft.cu (one translation unit, see its header)
+INCLUDED = {"kernels.cu": ["radon.cu", "fft.cu"]}
+UNITS = ["kernels.cu", "solver.cu", "capi.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,7 +48,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out_dir:
         src = os.path.join(SRC, u)
         obj = os.path.join(out, u.replace(".cu", ".o"))
         objs.append(obj)
-        if force or _stale(obj, [src] + HEADERS):
+        deps = [src] + HEADERS + [os.path.join(SRC, x) for x in INCLUDED.get(u, [])]
+        if force or _stale(obj, deps):
             jobs.append([nvcc()] + flags + ["-c", src, "-o", obj])
 
     def run(cmd):

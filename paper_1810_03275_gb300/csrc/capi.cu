@@ -958,6 +958,7 @@ void ctr_batch_destroy(ctr_batch *b)
     for (ctr_plan *p : b->plans) ctr_plan_destroy(p);
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_gb) cudaFree(b->d_gb);
     if (b->stream) cudaStreamDestroy(b->stream);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -983,7 +984,8 @@ ctr_status ctr_batch_create(const ctr_geometry *geos, int count, ctr_batch **out
     }
     if (st == CTR_OK) {
         if (cudaMalloc((void **)&b->d_desc, sizeof(SliceDesc) * count) != cudaSuccess ||
-            cudaMalloc((void **)&b->d_prefix, sizeof(int) * BS_COUNT * (count + 1)) != cudaSuccess) {
+            cudaMalloc((void **)&b->d_prefix, sizeof(int) * BS_COUNT * (count + 1)) != cudaSuccess ||
+            cudaMalloc((void **)&b->d_gb, sizeof(GridBarrier)) != cudaSuccess) {
             cudaGetLastError();
             st = fail(CTR_ENOMEM, "batch tables: cudaMalloc failed");
         }
@@ -1016,6 +1018,20 @@ ctr_plan *ctr_batch_plan(ctr_batch *b, int i)
 }
 
 unsigned long long ctr_batch_launch_count(const ctr_batch *b) { return b ? b->launches : 0ull; }
+
+ctr_status ctr_batch_set_mode(ctr_batch *b, int mode, unsigned long long spin_limit)
+{
+    if (!b) return fail(CTR_EINVAL, "batch is NULL");
+    if (mode != 0 && mode != 1) return fail(CTR_EINVAL, "mode must be 0 or 1");
+    if (mode == 1 && b->persist_grid <= 0)
+        return fail(CTR_EUNSUPPORTED, "the persistent iteration does not fit on this device (shared memory or registers)");
+    b->mode = mode;
+    b->spin_limit = spin_limit;
+    return CTR_OK;
+}
+
+int ctr_batch_get_mode(const ctr_batch *b) { return b ? b->mode : -1; }
+int ctr_batch_persistent_ctas(const ctr_batch *b) { return b ? b->persist_grid : 0; }
 
 ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const uint8_t *const *masks,
                                const double *alphas, const double *deltas, int iters, const ctr_params *prm,

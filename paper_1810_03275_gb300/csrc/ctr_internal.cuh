@@ -282,6 +282,14 @@ struct GraphCache {
     }
 };
 
+// Grid barrier of the persistent batched iteration (device memory, zeroed before use).
+struct GridBarrier {
+    unsigned count;   // CTAs arrived at the current barrier
+    unsigned gen;     // barriers completed
+    int status;       // nonzero: a CTA's bounded wait ran out (the launch was abandoned)
+    int pad;
+};
+
 // Diagnostics history of a solve with check_every > 0: one record of HIST_FIELDS doubles
 // per check (beta, c, objective, data_fit, tv, violation, gap, dual_residual, rel_change,
 // iters_done), at most MAX_CHECKS records per solve.
@@ -445,6 +453,10 @@ ctr_status launch_batch_radon(int stage, const SliceDesc *sd, const int *prefix,
 ctr_status launch_batch_fft(int stage, const SliceDesc *sd, const int *prefix, int ns, int blocks, size_t smem,
                             cudaStream_t s);
 ctr_status launch_batch_tv(const SliceDesc *sd, const int *prefix, int ns, int blocks, cudaStream_t s);
+// the persistent form: one cooperative launch per iteration over every stage (kernels.cu)
+int persist_blocks_per_sm(size_t smem);
+ctr_status launch_batch_iteration(const SliceDesc *sd, const int *prefix, int ns, GridBarrier *gb,
+                                  unsigned long long spin_limit, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace ctr
 
@@ -461,4 +473,11 @@ struct ctr_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     unsigned long long launches = 0;
     ctr::GraphCache graphs;
+    // iteration form: 0 = one launch per stage (graph-captured), 1 = one persistent
+    // cooperative launch per iteration (k_batch_iteration)
+    int mode = 0;
+    unsigned long long spin_limit = 1ull << 26;   // polls per grid barrier before giving up
+    ctr::GridBarrier *d_gb = nullptr;
+    int persist_grid = 0;                         // resident CTAs of the persistent kernel (0: unavailable)
+    size_t persist_smem = 0;
 };

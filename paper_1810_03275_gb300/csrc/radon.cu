@@ -28,6 +28,15 @@ namespace ctr {
 
 namespace {
 
+// CTA barrier of a stage body.  NAMED: the body runs on the first 128 threads of a larger
+// CTA (the persistent batched iteration) and synchronises them with named barrier 1.
+template <bool NAMED>
+__device__ __forceinline__ void body_sync()
+{
+    if constexpr (NAMED) asm volatile("bar.sync 1, 128;" ::: "memory");
+    else __syncthreads();
+}
+
 #ifndef CTR_BP_TY
 #define CTR_BP_TY 4
 #endif
@@ -121,7 +130,7 @@ __device__ __forceinline__ void bp_epilogue(const BackprojEpi<T> &epi, int n, in
 // One CTA of the backprojection: tile (bx, by), angle group bz.
 // part == nullptr: apply the epilogue directly (one angle group).  Otherwise write
 // this group's partial sums to part[bz][n][n].
-template <typename T, typename S>
+template <typename T, typename S, bool NAMED = false>
 __device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, int M, int F, int wstride,
                                         int angles_per_group, const AngleGeom *__restrict__ geom,
                                         const BackprojEpi<T> &epi, T *__restrict__ part, int bx, int by, int bz)
@@ -149,7 +158,7 @@ __device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, i
 
     for (int l0 = la; l0 < lb; l0 += BP_ACH) {
         const int na = min(BP_ACH, lb - l0);
-        __syncthreads();
+        body_sync<NAMED>();
         if (threadIdx.x < na) {
             const AngleGeom ag = geom[l0 + threadIdx.x];
             const long long P00 = (long long)i0 * ag.C + (long long)j0 * ag.S + ag.O;
@@ -163,7 +172,7 @@ __device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, i
             sC[threadIdx.x] = ag.C;
             sS[threadIdx.x] = ag.S;
         }
-        __syncthreads();
+        body_sync<NAMED>();
         for (int e = threadIdx.x; e < na * wstride; e += NT) {
             const int a = e / wstride;
             const int k = sK[a] + (e - a * wstride);
@@ -172,7 +181,7 @@ __device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, i
             const T g1 = (k + 1 >= 0 && k + 1 < M) ? (T)ldv(row + k + 1) : T(0);
             stage[e] = make_stage(g0, g1);
         }
-        __syncthreads();
+        body_sync<NAMED>();
 #pragma unroll 2
         for (int a = 0; a < na; ++a) {
             const long long C = sC[a];
@@ -736,7 +745,7 @@ constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 // Warp w of the CTA takes job by*ORBIT_SLOTS + w % ORBIT_SLOTS, bins bx*31 + [0, 31) and
 // the (w / ORBIT_SLOTS)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
-template <typename S>
+template <typename S, bool NAMED = false>
 __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
                                                    int n_jobs, int M, const OrbitJob *__restrict__ jobs,
                                                    const ForwardEpi<float> &epi, int bx, int by)
@@ -784,7 +793,7 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
             s_part[seg - 1][0][slot][lane] = Su;
             s_part[seg - 1][1][slot][lane] = Sf;
         }
-        __syncthreads();
+        body_sync<NAMED>();
         if (seg > 0) return;
 #pragma unroll
         for (int z = 0; z < ORBIT_SEGS - 1; ++z) {

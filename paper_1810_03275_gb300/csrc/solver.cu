@@ -13,6 +13,8 @@
 // next iteration, so R_h u is computed once per iteration (Sec. 4.4).
 #include <cmath>
 
+#include <algorithm>
+
 #include "ctr_internal.cuh"
 
 namespace ctr {
@@ -1584,13 +1586,29 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         b->launches += nl;
         return CTR_OK;
     };
-    const int blk = prm.graph_block;
-    std::vector<double> key = {6.0, (double)blk, (double)ns};
-    for (int stg = 0; stg < BS_COUNT; ++stg) {
-        key.push_back((double)b->blocks[stg]);
-        key.push_back((double)b->smem[stg]);
+    if (b->mode == 1 && body > 0) {
+        // one cooperative launch per iteration; the grid barriers' state starts at zero
+        CTR_CUDA(cudaMemsetAsync(b->d_gb, 0, sizeof(GridBarrier), s));
+        for (int k = 0; k < body; ++k) {
+            if ((st = launch_batch_iteration(b->d_desc, b->d_prefix, ns, b->d_gb, b->spin_limit, b->persist_grid,
+                                             b->persist_smem, s)) != CTR_OK)
+                return st;
+            b->launches++;
+        }
+        GridBarrier g{};
+        CTR_CUDA(cudaMemcpyAsync(&g, b->d_gb, sizeof(g), cudaMemcpyDeviceToHost, s));
+        CTR_CUDA(cudaStreamSynchronize(s));
+        if (g.status != 0)
+            return fail(CTR_ETIMEOUT, "persistent batched iteration: a grid barrier's bounded wait ran out");
+    } else {
+        const int blk = prm.graph_block;
+        std::vector<double> key = {6.0, (double)blk, (double)ns};
+        for (int stg = 0; stg < BS_COUNT; ++stg) {
+            key.push_back((double)b->blocks[stg]);
+            key.push_back((double)b->smem[stg]);
+        }
+        if ((st = run_graphed_in(b->graphs, b->launches, body, blk, one_iteration, s, &key)) != CTR_OK) return st;
     }
-    if ((st = run_graphed_in(b->graphs, b->launches, body, blk, one_iteration, s, &key)) != CTR_OK) return st;
     for (int i = 0; i < ns; ++i) {
         ctr_plan *p = b->plans[i];
         const unsigned long long l0 = p->launches;
@@ -1648,7 +1666,15 @@ ctr_status batch_prepare(ctr_batch *b)
     CTR_CUDA(cudaMemcpy(b->d_prefix, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     ctr_status st = configure_batch_radon(b->smem[BS_BP], b->smem[BS_BP_SYM]);
     if (st == CTR_OK) st = configure_batch_fft(b->smem[BS_FFT_ROWS], b->smem[BS_FFT_COLS]);
-    return st;
+    if (st != CTR_OK) return st;
+    // the persistent form: every stage's shared memory in one launch, all CTAs resident
+    b->persist_smem = 0;
+    for (int stg = 0; stg < BS_COUNT; ++stg) b->persist_smem = std::max(b->persist_smem, b->smem[stg]);
+    int sms = 0;
+    CTR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->persist_grid = persist_blocks_per_sm(b->persist_smem) * sms;
+    if (b->persist_grid <= 0 && b->mode == 1) b->mode = 0;
+    return CTR_OK;
 }
 
 #define CTR_INST(T)                                                                                                 \

@@ -68,7 +68,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "ctr_batch_launch_count", "tv_pd_solve_batched", "tv_pd_solve_state", "tv_pd_vjp_step",
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
            "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment", "ctr_plan_history",
-           "ctr_fp32_fma_rate"]
+           "ctr_fp32_fma_rate", "ctr_batch_set_mode", "ctr_batch_get_mode", "ctr_batch_persistent_ctas"]
 
 
 def load(path: str = LIB_PATH):
@@ -144,6 +144,12 @@ def load(path: str = LIB_PATH):
                                           ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.ctr_plan_history.argtypes = [vp, P(Diag), ctypes.c_int, P(ctypes.c_int)]
         lib.ctr_plan_history.restype = ctypes.c_int
+        lib.ctr_batch_set_mode.argtypes = [vp, ctypes.c_int, ctypes.c_ulonglong]
+        lib.ctr_batch_set_mode.restype = ctypes.c_int
+        lib.ctr_batch_get_mode.argtypes = [vp]
+        lib.ctr_batch_get_mode.restype = ctypes.c_int
+        lib.ctr_batch_persistent_ctas.argtypes = [vp]
+        lib.ctr_batch_persistent_ctas.restype = ctypes.c_int
         lib.ctr_fp32_fma_rate.argtypes = [P(ctypes.c_double), vp]
         lib.ctr_fp32_fma_rate.restype = ctypes.c_int
         lib.ctr_grad.argtypes = [vp, vp, vp, vp]
@@ -585,6 +591,18 @@ class Batch:
 
     def retune(self):
         _check(load().ctr_batch_retune(self._h))
+
+    @property
+    def mode(self) -> int:
+        """0: one launch per stage (graph-captured); 1: one persistent cooperative launch per iteration."""
+        return int(load().ctr_batch_get_mode(self._h))
+
+    @property
+    def persistent_ctas(self) -> int:
+        return int(load().ctr_batch_persistent_ctas(self._h))
+
+    def set_mode(self, mode: int, spin_limit: int = 1 << 26):
+        _check(load().ctr_batch_set_mode(self._h, int(mode), int(spin_limit)))
 
     def solve(self, fs, masks, alphas, deltas, iters: int, params: Optional[Params] = None, betas=None, cs=None,
               u_outs=None, want_diag: bool = True, stream=None):

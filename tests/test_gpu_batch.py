@@ -165,3 +165,60 @@ def test_batch_alg5(ct):
         ref = oracle.pdrq5_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, iters, sigma=1.0,
                                  tau=1 / np.sqrt(8), eps=np.pi / p.n, beta=d1["beta"], c=d1["c"])
         assert rel_l2(to_np(us[i]), ref.u) < 1e-5, i
+
+
+def test_persistent_iteration_matches_staged_form(ct):
+    """mode 1 (one persistent cooperative launch per iteration, stages separated by grid
+    barriers) gives the same slices as mode 0 (one launch per stage) and the oracle; one
+    launch per iteration."""
+    import torch
+    probs = _slices()
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    assert batch.mode == 0 and batch.persistent_ctas > 0
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    betas, cs = [], []
+    for p in probs:
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        b = oracle.power_beta(geo, 30)
+        betas.append(b)
+        cs.append(oracle.power_c(geo, b, np.pi / p.n, 30))
+    iters = 25
+    al, de = [p.alpha for p in probs], [p.delta for p in probs]
+    u0, d0 = batch.solve(fs, ms, al, de, iters, params=ct.default_params(graph_block=8), betas=betas, cs=cs)
+    batch.set_mode(1)
+    l0 = batch.launch_count
+    u1, d1 = batch.solve(fs, ms, al, de, iters, params=ct.default_params(graph_block=8), betas=betas, cs=cs)
+    assert batch.mode == 1
+    for i, p in enumerate(probs):
+        assert rel_l2(to_np(u1[i]), to_np(u0[i])) < 2e-6, i
+        assert d1[i]["objective"] == pytest.approx(d0[i]["objective"], rel=1e-5)
+        geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+        ref = oracle.pdrq_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, iters, sigma=1.0,
+                                tau=1 / np.sqrt(8), eps=np.pi / p.n, beta=betas[i], c=cs[i])
+        assert rel_l2(to_np(u1[i]), ref.u) < 1e-5, i
+    batch.set_mode(0)
+    assert batch.mode == 0
+
+
+def test_persistent_grid_barrier_gives_up(ct):
+    """With a spin limit of 0 every grid barrier gives up at once: the launch ends early,
+    the status word is set and the solve reports CTR_ETIMEOUT; the next solve (normal
+    limit) is unaffected."""
+    import torch
+    probs = _slices()[:3]
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [to_dev(p.f, torch.float32) for p in probs]
+    al, de = [p.alpha for p in probs], [p.delta for p in probs]
+    kw = dict(params=ct.default_params(), betas=[30.0] * 3, cs=[1.0] * 3)
+    ref, _ = batch.solve(fs, None, al, de, 6, **kw)
+    batch.set_mode(1, spin_limit=0)
+    with pytest.raises(ct.CtrError) as e:
+        batch.solve(fs, None, al, de, 6, **kw)
+    assert e.value.status == -4
+    batch.set_mode(1)
+    got, _ = batch.solve(fs, None, al, de, 6, **kw)
+    for a, b in zip(got, ref):
+        assert rel_l2(to_np(a), to_np(b)) < 2e-6
+    with pytest.raises(ct.CtrError):
+        batch.set_mode(2)
