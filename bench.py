@@ -331,6 +331,20 @@ def measure_batched(iters: int = 30, count: int = 64):
     torch.cuda.synchronize()
     t_batch = a.elapsed_time(b) / 1e3
     launches = batch.launch_count - l0
+    persistent = None
+    if batch.persistent_ctas > 0:                   # the same solve as one persistent launch per iteration
+        batch.set_mode(1)
+        batch.solve(fs, ms, al, de, 3, params=prm, betas=betas, cs=cs, want_diag=False)
+        torch.cuda.synchronize()
+        l1 = batch.launch_count
+        a.record()
+        batch.solve(fs, ms, al, de, iters, params=prm, betas=betas, cs=cs, want_diag=False)
+        b.record()
+        torch.cuda.synchronize()
+        t_p = a.elapsed_time(b) / 1e3
+        persistent = {"slice_iters_per_s": count * iters / t_p, "ctas": batch.persistent_ctas,
+                      "kernel_launches": batch.launch_count - l1, "vs_staged": t_batch / t_p}
+        batch.set_mode(0)
     us = [torch.empty((p.n, p.n), dtype=torch.float32, device="cuda") for p in probs]
     plans = [ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta) for p in probs]
     for pl, bp in zip(plans, batch.plans):
@@ -349,7 +363,7 @@ def measure_batched(iters: int = 30, count: int = 64):
             "batched": {"slice_iters_per_s": count * iters / t_batch, "gsamples_per_s": samples / t_batch / 1e9,
                         "kernel_launches": launches},
             "sequential": {"slice_iters_per_s": count * iters / t_seq, "gsamples_per_s": samples / t_seq / 1e9},
-            "speedup": t_seq / t_batch,
+            "speedup": t_seq / t_batch, "persistent": persistent,
             "workload": "64 slices, n in {256,384,512,768,1024}, 180-1440 views, ceil(sqrt(2) n) bins, FP32"}
 
 

@@ -34,11 +34,11 @@ ctr_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 // The dynamic shared-memory limit is an attribute of the kernel function for the
-// whole process, shared by every plan: only ever raise it.
+// whole process, shared by every plan: only ever raise it.  (Its default is 48 KB minus
+// the kernel's static shared memory, so the check is against the attribute itself.)
 template <typename K>
 inline ctr_status raise_smem_limit(K *kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return CTR_OK;
     cudaFuncAttributes a;
     CTR_CUDA(cudaFuncGetAttributes(&a, (const void *)kernel));
     if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return CTR_OK;
