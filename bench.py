@@ -432,6 +432,9 @@ def main():
     f = torch.as_tensor(pr.f, dtype=torch.float32, device="cuda")
     mask = torch.as_tensor(pr.mask, device="cuda")
     u = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    from paper_1810_03275_gb300 import autotune
+    tune_groups = autotune.tune_plan(plan, reps=5, use_cache=False)     # the project's tuner, untimed
+    tuned = {"bp_groups": tune_groups, "fwd_segments": plan.fwd_segments}
     prm = ct.default_params()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
@@ -534,7 +537,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "views": N, "bins": M, "iters_per_solve": iters,
                        "step": "one tv_pd_solve: power iterations (50+50) + iterations + diagnostics",
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
+                       "tuned": tuned},
             "gsamples_per_s": ws * samples / t_step / 1e9,
             "roofline": roof,
             "kernels": kernels,

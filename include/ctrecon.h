@@ -352,6 +352,13 @@ ctr_status tv_pd_vjp_segment(ctr_plan *plan, const void *f_dev, const uint8_t *m
 ctr_status ctr_plan_set_bp_groups(ctr_plan *plan, int groups);
 int ctr_plan_get_bp_groups(const ctr_plan *plan);
 
+/* Tuning hook: the number of warps (2, 4 or 8; default 4) that split the rows a job's rays
+ * cross in the symmetric forward projector (one CTA per job and 31 bins; the warps' sums
+ * are added in a fixed order, so the choice changes FP32 summation order only).
+ * CTR_EUNSUPPORTED off the symmetric path; ctr_plan_get_fwd_segments returns 0 there. */
+ctr_status ctr_plan_set_fwd_segments(ctr_plan *plan, int segments);
+int ctr_plan_get_fwd_segments(const ctr_plan *plan);
+
 
 /* Batches: many independent slices (each its own geometry, image size and view
  * count), FP32, solved together.  Each stage of an iteration of Alg. 4 is ONE kernel

@@ -1,12 +1,15 @@
-"""Project-written autotuner for the backprojection's angle split.
+"""Project-written autotuner for the projectors' launch shapes.
 
-The pixel-driven R_h^* runs one CTA per (32 x 32 tile, angle group); splitting the
-angles into G groups (partial images summed by a small epilogue kernel) trades an
-extra pass for more CTAs in flight.  The best G depends on the image size, the view
-count and, in a batch, on the other slices.  The tuner times the candidates with
-CUDA events through the C ABI and keeps the fastest; results are cached in a JSON
-file keyed by (device, n, views, bins) for single plans and by the batch signature
-for batches.  Tuning never changes results beyond FP32 summation order.
+Two runtime choices per plan, both selecting among compiled kernel instances through
+the C ABI (results change only in FP32 summation order):
+  * the backprojection's angle (or symmetric-job) split into G groups whose partial
+    images are summed: more CTAs in flight against an extra fold;
+  * the number of warps (2, 4 or 8) that split the rows a job's rays cross in the
+    symmetric forward projector: shorter serial marches against a larger reduction.
+The best values depend on the image size and view count and, in a batch, on the other
+slices.  The tuner times the candidates with CUDA events and keeps the fastest;
+results are cached in a JSON file keyed by (device, n, views, bins) for single plans and
+by the batch signature for batches.
 """
 from __future__ import annotations
 
@@ -61,16 +64,21 @@ def _time(fn, reps: int) -> float:
     return a.elapsed_time(b) / reps
 
 
-def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int = 5, use_cache: bool = True) -> int:
-    """Pick the angle-group count of `plan`'s backprojection; sets and returns it."""
+def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int = 5, use_cache: bool = True,
+              segments: Iterable[int] = (2, 4, 8)) -> int:
+    """Pick the angle-group count of `plan`'s backprojection and, on the symmetric path,
+    the forward projector's row segments; sets both and returns the group count."""
     import torch
     key = f"plan/{_device_key()}/{plan.dtype}/n{plan.n}/N{plan.n_angles}/M{plan.n_bins}"
     if use_cache:
         hit = _load_cache().get(key)
         if hit is not None:
             try:
-                plan.set_bp_groups(int(hit))
-                return int(hit)
+                hit = hit if isinstance(hit, dict) else {"bp_groups": int(hit)}
+                plan.set_bp_groups(int(hit["bp_groups"]))
+                if hit.get("fwd_segments") and plan.fwd_segments:
+                    plan.set_fwd_segments(int(hit["fwd_segments"]))
+                return int(hit["bp_groups"])
             except Exception:
                 pass
     g = torch.randn((plan.n_angles, plan.n_bins), device="cuda").to(plan.op_dtype)
@@ -85,7 +93,20 @@ def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int
         if best_t is None or t < best_t:
             best, best_t = G, t
     plan.set_bp_groups(best)
-    _store(key, best)
+    choice = {"bp_groups": best}
+    if plan.fwd_segments:
+        x = torch.randn((plan.n, plan.n), device="cuda").to(plan.op_dtype)
+        xt = x.t().contiguous()
+        gs = torch.empty((plan.n_angles, plan.n_bins), device="cuda", dtype=plan.torch_dtype)
+        best_s, best_st = plan.fwd_segments, None
+        for sg in segments:
+            plan.set_fwd_segments(sg)
+            t = _time(lambda: plan.rh_forward_t(x, xt, gs), reps)
+            if best_st is None or t < best_st:
+                best_s, best_st = sg, t
+        plan.set_fwd_segments(best_s)
+        choice["fwd_segments"] = best_s
+    _store(key, choice)
     return best
 
 

@@ -933,6 +933,17 @@ ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, do
     return p->dtype == CTR_F64 ? run(double{}) : run(float{});
 }
 
+ctr_status ctr_plan_set_fwd_segments(ctr_plan *p, int segs)
+{
+    if (!p) return fail(CTR_EINVAL, "plan is NULL");
+    if (segs != 2 && segs != 4 && segs != 8) return fail(CTR_EINVAL, "segments must be 2, 4 or 8");
+    if (!p->orbit) return fail(CTR_EUNSUPPORTED, "the plan projects angle by angle (no symmetric forward projector)");
+    p->fwd_segs = segs;
+    return CTR_OK;
+}
+
+int ctr_plan_get_fwd_segments(const ctr_plan *p) { return p && p->orbit ? p->fwd_segs : 0; }
+
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)
 {
     if (!p) return fail(CTR_EINVAL, "plan is NULL");

@@ -745,7 +745,7 @@ constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 // Warp w of the CTA takes job by*ORBIT_SLOTS + w % ORBIT_SLOTS, bins bx*31 + [0, 31) and
 // the (w / ORBIT_SLOTS)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
-template <typename S, bool NAMED = false>
+template <typename S, bool NAMED = false, int SEGS = ORBIT_SEGS>
 __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
                                                    int n_jobs, int M, const OrbitJob *__restrict__ jobs,
                                                    const ForwardEpi<float> &epi, int bx, int by)
@@ -772,8 +772,8 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
             rows_in<false>(Q0, am.binv, 0.5f, (float)n - 3.5f, n, ilo, ihi);
             int ilo_w = max(__reduce_max_sync(0xffffffffu, ilo), mlo_w);
             int ihi_w = min(__reduce_min_sync(0xffffffffu, ihi), mhi_w);
-            if (ORBIT_SEGS > 1) {                     // this warp's part of the rows
-                const int per = (mhi_w - mlo_w + ORBIT_SEGS) / ORBIT_SEGS;
+            if (SEGS > 1) {                     // this warp's part of the rows
+                const int per = (mhi_w - mlo_w + SEGS) / SEGS;
                 const int a = mlo_w + seg * per, b = min(mhi_w, a + per - 1);
                 mlo_w = a;
                 mhi_w = b;
@@ -787,8 +787,8 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
             }
         }
     }
-    if constexpr (ORBIT_SEGS > 1) {
-        __shared__ float4 s_part[ORBIT_SEGS > 1 ? ORBIT_SEGS - 1 : 1][2][ORBIT_SLOTS][32];
+    if constexpr (SEGS > 1) {
+        __shared__ float4 s_part[SEGS > 1 ? SEGS - 1 : 1][2][ORBIT_SLOTS][32];
         if (seg > 0) {
             s_part[seg - 1][0][slot][lane] = Su;
             s_part[seg - 1][1][slot][lane] = Sf;
@@ -796,7 +796,7 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
         body_sync<NAMED>();
         if (seg > 0) return;
 #pragma unroll
-        for (int z = 0; z < ORBIT_SEGS - 1; ++z) {
+        for (int z = 0; z < SEGS - 1; ++z) {
             const float4 a = s_part[z][0][slot][lane], b = s_part[z][1][slot][lane];
             Su.x += a.x; Su.y += a.y; Su.z += a.z; Su.w += a.w;
             Sf.x += b.x; Sf.y += b.y; Sf.z += b.z; Sf.w += b.w;
@@ -809,12 +809,26 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
     orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
 }
 
-template <typename S>
-__global__ void __launch_bounds__(ORBIT_THREADS, CTR_ORBIT_MINB)
+// SEGS warps split a job's rows (selected per plan: ctr_plan_set_fwd_segments); the
+// resident-CTA hint keeps 32 warps per SM for every choice.
+template <typename S, int SEGS>
+__global__ void __launch_bounds__(32 * ORBIT_SLOTS * SEGS, CTR_ORBIT_MINB * ORBIT_SEGS / SEGS)
 k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
                 const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
 {
-    forward_orbit_body<S>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+    forward_orbit_body<S, false, SEGS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+}
+
+template <typename S>
+void launch_forward_orbit(const ctr_plan *p, const typename OrbitRec<S>::type *ub, const ForwardEpi<float> &epi,
+                          cudaStream_t s)
+{
+    const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS);
+    switch (p->fwd_segs) {
+    case 2: k_forward_orbit<S, 2><<<grid, 32 * ORBIT_SLOTS * 2, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
+    case 8: k_forward_orbit<S, 8><<<grid, 32 * ORBIT_SLOTS * 8, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
+    default: k_forward_orbit<S, 4><<<grid, 32 * ORBIT_SLOTS * 4, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1242,9 +1256,7 @@ ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi
             }
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
-            k_forward_orbit<S><<<dim3(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS), ORBIT_THREADS,
-                                 0, s>>>(
-                ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
+            launch_forward_orbit<S>(p, ub, epi, s);
             CTR_CHECK_LAUNCH("k_forward_orbit");
             return CTR_OK;
         }

@@ -222,3 +222,38 @@ def test_persistent_grid_barrier_gives_up(ct):
         assert rel_l2(to_np(a), to_np(b)) < 2e-6
     with pytest.raises(ct.CtrError):
         batch.set_mode(2)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_forward_segment_variants_agree(ct, dtype):
+    """The symmetric forward projector's row-segment count (2, 4, 8 warps per job) is a
+    runtime choice among compiled instances: every choice matches the oracle, and the
+    autotuner sets one of them."""
+    import torch
+    n, N, M = 96, 120, 137
+    plan = ct.Plan(n, N, M, dtype=dtype)
+    assert plan.fwd_segments == 4
+    u = torch.randn((n, n), device="cuda").to(plan.op_dtype)
+    ref = oracle.rh_forward(u.double().cpu().numpy(), oracle.Geometry(n, N, M))
+    outs = {}
+    for sg in (2, 4, 8):
+        plan.set_fwd_segments(sg)
+        outs[sg] = to_np(plan.rh_forward(u))
+        assert rel_l2(outs[sg], ref) < 1e-5, sg
+    assert rel_l2(outs[2], outs[8]) < 2e-6
+    with pytest.raises(ct.CtrError):
+        plan.set_fwd_segments(3)
+    with pytest.raises(ct.CtrError):
+        ct.Plan(n, N, M, dtype="f64").set_fwd_segments(2)
+
+
+def test_autotuner_picks_forward_segments(ct, tmp_path, monkeypatch):
+    from paper_1810_03275_gb300 import autotune
+    monkeypatch.setenv("CTR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    plan = ct.Plan(256, 180, 363)
+    autotune.tune_plan(plan, reps=2)
+    assert plan.fwd_segments in (2, 4, 8)
+    seg = plan.fwd_segments
+    other = ct.Plan(256, 180, 363)
+    autotune.tune_plan(other, reps=2)                    # from the cache
+    assert other.fwd_segments == seg
