@@ -367,6 +367,29 @@ def measure_batched(iters: int = 30, count: int = 64):
             "workload": "64 slices, n in {256,384,512,768,1024}, 180-1440 views, ceil(sqrt(2) n) bins, FP32"}
 
 
+def run_ops(args):
+    """The two operator calls of one plan, `--steps` times each after `--warmup` (a profiler's
+    target: seeded uniform inputs, uniform angles over [0, pi))."""
+    import torch
+    from paper_1810_03275_gb300 import ctrecon as ct
+    n, N, M, dt = args.ops.split(",")
+    n, N, M = int(n), int(N), int(M)
+    plan = ct.Plan(n, N, M, dtype=dt)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    u = torch.rand((n, n), device="cuda", generator=gen).to(plan.op_dtype)
+    uT = u.t().contiguous()
+    g = torch.rand((N, M), device="cuda", generator=gen).to(plan.op_dtype)
+    go = torch.empty((N, M), device="cuda", dtype=plan.torch_dtype)
+    uo = torch.empty((n, n), device="cuda", dtype=plan.torch_dtype)
+    for k in range(args.warmup + args.steps):
+        torch.cuda.nvtx.range_push("ops_step" if k >= args.warmup else "ops_warmup")
+        plan.rh_forward_t(u, uT, go)
+        plan.rh_adjoint(g, uo)
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    return 0
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
@@ -412,7 +435,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16-vs-FP32 2048^2 timing")
+    ap.add_argument("--ops", default=None, help="n,views,bins,dtype: only run R_h and R_h^* of that plan --steps "
+                    "times (for a profiler), print nothing")
     args = ap.parse_args()
+    if args.ops:
+        return run_ops(args)
     if args.warmup < 3 and args.impl == "ours" and args.iters is None:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     rank, ws, local = dist_init()
@@ -453,9 +480,11 @@ def main():
     diag = None
     for k in range(args.steps):
         flush.fill_(float(k))                       # evict L2 between steps
+        torch.cuda.nvtx.range_push("bench_step")
         ev[k][0].record(stream)
         _, diag = plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, iters, params=prm, u_out=u)
         ev[k][1].record(stream)
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(ws)
     launches = (plan.launch_count - launches0) / args.steps

@@ -585,6 +585,7 @@ void ctr_plan_destroy(ctr_plan *p)
 
 ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
 {
+    CTR_NVTX("rh_forward");
     CTR_GUARD(p);
     if (!u || !g) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -607,6 +608,7 @@ ctr_status rh_forward(ctr_plan *p, const void *u, void *g, void *stream)
 ctr_status ctr_metal_trace(ctr_plan *p, const void *u, double threshold, int radius, double proj_tol,
                            uint8_t *marked, uint8_t *trace, void *stream)
 {
+    CTR_NVTX("ctr_metal_trace");
     CTR_GUARD(p);
     if (!u || !trace) return fail(CTR_EINVAL, "u and trace must not be NULL");
     if (!std::isfinite(threshold)) return fail(CTR_EINVAL, "threshold must be finite");
@@ -619,6 +621,7 @@ ctr_status ctr_metal_trace(ctr_plan *p, const void *u, double threshold, int rad
 
 ctr_status ctr_ramp_filter(ctr_plan *p, const void *g, void *y, void *stream)
 {
+    CTR_NVTX("ctr_ramp_filter");
     CTR_GUARD(p);
     if (!g || !y) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -628,6 +631,7 @@ ctr_status ctr_ramp_filter(ctr_plan *p, const void *g, void *y, void *stream)
 
 ctr_status ctr_fbp(ctr_plan *p, const void *g, void *u, void *stream)
 {
+    CTR_NVTX("ctr_fbp");
     CTR_GUARD(p);
     if (!g || !u) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -647,6 +651,7 @@ ctr_status ctr_fbp(ctr_plan *p, const void *g, void *u, void *stream)
 
 ctr_status rh_forward_t(ctr_plan *p, const void *u, const void *uT, void *g, void *stream)
 {
+    CTR_NVTX("rh_forward_t");
     CTR_GUARD(p);
     if (!u || !uT || !g) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -660,6 +665,7 @@ int ctr_plan_symmetric_jobs(const ctr_plan *p) { return p && p->orbit ? p->n_job
 
 ctr_status rh_adjoint(ctr_plan *p, const void *g, void *u, void *stream)
 {
+    CTR_NVTX("rh_adjoint");
     CTR_GUARD(p);
     if (!u || !g) return fail(CTR_EINVAL, "null buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -670,6 +676,7 @@ ctr_status rh_adjoint(ctr_plan *p, const void *g, void *u, void *stream)
 
 ctr_status precond_apply(ctr_plan *p, const ctr_params *prm, const void *y, void *x, void *stream)
 {
+    CTR_NVTX("precond_apply");
     CTR_GUARD(p);
     if (!prm || !y || !x) return fail(CTR_EINVAL, "null argument");
     ctr_params q = resolve(p, prm);
@@ -704,6 +711,7 @@ ctr_status tv_cp_solve(ctr_plan *p, const void *f, const uint8_t *mask, double a
                        double sigma_p, double tau_d, const ctr_params *prm, void *u_out, ctr_diag *diag,
                        void *stream)
 {
+    CTR_NVTX("tv_cp_solve");
     CTR_GUARD(p);
     if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
     if (std::isnan(delta) || std::isnan(sigma_p) || std::isnan(tau_d)) return fail(CTR_EINVAL, "NaN argument");
@@ -722,6 +730,7 @@ ctr_status tv_cp_solve(ctr_plan *p, const void *f, const uint8_t *mask, double a
 ctr_status tv_pd_solve(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,
                        const ctr_params *prm, void *u_out, ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_pd_solve");
     CTR_GUARD(p);
     if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
     if (std::isnan(delta)) return fail(CTR_EINVAL, "delta is NaN");
@@ -736,6 +745,7 @@ ctr_status tv_pd_solve(ctr_plan *p, const void *f, const uint8_t *mask, double a
 ctr_status tv_pdrq2_solve(ctr_plan *p, const void *f, double alpha, int iters, const ctr_params *prm, void *u_out,
                           ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_pdrq2_solve");
     CTR_GUARD(p);
     if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
     ctr_params q = resolve(p, prm);
@@ -756,6 +766,7 @@ ctr_status tv_pdrq2_solve(ctr_plan *p, const void *f, double alpha, int iters, c
 ctr_status tv_admm_solve(ctr_plan *p, const void *f, double alpha, int iters, double mu, int cg_iters,
                          const ctr_params *prm, void *u_out, ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_admm_solve");
     CTR_GUARD(p);
     if (!f || !u_out) return fail(CTR_EINVAL, "f and u_out must not be NULL");
     if (!(mu > 0) || !std::isfinite(mu)) return fail(CTR_EINVAL, "mu must be finite and > 0");
@@ -804,6 +815,7 @@ ctr_status tv_mar_solve(ctr_plan *p, const void *f, double alpha, double delta, 
                         double proj_tol, int iters_pre, int iters, const ctr_params *prm, uint8_t *trace_out,
                         void *u_out, ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_mar_solve");
     CTR_GUARD(p);
     if (!f || !u_out || !trace_out) return fail(CTR_EINVAL, "f, trace_out and u_out must not be NULL");
     if (iters_pre < 1) return fail(CTR_EINVAL, "iters_pre must be >= 1");
@@ -822,6 +834,7 @@ ctr_status tv_mar_solve(ctr_plan *p, const void *f, double alpha, double delta, 
 ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, const void *hi, double alpha, int iters,
                      const ctr_params *prm, ctr_state *state, void *u_out, ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_pd_run");
     CTR_GUARD(p);
     if (!w || !a || !lo || !hi) return fail(CTR_EINVAL, "data-term arrays must not be NULL");
     if (!state && !u_out) return fail(CTR_EINVAL, "state and u_out are both NULL");
@@ -838,6 +851,7 @@ ctr_status tv_pd_run(ctr_plan *p, const void *w, const void *a, const void *lo, 
 ctr_status tv_pd_solve_state(ctr_plan *p, const void *f, const uint8_t *mask, double alpha, double delta, int iters,
                              const ctr_params *prm, ctr_state *state, ctr_diag *diag, void *stream)
 {
+    CTR_NVTX("tv_pd_solve_state");
     CTR_GUARD(p);
     if (!f || !state || !state->u || !state->Ru || !state->v1b || !state->v2b)
         return fail(CTR_EINVAL, "f and every state buffer must be given");
@@ -856,6 +870,7 @@ ctr_status tv_pd_vjp_step(ctr_plan *p, const void *f, const uint8_t *mask, doubl
                           const ctr_params *prm, const ctr_state *s0, const ctr_state *s1, void *bu, void *b1,
                           void *b2, void *gf, double *galpha_dev, void *stream)
 {
+    CTR_NVTX("tv_pd_vjp_step");
     CTR_GUARD(p);
     if (!f || !s0 || !s1 || !bu || !b1 || !b2 || !gf || !galpha_dev) return fail(CTR_EINVAL, "null argument");
     if (!s0->u || !s0->v1b || !s0->v2b || !s1->u || !s1->Ru) return fail(CTR_EINVAL, "state buffer missing");
@@ -883,6 +898,7 @@ ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, do
                              const ctr_params *prm, const ctr_state *s_start, int length, void *workspace, void *bu,
                              void *b1, void *b2, void *gf, double *galpha_dev, void *stream)
 {
+    CTR_NVTX("tv_pd_vjp_segment");
     CTR_GUARD(p);
     if (!f || !s_start || !workspace || !bu || !b1 || !b2 || !gf || !galpha_dev) return fail(CTR_EINVAL, "null argument");
     if (!s_start->u || !s_start->Ru || !s_start->v1b || !s_start->v2b) return fail(CTR_EINVAL, "state buffer missing");
@@ -1049,6 +1065,7 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
                                const double *betas, const double *cs, void *const *u_outs, ctr_diag *diags,
                                void *stream)
 {
+    CTR_NVTX("tv_pd_solve_batched");
     if (!b) return fail(CTR_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
     if (!dg.ok) return fail(CTR_ECUDA, "cannot select the batch's device");
@@ -1079,6 +1096,7 @@ ctr_status tv_pd_solve_batched(ctr_batch *b, const void *const *f_devs, const ui
 
 ctr_status ctr_power_beta(ctr_plan *p, int iters, double *beta_out, void *stream)
 {
+    CTR_NVTX("ctr_power_beta");
     CTR_GUARD(p);
     if (!beta_out || iters < 1) return fail(CTR_EINVAL, "beta_out NULL or iters < 1");
     StreamJoin sj(p, stream);
@@ -1089,6 +1107,7 @@ ctr_status ctr_power_beta(ctr_plan *p, int iters, double *beta_out, void *stream
 
 ctr_status ctr_power_lambda(ctr_plan *p, double beta, double eps, int iters, double *lam, void *stream)
 {
+    CTR_NVTX("ctr_power_lambda");
     CTR_GUARD(p);
     if (!lam || iters < 1 || !(beta > 0) || !(eps > 0)) return fail(CTR_EINVAL, "bad argument");
     if (!p->fft_ok) return fail(CTR_EUNSUPPORTED, "image size n must be of the form 2^a 3^b for the Fourier preconditioner");

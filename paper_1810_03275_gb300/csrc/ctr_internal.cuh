@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -26,6 +27,18 @@ ctr_status cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                    \
         if (e_ != cudaSuccess) return ::ctr::cuda_fail(e_, #call);  \
     } while (0)
+
+// A named NVTX range over the enclosing scope (profilers group the kernels of each ABI
+// call and solver phase by it; without a tool attached it costs a function call).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+#define CTR_NVTX_CAT2(a, b) a##b
+#define CTR_NVTX_CAT(a, b) CTR_NVTX_CAT2(a, b)
+#define CTR_NVTX(name) ::ctr::NvtxScope CTR_NVTX_CAT(nvtx_scope_, __LINE__)(name)
 
 #define CTR_CHECK_LAUNCH(what)                                      \
     do {                                                            \

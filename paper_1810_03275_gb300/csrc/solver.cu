@@ -545,6 +545,7 @@ constexpr int POWER_GRAPH_BLOCK = CTR_POWER_GRAPH_BLOCK;   // power-iteration st
 template <typename T>
 ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
 {
+    CTR_NVTX("power iteration beta");
     const size_t nn = (size_t)p->n * p->n;
     T *x = (T *)p->x, *xt = (T *)p->xt, *y = (T *)p->du, *g = (T *)p->gs;
     p->launches++;
@@ -581,6 +582,7 @@ ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
 template <typename T>
 ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double *lam, cudaStream_t s)
 {
+    CTR_NVTX("power iteration c");
     const size_t nn = (size_t)p->n * p->n;
     T *z = (T *)p->x, *x = (T *)p->u, *xt = (T *)p->xt, *yp = (T *)p->du, *y = (T *)p->t2, *g = (T *)p->gs;
     ctr_status st;
@@ -1172,6 +1174,7 @@ template <typename T>
 ctr_status pdrq_loop(ctr_plan *p, double alpha, int iters, const ctr_params &prm, double beta, double c,
                      ctr_diag *diag, cudaStream_t s)
 {
+    CTR_NVTX("iterations");
     const int n = p->n;
     const size_t nn = (size_t)n * n, nm = (size_t)p->N * p->M;
     IterArgs<T> a;
