@@ -281,6 +281,8 @@ def measure_forms(iters: int = 30, fma_peak: float = 4.03e13):
     beta = c = None
     for dt in ("f32", "bf16"):
         plan = ct.Plan(pr.n, pr.n_angles, pr.n_bins, angles=pr.theta, dtype=dt)
+        from paper_1810_03275_gb300 import autotune
+        autotune.tune_plan(plan, reps=3, use_cache=False)           # the project's tuner, untimed
         if beta is None:
             beta = plan.power_beta(20)
             c = 1.05 * plan.power_lambda(beta, np.pi / pr.n, 20)
@@ -294,7 +296,8 @@ def measure_forms(iters: int = 30, fma_peak: float = 4.03e13):
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 1e3
         out[dt] = {"iters_per_s": iters / t, "gsamples_per_s": 2.0 * pr.n * pr.n * pr.n_angles * iters / t / 1e9,
-                   "operators": operator_roofline(plan, pr, fma_peak)}
+                   "operators": operator_roofline(plan, pr, fma_peak),
+                   "tuned": {"bp_groups": plan.bp_groups, "fwd_shape_jobs_segments": list(plan.fwd_shape)}}
         del plan
         torch.cuda.empty_cache()
     out["bf16_speedup"] = out["bf16"]["iters_per_s"] / out["f32"]["iters_per_s"]
@@ -461,7 +464,7 @@ def main():
     u = torch.empty((n, n), dtype=torch.float32, device="cuda")
     from paper_1810_03275_gb300 import autotune
     tune_groups = autotune.tune_plan(plan, reps=5, use_cache=False)     # the project's tuner, untimed
-    tuned = {"bp_groups": tune_groups, "fwd_segments": plan.fwd_segments}
+    tuned = {"bp_groups": tune_groups, "fwd_shape_jobs_segments": list(plan.fwd_shape)}
     prm = ct.default_params()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()

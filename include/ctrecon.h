@@ -352,12 +352,15 @@ ctr_status tv_pd_vjp_segment(ctr_plan *plan, const void *f_dev, const uint8_t *m
 ctr_status ctr_plan_set_bp_groups(ctr_plan *plan, int groups);
 int ctr_plan_get_bp_groups(const ctr_plan *plan);
 
-/* Tuning hook: the number of warps (2, 4 or 8; default 4) that split the rows a job's rays
- * cross in the symmetric forward projector (one CTA per job and 31 bins; the warps' sums
- * are added in a fixed order, so the choice changes FP32 summation order only).
- * CTR_EUNSUPPORTED off the symmetric path; ctr_plan_get_fwd_segments returns 0 there. */
-ctr_status ctr_plan_set_fwd_segments(ctr_plan *plan, int segments);
-int ctr_plan_get_fwd_segments(const ctr_plan *plan);
+/* Tuning hook: the launch shape of the symmetric forward projector, one of the compiled
+ * instances (jobs_per_cta, segments) = (1, 2), (1, 4) [default], (1, 8), (2, 2), (2, 4),
+ * (4, 2).  A CTA takes jobs_per_cta adjacent jobs (nearly coincident rays: they share the
+ * orbit image's lines in L1) and 31 bins; `segments` warps split the rows each job's rays
+ * cross, and their sums are added in a fixed order.  The shape changes FP32 summation order
+ * only.  CTR_EINVAL for other shapes, CTR_EUNSUPPORTED off the symmetric path;
+ * ctr_plan_get_fwd_shape reports (0, 0) there. */
+ctr_status ctr_plan_set_fwd_shape(ctr_plan *plan, int jobs_per_cta, int segments);
+ctr_status ctr_plan_get_fwd_shape(const ctr_plan *plan, int *jobs_per_cta, int *segments);
 
 
 /* Batches: many independent slices (each its own geometry, image size and view

@@ -4,8 +4,10 @@ Two runtime choices per plan, both selecting among compiled kernel instances thr
 the C ABI (results change only in FP32 summation order):
   * the backprojection's angle (or symmetric-job) split into G groups whose partial
     images are summed: more CTAs in flight against an extra fold;
-  * the number of warps (2, 4 or 8) that split the rows a job's rays cross in the
-    symmetric forward projector: shorter serial marches against a larger reduction.
+  * the symmetric forward projector's launch shape: adjacent jobs per CTA (their rays
+    nearly coincide, so they share the orbit image's lines in L1, which matters where the
+    kernel is bound by L2 bandwidth) and warps per job splitting its rows (shorter serial
+    marches against a larger reduction).
 The best values depend on the image size and view count and, in a batch, on the other
 slices.  The tuner times the candidates with CUDA events and keeps the fastest;
 results are cached in a JSON file keyed by (device, n, views, bins) for single plans and
@@ -65,9 +67,9 @@ def _time(fn, reps: int) -> float:
 
 
 def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int = 5, use_cache: bool = True,
-              segments: Iterable[int] = (2, 4, 8)) -> int:
+              shapes=None) -> int:
     """Pick the angle-group count of `plan`'s backprojection and, on the symmetric path,
-    the forward projector's row segments; sets both and returns the group count."""
+    the forward projector's launch shape; sets both and returns the group count."""
     import torch
     key = f"plan/{_device_key()}/{plan.dtype}/n{plan.n}/N{plan.n_angles}/M{plan.n_bins}"
     if use_cache:
@@ -76,8 +78,8 @@ def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int
             try:
                 hit = hit if isinstance(hit, dict) else {"bp_groups": int(hit)}
                 plan.set_bp_groups(int(hit["bp_groups"]))
-                if hit.get("fwd_segments") and plan.fwd_segments:
-                    plan.set_fwd_segments(int(hit["fwd_segments"]))
+                if hit.get("fwd_shape") and plan.fwd_shape[0]:
+                    plan.set_fwd_shape(*hit["fwd_shape"])
                 return int(hit["bp_groups"])
             except Exception:
                 pass
@@ -94,18 +96,18 @@ def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int
             best, best_t = G, t
     plan.set_bp_groups(best)
     choice = {"bp_groups": best}
-    if plan.fwd_segments:
+    if plan.fwd_shape[0]:
         x = torch.randn((plan.n, plan.n), device="cuda").to(plan.op_dtype)
         xt = x.t().contiguous()
         gs = torch.empty((plan.n_angles, plan.n_bins), device="cuda", dtype=plan.torch_dtype)
-        best_s, best_st = plan.fwd_segments, None
-        for sg in segments:
-            plan.set_fwd_segments(sg)
+        best_s, best_st = plan.fwd_shape, None
+        for shp in (shapes or plan.FWD_SHAPES):
+            plan.set_fwd_shape(*shp)
             t = _time(lambda: plan.rh_forward_t(x, xt, gs), reps)
             if best_st is None or t < best_st:
-                best_s, best_st = sg, t
-        plan.set_fwd_segments(best_s)
-        choice["fwd_segments"] = best_s
+                best_s, best_st = tuple(shp), t
+        plan.set_fwd_shape(*best_s)
+        choice["fwd_shape"] = list(best_s)
     _store(key, choice)
     return best
 

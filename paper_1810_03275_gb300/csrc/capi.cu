@@ -949,16 +949,26 @@ ctr_status tv_pd_vjp_segment(ctr_plan *p, const void *f, const uint8_t *mask, do
     return p->dtype == CTR_F64 ? run(double{}) : run(float{});
 }
 
-ctr_status ctr_plan_set_fwd_segments(ctr_plan *p, int segs)
+ctr_status ctr_plan_set_fwd_shape(ctr_plan *p, int jobs_per_cta, int segments)
 {
     if (!p) return fail(CTR_EINVAL, "plan is NULL");
-    if (segs != 2 && segs != 4 && segs != 8) return fail(CTR_EINVAL, "segments must be 2, 4 or 8");
+    const int key = jobs_per_cta * 16 + segments;
+    if (key != 1 * 16 + 2 && key != 1 * 16 + 4 && key != 1 * 16 + 8 && key != 2 * 16 + 2 && key != 2 * 16 + 4 &&
+        key != 4 * 16 + 2)
+        return fail(CTR_EINVAL, "forward shape must be (1, 2), (1, 4), (1, 8), (2, 2), (2, 4) or (4, 2)");
     if (!p->orbit) return fail(CTR_EUNSUPPORTED, "the plan projects angle by angle (no symmetric forward projector)");
-    p->fwd_segs = segs;
+    p->fwd_slots = jobs_per_cta;
+    p->fwd_segs = segments;
     return CTR_OK;
 }
 
-int ctr_plan_get_fwd_segments(const ctr_plan *p) { return p && p->orbit ? p->fwd_segs : 0; }
+ctr_status ctr_plan_get_fwd_shape(const ctr_plan *p, int *jobs_per_cta, int *segments)
+{
+    if (!p || !jobs_per_cta || !segments) return fail(CTR_EINVAL, "null argument");
+    *jobs_per_cta = p->orbit ? p->fwd_slots : 0;
+    *segments = p->orbit ? p->fwd_segs : 0;
+    return CTR_OK;
+}
 
 ctr_status ctr_plan_set_bp_groups(ctr_plan *p, int groups)
 {

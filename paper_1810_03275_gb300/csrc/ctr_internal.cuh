@@ -387,7 +387,8 @@ struct ctr_plan {
     int red_blocks = 0;
     cudaStream_t stream = nullptr;       // internal stream (graph capture)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    int fwd_segs = 4;                    // warps splitting a job's rows in the symmetric forward projector (2, 4, 8)
+    int fwd_slots = 1;                   // symmetric forward projector: adjacent jobs per CTA (1, 2, 4) ...
+    int fwd_segs = 4;                    // ... and warps splitting a job's rows (2, 4, 8); see ctr_plan_set_fwd_shape
     double *d_hist = nullptr;            // MAX_CHECKS x HIST_FIELDS diagnostics records
     int hist_count = 0;                  // records the last solve wrote
     ctr::GraphCache graphs;              // instantiated iteration graphs, reused across calls

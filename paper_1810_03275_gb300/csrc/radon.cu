@@ -745,15 +745,15 @@ constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 // Warp w of the CTA takes job by*ORBIT_SLOTS + w % ORBIT_SLOTS, bins bx*31 + [0, 31) and
 // the (w / ORBIT_SLOTS)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
-template <typename S, bool NAMED = false, int SEGS = ORBIT_SEGS>
+template <typename S, bool NAMED = false, int SEGS = ORBIT_SEGS, int SLOTS = ORBIT_SLOTS>
 __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
                                                    int n_jobs, int M, const OrbitJob *__restrict__ jobs,
                                                    const ForwardEpi<float> &epi, int bx, int by)
 {
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int slot = warp % ORBIT_SLOTS, seg = warp / ORBIT_SLOTS;
-    const int jb = by * ORBIT_SLOTS + slot;
+    const int slot = warp % SLOTS, seg = warp / SLOTS;
+    const int jb = by * SLOTS + slot;
     const int kb = bx * 31;
     const int k = kb + lane - 1;
     const bool active = jb < n_jobs && kb < M;        // warp-uniform
@@ -788,7 +788,7 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
         }
     }
     if constexpr (SEGS > 1) {
-        __shared__ float4 s_part[SEGS > 1 ? SEGS - 1 : 1][2][ORBIT_SLOTS][32];
+        __shared__ float4 s_part[SEGS > 1 ? SEGS - 1 : 1][2][SLOTS][32];
         if (seg > 0) {
             s_part[seg - 1][0][slot][lane] = Su;
             s_part[seg - 1][1][slot][lane] = Sf;
@@ -809,25 +809,36 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
     orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
 }
 
-// SEGS warps split a job's rows (selected per plan: ctr_plan_set_fwd_segments); the
-// resident-CTA hint keeps 32 warps per SM for every choice.
-template <typename S, int SEGS>
-__global__ void __launch_bounds__(32 * ORBIT_SLOTS * SEGS, CTR_ORBIT_MINB * ORBIT_SEGS / SEGS)
+// SLOTS adjacent jobs per CTA (their rays nearly coincide, so they share the orbit
+// image's lines in L1) and SEGS warps per job splitting its rows; the shape is selected per
+// plan (ctr_plan_set_fwd_shape).  The resident-CTA hint keeps 32 warps per SM.
+template <typename S, int SLOTS, int SEGS>
+__global__ void __launch_bounds__(32 * SLOTS * SEGS, CTR_ORBIT_MINB * ORBIT_SLOTS * ORBIT_SEGS / (SLOTS * SEGS))
 k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
                 const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
 {
-    forward_orbit_body<S, false, SEGS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+    forward_orbit_body<S, false, SEGS, SLOTS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+}
+
+template <typename S, int SLOTS, int SEGS>
+void launch_forward_orbit_shape(const ctr_plan *p, const typename OrbitRec<S>::type *ub, const ForwardEpi<float> &epi,
+                                cudaStream_t s)
+{
+    const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + SLOTS - 1) / SLOTS);
+    k_forward_orbit<S, SLOTS, SEGS><<<grid, 32 * SLOTS * SEGS, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
 }
 
 template <typename S>
 void launch_forward_orbit(const ctr_plan *p, const typename OrbitRec<S>::type *ub, const ForwardEpi<float> &epi,
                           cudaStream_t s)
 {
-    const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS);
-    switch (p->fwd_segs) {
-    case 2: k_forward_orbit<S, 2><<<grid, 32 * ORBIT_SLOTS * 2, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
-    case 8: k_forward_orbit<S, 8><<<grid, 32 * ORBIT_SLOTS * 8, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
-    default: k_forward_orbit<S, 4><<<grid, 32 * ORBIT_SLOTS * 4, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi); break;
+    switch (p->fwd_slots * 16 + p->fwd_segs) {
+    case 1 * 16 + 2: launch_forward_orbit_shape<S, 1, 2>(p, ub, epi, s); break;
+    case 1 * 16 + 8: launch_forward_orbit_shape<S, 1, 8>(p, ub, epi, s); break;
+    case 2 * 16 + 2: launch_forward_orbit_shape<S, 2, 2>(p, ub, epi, s); break;
+    case 2 * 16 + 4: launch_forward_orbit_shape<S, 2, 4>(p, ub, epi, s); break;
+    case 4 * 16 + 2: launch_forward_orbit_shape<S, 4, 2>(p, ub, epi, s); break;
+    default: launch_forward_orbit_shape<S, 1, 4>(p, ub, epi, s); break;
     }
 }
 

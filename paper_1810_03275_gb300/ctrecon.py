@@ -69,7 +69,7 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
            "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment", "ctr_plan_history",
            "ctr_fp32_fma_rate", "ctr_batch_set_mode", "ctr_batch_get_mode", "ctr_batch_persistent_ctas",
-           "ctr_plan_set_fwd_segments", "ctr_plan_get_fwd_segments"]
+           "ctr_plan_set_fwd_shape", "ctr_plan_get_fwd_shape"]
 
 
 def load(path: str = LIB_PATH):
@@ -145,10 +145,10 @@ def load(path: str = LIB_PATH):
                                           ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.ctr_plan_history.argtypes = [vp, P(Diag), ctypes.c_int, P(ctypes.c_int)]
         lib.ctr_plan_history.restype = ctypes.c_int
-        lib.ctr_plan_set_fwd_segments.argtypes = [vp, ctypes.c_int]
-        lib.ctr_plan_set_fwd_segments.restype = ctypes.c_int
-        lib.ctr_plan_get_fwd_segments.argtypes = [vp]
-        lib.ctr_plan_get_fwd_segments.restype = ctypes.c_int
+        lib.ctr_plan_set_fwd_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        lib.ctr_plan_set_fwd_shape.restype = ctypes.c_int
+        lib.ctr_plan_get_fwd_shape.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
+        lib.ctr_plan_get_fwd_shape.restype = ctypes.c_int
         lib.ctr_batch_set_mode.argtypes = [vp, ctypes.c_int, ctypes.c_ulonglong]
         lib.ctr_batch_set_mode.restype = ctypes.c_int
         lib.ctr_batch_get_mode.argtypes = [vp]
@@ -317,13 +317,17 @@ class Plan:
     def set_bp_groups(self, groups: int):
         _check(load().ctr_plan_set_bp_groups(self._h, int(groups)))
 
-    @property
-    def fwd_segments(self) -> int:
-        """Warps splitting a job's rows in the symmetric forward projector (0: per-angle path)."""
-        return int(load().ctr_plan_get_fwd_segments(self._h))
+    FWD_SHAPES = ((1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (4, 2))
 
-    def set_fwd_segments(self, segments: int):
-        _check(load().ctr_plan_set_fwd_segments(self._h, int(segments)))
+    @property
+    def fwd_shape(self):
+        """(jobs per CTA, row segments) of the symmetric forward projector ((0, 0): per-angle path)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().ctr_plan_get_fwd_shape(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return (a.value, b.value)
+
+    def set_fwd_shape(self, jobs_per_cta: int, segments: int):
+        _check(load().ctr_plan_set_fwd_shape(self._h, int(jobs_per_cta), int(segments)))
 
     def rh_adjoint(self, g, u=None, stream=None):
         u = self.empty_image() if u is None else u

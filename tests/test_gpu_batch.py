@@ -225,35 +225,36 @@ def test_persistent_grid_barrier_gives_up(ct):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_forward_segment_variants_agree(ct, dtype):
-    """The symmetric forward projector's row-segment count (2, 4, 8 warps per job) is a
-    runtime choice among compiled instances: every choice matches the oracle, and the
-    autotuner sets one of them."""
+def test_forward_shape_variants_agree(ct, dtype):
+    """The symmetric forward projector's launch shape (adjacent jobs per CTA, warps per job)
+    is a runtime choice among compiled instances: every shape matches the oracle (on the
+    BF16 plan, for the rounded input), and the autotuner sets one of them."""
     import torch
     n, N, M = 96, 120, 137
     plan = ct.Plan(n, N, M, dtype=dtype)
-    assert plan.fwd_segments == 4
+    assert plan.fwd_shape == (1, 4)
     u = torch.randn((n, n), device="cuda").to(plan.op_dtype)
     ref = oracle.rh_forward(u.double().cpu().numpy(), oracle.Geometry(n, N, M))
     outs = {}
-    for sg in (2, 4, 8):
-        plan.set_fwd_segments(sg)
-        outs[sg] = to_np(plan.rh_forward(u))
-        assert rel_l2(outs[sg], ref) < 1e-5, sg
-    assert rel_l2(outs[2], outs[8]) < 2e-6
+    for shp in plan.FWD_SHAPES:
+        plan.set_fwd_shape(*shp)
+        assert plan.fwd_shape == shp
+        outs[shp] = to_np(plan.rh_forward(u))
+        assert rel_l2(outs[shp], ref) < 1e-5, shp
+    assert rel_l2(outs[(1, 2)], outs[(4, 2)]) < 2e-6
     with pytest.raises(ct.CtrError):
-        plan.set_fwd_segments(3)
+        plan.set_fwd_shape(3, 4)
     with pytest.raises(ct.CtrError):
-        ct.Plan(n, N, M, dtype="f64").set_fwd_segments(2)
+        ct.Plan(n, N, M, dtype="f64").set_fwd_shape(1, 2)
 
 
-def test_autotuner_picks_forward_segments(ct, tmp_path, monkeypatch):
+def test_autotuner_picks_forward_shape(ct, tmp_path, monkeypatch):
     from paper_1810_03275_gb300 import autotune
     monkeypatch.setenv("CTR_TUNE_CACHE", str(tmp_path / "tune.json"))
     plan = ct.Plan(256, 180, 363)
     autotune.tune_plan(plan, reps=2)
-    assert plan.fwd_segments in (2, 4, 8)
-    seg = plan.fwd_segments
+    assert plan.fwd_shape in plan.FWD_SHAPES
+    shp = plan.fwd_shape
     other = ct.Plan(256, 180, 363)
     autotune.tune_plan(other, reps=2)                    # from the cache
-    assert other.fwd_segments == seg
+    assert other.fwd_shape == shp
