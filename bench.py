@@ -282,11 +282,11 @@ def measure_forms(iters: int = 30, fma_peak: float = 4.03e13):
     for dt in ("f32", "bf16"):
         plan = ct.Plan(pr.n, pr.n_angles, pr.n_bins, angles=pr.theta, dtype=dt)
         from paper_1810_03275_gb300 import autotune
-        autotune.tune_plan(plan, reps=3, use_cache=False)           # the project's tuner, untimed
         if beta is None:
             beta = plan.power_beta(20)
             c = 1.05 * plan.power_lambda(beta, np.pi / pr.n, 20)
         prm = ct.default_params(beta=beta, c=c)
+        autotune.tune_solve(plan, f, mask, pr.alpha, pr.delta, iters=4, reps=1, params=prm, use_cache=False)  # untimed
         plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, 5, params=prm)      # warm-up
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -463,8 +463,7 @@ def main():
     mask = torch.as_tensor(pr.mask, device="cuda")
     u = torch.empty((n, n), dtype=torch.float32, device="cuda")
     from paper_1810_03275_gb300 import autotune
-    tune_groups = autotune.tune_plan(plan, reps=5, use_cache=False)     # the project's tuner, untimed
-    tuned = {"bp_groups": tune_groups, "fwd_shape_jobs_segments": list(plan.fwd_shape)}
+    tuned = autotune.tune_solve(plan, f, mask, pr.alpha, pr.delta, iters=40, use_cache=False)   # untimed
     prm = ct.default_params()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()

@@ -155,3 +155,53 @@ def tune_batch(batch, fs, masks, alphas, deltas, policies: Iterable[Optional[int
     apply(best)
     _store(key, best)
     return best
+
+
+def tune_solve(plan, f, mask, alpha: float, delta: float, iters: int = 30, reps: int = 2, params=None,
+               groups: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), shapes=None, use_cache: bool = True):
+    """Pick the backprojection split and the forward projector's launch shape by timing
+    `iters` iterations of Alg. 4 on the given data (beta and c from params, or from short
+    power iterations): inside the solve the split also decides how many partial images the
+    preconditioner's first pass folds, which a standalone operator timing does not see.
+    The split is chosen first (default shape), then the shape.  Sets both; returns
+    {"bp_groups": G, "fwd_shape": [jobs_per_cta, segments]} (no shape off the symmetric path)."""
+    import numpy as np
+    from . import ctrecon as ct
+    key = f"solve/{_device_key()}/{plan.dtype}/n{plan.n}/N{plan.n_angles}/M{plan.n_bins}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if isinstance(hit, dict):
+            try:
+                plan.set_bp_groups(int(hit["bp_groups"]))
+                if hit.get("fwd_shape") and plan.fwd_shape[0]:
+                    plan.set_fwd_shape(*hit["fwd_shape"])
+                return hit
+            except Exception:
+                pass
+    if params is None or not (params.beta > 0 and params.c > 0):
+        beta = plan.power_beta(10)
+        params = ct.default_params(beta=beta, c=1.05 * plan.power_lambda(beta, np.pi / plan.n, 10))
+    run = lambda: plan.tv_pd_solve(f, mask, alpha, delta, iters, params=params)
+
+    best_g, best_t = plan.bp_groups, None
+    for G in groups:
+        try:
+            plan.set_bp_groups(G)
+        except Exception:
+            continue
+        t = _time(run, reps)
+        if best_t is None or t < best_t:
+            best_g, best_t = G, t
+    plan.set_bp_groups(best_g)
+    choice = {"bp_groups": best_g}
+    if plan.fwd_shape[0]:
+        best_s, best_st = plan.fwd_shape, None
+        for shp in (shapes or plan.FWD_SHAPES):
+            plan.set_fwd_shape(*shp)
+            t = _time(run, reps)
+            if best_st is None or t < best_st:
+                best_s, best_st = tuple(shp), t
+        plan.set_fwd_shape(*best_s)
+        choice["fwd_shape"] = list(best_s)
+    _store(key, choice)
+    return choice

@@ -258,3 +258,24 @@ def test_autotuner_picks_forward_shape(ct, tmp_path, monkeypatch):
     other = ct.Plan(256, 180, 363)
     autotune.tune_plan(other, reps=2)                    # from the cache
     assert other.fwd_shape == shp
+
+
+def test_solve_tuner_keeps_results(ct, tmp_path, monkeypatch):
+    """The solve-level tuner (split and forward shape timed on Alg. 4 itself) leaves the
+    iterates within FP32 rounding of the oracle."""
+    import torch
+    from paper_1810_03275_gb300 import autotune
+    monkeypatch.setenv("CTR_TUNE_CACHE", str(tmp_path / "tune.json"))
+    p = phantom.make_problem("ts", 96, 120, 137, seed=7, n_ellipses=4, n_metal=1, noise="gaussian", alpha=0.05)
+    plan = ct.Plan(p.n, p.n_angles, p.n_bins, angles=p.theta)
+    geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)
+    beta = oracle.power_beta(geo, 20)
+    c = oracle.power_c(geo, beta, np.pi / p.n, 20)
+    prm = ct.default_params(beta=beta, c=c)
+    f, m = to_dev(p.f, torch.float32), torch.as_tensor(p.mask, device="cuda")
+    choice = autotune.tune_solve(plan, f, m, p.alpha, p.delta, iters=5, reps=1, params=prm)
+    assert choice["bp_groups"] == plan.bp_groups and tuple(choice["fwd_shape"]) == plan.fwd_shape
+    u, _ = plan.tv_pd_solve(f, m, p.alpha, p.delta, 20, params=prm)
+    ref = oracle.pdrq_solve(geo, oracle.make_descriptors(p.f, p.mask, p.delta), p.alpha, 20, sigma=1.0,
+                            tau=1 / np.sqrt(8), eps=np.pi / p.n, beta=beta, c=c)
+    assert rel_l2(to_np(u), ref.u) < 1e-5
