@@ -59,8 +59,16 @@ def _clone(st):
 class UnrolledPDRQ(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, alpha, plan, mask, delta, iters, ckpt, params):
-        a = float(alpha.detach().cpu()) if isinstance(alpha, torch.Tensor) else float(alpha)
+        # alpha is a host scalar of the C ABI: a CPU tensor (or float) costs no device
+        # synchronisation; a CUDA tensor is read back once here
+        a = float(alpha.detach().item()) if isinstance(alpha, torch.Tensor) else float(alpha)
         f = f.detach().contiguous()
+        if params.graph_block > max(ckpt - 1, 0):
+            # each segment is ckpt iterations (the last one kept apart for the diagnostics
+            # state): capture graphs of ckpt - 1 iterations, which the plan replays from its
+            # graph cache on every segment and every later call
+            params = ct.Params.from_buffer_copy(params)
+            params.graph_block = max(ckpt - 1, 0)
         state = plan.new_state()
         ckpts = []
         done = 0
