@@ -375,9 +375,11 @@ def run_ops(args):
     target: seeded uniform inputs, uniform angles over [0, pi))."""
     import torch
     from paper_1810_03275_gb300 import ctrecon as ct
-    n, N, M, dt = args.ops.split(",")
-    n, N, M = int(n), int(N), int(M)
+    fields = args.ops.split(",")
+    n, N, M, dt = int(fields[0]), int(fields[1]), int(fields[2]), fields[3]
     plan = ct.Plan(n, N, M, dtype=dt)
+    if len(fields) > 4:                             # forward shape "JxS" (jobs per CTA x row segments)
+        plan.set_fwd_shape(*(int(x) for x in fields[4].split("x")))
     gen = torch.Generator(device="cuda").manual_seed(0)
     u = torch.rand((n, n), device="cuda", generator=gen).to(plan.op_dtype)
     uT = u.t().contiguous()
@@ -438,8 +440,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16-vs-FP32 2048^2 timing")
-    ap.add_argument("--ops", default=None, help="n,views,bins,dtype: only run R_h and R_h^* of that plan --steps "
-                    "times (for a profiler), print nothing")
+    ap.add_argument("--ops", default=None, help="n,views,bins,dtype[,JxS]: only run R_h and R_h^* of that plan "
+                    "--steps times (for a profiler; JxS a forward shape), print nothing")
     args = ap.parse_args()
     if args.ops:
         return run_ops(args)

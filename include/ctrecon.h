@@ -354,10 +354,13 @@ int ctr_plan_get_bp_groups(const ctr_plan *plan);
 
 /* Tuning hook: the launch shape of the symmetric forward projector, one of the compiled
  * instances (jobs_per_cta, segments) = (1, 2), (1, 4) [default], (1, 8), (2, 2), (2, 4),
- * (4, 2).  A CTA takes jobs_per_cta adjacent jobs (nearly coincident rays: they share the
- * orbit image's lines in L1) and 31 bins; `segments` warps split the rows each job's rays
- * cross, and their sums are added in a fixed order.  The shape changes FP32 summation order
- * only.  CTR_EINVAL for other shapes, CTR_EUNSUPPORTED off the symmetric path;
+ * (4, 2), (4, 1).  A CTA takes jobs_per_cta adjacent jobs (nearly coincident rays: they
+ * share the orbit image's lines in L1) and 31 bins; `segments` warps split the rows each
+ * job's rays cross, and their sums are added in a fixed order.  (4, 1) is the staged form:
+ * one warp per job, and for every block of 8 rows the union of the four jobs' bands of the
+ * orbit image is copied into shared memory (cp.async, zero-filled outside the image) ahead
+ * of the march, so each pixel comes from L2 once per four jobs.  The shape changes FP32
+ * summation order only.  CTR_EINVAL for other shapes, CTR_EUNSUPPORTED off the symmetric path;
  * ctr_plan_get_fwd_shape reports (0, 0) there. */
 ctr_status ctr_plan_set_fwd_shape(ctr_plan *plan, int jobs_per_cta, int segments);
 ctr_status ctr_plan_get_fwd_shape(const ctr_plan *plan, int *jobs_per_cta, int *segments);

@@ -177,6 +177,8 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
     p->n_jobs = (int)jobs.size();
     p->orbit = true;
+    p->stg_wmax = stg_window(jobs, n, M);
+    p->stg_nst = stg_blocks_max(n);
     return CTR_OK;
 }
 
@@ -954,8 +956,8 @@ ctr_status ctr_plan_set_fwd_shape(ctr_plan *p, int jobs_per_cta, int segments)
     if (!p) return fail(CTR_EINVAL, "plan is NULL");
     const int key = jobs_per_cta * 16 + segments;
     if (key != 1 * 16 + 2 && key != 1 * 16 + 4 && key != 1 * 16 + 8 && key != 2 * 16 + 2 && key != 2 * 16 + 4 &&
-        key != 4 * 16 + 2)
-        return fail(CTR_EINVAL, "forward shape must be (1, 2), (1, 4), (1, 8), (2, 2), (2, 4) or (4, 2)");
+        key != 4 * 16 + 2 && key != 4 * 16 + 1)
+        return fail(CTR_EINVAL, "forward shape must be (1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (4, 2) or (4, 1)");
     if (!p->orbit) return fail(CTR_EUNSUPPORTED, "the plan projects angle by angle (no symmetric forward projector)");
     p->fwd_slots = jobs_per_cta;
     p->fwd_segs = segments;

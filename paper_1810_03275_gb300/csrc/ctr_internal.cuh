@@ -389,6 +389,8 @@ struct ctr_plan {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int fwd_slots = 1;                   // symmetric forward projector: adjacent jobs per CTA (1, 2, 4) ...
     int fwd_segs = 4;                    // ... and warps splitting a job's rows (2, 4, 8); see ctr_plan_set_fwd_shape
+    int stg_wmax = 0;                    // staged forward shape (4, 1): widest window (pixels) ...
+    int stg_nst = 0;                     // ... and most row blocks of one CTA
     double *d_hist = nullptr;            // MAX_CHECKS x HIST_FIELDS diagnostics records
     int hist_count = 0;                  // records the last solve wrote
     ctr::GraphCache graphs;              // instantiated iteration graphs, reused across calls
@@ -450,6 +452,9 @@ template <typename T> bool bp_deferred(const ctr_plan *p);
 // orbit image): callers may then skip making the transposed copy uT
 template <typename T> inline bool fwd_needs_transpose(const ctr_plan *p) { return !(sizeof(T) == 4 && p->orbit); }
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
+size_t stg_smem_bytes(int wmax, int nst_max, int rec_bytes);   // the staged forward projector's shared memory
+int stg_blocks_max(int n);
+int stg_window(const std::vector<OrbitJob> &jobs, int n, int M);
 int orbit_fwd_grid_y(int n_jobs);   // symmetric forward projector: job groups per bin chunk
 int fwd_grid_y(int N);         // forward-projector grid: angle groups
 

@@ -820,6 +820,173 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
     forward_orbit_body<S, false, SEGS, SLOTS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric forward projector with shared staging (launch shape (4, 1)).  A CTA takes
+// STG_JOBS consecutive jobs -- adjacent canonical angles, whose rays nearly coincide --
+// one warp each, and the same 31 bins.  All warps march the same rows; for every block of
+// STG_ROWS rows the union of the jobs' bands of the orbit image (the pixels their rays
+// cross there) is copied into shared memory with 16-byte cp.async (zero-filled outside the
+// image) while the previous block is marched, so each pixel the group reads comes once from
+// L2 for the four jobs instead of once per job.  Weights, march and sums are those of
+// k_forward_orbit (one warp per job, no row split), so the results equal its shape (1, 1).
+// The window of a block is the union over the jobs of [first pixel of interval kb - 1 on
+// the block's last row, last pixel of interval kb + 30 on its first row]; the plan holds
+// the widest window any block can need (stg_window), which sizes the row pitch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int STG_JOBS = 4;
+constexpr int STG_ROWS = 8;
+
+template <typename R>
+__device__ __forceinline__ void cp_async_rec(R *dst, const R *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(R) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0)
+                     : "memory");
+}
+
+template <typename S>
+__global__ void __launch_bounds__(32 * STG_JOBS)
+k_forward_orbit_staged(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
+                       const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi, int wmax, int nst_max)
+{
+    using R = typename OrbitRec<S>::type;
+    constexpr long long ONE = 4294967296ll;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *stage = reinterpret_cast<R *>(smem_raw);                        // [2][STG_ROWS][wmax]
+    int *s_qlo = reinterpret_cast<int *>(stage + 2 * STG_ROWS * wmax);  // [nst_max]
+    int *s_qhi = s_qlo + nst_max;
+    __shared__ int s_mlo, s_mhi;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kb = blockIdx.x * 31;
+    const int k = kb + lane - 1;                 // this lane's interval [k, k + 1)
+    const int j0 = blockIdx.y * STG_JOBS;
+    const int nj = min(STG_JOBS, n_jobs - j0);
+    const bool has_job = warp < nj;              // warp-uniform
+    AngleMarch am{};
+    int4 ls = make_int4(-1, -1, -1, -1);
+    if (has_job) {
+        am = jobs[j0 + warp].am;
+        ls = *reinterpret_cast<const int4 *>(jobs[j0 + warp].l);
+    }
+    if (threadIdx.x == 0) {
+        s_mlo = n;
+        s_mhi = -1;
+    }
+    __syncthreads();
+    {   // rows crossed by the CTA's rays on the detector (outer bounds, as k_forward_orbit)
+        int mlo = n, mhi = -1;
+        if (has_job && k < M) {
+            const float Q0 = (float)k * am.kA - am.oA;
+            rows_in<true>(Q0, am.binv, -3.f, (float)n + 1.f, n, mlo, mhi);
+        }
+        mlo = __reduce_min_sync(0xffffffffu, mlo);
+        mhi = __reduce_max_sync(0xffffffffu, mhi);
+        if (lane == 0 && mlo <= mhi) {
+            atomicMin(&s_mlo, mlo);
+            atomicMax(&s_mhi, mhi);
+        }
+    }
+    __syncthreads();
+    const int mlo = s_mlo, mhi = s_mhi;
+    const int nst = mlo <= mhi ? min((mhi - mlo + STG_ROWS) / STG_ROWS, nst_max) : 0;
+    for (int e = threadIdx.x; e < nst; e += blockDim.x) {
+        s_qlo[e] = 0x7fffffff;
+        s_qhi[e] = -0x7fffffff;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nst * nj; e += blockDim.x) {   // every block's window
+        const int st = e / nj;
+        const AngleMarch a = jobs[j0 + (e - st * nj)].am;
+        const int mf = mlo + st * STG_ROWS, ml = min(mf + STG_ROWS - 1, mhi);
+        const long long lo = ceil_div_ll((long long)(kb - 1) * ONE - (long long)ml * a.B - a.Op, a.A);
+        const long long hi = ceil_div_ll((long long)(kb + 31) * ONE - (long long)mf * a.B - a.Op, a.A) - 1;
+        atomicMin(&s_qlo[st], (int)lo);
+        atomicMax(&s_qhi[st], (int)hi);
+    }
+    __syncthreads();
+    // block st of rows into buffer st & 1: row rr at stage[(st & 1)][rr][c] = pixel q_lo + c
+    auto prefetch = [&](int st) {
+        R *dst = stage + (size_t)(st & 1) * STG_ROWS * wmax;
+        const int q0 = s_qlo[st];
+        const int w = min(s_qhi[st] - q0 + 1, wmax);
+        const int mf = mlo + st * STG_ROWS;
+        const int rows = min(STG_ROWS, mhi - mf + 1);
+        for (int rr = 0; rr < rows; ++rr) {
+            const R *src_row = ubar + (size_t)(mf + rr) * n;
+            for (int c = threadIdx.x; c < w; c += blockDim.x) {
+                const int q = q0 + c;
+                const bool ok = (unsigned)q < (unsigned)n;
+                cp_async_rec(dst + rr * wmax + c, ok ? src_row + q : ubar, ok);
+            }
+        }
+    };
+    float4 Su = make_float4(0.f, 0.f, 0.f, 0.f), Sf = Su;
+    // the lane's march state at row mlo: q = first pixel with P >= K, r = P - K in [0, A)
+    const long long A = am.A > 0 ? am.A : 1, B = am.B;
+    const long long K = (long long)k * ONE;
+    const long long qa = ceil_div_ll(K - (long long)mlo * B - am.Op, A);
+    unsigned r = (unsigned)(qa * A + (long long)mlo * B + am.Op - K);
+    int q = (int)qa;
+    const unsigned A32 = (unsigned)A, B32 = (unsigned)B;
+    const unsigned lim = (unsigned)(ONE - A);
+    // the first pixel moves one to the left when r + B reaches A; with B = 0 it never moves
+    // (and A - B may be 2^32, which a 32-bit threshold cannot hold)
+    const unsigned thr = (unsigned)(A - B);
+    const bool moves = B > 0;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (nst > 0) prefetch(0);
+    cp_async_commit();
+    for (int st = 0; st < nst; ++st) {
+        if (st + 1 < nst) prefetch(st + 1);
+        cp_async_commit();
+        cp_async_wait<1>();                      // this thread's copies of block st
+        __syncthreads();                         // everyone's
+        if (has_job) {
+            const R *blk = stage + (size_t)(st & 1) * STG_ROWS * wmax;
+            const int rows = min(STG_ROWS, mhi - (mlo + st * STG_ROWS) + 1);
+            int idx = q - s_qlo[st];
+#pragma unroll
+            for (int rr = 0; rr < STG_ROWS; ++rr) {
+                if (rr < rows) {
+                    const R *row = blk + rr * wmax;
+                    const float4 v1 = rec_f32(row[idx]);
+                    const float4 v2 = r < lim ? rec_f32(row[idx + 1]) : zero;
+                    acc4(Su, Sf, v1, one_plus_frac32u(r));
+                    acc4(Su, Sf, v2, one_plus_frac32u(r + A32));
+                    const bool sdn = moves && r >= thr;
+                    r += sdn ? B32 - A32 : B32;
+                    idx -= sdn ? 1 : 0;
+                    q -= sdn ? 1 : 0;
+                }
+            }
+        }
+        __syncthreads();                         // buffer st & 1 is refilled next
+    }
+    cp_async_wait<0>();
+    if (!has_job || kb >= M) return;             // warp-uniform
+    orbit_out(epi, ls.x, M, k, lane, Su.x, Sf.x);
+    orbit_out(epi, ls.y, M, k, lane, Su.y, Sf.y);
+    orbit_out(epi, ls.z, M, k, lane, Su.z, Sf.z);
+    orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
+}
+
+template <typename S>
+void launch_forward_orbit_staged(const ctr_plan *p, const typename OrbitRec<S>::type *ub,
+                                 const ForwardEpi<float> &epi, cudaStream_t s)
+{
+    const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + STG_JOBS - 1) / STG_JOBS);
+    const int rec = (int)sizeof(typename OrbitRec<S>::type);
+    k_forward_orbit_staged<S><<<grid, 32 * STG_JOBS, stg_smem_bytes(p->stg_wmax, p->stg_nst, rec), s>>>(
+        ub, p->n, p->n_jobs, p->M, p->d_jobs, epi, p->stg_wmax, p->stg_nst);
+}
+
 template <typename S, int SLOTS, int SEGS>
 void launch_forward_orbit_shape(const ctr_plan *p, const typename OrbitRec<S>::type *ub, const ForwardEpi<float> &epi,
                                 cudaStream_t s)
@@ -838,6 +1005,7 @@ void launch_forward_orbit(const ctr_plan *p, const typename OrbitRec<S>::type *u
     case 2 * 16 + 2: launch_forward_orbit_shape<S, 2, 2>(p, ub, epi, s); break;
     case 2 * 16 + 4: launch_forward_orbit_shape<S, 2, 4>(p, ub, epi, s); break;
     case 4 * 16 + 2: launch_forward_orbit_shape<S, 4, 2>(p, ub, epi, s); break;
+    case 4 * 16 + 1: launch_forward_orbit_staged<S>(p, ub, epi, s); break;
     default: launch_forward_orbit_shape<S, 1, 4>(p, ub, epi, s); break;
     }
 }
@@ -890,8 +1058,6 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool val
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // The FP32 symmetric backprojection with asynchronous staging: the group's job tables
 // are built once; chunk c + 1's four sinogram rows per job are copied raw into the
@@ -1301,6 +1467,11 @@ ctr_status configure_radon(const ctr_plan *p)
     if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, osm);
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
+    if (st == CTR_OK && p->orbit) {
+        st = raise_smem_limit(k_forward_orbit_staged<float>, stg_smem_bytes(p->stg_wmax, p->stg_nst, 16));
+        if (st == CTR_OK)
+            st = raise_smem_limit(k_forward_orbit_staged<__nv_bfloat16>, stg_smem_bytes(p->stg_wmax, p->stg_nst, 8));
+    }
     return st;
 }
 
@@ -1351,6 +1522,41 @@ template bool bp_deferred<float>(const ctr_plan *);
 template bool bp_deferred<double>(const ctr_plan *);
 
 int fwd_grid_x(int M) { return (M + 30) / 31; }
+
+size_t stg_smem_bytes(int wmax, int nst_max, int rec_bytes)
+{
+    return (size_t)2 * STG_ROWS * wmax * rec_bytes + 2 * sizeof(int) * (size_t)nst_max;
+}
+
+int stg_blocks_max(int n) { return (n + STG_ROWS) / STG_ROWS + 1; }
+
+// The widest window a staged block can need, over every group of STG_JOBS consecutive jobs:
+// the spread of the jobs' first pixels at equal (K, m) (linear in K and m for each job, so
+// its extremes lie at the corners of the detector x row range) plus the pixels 32 intervals
+// and STG_ROWS - 1 rows span for the steepest job, plus the rounding of both window ends.
+int stg_window(const std::vector<OrbitJob> &jobs, int n, int M)
+{
+    const double one = 4294967296.0;
+    double w = 0.0;
+    for (size_t g = 0; g < jobs.size(); g += STG_JOBS) {
+        const size_t e = std::min(jobs.size(), g + STG_JOBS);
+        double spread = 0.0, span = 0.0;
+        for (double K : {-one, (double)(M + 32) * one})
+            for (double m : {0.0, (double)(n - 1)}) {
+                double lo = 1e300, hi = -1e300;
+                for (size_t j = g; j < e; ++j) {
+                    const double x = (K - m * (double)jobs[j].am.B - (double)jobs[j].am.Op) / (double)jobs[j].am.A;
+                    lo = std::min(lo, x);
+                    hi = std::max(hi, x);
+                }
+                spread = std::max(spread, hi - lo);
+            }
+        for (size_t j = g; j < e; ++j)
+            span = std::max(span, (32.0 * one + (STG_ROWS - 1) * (double)jobs[j].am.B) / (double)jobs[j].am.A);
+        w = std::max(w, std::ceil(spread + span) + 4.0);
+    }
+    return (int)w;
+}
 
 int orbit_fwd_grid_y(int n_jobs) { return (n_jobs + ORBIT_SLOTS - 1) / ORBIT_SLOTS; }
 int fwd_grid_y(int N) { return (N + FWD_AW - 1) / FWD_AW; }

@@ -317,7 +317,7 @@ class Plan:
     def set_bp_groups(self, groups: int):
         _check(load().ctr_plan_set_bp_groups(self._h, int(groups)))
 
-    FWD_SHAPES = ((1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (4, 2))
+    FWD_SHAPES = ((1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (4, 2), (4, 1))
 
     @property
     def fwd_shape(self):

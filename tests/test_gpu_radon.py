@@ -179,3 +179,26 @@ def test_point_projection(ct):
     np.testing.assert_allclose(got.sum(1), 1.0, atol=1e-6)
     np.testing.assert_allclose((got * np.arange(M)).sum(1), pos, atol=2e-5)
 
+
+
+@pytest.mark.parametrize("geom", [g for g in GEOMS if g[5] == "uniform" and g[0] > 1] +
+                         [(512, 720, 729, 1.0, 1.0, "uniform"), (96, 120, 137, 1.0, 1.0, "uniform")])
+def test_staged_forward_shape(ct, geom):
+    """The staged forward projector (shape (4, 1): four adjacent jobs per CTA share a
+    cp.async-staged window of the orbit image) on every symmetric-path geometry, FP32 and
+    BF16: equal to the default shape up to FP32 summation order and to the oracle."""
+    import torch
+    n, N, M, h, ds, _ = geom
+    th = np.arange(N) * (np.pi / N)
+    for dtype in ("f32", "bf16"):
+        plan = ct.Plan(n, N, M, angles=th, h=h, ds=ds, dtype=dtype)
+        if plan.symmetric_jobs == 0:
+            pytest.skip("per-angle path")
+        u = torch.as_tensor(np.random.default_rng(n).standard_normal((n, n)), dtype=torch.float32,
+                            device="cuda").to(plan.op_dtype)
+        base = to_np(plan.rh_forward(u))
+        plan.set_fwd_shape(4, 1)
+        got = to_np(plan.rh_forward(u))
+        ref = oracle.rh_forward(u.double().cpu().numpy(), oracle.Geometry(n, N, M, h=h, ds=ds, theta=th))
+        assert rel_l2(got, base) < 2e-6, dtype
+        assert rel_l2(got, ref) < 1e-5, dtype
