@@ -175,6 +175,16 @@ def measure_algorithms(plan, f, mask, pr, iters: int = 200):
         prm = ct.default_params(beta=beta, c=ck, precond=kind)
         out[f"alg4_precond{kind}"] = timed(lambda k: plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, k, params=prm)[0])
     prm = ct.default_params(beta=beta, c=c)
+    # Alg. 4 (kind 0) with each launch option switched back: plain stream order instead of
+    # programmatic dependent launch, and the CTA-level preconditioner passes (form 1)
+    run4 = lambda k: plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, k, params=prm)[0]
+    plan.set_launch_overlap(0)
+    out["alg4_launch_overlap_off"] = timed(run4)
+    plan.set_launch_overlap(1)
+    form0 = plan.fft_form
+    plan.set_fft_form(1)
+    out["alg4_fft_form1"] = timed(run4)
+    plan.set_fft_form(form0)
     out["alg5_nonneg"] = timed(lambda k: plan.tv_pd_solve(f, mask, pr.alpha, pr.delta, k,
                                                           params=ct.default_params(beta=beta, c=c, nonneg=1))[0])
     out["alg3_unconstrained"] = timed(lambda k: plan.tv_pdrq2_solve(f, pr.alpha, k, params=prm)[0])
@@ -371,8 +381,9 @@ def measure_batched(iters: int = 30, count: int = 64):
 
 
 def run_ops(args):
-    """The two operator calls of one plan, `--steps` times each after `--warmup` (a profiler's
-    target: seeded uniform inputs, uniform angles over [0, pi))."""
+    """The operator calls of one plan (R_h, R_h^* and the preconditioner), `--steps` times
+    each after `--warmup` (a profiler's target: seeded uniform inputs, uniform angles over
+    [0, pi))."""
     import torch
     from paper_1810_03275_gb300 import ctrecon as ct
     fields = args.ops.split(",")
@@ -386,10 +397,14 @@ def run_ops(args):
     g = torch.rand((N, M), device="cuda", generator=gen).to(plan.op_dtype)
     go = torch.empty((N, M), device="cuda", dtype=plan.torch_dtype)
     uo = torch.empty((n, n), device="cuda", dtype=plan.torch_dtype)
+    uf = u.to(plan.torch_dtype)
+    xo = torch.empty_like(uo)
+    prm = ct.default_params(c=1.0)
     for k in range(args.warmup + args.steps):
         torch.cuda.nvtx.range_push("ops_step" if k >= args.warmup else "ops_warmup")
         plan.rh_forward_t(u, uT, go)
         plan.rh_adjoint(g, uo)
+        plan.precond_apply(uf, prm, xo)
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return 0
@@ -519,6 +534,25 @@ def main():
         torch.cuda.synchronize()
         kt[name] = a.elapsed_time(b) / reps / 1e3
     dom = max(kt, key=kt.get)
+    # the preconditioner passes alone (M^{-1} y, symbols cached), in both kernel forms
+    prm_pc = ct.default_params(c=1.0, eps=np.pi / n)
+    xo = torch.empty_like(u)
+    form0, pc_ms = plan.fft_form, {}
+    for form in (0, 1):
+        plan.set_fft_form(form)
+        if plan.fft_form != form:
+            continue
+        for _ in range(3):
+            plan.precond_apply(u, prm_pc, xo)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            plan.precond_apply(u, prm_pc, xo)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pc_ms[f"form{form}"] = a.elapsed_time(b) / reps
+    plan.set_fft_form(form0)
     hbm_peak, peak_kind = peaks()
     nominal = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6                # FMA/s, FP32 lanes x max clock
     fmas = FMA_PER_SAMPLE * n * n * N                                  # algorithmic FMAs per operator call
@@ -526,6 +560,8 @@ def main():
     kernels = {k: {"ms": 1e3 * v, "kernels": call_kernels[k], "gsamples_per_s": n * n * N / v / 1e9,
                    "gfma_s": fmas / v / 1e9, "fma_frac": fmas / v / fma_peak, "hbm_gbs": bytes_alg / v / 1e9,
                    "hbm_frac": bytes_alg / v / 1e9 / hbm_peak} for k, v in kt.items()}
+    kernels["precond_apply"] = {"ms": pc_ms.get(f"form{plan.fft_form}"), "form": plan.fft_form, "forms_ms": pc_ms,
+                                "note": "form 0: warp-level passes, form 1: CTA-level Stockham passes"}
     roof = {"bound": "alu", "kernel": f"{dom} ({' + '.join(call_kernels[dom])})", "path":
             f"symmetric, {plan.symmetric_jobs} jobs for {N} angles" if sym else "per angle",
             "achieved": fmas / kt[dom] / 1e9, "peak": fma_peak / 1e9, "unit": "GFMA/s",

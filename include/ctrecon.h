@@ -360,10 +360,31 @@ int ctr_plan_get_bp_groups(const ctr_plan *plan);
  * one warp per job, and for every block of 8 rows the union of the four jobs' bands of the
  * orbit image is copied into shared memory (cp.async, zero-filled outside the image) ahead
  * of the march, so each pixel comes from L2 once per four jobs.  The shape changes FP32
- * summation order only.  CTR_EINVAL for other shapes, CTR_EUNSUPPORTED off the symmetric path;
- * ctr_plan_get_fwd_shape reports (0, 0) there. */
+ * summation order only.  CTR_EINVAL for other shapes, CTR_EUNSUPPORTED off the symmetric path
+ * and, for (4, 1), where the staged window would exceed one CTA's shared memory;
+ * ctr_plan_get_fwd_shape reports (0, 0) off the symmetric path. */
 ctr_status ctr_plan_set_fwd_shape(ctr_plan *plan, int jobs_per_cta, int segments);
 ctr_status ctr_plan_get_fwd_shape(const ctr_plan *plan, int *jobs_per_cta, int *segments);
+
+/* Tuning hook: the kernels of the Fourier preconditioner passes (Sec. 4.3.1, the 2-D DFT
+ * diagonalisation of M).  form 0 [default]: on FP32 plans with n = 256, 512 or 1024 each
+ * row pair and each column is one warp's transform (a four-step factorisation n = 32 x
+ * n/32 in registers, no CTA barrier); other plans use form 1.  form 1: the CTA-level
+ * mixed-radix Stockham passes through shared memory (every n = 2^a 3^b, FP64).  Both
+ * compute the same DFT up to FP32 rounding.  CTR_EINVAL for other values.  No allocation;
+ * ctr_plan_get_fft_form returns the form the plan's passes take (1 where 0 does not apply). */
+ctr_status ctr_plan_set_fft_form(ctr_plan *plan, int form);
+int ctr_plan_get_fft_form(const ctr_plan *plan);
+
+/* Tuning hook: programmatic dependent launch of the kernels of one iteration on the
+ * symmetric FP32 / BF16 path (the backprojection, the three preconditioner passes of form 0,
+ * the orbit image with the TV step, the forward projector).  on = 1 [default]: each of them
+ * is launched with the programmatic-serialization attribute and waits, before its first
+ * global-memory access, for the kernel before it to complete, so its launch overlaps that
+ * kernel's last wave; results are identical to on = 0 (plain stream order).  CTR_EINVAL
+ * for values other than 0 and 1.  No allocation; ctr_plan_get_launch_overlap returns it. */
+ctr_status ctr_plan_set_launch_overlap(ctr_plan *plan, int on);
+int ctr_plan_get_launch_overlap(const ctr_plan *plan);
 
 
 /* Batches: many independent slices (each its own geometry, image size and view

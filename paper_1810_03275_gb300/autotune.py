@@ -66,6 +66,17 @@ def _time(fn, reps: int) -> float:
     return a.elapsed_time(b) / reps
 
 
+def _try_shape(plan, shape) -> bool:
+    """Set a forward launch shape; False where the plan does not offer it (the staged
+    shape needs its orbit-image window to fit one CTA's shared memory)."""
+    from . import ctrecon as ct
+    try:
+        plan.set_fwd_shape(*shape)
+        return True
+    except ct.CtrError:
+        return False
+
+
 def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int = 5, use_cache: bool = True,
               shapes=None) -> int:
     """Pick the angle-group count of `plan`'s backprojection and, on the symmetric path,
@@ -102,7 +113,8 @@ def tune_plan(plan, candidates: Iterable[int] = (1, 2, 3, 4, 5, 6, 8), reps: int
         gs = torch.empty((plan.n_angles, plan.n_bins), device="cuda", dtype=plan.torch_dtype)
         best_s, best_st = plan.fwd_shape, None
         for shp in (shapes or plan.FWD_SHAPES):
-            plan.set_fwd_shape(*shp)
+            if not _try_shape(plan, shp):
+                continue
             t = _time(lambda: plan.rh_forward_t(x, xt, gs), reps)
             if best_st is None or t < best_st:
                 best_s, best_st = tuple(shp), t
@@ -197,7 +209,8 @@ def tune_solve(plan, f, mask, alpha: float, delta: float, iters: int = 30, reps:
     if plan.fwd_shape[0]:
         best_s, best_st = plan.fwd_shape, None
         for shp in (shapes or plan.FWD_SHAPES):
-            plan.set_fwd_shape(*shp)
+            if not _try_shape(plan, shp):
+                continue
             t = _time(run, reps)
             if best_st is None or t < best_st:
                 best_s, best_st = tuple(shp), t

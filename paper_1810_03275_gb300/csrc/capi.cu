@@ -177,8 +177,11 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
     p->n_jobs = (int)jobs.size();
     p->orbit = true;
+    // the staged forward shape only where its double-buffered window fits one CTA's shared
+    // memory (stg_wmax = 0: shape (4, 1) unavailable on this plan)
     p->stg_wmax = stg_window(jobs, n, M);
     p->stg_nst = stg_blocks_max(n);
+    if (stg_smem_bytes(p->stg_wmax, p->stg_nst, 16) > STG_SMEM_LIMIT) p->stg_wmax = 0;
     return CTR_OK;
 }
 
@@ -959,9 +962,36 @@ ctr_status ctr_plan_set_fwd_shape(ctr_plan *p, int jobs_per_cta, int segments)
         key != 4 * 16 + 2 && key != 4 * 16 + 1)
         return fail(CTR_EINVAL, "forward shape must be (1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (4, 2) or (4, 1)");
     if (!p->orbit) return fail(CTR_EUNSUPPORTED, "the plan projects angle by angle (no symmetric forward projector)");
+    if (key == 4 * 16 + 1 && p->stg_wmax <= 0)
+        return fail(CTR_EUNSUPPORTED, "the staged forward shape (4, 1): its orbit-image window exceeds shared memory "
+                                      "on this geometry");
     p->fwd_slots = jobs_per_cta;
     p->fwd_segs = segments;
     return CTR_OK;
+}
+
+ctr_status ctr_plan_set_fft_form(ctr_plan *p, int form)
+{
+    if (!p) return fail(CTR_EINVAL, "plan is NULL");
+    if (form != 0 && form != 1) return fail(CTR_EINVAL, "fft form must be 0 (warp-level) or 1 (CTA-level)");
+    p->fft_form = form;
+    return CTR_OK;
+}
+
+ctr_status ctr_plan_set_launch_overlap(ctr_plan *p, int on)
+{
+    if (!p) return fail(CTR_EINVAL, "plan is NULL");
+    if (on != 0 && on != 1) return fail(CTR_EINVAL, "launch overlap must be 0 or 1");
+    p->pdl = on;
+    return CTR_OK;
+}
+
+int ctr_plan_get_launch_overlap(const ctr_plan *p) { return p ? p->pdl : -1; }
+
+int ctr_plan_get_fft_form(const ctr_plan *p)
+{
+    if (!p) return -1;
+    return (p->fft_form == 0 && wfft_supported(p)) ? 0 : 1;
 }
 
 ctr_status ctr_plan_get_fwd_shape(const ctr_plan *p, int *jobs_per_cta, int *segments)

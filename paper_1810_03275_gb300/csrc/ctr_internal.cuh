@@ -46,6 +46,33 @@ struct NvtxScope {
         if (e_ != cudaSuccess) return ::ctr::cuda_fail(e_, what);   \
     } while (0)
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl(true, ...) may be
+// scheduled while the kernel before it in the stream is still running: it executes
+// pdl_wait() before its first global-memory access, which returns once that kernel has
+// completed and its writes are visible (and, since that kernel did the same, every
+// earlier one).  pdl_trigger() lets the next such launch be scheduled as soon as every CTA
+// of this grid is resident, so the launch latency overlaps the tail of this kernel.
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // The dynamic shared-memory limit is an attribute of the kernel function for the
 // whole process, shared by every plan: only ever raise it.  (Its default is 48 KB minus
 // the kernel's static shared memory, so the check is against the attribute itself.)
@@ -364,6 +391,8 @@ struct ctr_plan {
     void *v1b = nullptr;       // N*M
     void *t1 = nullptr;        // N*M
     void *ubar_u = nullptr;    // n*n bar u of Alg. 5 (non-negativity)
+    int pdl = 1;               // programmatic dependent launch of the iteration's kernels
+    int fft_form = 0;          // preconditioner passes: 0 warp-level where n allows (FP32, n = 256/512/1024), 1 CTA-level
     int precond_kind = 0;      // 0: inverse norm (Sec. 4.3.1); 1: impulse response; 2: circulant; 3: Richardson
     void *pk_s = nullptr;      // n*n DFT (2-D for kind 1, 1-D of the flattened image for kind 2) of the
                                // symmetrised impulse response of R_h^* R_h (built on first use)
@@ -453,6 +482,7 @@ template <typename T> bool bp_deferred(const ctr_plan *p);
 template <typename T> inline bool fwd_needs_transpose(const ctr_plan *p) { return !(sizeof(T) == 4 && p->orbit); }
 int fwd_grid_x(int M);         // forward-projector grid: bin chunks
 size_t stg_smem_bytes(int wmax, int nst_max, int rec_bytes);   // the staged forward projector's shared memory
+constexpr size_t STG_SMEM_LIMIT = 227 * 1024;                   // dynamic shared memory one CTA may opt into
 int stg_blocks_max(int n);
 int stg_window(const std::vector<OrbitJob> &jobs, int n, int M);
 int orbit_fwd_grid_y(int n_jobs);   // symmetric forward projector: job groups per bin chunk
@@ -463,6 +493,7 @@ size_t bp_smem_bytes(int wstride);
 size_t obp_smem_bytes(int wstride, int jobs_per_group);   // the symmetric backprojection's dynamic shared memory
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
+bool wfft_supported(const ctr_plan *p);        // the warp-level preconditioner passes apply
 size_t fft_rows_smem(int n, size_t esize);   // dynamic shared memory of the row passes
 size_t fft_cols_smem(int n, size_t esize);   // ... and of the column pass
 int fft_cols_per_cta(int n, size_t esize);

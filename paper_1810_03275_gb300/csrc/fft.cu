@@ -607,6 +607,385 @@ k_fft_rows_inv(const typename C2<T>::type *__restrict__ cbuf, int n, int rows_pe
     fft_rows_inv_body<T>(cbuf, n, rows_per_cta, fp, tw, out, mode, outT, dout, outh, outTh, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------------------
+// Warp-level transforms for n = 32 V (V = 8, 16, 32: n = 256, 512, 1024), FP32.
+// One warp computes one length-n DFT with no CTA barrier (four-step factorisation
+// n = V x 32):
+//   1. lane l holds x[l + 32 m], m < V; a V-point DFT over m in registers gives A_l(k1);
+//   2. A_l(k1) is multiplied by W_n^{l k1} and transposed through a warp-private shared
+//      buffer, so that the G = 32 / V lanes of group k1 hold the 32 values over l;
+//   3. with l = la + G lb, a V-point DFT over lb in registers, the twiddle W_32^{la k2'}
+//      and a G-point DFT across the group's lanes (shuffles) give
+//      X[k1 + V k2' + V^2 k2''].
+// The adjoint steps in reverse order (conjugate twiddles, decimation in time) map that
+// layout back to lane l holding y[l + 32 m]: the unnormalised inverse DFT.  So the
+// column pass multiplies by the symbol in the scrambled layout and the inverse row pass
+// loads its coefficients straight into it.
+
+// cos(2 pi j / 32) for 0 <= j <= 8: cos(k pi / 16), k = 0..8
+__host__ __device__ constexpr double w32_octant(int j)
+{
+    return j == 0 ? 1.0
+         : j == 1 ? 0.98078528040323044913
+         : j == 2 ? 0.92387953251128675613
+         : j == 3 ? 0.83146961230254523708
+         : j == 4 ? 0.70710678118654752440
+         : j == 5 ? 0.55557023301960222474
+         : j == 6 ? 0.38268343236508977173
+         : j == 7 ? 0.19509032201612826785
+         : 0.0;
+}
+// cos and sin of 2 pi t / 32 for any integer t, by quadrant symmetry
+__host__ __device__ constexpr float w32_cos(int t)
+{
+    return (t & 31) <= 8 ? (float)w32_octant(t & 31)
+         : (t & 31) <= 16 ? (float)-w32_octant(16 - (t & 31))
+         : (t & 31) <= 24 ? (float)-w32_octant((t & 31) - 16)
+         : (float)w32_octant(32 - (t & 31));
+}
+__host__ __device__ constexpr float w32_sin(int t) { return w32_cos(t - 8); }
+
+// d * exp(S 2 pi i t / 32) (t a compile-time constant after unrolling: the quarter turns
+// are exact swaps and sign changes)
+template <int S>
+__device__ __forceinline__ float2 rot32(float2 d, int t)
+{
+    t &= 31;
+    if (t == 0) return d;
+    if (t == 8) return S > 0 ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+    if (t == 16) return make_float2(-d.x, -d.y);
+    if (t == 24) return S > 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);
+    const float c = w32_cos(t), s = (float)S * w32_sin(t);
+    return make_float2(d.x * c - d.y * s, d.x * s + d.y * c);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// W_n^{S t} from the table tw[t] = exp(-2 pi i t / n) (staged in shared memory)
+template <int S>
+__device__ __forceinline__ float2 tw_n(const float2 *tw, int t)
+{
+    float2 w = tw[t];
+    if (S > 0) w.y = -w.y;
+    return w;
+}
+
+// the twiddle table into shared memory, 16 bytes per thread and step
+template <int N>
+__device__ __forceinline__ void stage_tw(float2 *s_tw, const float2 *__restrict__ tw)
+{
+    const float4 *src = reinterpret_cast<const float4 *>(tw);
+    float4 *dst = reinterpret_cast<float4 *>(s_tw);
+    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) dst[t] = __ldg(src + t);
+}
+
+template <int B> __host__ __device__ constexpr int brev(int i)
+{
+    int r = 0;
+    for (int b = 0; b < B; ++b) r |= ((i >> b) & 1) << (B - 1 - b);
+    return r;
+}
+template <int V> __host__ __device__ constexpr int ilog2c() { return V <= 1 ? 0 : 1 + ilog2c<V / 2>(); }
+
+// V-point DFT with sign S in registers, decimation in frequency: natural order in,
+// v[i] = X[brev(i)] out.
+template <int V, int S>
+__device__ __forceinline__ void dft_dif(float2 (&v)[V])
+{
+    constexpr int L = ilog2c<V>();
+#pragma unroll
+    for (int st = 0; st < L; ++st) {
+        const int span = V >> (st + 1);
+#pragma unroll
+        for (int b = 0; b < V; b += 2 * span)
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                const float2 a = v[b + j], c = v[b + j + span];
+                v[b + j] = make_float2(a.x + c.x, a.y + c.y);
+                v[b + j + span] = rot32<S>(make_float2(a.x - c.x, a.y - c.y), j * (16 / span));
+            }
+    }
+}
+
+// Its adjoint up to the sign: decimation in time, v[i] = X[brev(i)] in, natural order out
+// (dft_dit<V, +1> after dft_dif<V, -1> is V times the identity).
+template <int V, int S>
+__device__ __forceinline__ void dft_dit(float2 (&v)[V])
+{
+    constexpr int L = ilog2c<V>();
+#pragma unroll
+    for (int st = L - 1; st >= 0; --st) {
+        const int span = V >> (st + 1);
+#pragma unroll
+        for (int b = 0; b < V; b += 2 * span)
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                const float2 a = v[b + j], c = rot32<S>(v[b + j + span], j * (16 / span));
+                v[b + j] = make_float2(a.x + c.x, a.y + c.y);
+                v[b + j + span] = make_float2(a.x - c.x, a.y - c.y);
+            }
+    }
+}
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int d)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d));
+}
+
+// G-point DFT (sign S) across the lanes la = lane % G of a group, decimation in
+// frequency: lane la ends with coefficient brev(la).
+template <int V, int G, int S>
+__device__ __forceinline__ void xlane_dif(float2 (&v)[V], int la)
+{
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) {
+        const bool bot = (la & d) != 0;
+        const bool turn = bot && (la & (d - 1)) != 0;      // d = 2, la = 3: W_4^{S}
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const float2 p = shfl_xor2(v[i], d), x = v[i];
+            float2 o = bot ? make_float2(p.x - x.x, p.y - x.y) : make_float2(x.x + p.x, x.y + p.y);
+            if (turn) o = rot32<S>(o, 8);
+            v[i] = o;
+        }
+    }
+}
+
+// Adjoint of xlane_dif (with S = +1 after a forward S = -1): stages in reverse order.
+template <int V, int G, int S>
+__device__ __forceinline__ void xlane_dit(float2 (&v)[V], int la)
+{
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) {
+        const bool bot = (la & d) != 0;
+        const bool turn = bot && (la & (d - 1)) != 0;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const float2 t = turn ? rot32<S>(v[i], 8) : v[i];
+            const float2 p = shfl_xor2(t, d);
+            v[i] = bot ? make_float2(p.x - t.x, p.y - t.y) : make_float2(t.x + p.x, t.y + p.y);
+        }
+    }
+}
+
+// frequency held by (lane, register i) after wfft_fwd
+template <int V>
+__device__ __forceinline__ int wfft_k(int lane, int i)
+{
+    constexpr int G = 32 / V;
+    return lane / G + V * brev<ilog2c<V>()>(i) + V * V * brev<ilog2c<G>()>(lane % G);
+}
+
+// Forward (S = -1) or inverse (S = +1) length-32V DFT of one warp: v[m] = x[lane + 32 m]
+// in, v[i] = X[wfft_k(lane, i)] out.  buf: (32 + G) V complex of this warp's shared memory.
+template <int V, int S>
+__device__ __forceinline__ void wfft_fwd(float2 (&v)[V], int lane, float2 *buf, const float2 *tw)
+{
+    constexpr int G = 32 / V, P = 32 + G, LB = ilog2c<V>();
+    dft_dif<V, S>(v);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int k1 = brev<LB>(i);
+        buf[k1 * P + lane] = k1 ? cmulf(v[i], tw_n<S>(tw, lane * k1)) : v[i];
+    }
+    __syncwarp();
+    const int k1 = lane / G, la = lane % G;
+#pragma unroll
+    for (int lb = 0; lb < V; ++lb) v[lb] = buf[k1 * P + la + G * lb];
+    __syncwarp();
+    dft_dif<V, S>(v);
+    if (G > 1 && la) {
+#pragma unroll
+        for (int i = 1; i < V; ++i) v[i] = cmulf(v[i], tw_n<S>(tw, la * brev<LB>(i) * V));
+    }
+    xlane_dif<V, G, S>(v, la);
+}
+
+// The adjoint steps of wfft_fwd<V, -S>: v[i] = X[wfft_k(lane, i)] in, v[m] = y[lane + 32 m]
+// out, y[j] = sum_k X[k] exp(S 2 pi i j k / n) (S = +1: the unnormalised inverse DFT).
+template <int V, int S>
+__device__ __forceinline__ void wfft_adj(float2 (&v)[V], int lane, float2 *buf, const float2 *tw)
+{
+    constexpr int G = 32 / V, P = 32 + G, LB = ilog2c<V>();
+    const int k1 = lane / G, la = lane % G;
+    xlane_dit<V, G, S>(v, la);
+    if (G > 1 && la) {
+#pragma unroll
+        for (int i = 1; i < V; ++i) v[i] = cmulf(v[i], tw_n<S>(tw, la * brev<LB>(i) * V));
+    }
+    dft_dit<V, S>(v);
+#pragma unroll
+    for (int lb = 0; lb < V; ++lb) buf[k1 * P + la + G * lb] = v[lb];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int kk = brev<LB>(i);
+        const float2 x = buf[kk * P + lane];
+        v[i] = kk ? cmulf(x, tw_n<S>(tw, lane * kk)) : x;
+    }
+    __syncwarp();
+    dft_dit<V, S>(v);
+}
+
+constexpr int WFFT_COL_WARPS = 4;   // adjacent columns per CTA (they share L2 sectors)
+constexpr int WFFT_INV_WARPS = 2;   // row pairs per CTA of the inverse row pass
+
+// Forward row pass of the real-input form, one row pair per CTA: the CTA's 256 threads
+// form the real inputs of rows 2b and 2b + 1 (the fold of the backprojection's partial
+// planes and the step-A epilogue, or a real image) into shared memory with many loads in
+// flight, then one warp transforms z = x_a + i x_b and writes X_a(k), X_b(k), k <= n/2.
+template <int V>
+__global__ void __launch_bounds__(FFT_THREADS)
+k_wfft_rows_fwd_packed(RowsInput<float> src, float2 *cbuf, const float2 *__restrict__ tw)
+{
+    constexpr int n = 32 * V, H = n / 2 + 1, G = 32 / V;
+    __shared__ __align__(16) float s_in[2 * n];
+    __shared__ __align__(16) float2 s_buf[(32 + G) * V];
+    __shared__ __align__(16) float2 s_tw[n];
+    const int ra = 2 * blockIdx.x;
+    pdl_wait();
+    pdl_trigger();
+    stage_tw<n>(s_tw, tw);
+    staged_copy(2 * n, [&](int e) { return rows_input_value(src, n, ra + (e >= n ? 1 : 0), e & (n - 1)); },
+                [&](int e, float x) { s_in[e] = x; });
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    float2 v[V];
+#pragma unroll
+    for (int m = 0; m < V; ++m) v[m] = make_float2(s_in[lane + 32 * m], s_in[n + lane + 32 * m]);
+    wfft_fwd<V, -1>(v, lane, s_buf, s_tw);
+#pragma unroll
+    for (int i = 0; i < V; ++i) s_buf[wfft_k<V>(lane, i)] = v[i];     // natural order (n <= (32 + G) V)
+    __syncwarp();
+    float2 *xa_row = cbuf + (size_t)ra * H, *xb_row = xa_row + H;
+    for (int k = lane; k < H; k += 32) {
+        const float2 z = s_buf[k], zm = s_buf[(n - k) & (n - 1)];
+        xa_row[k] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+        xb_row[k] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+}
+
+// Column pass of the real-input form: one warp per stored column c < n/2 + 1: forward
+// DFT, times the real symbol sym[k][c] in the scrambled layout, inverse DFT.
+template <int V>
+__global__ void __launch_bounds__(32 * WFFT_COL_WARPS)
+k_wfft_cols_packed(float2 *cbuf, const float *__restrict__ sym, const float2 *__restrict__ tw)
+{
+    constexpr int n = 32 * V, H = n / 2 + 1, G = 32 / V;
+    __shared__ __align__(16) float2 s_buf[WFFT_COL_WARPS][(32 + G) * V];
+    __shared__ __align__(16) float2 s_tw[n];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * WFFT_COL_WARPS + w;
+    const bool live = c < H;                             // warp-uniform
+    pdl_wait();
+    pdl_trigger();
+    float2 v[V];
+    float sy[V];                                         // the symbol, fetched with the data
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < V; ++m) v[m] = cbuf[(size_t)(lane + 32 * m) * H + c];
+#pragma unroll
+        for (int i = 0; i < V; ++i) sy[i] = __ldg(sym + (size_t)wfft_k<V>(lane, i) * n + c);
+    }
+    stage_tw<n>(s_tw, tw);
+    __syncthreads();
+    if (!live) return;
+    wfft_fwd<V, -1>(v, lane, s_buf[w], s_tw);
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        v[i].x *= sy[i];
+        v[i].y *= sy[i];
+    }
+    wfft_adj<V, +1>(v, lane, s_buf[w], s_tw);
+#pragma unroll
+    for (int m = 0; m < V; ++m) cbuf[(size_t)(lane + 32 * m) * H + c] = v[m];
+}
+
+// Inverse row pass of the real-input form: one warp per row pair, the coefficients loaded
+// straight into the scrambled layout (X(k) = conj X(n - k) beyond n/2), Z = X_a + i X_b
+// inverted, real part -> row 2c, imaginary part -> row 2c + 1, with the epilogue of
+// fft_rows_inv_packed_body (mode 0: out = v; mode 1: out += v; dout = v; bfloat16 copies;
+// transposed copies written as (row 2c, row 2c + 1) pairs).
+template <int V>
+__global__ void __launch_bounds__(32 * WFFT_INV_WARPS)
+k_wfft_rows_inv_packed(const float2 *__restrict__ cbuf, const float2 *__restrict__ tw, float *out, int mode,
+                       float *outT, float *dout, __nv_bfloat16 *outh, __nv_bfloat16 *outTh)
+{
+    constexpr int n = 32 * V, H = n / 2 + 1, G = 32 / V;
+    __shared__ __align__(16) float2 s_buf[WFFT_INV_WARPS][(32 + G) * V];
+    __shared__ __align__(16) float2 s_tw[n];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ra = 2 * (blockIdx.x * WFFT_INV_WARPS + w);     // < n: the grid covers n / 2 row pairs exactly
+    pdl_wait();
+    pdl_trigger();
+    stage_tw<n>(s_tw, tw);
+    const float2 *xa_row = cbuf + (size_t)ra * H, *xb_row = xa_row + H;
+    float2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int k = wfft_k<V>(lane, i);
+        const bool lo = k <= n / 2;
+        const int kk = lo ? k : n - k;
+        float2 xa = xa_row[kk], xb = xb_row[kk];
+        if (!lo) {
+            xa.y = -xa.y;
+            xb.y = -xb.y;
+        }
+        v[i] = make_float2(xa.x - xb.y, xa.y + xb.x);
+    }
+    float pa[V], pb[V];
+    const size_t ga = (size_t)ra * n, gb = ga + n;
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+        pa[m] = mode == 1 ? out[ga + lane + 32 * m] : 0.f;
+        pb[m] = mode == 1 ? out[gb + lane + 32 * m] : 0.f;
+    }
+    __syncthreads();
+    wfft_adj<V, +1>(v, lane, s_buf[w], s_tw);
+#pragma unroll
+    for (int m = 0; m < V; ++m) {
+        const int j = lane + 32 * m;
+        const float va = v[m].x, vb = v[m].y;
+        if (dout) {
+            dout[ga + j] = va;
+            dout[gb + j] = vb;
+        }
+        const float oa = va + pa[m], ob = vb + pb[m];
+        out[ga + j] = oa;
+        out[gb + j] = ob;
+        if (outh) {
+            outh[ga + j] = __float2bfloat16_rn(oa);
+            outh[gb + j] = __float2bfloat16_rn(ob);
+        }
+        if (outT) *reinterpret_cast<float2 *>(outT + (size_t)j * n + ra) = make_float2(oa, ob);
+        if (outTh) *reinterpret_cast<__nv_bfloat162 *>(outTh + (size_t)j * n + ra) = __floats2bfloat162_rn(oa, ob);
+    }
+}
+
+// The warp-level form covers FP32 plans with n = 256, 512 or 1024.
+int wfft_v(const ctr_plan *p)
+{
+    if (p->esize != 4) return 0;
+    return p->n == 256 ? 8 : p->n == 512 ? 16 : p->n == 1024 ? 32 : 0;
+}
+
+template <int V>
+void launch_wfft_packed(bool pdl, const RowsInput<float> &src, float2 *cb, const float *sym, const float2 *tw,
+                        float *out, int mode, float *outT, float *dout, __nv_bfloat16 *outh, __nv_bfloat16 *outTh,
+                        cudaStream_t s)
+{
+    constexpr int n = 32 * V, H = n / 2 + 1;
+    launch_pdl(pdl, k_wfft_rows_fwd_packed<V>, dim3(n / 2), dim3(FFT_THREADS), 0, s, src, cb, tw);
+    launch_pdl(pdl, k_wfft_cols_packed<V>, dim3((H + WFFT_COL_WARPS - 1) / WFFT_COL_WARPS), dim3(32 * WFFT_COL_WARPS), 0,
+               s, cb, sym, tw);
+    launch_pdl(pdl, k_wfft_rows_inv_packed<V>, dim3(n / (2 * WFFT_INV_WARPS)), dim3(32 * WFFT_INV_WARPS), 0, s,
+               (const float2 *)cb, tw, out, mode, outT, dout, outh, outTh);
+}
+
 __device__ __forceinline__ int find_slice_fft(const int *__restrict__ prefix, int ns, int b)
 {
     int lo = 0, hi = ns - 1;
@@ -730,6 +1109,8 @@ size_t packed_cols_smem(const ctr_plan *p) { return (2 * (size_t)packed_cols_per
 
 }  // namespace
 
+bool wfft_supported(const ctr_plan *p) { return wfft_v(p) != 0; }
+
 size_t fft_smem_bytes(const ctr_plan *p, int which)
 {
     return which == 0 ? fft_rows_smem(p->n, p->esize) : fft_cols_smem(p->n, p->esize);
@@ -763,6 +1144,18 @@ ctr_status launch_circulant(const ctr_plan *p, const T *in_real, bool in_is_cbuf
     // but the circulant one, whose 1-D transform is not the 2-D DFT); its packed rows
     // would overwrite unread input rows if the input were cbuf itself.
     if (p->precond_kind != 2 && (bp_in || !in_is_cbuf)) {
+        if constexpr (sizeof(T) == 4) {
+            const int V = p->fft_form == 0 ? wfft_v(p) : 0;
+            if (V) {
+                p->launches += 2;
+                const bool pdl = p->pdl != 0;
+                if (V == 8) launch_wfft_packed<8>(pdl, src, cb, sym, tw, out, mode, outT, dout, outh, outTh, s);
+                else if (V == 16) launch_wfft_packed<16>(pdl, src, cb, sym, tw, out, mode, outT, dout, outh, outTh, s);
+                else launch_wfft_packed<32>(pdl, src, cb, sym, tw, out, mode, outT, dout, outh, outTh, s);
+                CTR_CHECK_LAUNCH("k_wfft_packed");
+                return CTR_OK;
+            }
+        }
         const int prp = packed_rows_per_cta(p), pcw = packed_cols_per_cta(p);
         const int pgr = (n + prp - 1) / prp, pgc = (n / 2 + 1 + pcw - 1) / pcw;
         const size_t psr = packed_rows_smem(p), psc = packed_cols_smem(p);

@@ -575,6 +575,8 @@ template <typename S>
 __global__ void __launch_bounds__(256)
 k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ ubar, int n)
 {
+    pdl_wait();
+    pdl_trigger();
     orbit_image_body<S>(u, ubar, n, blockIdx.x, blockIdx.y);
 }
 
@@ -583,6 +585,8 @@ k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ 
 __global__ void __launch_bounds__(256)
 k_orbit_image_tv(const float *__restrict__ u, OrbitRec<float>::type *__restrict__ ubar, int n, TvDualJob<float> tv)
 {
+    pdl_wait();
+    pdl_trigger();
     orbit_image_body<float>(u, ubar, n, blockIdx.x, blockIdx.y);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int r = ty; r < 32; r += 8) {
@@ -817,6 +821,8 @@ __global__ void __launch_bounds__(32 * SLOTS * SEGS, CTR_ORBIT_MINB * ORBIT_SLOT
 k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
                 const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
 {
+    pdl_wait();
+    pdl_trigger();
     forward_orbit_body<S, false, SEGS, SLOTS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
 }
 
@@ -863,6 +869,8 @@ k_forward_orbit_staged(const typename OrbitRec<S>::type *__restrict__ ubar, int 
     int *s_qlo = reinterpret_cast<int *>(stage + 2 * STG_ROWS * wmax);  // [nst_max]
     int *s_qhi = s_qlo + nst_max;
     __shared__ int s_mlo, s_mhi;
+    pdl_wait();
+    pdl_trigger();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x * 31;
     const int k = kb + lane - 1;                 // this lane's interval [k, k + 1)
@@ -983,8 +991,9 @@ void launch_forward_orbit_staged(const ctr_plan *p, const typename OrbitRec<S>::
 {
     const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + STG_JOBS - 1) / STG_JOBS);
     const int rec = (int)sizeof(typename OrbitRec<S>::type);
-    k_forward_orbit_staged<S><<<grid, 32 * STG_JOBS, stg_smem_bytes(p->stg_wmax, p->stg_nst, rec), s>>>(
-        ub, p->n, p->n_jobs, p->M, p->d_jobs, epi, p->stg_wmax, p->stg_nst);
+    launch_pdl(p->pdl != 0, k_forward_orbit_staged<S>, grid, dim3(32 * STG_JOBS),
+               stg_smem_bytes(p->stg_wmax, p->stg_nst, rec), s, ub, p->n, p->n_jobs, p->M,
+               (const OrbitJob *)p->d_jobs, epi, p->stg_wmax, p->stg_nst);
 }
 
 template <typename S, int SLOTS, int SEGS>
@@ -992,7 +1001,8 @@ void launch_forward_orbit_shape(const ctr_plan *p, const typename OrbitRec<S>::t
                                 cudaStream_t s)
 {
     const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + SLOTS - 1) / SLOTS);
-    k_forward_orbit<S, SLOTS, SEGS><<<grid, 32 * SLOTS * SEGS, 0, s>>>(ub, p->n, p->n_jobs, p->M, p->d_jobs, epi);
+    launch_pdl(p->pdl != 0, k_forward_orbit<S, SLOTS, SEGS>, grid, dim3(32 * SLOTS * SEGS), 0, s, ub, p->n, p->n_jobs,
+               p->M, (const OrbitJob *)p->d_jobs, epi);
 }
 
 template <typename S>
@@ -1263,6 +1273,8 @@ __global__ void __launch_bounds__(32 * OBP_TY, CTR_OBP_MINB)
 k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
                     const OrbitJob *__restrict__ jobs, float *__restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     obp_body<S>(g, n, M, wstride, jobs_per_group, n_jobs, jobs, part, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
@@ -1381,8 +1393,8 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
             float *part = (float *)p->obp_part;
             p->launches++;
             const int jpg = (p->n_jobs + G - 1) / G;
-            k_backproject_orbit<S><<<grid, 32 * OBP_TY, obp_smem(p->wstride, jpg), s>>>(
-                g, p->n, p->M, p->wstride, jpg, p->n_jobs, p->d_jobs, part);
+            launch_pdl(p->pdl != 0, k_backproject_orbit<S>, grid, dim3(32 * OBP_TY), obp_smem(p->wstride, jpg), s,
+                       g, p->n, p->M, p->wstride, jpg, p->n_jobs, (const OrbitJob *)p->d_jobs, part);
             CTR_CHECK_LAUNCH("k_backproject_orbit");
             if (!defer_reduce) {
                 const size_t nn = (size_t)p->n * p->n;
@@ -1426,10 +1438,10 @@ ctr_status fwd_impl(const ctr_plan *p, const S *u, const S *uT, const ForwardEpi
             p->launches++;
             const dim3 og((p->n + 31) / 32, (p->n + 31) / 32);
             if constexpr (std::is_same<S, float>::value) {
-                if (tv) k_orbit_image_tv<<<og, 256, 0, s>>>(u, ub, p->n, *tv);
-                else k_orbit_image<S><<<og, 256, 0, s>>>(u, ub, p->n);
+                if (tv) launch_pdl(p->pdl != 0, k_orbit_image_tv, og, dim3(256), 0, s, u, ub, p->n, *tv);
+                else launch_pdl(p->pdl != 0, k_orbit_image<S>, og, dim3(256), 0, s, u, ub, p->n);
             } else {
-                k_orbit_image<S><<<og, 256, 0, s>>>(u, ub, p->n);
+                launch_pdl(p->pdl != 0, k_orbit_image<S>, og, dim3(256), 0, s, u, ub, p->n);
             }
             CTR_CHECK_LAUNCH("k_orbit_image");
             p->launches++;
@@ -1467,7 +1479,7 @@ ctr_status configure_radon(const ctr_plan *p)
     if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, osm);
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
-    if (st == CTR_OK && p->orbit) {
+    if (st == CTR_OK && p->orbit && p->stg_wmax > 0) {
         st = raise_smem_limit(k_forward_orbit_staged<float>, stg_smem_bytes(p->stg_wmax, p->stg_nst, 16));
         if (st == CTR_OK)
             st = raise_smem_limit(k_forward_orbit_staged<__nv_bfloat16>, stg_smem_bytes(p->stg_wmax, p->stg_nst, 8));

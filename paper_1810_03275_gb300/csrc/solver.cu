@@ -528,12 +528,19 @@ ctr_status run_graphed(ctr_plan *p, int count, int blk, F &&step, cudaStream_t s
 
 // The plan state that decides which kernels (and shapes) the projector and FFT
 // launches use, for graph keys.
+// Everything a captured graph bakes in besides the launch arguments: the kernels chosen by
+// the tuning hooks (group split, forward launch shape, preconditioner form) and the
+// preconditioner kind.  A graph recorded under other settings is never replayed.
 inline void plan_state_key(const ctr_plan *p, std::vector<double> &k)
 {
     k.push_back((double)p->bp_groups);
     k.push_back((double)p->obp_groups);
     k.push_back((double)p->precond_kind);
     k.push_back((double)p->alg3);
+    k.push_back((double)p->fwd_slots);
+    k.push_back((double)p->fwd_segs);
+    k.push_back((double)p->fft_form);
+    k.push_back((double)p->pdl);
 }
 
 #ifndef CTR_POWER_GRAPH_BLOCK

@@ -69,7 +69,8 @@ EXPORTS = ["ctr_plan_create", "ctr_plan_destroy", "ctr_default_params", "ctr_las
            "tv_cp_solve", "tv_pdrq2_solve", "ctr_metal_trace", "tv_mar_solve",
            "tv_admm_solve", "ctr_ramp_filter", "ctr_fbp", "tv_pd_vjp_segment", "ctr_plan_history",
            "ctr_fp32_fma_rate", "ctr_batch_set_mode", "ctr_batch_get_mode", "ctr_batch_persistent_ctas",
-           "ctr_plan_set_fwd_shape", "ctr_plan_get_fwd_shape"]
+           "ctr_plan_set_fwd_shape", "ctr_plan_get_fwd_shape", "ctr_plan_set_fft_form", "ctr_plan_get_fft_form",
+           "ctr_plan_set_launch_overlap", "ctr_plan_get_launch_overlap"]
 
 
 def load(path: str = LIB_PATH):
@@ -149,6 +150,14 @@ def load(path: str = LIB_PATH):
         lib.ctr_plan_set_fwd_shape.restype = ctypes.c_int
         lib.ctr_plan_get_fwd_shape.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_int)]
         lib.ctr_plan_get_fwd_shape.restype = ctypes.c_int
+        lib.ctr_plan_set_fft_form.argtypes = [vp, ctypes.c_int]
+        lib.ctr_plan_set_fft_form.restype = ctypes.c_int
+        lib.ctr_plan_get_fft_form.argtypes = [vp]
+        lib.ctr_plan_get_fft_form.restype = ctypes.c_int
+        lib.ctr_plan_set_launch_overlap.argtypes = [vp, ctypes.c_int]
+        lib.ctr_plan_set_launch_overlap.restype = ctypes.c_int
+        lib.ctr_plan_get_launch_overlap.argtypes = [vp]
+        lib.ctr_plan_get_launch_overlap.restype = ctypes.c_int
         lib.ctr_batch_set_mode.argtypes = [vp, ctypes.c_int, ctypes.c_ulonglong]
         lib.ctr_batch_set_mode.restype = ctypes.c_int
         lib.ctr_batch_get_mode.argtypes = [vp]
@@ -328,6 +337,22 @@ class Plan:
 
     def set_fwd_shape(self, jobs_per_cta: int, segments: int):
         _check(load().ctr_plan_set_fwd_shape(self._h, int(jobs_per_cta), int(segments)))
+
+    @property
+    def fft_form(self) -> int:
+        """Kernels of the preconditioner passes: 0 warp-level (FP32, n = 256/512/1024), 1 CTA-level."""
+        return int(load().ctr_plan_get_fft_form(self._h))
+
+    def set_fft_form(self, form: int):
+        _check(load().ctr_plan_set_fft_form(self._h, int(form)))
+
+    @property
+    def launch_overlap(self) -> int:
+        """1: the iteration's kernels use programmatic dependent launch (default), 0: plain stream order."""
+        return int(load().ctr_plan_get_launch_overlap(self._h))
+
+    def set_launch_overlap(self, on: int):
+        _check(load().ctr_plan_set_launch_overlap(self._h, int(on)))
 
     def rh_adjoint(self, g, u=None, stream=None):
         u = self.empty_image() if u is None else u

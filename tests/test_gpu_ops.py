@@ -31,7 +31,7 @@ def test_grad_div(ct, n, h, dtype):
 
 @pytest.mark.parametrize("dtype,n", [("f64", 64), ("f32", 64), ("f32", 48), ("f32", 384), ("f32", 512),
                                      ("f64", 27), ("f32", 1), ("f32", 2048), ("f32", 81), ("f64", 3),
-                                     ("f32", 6), ("f64", 1024)])
+                                     ("f32", 6), ("f64", 1024), ("f32", 256), ("f32", 1024)])
 def test_precond_apply(ct, n, dtype):
     """M^{-1} y of Alg. 4 vs numpy's FFT on the oracle's symbol (radix 2, 3, 4 paths; the
     real-input form with paired rows and n/2 + 1 columns, odd n included)."""
@@ -78,3 +78,42 @@ def test_power_iterations(ct, dtype):
     lam_ref = oracle.power_c(geo, beta_ref, eps, 30, margin=1.0)
     lam = plan.power_lambda(beta_ref, eps, 30)
     assert lam == pytest.approx(lam_ref, rel=1e-5 if dtype == "f32" else 1e-11)
+
+
+@pytest.mark.parametrize("n", [256, 512, 1024])
+def test_fft_forms_agree(ct, n):
+    """The warp-level preconditioner passes (form 0: one warp per row pair / column, the
+    four-step factorisation n = 32 x n/32) against the CTA-level Stockham passes (form 1)
+    and the oracle: precond_apply, and a few Alg. 4 iterations (the fused fold of the
+    backprojection into the first pass, u += in the last) on FP32 and BF16 plans."""
+    import torch
+    sigma, tau, c, eps = 1.3, 0.35, 0.7, np.pi / n
+    prm = ct.default_params(sigma=sigma, tau=tau, c=c, eps=eps)
+    plan = ct.Plan(n, 4, 5)
+    assert plan.fft_form == 0
+    y = np.random.default_rng(n + 1).standard_normal((n, n))
+    a = to_np(plan.precond_apply(to_dev(y, torch.float32), prm))
+    plan.set_fft_form(1)
+    assert plan.fft_form == 1
+    b = to_np(plan.precond_apply(to_dev(y, torch.float32), prm))
+    ref = oracle.precond_apply(y, oracle.precond_symbol(n, sigma, tau, c, eps))
+    assert rel_l2(a, ref) < 2e-6
+    assert rel_l2(a, b) < 2e-6
+    with pytest.raises(ct.CtrError):
+        plan.set_fft_form(2)
+    N = max(8, n // 4)
+    M = int(np.ceil(np.sqrt(2) * n))
+    th = np.arange(N) * (np.pi / N)
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal((N, M)).astype(np.float32)
+    mask = (rng.random((N, M)) < 0.05).astype(np.uint8)
+    for dtype in ("f32", "bf16"):
+        us = []
+        for form in (0, 1):
+            pl = ct.Plan(n, N, M, angles=th, dtype=dtype)
+            pl.set_fft_form(form)
+            p2 = ct.default_params(beta=float(M), c=1.0, eps=np.pi / n)
+            u, _ = pl.tv_pd_solve(to_dev(f, torch.float32), torch.as_tensor(mask, device="cuda"), 0.3, 0.05, 6,
+                                  params=p2)
+            us.append(to_np(u))
+        assert rel_l2(us[0], us[1]) < (2e-6 if dtype == "f32" else 2e-3), dtype

@@ -202,3 +202,20 @@ def test_staged_forward_shape(ct, geom):
         ref = oracle.rh_forward(u.double().cpu().numpy(), oracle.Geometry(n, N, M, h=h, ds=ds, theta=th))
         assert rel_l2(got, base) < 2e-6, dtype
         assert rel_l2(got, ref) < 1e-5, dtype
+
+
+def test_staged_shape_refused_where_window_exceeds_shared_memory(ct):
+    """A plan whose staged window would not fit one CTA's shared memory (2048^2, 4 views)
+    is still created, and refuses the staged shape with CTR_EUNSUPPORTED; the default
+    shape projects as before."""
+    import torch
+    n, N, M = 2048, 4, 2897
+    plan = ct.Plan(n, N, M, angles=np.arange(N) * (np.pi / N))
+    if plan.symmetric_jobs == 0:
+        pytest.skip("per-angle path")
+    with pytest.raises(ct.CtrError) as e:
+        plan.set_fwd_shape(4, 1)
+    assert e.value.status == -6      # CTR_EUNSUPPORTED
+    u = torch.ones((n, n), device="cuda")
+    g = to_np(plan.rh_forward(u))
+    assert np.all(np.isfinite(g)) and g.max() > 0
