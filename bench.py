@@ -455,6 +455,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16-vs-FP32 2048^2 timing")
+    ap.add_argument("--shape", default=None, help="G,J,S: backprojection groups and forward shape instead of the "
+                                                  "tuner (for runs under a profiler)")
     ap.add_argument("--ops", default=None, help="n,views,bins,dtype[,JxS]: only run R_h and R_h^* of that plan "
                     "--steps times (for a profiler; JxS a forward shape), print nothing")
     args = ap.parse_args()
@@ -480,7 +482,13 @@ def main():
     mask = torch.as_tensor(pr.mask, device="cuda")
     u = torch.empty((n, n), dtype=torch.float32, device="cuda")
     from paper_1810_03275_gb300 import autotune
-    tuned = autotune.tune_solve(plan, f, mask, pr.alpha, pr.delta, iters=40, use_cache=False)   # untimed
+    if args.shape:                                  # a fixed launch setting (profiling: no timing under a profiler)
+        g, j, sg = (int(x) for x in args.shape.split(","))
+        plan.set_bp_groups(g)
+        plan.set_fwd_shape(j, sg)
+        tuned = {"bp_groups": g, "fwd_shape": [j, sg], "fixed": True}
+    else:
+        tuned = autotune.tune_solve(plan, f, mask, pr.alpha, pr.delta, iters=40, use_cache=False)   # untimed
     prm = ct.default_params()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
