@@ -234,12 +234,27 @@ __global__ void k_start_pattern(T *x, int n)
     }
 }
 
+// A block-uniform value evaluated once by thread 0 and broadcast through shared memory:
+// FP64 arithmetic (a square root, a division) runs at a small fraction of the FP32 rate
+// on this GPU, so a per-thread evaluation of a uniform FP64 expression costs more than the
+// kernel's own work.
+template <typename T, typename F>
+__device__ __forceinline__ T block_uniform(F f)
+{
+    __shared__ T s_val;
+    if (threadIdx.x == 0) s_val = f();
+    __syncthreads();
+    return s_val;
+}
+
 // x = y / sqrt(scal[idx])   (scal holds a squared norm)
 template <typename T>
 __global__ void k_normalize(const T *__restrict__ y, size_t len, const double *__restrict__ scal, int idx, T *x)
 {
-    const double s = scal[idx];
-    const T inv = s > 0 ? (T)(1.0 / sqrt(s)) : T(0);
+    const T inv = block_uniform<T>([&] {
+        const double s = scal[idx];
+        return s > 0 ? (T)(1.0 / sqrt(s)) : T(0);
+    });
     for (size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x; r < len; r += (size_t)gridDim.x * blockDim.x)
         x[r] = y[r] * inv;
 }
@@ -370,7 +385,7 @@ inline int grid_for(size_t len, int threads = 256, int cap = 2048)
 template <typename T>
 ctr_status dot2(ctr_plan *p, const T *a, const T *b, size_t len, double *out_dev, cudaStream_t s)
 {
-    const int nb = grid_for(len, RED_THREADS, p->red_blocks);
+    const int nb = grid_for(len, RED_THREADS * 8, p->red_blocks);   // 8 elements per thread: fewer FP64 tree adds
     p->launches++;
     k_dot2<T><<<nb, RED_THREADS, 0, s>>>(a, b, len, p->d_red);
     p->launches++;
@@ -866,8 +881,10 @@ template <typename T>
 __global__ void k_cg_step(T *u, T *r, const T *__restrict__ pd, const T *__restrict__ Ap, size_t nn, T *Ru,
                           const T *__restrict__ Rp, size_t nm, const double *__restrict__ sc, int slot_rz)
 {
-    const double pap = sc[CG_SLOT_PAP];
-    const T alpha = (T)(pap != 0.0 ? sc[slot_rz] / pap : 0.0);
+    const T alpha = block_uniform<T>([&] {
+        const double pap = sc[CG_SLOT_PAP];
+        return (T)(pap != 0.0 ? sc[slot_rz] / pap : 0.0);
+    });
     const size_t total = nm > nn ? nm : nn;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         if (e < nn) {
@@ -883,8 +900,10 @@ template <typename T>
 __global__ void k_cg_dir(const T *__restrict__ z, T *pd, size_t nn, const double *__restrict__ sc, int slot_old,
                          int slot_new)
 {
-    const double old = sc[slot_old];
-    const T b = (T)(old != 0.0 ? sc[slot_new] / old : 0.0);
+    const T b = block_uniform<T>([&] {
+        const double old = sc[slot_old];
+        return (T)(old != 0.0 ? sc[slot_new] / old : 0.0);
+    });
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x)
         pd[e] = z[e] + b * pd[e];
 }
