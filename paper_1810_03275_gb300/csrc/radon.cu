@@ -313,6 +313,28 @@ __device__ __forceinline__ void forward_epilogue(const ForwardEpi<T> &epi, size_
     if (epi.t1) epi.t1[r] = t;
 }
 
+// The same epilogue (modes 1 and 2) on operands fetched ahead: vb = v1b[r], w, a, lo, hi.
+__device__ __forceinline__ void forward_epilogue_pre(const ForwardEpi<float> &epi, size_t r, float val, float vb,
+                                                     float w, float a, float lo, float hi)
+{
+    const float sigma = epi.sigma;
+    if (epi.mode == 2) {
+        const float z = vb + sigma * (val * epi.scale);
+        epi.v1b[r] = data_resolvent(z, sigma, w, a, lo, hi);
+        return;
+    }
+    const float Ru = val * epi.scale;
+    const float v1 = vb + sigma * Ru;
+    const float z = 2.f * v1 - vb;
+    const float t = data_resolvent(z, sigma, w, a, lo, hi);
+    const float vbn = vb + t - v1;
+    epi.Ru[r] = Ru;
+    epi.v1b[r] = vbn;
+    if (epi.y1h) epi.y1h[r] = __float2bfloat16_rn(vbn + sigma * Ru);
+    else epi.y1[r] = vbn + sigma * Ru;
+    if (epi.t1) epi.t1[r] = t;
+}
+
 // One row of the march: the NC candidate pixels q, q+1, ... of the lane's interval.
 // EXACT1: the first candidate is always inside the interval (A <= 2^F, i.e. h <= ds).
 template <typename T, typename S, int NC, bool EXACT1>
@@ -595,6 +617,16 @@ k_orbit_image_tv(const float *__restrict__ u, OrbitRec<float>::type *__restrict_
     }
 }
 
+// Asynchronous copies global -> shared (cp.async): one 4-byte element (src_size 0 stores
+// zero and reads nothing), commit and wait on this thread's groups.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Paired FP32 arithmetic (add / sub / fma on two lanes of a 64-bit register pair, one
 // instruction for two values; each lane rounds exactly as the scalar instruction).
 #ifndef CTR_F32X2
@@ -721,11 +753,32 @@ __device__ __forceinline__ void march_orbit_rows(const R *__restrict__ ub, int n
 }
 
 __device__ __forceinline__ void orbit_out(const ForwardEpi<float> &epi, int l, int M, int k, int lane, float Su,
-                                          float Sf)
+                                          float Sf, const float *pre = nullptr)
 {
     const float Bk = Sf - Su, Ak = Su - Bk;
     const float Bprev = __shfl_up_sync(0xffffffffu, Bk, 1);
-    if (l >= 0 && lane >= 1 && k < M) forward_epilogue(epi, (size_t)l * M + k, Ak + Bprev);
+    if (l >= 0 && lane >= 1 && k < M) {
+        if (pre) forward_epilogue_pre(epi, (size_t)l * M + k, Ak + Bprev, pre[0], pre[32], pre[64], pre[96], pre[128]);
+        else forward_epilogue(epi, (size_t)l * M + k, Ak + Bprev);
+    }
+}
+
+// The data-dual epilogue's per-bin operands (v1b, w, a, lo, hi) of the lane's four angles,
+// copied into shared memory [angle][operand][lane] at the start of the march so that their
+// latency is hidden behind it (modes 1 and 2 read them; each (angle, bin) belongs to one lane).
+__device__ __forceinline__ void orbit_epi_prefetch(const ForwardEpi<float> &epi, int4 ls, int M, int k, int lane,
+                                                   float *s)
+{
+    const int l4[4] = {ls.x, ls.y, ls.z, ls.w};
+    const float *src[5] = {epi.v1b, epi.dw, epi.da, epi.dlo, epi.dhi};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const bool ok = l4[c] >= 0 && lane >= 1 && k < M;
+        const size_t r = ok ? (size_t)l4[c] * M + k : 0;
+#pragma unroll
+        for (int o = 0; o < 5; ++o) cp_async4(s + (c * 5 + o) * 32 + lane, src[o] + r, ok);
+    }
+    cp_async_commit();
 }
 
 #ifndef CTR_ORBIT_SEGS
@@ -763,9 +816,12 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
     const bool active = jb < n_jobs && kb < M;        // warp-uniform
     float4 Su = make_float4(0.f, 0.f, 0.f, 0.f), Sf = Su;
     int4 ls = make_int4(-1, -1, -1, -1);             // the job's angles
+    __shared__ float s_epi[SLOTS][4 * 5 * 32];
+    const bool pre = (epi.mode == 1 || epi.mode == 2) && seg == 0 && active;   // warp-uniform
     if (active) {
         const AngleMarch am = jobs[jb].am;
         ls = *reinterpret_cast<const int4 *>(jobs[jb].l);
+        if (pre) orbit_epi_prefetch(epi, ls, M, k, lane, s_epi[slot]);
         const float Q0 = (float)k * am.kA - am.oA;
         int mlo, mhi;
         rows_in<true>(Q0, am.binv, -3.f, (float)n + 1.f, n, mlo, mhi);
@@ -807,10 +863,12 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
         }
     }
     if (!active) return;
-    orbit_out(epi, ls.x, M, k, lane, Su.x, Sf.x);
-    orbit_out(epi, ls.y, M, k, lane, Su.y, Sf.y);
-    orbit_out(epi, ls.z, M, k, lane, Su.z, Sf.z);
-    orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w);
+    if (pre) cp_async_wait<0>();                      // this lane's own copies: no barrier needed
+    const float *pe = pre ? s_epi[slot] + lane : nullptr;
+    orbit_out(epi, ls.x, M, k, lane, Su.x, Sf.x, pe ? pe + 0 * 160 : nullptr);
+    orbit_out(epi, ls.y, M, k, lane, Su.y, Sf.y, pe ? pe + 1 * 160 : nullptr);
+    orbit_out(epi, ls.z, M, k, lane, Su.z, Sf.z, pe ? pe + 2 * 160 : nullptr);
+    orbit_out(epi, ls.w, M, k, lane, Su.w, Sf.w, pe ? pe + 3 * 160 : nullptr);
 }
 
 // SLOTS adjacent jobs per CTA (their rays nearly coincide, so they share the orbit
@@ -839,9 +897,6 @@ k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int 
 // the block's last row, last pixel of interval kb + 30 on its first row]; the plan holds
 // the widest window any block can need (stg_window), which sizes the row pitch.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 constexpr int STG_JOBS = 4;
 constexpr int STG_ROWS = 8;
 
@@ -1062,13 +1117,6 @@ size_t obp_smem(int wstride, int jobs_per_group)
     return std::max(std::max(stage, async), tr);
 }
 
-// cp.async of one 4-byte element into shared memory; src_size 0 stores zero.
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
-}
-
 // The FP32 symmetric backprojection with asynchronous staging: the group's job tables
 // are built once; chunk c + 1's four sinogram rows per job are copied raw into the
 // second of two shared buffers (cp.async, zero-filled outside the detector) while
@@ -1283,6 +1331,8 @@ k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs
 __global__ void __launch_bounds__(256)
 k_bp_fold(const float *__restrict__ part, int groups, int n, BackprojEpi<float> epi)
 {
+    pdl_wait();
+    pdl_trigger();
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / n), j = (int)(e % n);
@@ -1401,7 +1451,7 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
                 int blocks = (int)((nn + 255) / 256);
                 if (blocks > 4096) blocks = 4096;
                 p->launches++;
-                k_bp_fold<<<blocks, 256, 0, s>>>(part, G, p->n, epi);
+                launch_pdl(p->pdl != 0, k_bp_fold, dim3(blocks), dim3(256), 0, s, (const float *)part, G, p->n, epi);
                 CTR_CHECK_LAUNCH("k_bp_fold");
             }
             return CTR_OK;

@@ -251,6 +251,8 @@ __device__ __forceinline__ T block_uniform(F f)
 template <typename T>
 __global__ void k_normalize(const T *__restrict__ y, size_t len, const double *__restrict__ scal, int idx, T *x)
 {
+    pdl_wait();
+    pdl_trigger();
     const T inv = block_uniform<T>([&] {
         const double s = scal[idx];
         return s > 0 ? (T)(1.0 / sqrt(s)) : T(0);
@@ -290,6 +292,8 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], unsigned maxmask, 
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS) k_finalize(const double *__restrict__ part, int nblk, unsigned maxmask, double *out)
 {
+    pdl_wait();
+    pdl_trigger();
     double v[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = ((maxmask >> q) & 1u) ? -INFINITY : 0.0;
@@ -306,6 +310,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(const double *__restri
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_dot2(const T *__restrict__ a, const T *__restrict__ b, size_t len, double *part)
 {
+    pdl_wait();
+    pdl_trigger();
     double v[2] = {0.0, 0.0};
     for (size_t r = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; r < len; r += (size_t)gridDim.x * RED_THREADS) {
         const double x = (double)a[r], y = (double)b[r];
@@ -387,9 +393,9 @@ ctr_status dot2(ctr_plan *p, const T *a, const T *b, size_t len, double *out_dev
 {
     const int nb = grid_for(len, RED_THREADS * 8, p->red_blocks);   // 8 elements per thread: fewer FP64 tree adds
     p->launches++;
-    k_dot2<T><<<nb, RED_THREADS, 0, s>>>(a, b, len, p->d_red);
+    launch_pdl(p->pdl != 0, k_dot2<T>, dim3(nb), dim3(RED_THREADS), 0, s, a, b, len, p->d_red);
     p->launches++;
-    k_finalize<2><<<1, RED_THREADS, 0, s>>>(p->d_red, nb, 0u, out_dev);
+    launch_pdl(p->pdl != 0, k_finalize<2>, dim3(1), dim3(RED_THREADS), 0, s, (const double *)p->d_red, nb, 0u, out_dev);
     CTR_CHECK_LAUNCH("k_dot2");
     return CTR_OK;
 }
@@ -584,7 +590,8 @@ ctr_status power_beta(ctr_plan *p, int iters, double *beta, cudaStream_t s)
         if ((s2 = op_adjoint<T>(p, g, y, 1.0, s)) != CTR_OK) return s2;
         if ((s2 = dot2<T>(p, x, y, nn, p->d_scal, s)) != CTR_OK) return s2;
         p->launches++;
-        k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, x);
+        launch_pdl(p->pdl != 0, k_normalize<T>, dim3(grid_for(nn)), dim3(256), 0, s, (const T *)y, nn,
+               (const double *)p->d_scal, 1, x);
         return CTR_OK;
     };
     std::vector<double> key = {3.0, (double)POWER_GRAPH_BLOCK};
@@ -636,7 +643,8 @@ ctr_status power_lambda(ctr_plan *p, double beta, double eps, int iters, double 
             return s2;
         if ((s2 = dot2<T>(p, z, y, nn, p->d_scal, s)) != CTR_OK) return s2;
         p->launches++;
-        k_normalize<T><<<grid_for(nn), 256, 0, s>>>(y, nn, p->d_scal, 1, z);
+        launch_pdl(p->pdl != 0, k_normalize<T>, dim3(grid_for(nn)), dim3(256), 0, s, (const T *)y, nn,
+                   (const double *)p->d_scal, 1, z);
         return CTR_OK;
     };
     std::vector<double> key = {4.0, (double)POWER_GRAPH_BLOCK, ib};
