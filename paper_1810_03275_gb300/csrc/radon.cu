@@ -603,17 +603,78 @@ k_orbit_image(const S *__restrict__ u, typename OrbitRec<S>::type *__restrict__ 
 }
 
 // The orbit image and, for the pixels (m, q) of the CTA's tile, the TV dual step of
-// Alg. 4 (both read u; each pixel's TV step runs exactly once over the grid).
+// Alg. 4 (both read u; each pixel's TV step runs exactly once over the grid).  The TV
+// operands (bar v2, and bar u for Alg. 5) are fetched before the tile barrier, and u with
+// its forward neighbours comes from tile A (rows m, columns q, plus a one-pixel halo), so
+// the kernel waits on global memory once; the arithmetic is that of tv_dual_at.
 __global__ void __launch_bounds__(256)
 k_orbit_image_tv(const float *__restrict__ u, OrbitRec<float>::type *__restrict__ ubar, int n, TvDualJob<float> tv)
 {
     pdl_wait();
     pdl_trigger();
-    orbit_image_body<float>(u, ubar, n, blockIdx.x, blockIdx.y);
+    __shared__ float tA[33][33], tB[32][33], tC[32][33], tD[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int q0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+    const size_t nn = (size_t)n * n;
+    float vbx[4], vby[4], ubv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int m = m0 + ty + 8 * k, q = q0 + tx;
+        vbx[k] = vby[k] = ubv[k] = 0.f;
+        if (m < n && q < n) {
+            const size_t e = (size_t)m * n + q;
+            vbx[k] = tv.v2b[e];
+            vby[k] = tv.v2b[e + nn];
+            if (tv.ub) ubv[k] = tv.ub[e];
+        }
+    }
     for (int r = ty; r < 32; r += 8) {
-        const int m = blockIdx.y * 32 + r, q = blockIdx.x * 32 + tx;
-        if (m < n && q < n) tv_dual_at(tv, m, q);
+        const int mr = m0 + r, qc = q0 + tx;          // tiles A, B: rows m, columns q
+        if (mr < n && qc < n) {
+            tA[r][tx] = u[(size_t)mr * n + qc];
+            tB[r][tx] = u[(size_t)(n - 1 - mr) * n + qc];
+        }
+        const int qr = q0 + r, mc = m0 + tx;          // tiles C, D: rows q, columns m
+        if (qr < n && mc < n) {
+            tC[r][tx] = u[(size_t)qr * n + mc];
+            tD[r][tx] = u[(size_t)(n - 1 - qr) * n + mc];
+        }
+    }
+    if (ty == 0 && m0 + 32 < n && q0 + tx < n) tA[32][tx] = u[(size_t)(m0 + 32) * n + q0 + tx];   // halo row
+    if (ty == 1 && q0 + 32 < n && m0 + tx < n) tA[tx][32] = u[(size_t)(m0 + tx) * n + q0 + 32];   // halo column
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int m = m0 + r, q = q0 + tx;
+        if (m < n && q < n) ubar[(size_t)m * n + q] = make_rec(tC[tx][r], tD[tx][r], tA[r][tx], tB[r][tx]);
+    }
+    const float st = tv.sigma * tv.tau;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = ty + 8 * k, m = m0 + r, q = q0 + tx;
+        if (m >= n || q >= n) continue;
+        const size_t e = (size_t)m * n + q;
+        const float c = tA[r][tx];
+        const float gx = (m < n - 1) ? (tA[r + 1][tx] - c) * tv.inv_h : 0.f;
+        const float gy = (q < n - 1) ? (tA[r][tx + 1] - c) * tv.inv_h : 0.f;
+        const float bx = vbx[k], by = vby[k];
+        const float vx = bx + st * gx, vy = by + st * gy;
+        const float zx = 2.f * vx - bx, zy = 2.f * vy - by;
+        float tx2 = 0.f, ty2 = 0.f;
+        if (tv.lam > 0.f) {
+            const float den = fmax(1.f, tv.tau * sqrt(zx * zx + zy * zy) / tv.lam);
+            tx2 = zx / den;
+            ty2 = zy / den;
+        }
+        const float nbx = bx + tx2 - vx, nby = by + ty2 - vy;
+        tv.v2b[e] = nbx;
+        tv.v2b[e + nn] = nby;
+        tv.y2[e] = nbx + st * gx;
+        tv.y2[e + nn] = nby + st * gy;
+        if (tv.t2) {
+            tv.t2[e] = tx2;
+            tv.t2[e + nn] = ty2;
+        }
+        if (tv.ub) tv.ub[e] = ubv[k] + fmax(2.f * c - ubv[k], 0.f) - c;
     }
 }
 
