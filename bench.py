@@ -560,6 +560,24 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         pc_ms[f"form{form}"] = a.elapsed_time(b) / reps
+        # the same calls replayed from a CUDA graph: the GPU time without the host's launch cost
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            plan.precond_apply(u, prm_pc, xo)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            for _ in range(reps):
+                plan.precond_apply(u, prm_pc, xo)
+        graph.replay()
+        torch.cuda.synchronize()
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pc_ms[f"form{form}_graph"] = a.elapsed_time(b) / reps
+        del graph
     plan.set_fft_form(form0)
     hbm_peak, peak_kind = peaks()
     nominal = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6                # FMA/s, FP32 lanes x max clock
@@ -568,8 +586,12 @@ def main():
     kernels = {k: {"ms": 1e3 * v, "kernels": call_kernels[k], "gsamples_per_s": n * n * N / v / 1e9,
                    "gfma_s": fmas / v / 1e9, "fma_frac": fmas / v / fma_peak, "hbm_gbs": bytes_alg / v / 1e9,
                    "hbm_frac": bytes_alg / v / 1e9 / hbm_peak} for k, v in kt.items()}
-    kernels["precond_apply"] = {"ms": pc_ms.get(f"form{plan.fft_form}"), "form": plan.fft_form, "forms_ms": pc_ms,
-                                "note": "form 0: warp-level passes, form 1: CTA-level Stockham passes"}
+    kernels["precond_apply"] = {"ms": pc_ms.get(f"form{plan.fft_form}"),
+                                "graph_ms": pc_ms.get(f"form{plan.fft_form}_graph"), "form": plan.fft_form,
+                                "forms_ms": pc_ms,
+                                "note": "form 0: warp-level passes, form 1: CTA-level Stockham passes; ms: calls "
+                                        "launched from the host one by one, graph_ms: the same calls replayed from a "
+                                        "CUDA graph (GPU time without the host launch cost)"}
     roof = {"bound": "alu", "kernel": f"{dom} ({' + '.join(call_kernels[dom])})", "path":
             f"symmetric, {plan.symmetric_jobs} jobs for {N} angles" if sym else "per angle",
             "achieved": fmas / kt[dom] / 1e9, "peak": fma_peak / 1e9, "unit": "GFMA/s",

@@ -830,8 +830,14 @@ __device__ __forceinline__ void wfft_adj(float2 (&v)[V], int lane, float2 *buf, 
     dft_dit<V, S>(v);
 }
 
-constexpr int WFFT_COL_WARPS = 4;   // adjacent columns per CTA (they share L2 sectors)
-constexpr int WFFT_INV_WARPS = 2;   // row pairs per CTA of the inverse row pass
+#ifndef CTR_WFFT_COL_WARPS
+#define CTR_WFFT_COL_WARPS 4
+#endif
+#ifndef CTR_WFFT_INV_WARPS
+#define CTR_WFFT_INV_WARPS 2
+#endif
+constexpr int WFFT_COL_WARPS = CTR_WFFT_COL_WARPS;   // adjacent columns per CTA (they share L2 sectors)
+constexpr int WFFT_INV_WARPS = CTR_WFFT_INV_WARPS;   // row pairs per CTA of the inverse row pass
 
 // Forward row pass of the real-input form, one row pair per CTA: the CTA's 256 threads
 // form the real inputs of rows 2b and 2b + 1 (the fold of the backprojection's partial
