@@ -836,8 +836,10 @@ __device__ __forceinline__ void wfft_adj(float2 (&v)[V], int lane, float2 *buf, 
 #ifndef CTR_WFFT_INV_WARPS
 #define CTR_WFFT_INV_WARPS 2
 #endif
-constexpr int WFFT_COL_WARPS = CTR_WFFT_COL_WARPS;   // adjacent columns per CTA (they share L2 sectors)
-constexpr int WFFT_INV_WARPS = CTR_WFFT_INV_WARPS;   // row pairs per CTA of the inverse row pass
+// adjacent columns per CTA of the column pass (they share L1 sectors; at V = 32 at most 4,
+// the static shared-memory limit) and row pairs per CTA of the inverse row pass
+template <int V> constexpr int wfft_col_warps() { return V >= 32 && CTR_WFFT_COL_WARPS > 4 ? 4 : CTR_WFFT_COL_WARPS; }
+constexpr int WFFT_INV_WARPS = CTR_WFFT_INV_WARPS;
 
 // Forward row pass of the real-input form, one row pair per CTA: the CTA's 256 threads
 // form the real inputs of rows 2b and 2b + 1 (the fold of the backprojection's partial
@@ -855,8 +857,35 @@ k_wfft_rows_fwd_packed(RowsInput<float> src, float2 *cbuf, const float2 *__restr
     pdl_wait();
     pdl_trigger();
     stage_tw<n>(s_tw, tw);
-    staged_copy(2 * n, [&](int e) { return rows_input_value(src, n, ra + (e >= n ? 1 : 0), e & (n - 1)); },
-                [&](int e, float x) { s_in[e] = x; });
+    if (src.part && src.orbit) {
+        // the fold of the partial planes four columns at a time (16-byte loads; each column's
+        // sum in the order of orbit_fold), then the step-A epilogue per pixel
+        const size_t nn = (size_t)n * n;
+        for (int e4 = threadIdx.x; e4 < n / 2; e4 += blockDim.x) {
+            const int row = ra + (4 * e4 >= n ? 1 : 0), col = (4 * e4) & (n - 1);
+            const size_t e = (size_t)row * n + col, em = (size_t)(n - 1 - row) * n + col;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int z = 0; z < src.groups; ++z) {
+                const float *pz = src.part + (size_t)z * 4 * nn;
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(pz + e));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(pz + nn + em));
+                const float4 c = __ldg(reinterpret_cast<const float4 *>(pz + 2 * nn + e));
+                const float4 d = __ldg(reinterpret_cast<const float4 *>(pz + 3 * nn + em));
+                acc.x += a.x + b.x + c.x + d.x;
+                acc.y += a.y + b.y + c.y + d.y;
+                acc.z += a.z + b.z + c.z + d.z;
+                acc.w += a.w + b.w + c.w + d.w;
+            }
+            float *dst = s_in + 4 * e4;
+            dst[0] = bp_epilogue_value(src.epi, n, row, col, acc.x);
+            dst[1] = bp_epilogue_value(src.epi, n, row, col + 1, acc.y);
+            dst[2] = bp_epilogue_value(src.epi, n, row, col + 2, acc.z);
+            dst[3] = bp_epilogue_value(src.epi, n, row, col + 3, acc.w);
+        }
+    } else {
+        staged_copy(2 * n, [&](int e) { return rows_input_value(src, n, ra + (e >= n ? 1 : 0), e & (n - 1)); },
+                    [&](int e, float x) { s_in[e] = x; });
+    }
     __syncthreads();
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
@@ -878,14 +907,15 @@ k_wfft_rows_fwd_packed(RowsInput<float> src, float2 *cbuf, const float2 *__restr
 // Column pass of the real-input form: one warp per stored column c < n/2 + 1: forward
 // DFT, times the real symbol sym[k][c] in the scrambled layout, inverse DFT.
 template <int V>
-__global__ void __launch_bounds__(32 * WFFT_COL_WARPS)
+__global__ void __launch_bounds__(32 * wfft_col_warps<V>())
 k_wfft_cols_packed(float2 *cbuf, const float *__restrict__ sym, const float2 *__restrict__ tw)
 {
     constexpr int n = 32 * V, H = n / 2 + 1, G = 32 / V;
-    __shared__ __align__(16) float2 s_buf[WFFT_COL_WARPS][(32 + G) * V];
+    constexpr int CW = wfft_col_warps<V>();
+    __shared__ __align__(16) float2 s_buf[CW][(32 + G) * V];
     __shared__ __align__(16) float2 s_tw[n];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * WFFT_COL_WARPS + w;
+    const int c = blockIdx.x * CW + w;
     const bool live = c < H;                             // warp-uniform
     pdl_wait();
     pdl_trigger();
@@ -986,7 +1016,8 @@ void launch_wfft_packed(bool pdl, const RowsInput<float> &src, float2 *cb, const
 {
     constexpr int n = 32 * V, H = n / 2 + 1;
     launch_pdl(pdl, k_wfft_rows_fwd_packed<V>, dim3(n / 2), dim3(FFT_THREADS), 0, s, src, cb, tw);
-    launch_pdl(pdl, k_wfft_cols_packed<V>, dim3((H + WFFT_COL_WARPS - 1) / WFFT_COL_WARPS), dim3(32 * WFFT_COL_WARPS), 0,
+    constexpr int CW = wfft_col_warps<V>();
+    launch_pdl(pdl, k_wfft_cols_packed<V>, dim3((H + CW - 1) / CW), dim3(32 * CW), 0,
                s, cb, sym, tw);
     launch_pdl(pdl, k_wfft_rows_inv_packed<V>, dim3(n / (2 * WFFT_INV_WARPS)), dim3(32 * WFFT_INV_WARPS), 0, s,
                (const float2 *)cb, tw, out, mode, outT, dout, outh, outTh);
