@@ -1194,10 +1194,10 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
     float4 *raw = reinterpret_cast<float4 *>(smem_raw);                   // [2][JCH][WR], channels in x..w
     const int la = bz * jobs_per_group;
     const int nj = max(0, min(n_jobs, la + jobs_per_group) - la);
-    long long *sPb = reinterpret_cast<long long *>(raw + 2 * OBP_AJCH * WR);
-    long long *sC = sPb + jobs_per_group;
-    long long *sS = sC + jobs_per_group;
-    int *sK = reinterpret_cast<int *>(sS + jobs_per_group);
+    // per job one 16-byte record {fraction of the tile's first P, S, C - 1} (on the symmetric
+    // path 0 <= S < 2^32 and 1 <= C <= 2^32): one shared load per warp and job
+    uint4 *sT = reinterpret_cast<uint4 *>(raw + 2 * OBP_AJCH * WR);
+    int *sK = reinterpret_cast<int *>(sT + jobs_per_group);
     int *sL = sK + jobs_per_group;                                        // [job][channel]
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int i0 = by * 32, j0 = bx * 32;
@@ -1207,9 +1207,7 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
         const long long P00 = (long long)i0 * Cc + (long long)j0 * Sc + jb.am.Op;
         const long long kmin = P00 >> 32;                                // Cc, Sc >= 0: the tile's minimum
         sK[t] = (int)kmin;
-        sPb[t] = P00 - (kmin << 32);
-        sC[t] = Cc;
-        sS[t] = Sc;
+        sT[t] = make_uint4((unsigned)(P00 - (kmin << 32)), (unsigned)Sc, (unsigned)(Cc - 1), 0u);
         for (int c = 0; c < 4; ++c) sL[4 * t + c] = jb.l[c];
     }
     __syncthreads();
@@ -1236,8 +1234,9 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
         const float4 *buf = raw + (size_t)(ch & 1) * OBP_AJCH * WR;
 #pragma unroll 2
         for (int a = 0; a < na; ++a) {
-            const long long C = sC[a0 + a];
-            long long P = sPb[a0 + a] + (long long)ty * C + (long long)tx * sS[a0 + a];
+            const uint4 tj = sT[a0 + a];
+            const long long C = (long long)tj.z + 1;
+            long long P = (long long)tj.x + (long long)ty * C + (long long)tx * (long long)tj.y;
             const long long D = C * OBP_TY;
             const float4 *row = buf + a * WR;
 #pragma unroll
