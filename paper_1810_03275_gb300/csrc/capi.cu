@@ -122,6 +122,9 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
         const long long C = geo[l].C, S = geo[l].S;
         const long long aC = C < 0 ? -C : C, aS = S < 0 ? -S : S;
         const long long a = aC >= aS ? aC : aS, b = aC >= aS ? aS : aC;
+        // the symmetric kernels track 32-bit remainders and step at most one bin per row:
+        // 1 <= a <= 2^32 (h <= ds makes it so; anything else takes the per-angle path)
+        if (a < 1 || a > (1ll << 32)) return CTR_OK;
         const long long img[4][2] = {{a, b}, {-a, b}, {b, a}, {-b, a}};
         bool placed = false, member = false;
         std::vector<int> &js = by_pair[{a, b}];
