@@ -158,7 +158,9 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
             jobs.push_back(jb);
         }
     }
-    if (2 * jobs.size() > (size_t)N) return CTR_OK;
+    // at least two angles per job on average; an odd view count pairs every angle but 0 with
+    // its mirror pi - theta ((N + 1) / 2 jobs), which the pair-job kernels serve at half cost
+    if (2 * jobs.size() > (size_t)N + 1) return CTR_OK;
     ctr_status st;
     void *tmp = nullptr;
     if ((st = alloc(p, &tmp, sizeof(OrbitJob) * jobs.size())) != CTR_OK) return st;
@@ -180,6 +182,12 @@ ctr_status build_orbit_jobs(ctr_plan *p, const std::vector<AngleGeom> &geo)
     CTR_CUDA(cudaMemcpy(p->d_jobs, jobs.data(), sizeof(OrbitJob) * jobs.size(), cudaMemcpyHostToDevice));
     p->n_jobs = (int)jobs.size();
     p->orbit = true;
+    {
+        size_t pairs = 0;                          // jobs whose angles sit in channels {0, 1} or {2, 3} only
+        for (const OrbitJob &jb : jobs)
+            if ((jb.l[2] < 0 && jb.l[3] < 0) || (jb.l[0] < 0 && jb.l[1] < 0)) ++pairs;
+        p->pair_jobs = 2 * pairs > jobs.size() ? 1 : 0;
+    }
     // the staged forward shape only where its double-buffered window fits one CTA's shared
     // memory (stg_wmax = 0: shape (4, 1) unavailable on this plan)
     p->stg_wmax = stg_window(jobs, n, M);

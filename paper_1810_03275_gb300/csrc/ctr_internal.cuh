@@ -278,6 +278,7 @@ struct SliceDesc {
     FftPasses fp;
     float *u, *uT, *y1, *y2, *v2b, *bp_part;   // bp_part: angle-group images, or the symmetric planes
     int orbit;                    // symmetric projector path (per_group, bp_groups count jobs)
+    int pair_jobs;                // the symmetric projectors' pair-job variants
     int twist;                    // the circulant preconditioner's 1-D transform in the column pass
     float *ub;                    // Alg. 5: bar u (updated by the TV stage); null for Alg. 4
     int n_jobs;
@@ -369,6 +370,7 @@ struct ctr_plan {
     ctr::OrbitJob *d_jobs = nullptr;
     void *ubar = nullptr;                // n*n float4 orbit image
     int obp_groups = 1;                  // job groups of the symmetric backprojection
+    int pair_jobs = 0;                   // most jobs are pair jobs: both projectors take their pair variants
     int obp_cap = 1;                     // groups the partial-plane workspace has room for
     void *obp_part = nullptr;            // obp_groups * 4 * n*n partial planes
     void *d_twiddle = nullptr;  // n complex exp(-2 pi i t/n)

@@ -755,26 +755,49 @@ __device__ __forceinline__ void acc4(float4 &Su, float4 &Sf, float4 v, float f)
     Sf.w = fmaf(f, v.w, Sf.w);
 }
 
+// What the march reads at a pixel: the whole orbit record (four channels), or for a pair
+// job (whose angles all sit in channels {0, 1} or {2, 3}) the two live channels of the
+// FP32 record as one 8-byte load.  acc_v accumulates each channel exactly as acc4 does.
+template <typename R>
+struct RecLoad {
+    using V = float4;
+    const R *__restrict__ ub;
+    __device__ __forceinline__ float4 operator()(int off) const { return rec_f32(ub[off]); }
+    __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+struct PairLoad {
+    using V = float2;
+    const float2 *__restrict__ ub2;     // (const float2 *)ub + h: channels 2h, 2h + 1 of each record
+    __device__ __forceinline__ float2 operator()(int off) const { return ub2[2 * (size_t)off]; }
+    __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+};
+__device__ __forceinline__ void acc_v(float4 &Su, float4 &Sf, float4 v, float f) { acc4(Su, Sf, v, f); }
+__device__ __forceinline__ void acc_v(float2 &Su, float2 &Sf, float2 v, float f)
+{
+    Su = fadd2(Su, v);
+    Sf = ffma2(make_float2(f, f), v, Sf);
+}
+
 // The canonical march (flip 0, B >= 0) over `rows` rows of the orbit image; the
 // state and the second-pixel rule are those of march32.
-template <bool BPOS, bool CHECK, typename R>
-__device__ __forceinline__ void march_orbit(const R *__restrict__ ub, int n, int rows, unsigned &r, int &q,
-                                            int &off, unsigned A32, unsigned lim, unsigned B32, unsigned thr,
-                                            float4 &Su, float4 &Sf)
+template <bool BPOS, bool CHECK, typename L>
+__device__ __forceinline__ void march_orbit(const L &ld, int n, int rows, unsigned &r, int &q, int &off,
+                                            unsigned A32, unsigned lim, unsigned B32, unsigned thr,
+                                            typename L::V &Su, typename L::V &Sf)
 {
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    using V = typename L::V;
 #pragma unroll FWD_UNROLL_ORBIT
     for (int rr = 0; rr < rows; ++rr) {
-        float4 v1, v2;
+        V v1, v2;
         if constexpr (CHECK) {
-            v1 = ((unsigned)q < (unsigned)n) ? rec_f32(ub[off]) : zero;
-            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? rec_f32(ub[off + 1]) : zero;
+            v1 = ((unsigned)q < (unsigned)n) ? ld(off) : L::zero();
+            v2 = (r < lim && (unsigned)(q + 1) < (unsigned)n) ? ld(off + 1) : L::zero();
         } else {
-            v1 = rec_f32(ub[off]);
-            v2 = r < lim ? rec_f32(ub[off + 1]) : zero;
+            v1 = ld(off);
+            v2 = r < lim ? ld(off + 1) : L::zero();
         }
-        acc4(Su, Sf, v1, one_plus_frac32u(r));
-        acc4(Su, Sf, v2, one_plus_frac32u(r + A32));
+        acc_v(Su, Sf, v1, one_plus_frac32u(r));
+        acc_v(Su, Sf, v2, one_plus_frac32u(r + A32));
         if constexpr (BPOS) {
             const bool s = r >= thr;
             r += s ? B32 - A32 : B32;
@@ -789,10 +812,9 @@ __device__ __forceinline__ void march_orbit(const R *__restrict__ ub, int n, int
     }
 }
 
-template <bool BPOS, typename R>
-__device__ __forceinline__ void march_orbit_rows(const R *__restrict__ ub, int n, long long K,
-                                                 const AngleMarch &am, int mlo, int mhi, int ilo, int ihi,
-                                                 float4 &Su, float4 &Sf)
+template <bool BPOS, typename L>
+__device__ __forceinline__ void march_orbit_rows(const L &ub, int n, long long K, const AngleMarch &am, int mlo,
+                                                 int mhi, int ilo, int ihi, typename L::V &Su, typename L::V &Sf)
 {
     const long long A = am.A, B = am.B;
     const long long qa = ceil_div_ll(K - (long long)mlo * B - am.Op, A);
@@ -863,7 +885,7 @@ constexpr int ORBIT_THREADS = 32 * ORBIT_SLOTS * ORBIT_SEGS;
 // Warp w of the CTA takes job by*ORBIT_SLOTS + w % ORBIT_SLOTS, bins bx*31 + [0, 31) and
 // the (w / ORBIT_SLOTS)-th of ORBIT_SEGS equal parts of the rows its rays cross; the parts' sums
 // are added in a fixed order through shared memory.
-template <typename S, bool NAMED = false, int SEGS = ORBIT_SEGS, int SLOTS = ORBIT_SLOTS>
+template <typename S, bool NAMED = false, int SEGS = ORBIT_SEGS, int SLOTS = ORBIT_SLOTS, bool PAIRS = false>
 __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::type *__restrict__ ubar, int n,
                                                    int n_jobs, int M, const OrbitJob *__restrict__ jobs,
                                                    const ForwardEpi<float> &epi, int bx, int by)
@@ -903,8 +925,30 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
             }
             if (mlo_w <= mhi_w) {
                 const long long K = (long long)k << 32;
-                if (am.B > 0) march_orbit_rows<true>(ubar, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
-                else march_orbit_rows<false>(ubar, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                // a pair job (channels {0, 1} or {2, 3} only; odd view counts give only these)
+                // reads and accumulates its two live channels; the others stay zero as they
+                // would in the four-channel march
+                bool done = false;
+                if constexpr (PAIRS && std::is_same<S, float>::value) {
+                    const int pair = (ls.z < 0 && ls.w < 0) ? 1 : ((ls.x < 0 && ls.y < 0) ? 2 : 0);
+                    if (pair) {
+                        const PairLoad ld{reinterpret_cast<const float2 *>(ubar) + (pair - 1)};
+                        float2 su = make_float2(0.f, 0.f), sf = su;
+                        if (am.B > 0) march_orbit_rows<true>(ld, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, su, sf);
+                        else march_orbit_rows<false>(ld, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, su, sf);
+                        if (pair == 1) {
+                            Su.x = su.x; Su.y = su.y; Sf.x = sf.x; Sf.y = sf.y;
+                        } else {
+                            Su.z = su.x; Su.w = su.y; Sf.z = sf.x; Sf.w = sf.y;
+                        }
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    const RecLoad<typename OrbitRec<S>::type> ld{ubar};
+                    if (am.B > 0) march_orbit_rows<true>(ld, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                    else march_orbit_rows<false>(ld, n, K, am, mlo_w, mhi_w, ilo_w, ihi_w, Su, Sf);
+                }
             }
         }
     }
@@ -935,14 +979,14 @@ __device__ __forceinline__ void forward_orbit_body(const typename OrbitRec<S>::t
 // SLOTS adjacent jobs per CTA (their rays nearly coincide, so they share the orbit
 // image's lines in L1) and SEGS warps per job splitting its rows; the shape is selected per
 // plan (ctr_plan_set_fwd_shape).  The resident-CTA hint keeps 32 warps per SM.
-template <typename S, int SLOTS, int SEGS>
+template <typename S, int SLOTS, int SEGS, bool PAIRS = false>
 __global__ void __launch_bounds__(32 * SLOTS * SEGS, CTR_ORBIT_MINB * ORBIT_SLOTS * ORBIT_SEGS / (SLOTS * SEGS))
 k_forward_orbit(const typename OrbitRec<S>::type *__restrict__ ubar, int n, int n_jobs, int M,
                 const OrbitJob *__restrict__ jobs, ForwardEpi<float> epi)
 {
     pdl_wait();
     pdl_trigger();
-    forward_orbit_body<S, false, SEGS, SLOTS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
+    forward_orbit_body<S, false, SEGS, SLOTS, PAIRS>(ubar, n, n_jobs, M, jobs, epi, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1117,8 +1161,11 @@ void launch_forward_orbit_shape(const ctr_plan *p, const typename OrbitRec<S>::t
                                 cudaStream_t s)
 {
     const dim3 grid(fwd_grid_x(p->M), (p->n_jobs + SLOTS - 1) / SLOTS);
-    launch_pdl(p->pdl != 0, k_forward_orbit<S, SLOTS, SEGS>, grid, dim3(32 * SLOTS * SEGS), 0, s, ub, p->n, p->n_jobs,
-               p->M, (const OrbitJob *)p->d_jobs, epi);
+    auto kern = k_forward_orbit<S, SLOTS, SEGS, false>;
+    if constexpr (std::is_same<S, float>::value)                  // pair-job variant (two live channels)
+        if (p->pair_jobs) kern = k_forward_orbit<S, SLOTS, SEGS, true>;
+    launch_pdl(p->pdl != 0, kern, grid, dim3(32 * SLOTS * SEGS), 0, s, ub, p->n, p->n_jobs, p->M,
+               (const OrbitJob *)p->d_jobs, epi);
 }
 
 template <typename S>
@@ -1184,6 +1231,7 @@ size_t obp_smem(int wstride, int jobs_per_group)
 // chunk c is computed, so no global-load latency sits between chunks.  Each bin holds
 // the four channels' g as one float4; a (pixel, job) reads bins b and b + 1 and
 // interpolates g_b + f (g_{b+1} - g_b) per channel.
+template <bool PAIRS>
 __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int n, int M, int wstride,
                                                int jobs_per_group, int n_jobs, const OrbitJob *__restrict__ jobs,
                                                float (&acc)[OBP_R][4], int bx, int by, int bz)
@@ -1194,8 +1242,9 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
     float4 *raw = reinterpret_cast<float4 *>(smem_raw);                   // [2][JCH][WR], channels in x..w
     const int la = bz * jobs_per_group;
     const int nj = max(0, min(n_jobs, la + jobs_per_group) - la);
-    // per job one 16-byte record {fraction of the tile's first P, S, C - 1} (on the symmetric
-    // path 0 <= S < 2^32 and 1 <= C <= 2^32): one shared load per warp and job
+    // per job one 16-byte record {fraction of the tile's first P, S, C - 1, pair} (on the
+    // symmetric path 0 <= S < 2^32 and 1 <= C <= 2^32; pair = 1 or 2 for a job whose angles
+    // sit in channels {0, 1} or {2, 3} only, 0 otherwise): one shared load per warp and job
     uint4 *sT = reinterpret_cast<uint4 *>(raw + 2 * OBP_AJCH * WR);
     int *sK = reinterpret_cast<int *>(sT + jobs_per_group);
     int *sL = sK + jobs_per_group;                                        // [job][channel]
@@ -1207,7 +1256,8 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
         const long long P00 = (long long)i0 * Cc + (long long)j0 * Sc + jb.am.Op;
         const long long kmin = P00 >> 32;                                // Cc, Sc >= 0: the tile's minimum
         sK[t] = (int)kmin;
-        sT[t] = make_uint4((unsigned)(P00 - (kmin << 32)), (unsigned)Sc, (unsigned)(Cc - 1), 0u);
+        const unsigned pair = !PAIRS ? 0u : (jb.l[2] < 0 && jb.l[3] < 0) ? 1u : ((jb.l[0] < 0 && jb.l[1] < 0) ? 2u : 0u);
+        sT[t] = make_uint4((unsigned)(P00 - (kmin << 32)), (unsigned)Sc, (unsigned)(Cc - 1), pair);
         for (int c = 0; c < 4; ++c) sL[4 * t + c] = jb.l[c];
     }
     __syncthreads();
@@ -1215,10 +1265,14 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
     auto prefetch = [&](int ch) {
         const int a0 = ch * OBP_AJCH, na = min(OBP_AJCH, nj - a0);
         float *dst = reinterpret_cast<float *>(raw + (size_t)(ch & 1) * OBP_AJCH * WR);
+        // four-channel jobs: slot w = the four channels at bin k + w; pair jobs: slot w = the two
+        // live channels at bins k + w and k + w + 1 (lo and hi of one interpolation)
         for (int e = threadIdx.x; e < na * WR * 4; e += NT) {
             const int c = e & 3, rest = e >> 2;
             const int a = rest / WR, w = rest - a * WR;
-            const int k = sK[a0 + a] + w, l = sL[4 * (a0 + a) + c];
+            const unsigned pair = PAIRS ? sT[a0 + a].w : 0u;
+            const int ch = pair ? 2 * (int)(pair - 1) + (c & 1) : c;
+            const int k = sK[a0 + a] + w + (pair ? (c >> 1) : 0), l = sL[4 * (a0 + a) + ch];
             const bool ok = l >= 0 && k >= 0 && k < M;
             cp_async4(dst + (size_t)rest * 4 + c, ok ? g + (size_t)l * M + k : g, ok);
         }
@@ -1239,6 +1293,28 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
             long long P = (long long)tj.x + (long long)ty * C + (long long)tx * (long long)tj.y;
             const long long D = C * OBP_TY;
             const float4 *row = buf + a * WR;
+            if (PAIRS && tj.w) {                                          // pair job (CTA-uniform)
+                const bool p01 = tj.w == 1;
+#pragma unroll
+                for (int r = 0; r < OBP_R; ++r) {
+                    const int b = (int)(P >> 32);
+                    const float f = one_plus_frac32(P) - 1.f;
+                    const float4 v = row[b];                              // (lo, lo, hi, hi)
+                    const float2 lo = make_float2(v.x, v.y);
+                    const float2 t = ffma2(make_float2(f, f), fsub2(make_float2(v.z, v.w), lo), lo);
+                    if (p01) {
+                        const float2 s = fadd2(make_float2(acc[r][0], acc[r][1]), t);
+                        acc[r][0] = s.x;
+                        acc[r][1] = s.y;
+                    } else {
+                        const float2 s = fadd2(make_float2(acc[r][2], acc[r][3]), t);
+                        acc[r][2] = s.x;
+                        acc[r][3] = s.y;
+                    }
+                    P += D;
+                }
+                continue;
+            }
 #pragma unroll
             for (int r = 0; r < OBP_R; ++r) {
                 const int b = (int)(P >> 32);
@@ -1262,7 +1338,7 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
     cp_async_wait<0>();
 }
 
-template <typename S>
+template <typename S, bool PAIRS = false>
 __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group,
                                          int n_jobs, const OrbitJob *__restrict__ jobs, float *__restrict__ part,
                                          int bx, int by, int bz)
@@ -1286,7 +1362,7 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
     for (int r = 0; r < OBP_R; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
 
     if constexpr (sizeof(S) == 4 && OBP_ASYNC)
-        obp_body_async(g, n, M, wstride, jobs_per_group, n_jobs, jobs, acc, bx, by, bz);
+        obp_body_async<PAIRS>(g, n, M, wstride, jobs_per_group, n_jobs, jobs, acc, bx, by, bz);
     else
     for (int c0 = la; c0 < lb; c0 += OBP_JCH) {
         const int na = min(OBP_JCH, lb - c0);
@@ -1376,14 +1452,14 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
     }
 }
 
-template <typename S>
+template <typename S, bool PAIRS>
 __global__ void __launch_bounds__(32 * OBP_TY, CTR_OBP_MINB)
 k_backproject_orbit(const S *__restrict__ g, int n, int M, int wstride, int jobs_per_group, int n_jobs,
                     const OrbitJob *__restrict__ jobs, float *__restrict__ part)
 {
     pdl_wait();
     pdl_trigger();
-    obp_body<S>(g, n, M, wstride, jobs_per_group, n_jobs, jobs, part, blockIdx.x, blockIdx.y, blockIdx.z);
+    obp_body<S, PAIRS>(g, n, M, wstride, jobs_per_group, n_jobs, jobs, part, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The fold of the symmetric backprojection's partial planes, then the
@@ -1433,7 +1509,8 @@ k_backproject_orbit_batch(const SliceDesc *__restrict__ sd, const int *__restric
     const int local = blockIdx.x - prefix[s];
     const int bx = local % d.bp_tiles_x, rest = local / d.bp_tiles_x;
     const int by = rest % d.bp_tiles_y, bz = rest / d.bp_tiles_y;
-    obp_body<float>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
+    if (d.pair_jobs) obp_body<float, true>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
+    else obp_body<float, false>(d.y1, d.n, d.M, d.wstride, d.per_group, d.n_jobs, d.jobs, d.bp_part, bx, by, bz);
 }
 
 __global__ void __launch_bounds__(256)
@@ -1451,7 +1528,11 @@ k_forward_orbit_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ 
     const int s = find_slice(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
     const int local = blockIdx.x - prefix[s];
-    forward_orbit_body<float>(d.ubar, d.n, d.n_jobs, d.M, d.jobs, d.fwe, local % d.fwd_chunks, local / d.fwd_chunks);
+    if (d.pair_jobs)
+        forward_orbit_body<float, false, ORBIT_SEGS, ORBIT_SLOTS, true>(d.ubar, d.n, d.n_jobs, d.M, d.jobs, d.fwe,
+                                                                       local % d.fwd_chunks, local / d.fwd_chunks);
+    else
+        forward_orbit_body<float>(d.ubar, d.n, d.n_jobs, d.M, d.jobs, d.fwe, local % d.fwd_chunks, local / d.fwd_chunks);
 }
 
 __global__ void __launch_bounds__(FWD_THREADS)
@@ -1503,7 +1584,10 @@ ctr_status bp_impl(const ctr_plan *p, const S *g, const BackprojEpi<T> &epi, cud
             float *part = (float *)p->obp_part;
             p->launches++;
             const int jpg = (p->n_jobs + G - 1) / G;
-            launch_pdl(p->pdl != 0, k_backproject_orbit<S>, grid, dim3(32 * OBP_TY), obp_smem(p->wstride, jpg), s,
+            auto kern = k_backproject_orbit<S, false>;
+            if constexpr (sizeof(S) == 4)                                 // pair-job variant: FP32 staging only
+                if (p->pair_jobs) kern = k_backproject_orbit<S, true>;
+            launch_pdl(p->pdl != 0, kern, grid, dim3(32 * OBP_TY), obp_smem(p->wstride, jpg), s,
                        g, p->n, p->M, p->wstride, jpg, p->n_jobs, (const OrbitJob *)p->d_jobs, part);
             CTR_CHECK_LAUNCH("k_backproject_orbit");
             if (!defer_reduce) {
@@ -1585,8 +1669,9 @@ ctr_status configure_radon(const ctr_plan *p)
     const size_t smem = bp_smem<T>(p);
     ctr_status st = raise_smem_limit(k_backproject<T, T>, smem);
     const size_t osm = p->orbit ? obp_smem(p->wstride, p->n_jobs) : 0;   // any group split
-    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float>, osm);
-    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16>, osm);
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float, false>, osm);
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<float, true>, osm);
+    if (st == CTR_OK && p->orbit) st = raise_smem_limit(k_backproject_orbit<__nv_bfloat16, false>, osm);
     if constexpr (sizeof(T) == 4)
         if (st == CTR_OK) st = raise_smem_limit(k_backproject<float, __nv_bfloat16>, smem);
     if (st == CTR_OK && p->orbit && p->stg_wmax > 0) {

@@ -1549,6 +1549,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.M = p->M;
         d.wstride = p->wstride;
         d.orbit = p->orbit ? 1 : 0;
+        d.pair_jobs = p->orbit ? p->pair_jobs : 0;
         d.twist = prm.precond == 2 ? 1 : 0;
         d.n_jobs = p->n_jobs;
         d.jobs = p->d_jobs;

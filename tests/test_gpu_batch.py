@@ -23,8 +23,12 @@ def ct():
 def _slices():
     # uneven sizes (radix 2 and 3), view counts and bins; one with no metal
     spec = [(32, 40, 46, 1), (48, 25, 69, 2), (64, 90, 91, 0), (96, 57, 136, 2), (24, 33, 34, 1)]
-    return [phantom.make_problem(f"s{i}", n, N, M, seed=20 + i, n_ellipses=3, n_metal=m, noise="gaussian",
-                                 alpha=0.05 * (i + 1)) for i, (n, N, M, m) in enumerate(spec)]
+    probs = [phantom.make_problem(f"s{i}", n, N, M, seed=20 + i, n_ellipses=3, n_metal=m, noise="gaussian",
+                                  alpha=0.05 * (i + 1)) for i, (n, N, M, m) in enumerate(spec)]
+    # slices 1 and 4: angles offset from the uniform grid (no symmetric images: per-angle path)
+    for i in (1, 4):
+        probs[i].theta = probs[i].theta + 0.013
+    return probs
 
 
 def test_batch_matches_single_slices_and_oracle(ct):
@@ -33,8 +37,9 @@ def test_batch_matches_single_slices_and_oracle(ct):
     batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
     fs = [to_dev(p.f, torch.float32) for p in probs]
     ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
-    # even view counts take the symmetric path, odd ones the per-angle path: both in one batch
-    assert [pl.symmetric_jobs > 0 for pl in batch.plans] == [True, False, True, False, False]
+    # uniform angle sets take the symmetric path (slice 3, odd, as pair jobs), offset sets the
+    # per-angle path: both in one batch
+    assert [pl.symmetric_jobs > 0 for pl in batch.plans] == [True, False, True, True, False]
     betas, cs = [], []
     for p in probs:
         geo = oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta)

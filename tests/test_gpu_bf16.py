@@ -39,13 +39,13 @@ def ct():
 @pytest.mark.parametrize("geom", [(64, 90, 95, "uniform"), (37, 50, 53, "uniform"), (256, 120, 363, "uniform"),
                                   (64, 45, 95, "uniform"), (48, 30, 70, "random")])
 def test_bf16_projectors_match_oracle_on_rounded_inputs(ct, geom):
-    """Even uniform angle counts take the symmetric path (bfloat16 orbit image), odd
-    counts and random angles the per-angle path."""
+    """Uniform angle counts take the symmetric path (bfloat16 orbit image; odd counts as
+    pair jobs), random angles the per-angle path."""
     import torch
     n, N, M, kind = geom
     th = np.arange(N) * np.pi / N if kind == "uniform" else np.random.default_rng(N).uniform(-np.pi, 2 * np.pi, N)
     plan = ct.Plan(n, N, M, angles=th, dtype="bf16")
-    assert (plan.symmetric_jobs > 0) == (kind == "uniform" and N % 2 == 0)
+    assert (plan.symmetric_jobs > 0) == (kind == "uniform")
     geo = oracle.Geometry(n, N, M, theta=th)
     rng = np.random.default_rng(n)
     u = _bf16_round(rng.uniform(0, 1, (n, n)))

@@ -53,18 +53,21 @@ def test_headline_workload_iterates_match_oracle(ct):
 
 
 def _config3_slices():
-    spec = [(256, 1440), (512, 361), (1024, 180)]
-    return [phantom.make_problem(f"c3_{n}", n, N, int(np.ceil(np.sqrt(2.0) * n)), seed=31 + i, n_ellipses=4,
-                                 n_metal=2, noise="poisson", alpha=0.3) for i, (n, N) in enumerate(spec)]
+    spec = [(256, 1440), (512, 361), (1024, 180), (384, 241)]
+    probs = [phantom.make_problem(f"c3_{n}", n, N, int(np.ceil(np.sqrt(2.0) * n)), seed=31 + i, n_ellipses=4,
+                                  n_metal=2, noise="poisson", alpha=0.3) for i, (n, N) in enumerate(spec)]
+    probs[3].theta = probs[3].theta + 0.013      # off the uniform grid: the per-angle path
+    return probs
 
 
 def test_batched_form_at_config3_sizes(ct):
-    """One batch of 256^2/1440, 512^2/361 and 1024^2/180 (symmetric and per-angle slices):
-    30 iterations equal the same slices solved alone (<= 2e-6) and the oracle (<= 1e-5)."""
+    """One batch of 256^2/1440, 512^2/361 (odd: pair jobs), 1024^2/180 and 384^2/241 with
+    angles off the uniform grid (per-angle path): 30 iterations equal the same slices solved
+    alone (<= 2e-6) and the oracle (<= 1e-5)."""
     import torch
     probs = _config3_slices()
     batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
-    assert [pl.symmetric_jobs > 0 for pl in batch.plans] == [True, False, True]
+    assert [pl.symmetric_jobs > 0 for pl in batch.plans] == [True, True, True, False]
     fs = [to_dev(p.f, torch.float32) for p in probs]
     ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
     consts = [_oracle_constants(oracle.Geometry(p.n, p.n_angles, p.n_bins, theta=p.theta), np.pi / p.n, 15)

@@ -59,14 +59,15 @@ def test_forward_adjoint_match_oracle(ct, geom, dtype):
 
 
 def test_symmetric_path_selection(ct):
-    """FP32 and BF16 plans with uniform angles over [0, pi) and an even count take the
-    symmetric path (at most one job per two angles); odd counts, angles outside [0, pi),
-    FP64 plans and pixels smaller than ds/2 (three per interval) project angle by angle."""
+    """FP32 and BF16 plans with uniform angles over [0, pi) take the symmetric path: an even
+    count in jobs of up to four angles, an odd count in (N + 1) / 2 pair jobs (theta with
+    pi - theta); angles outside [0, pi), FP64 plans and pixels smaller than ds/2 (three per
+    interval) project angle by angle."""
     uni = lambda N: np.arange(N) * (np.pi / N)
     p = ct.Plan(64, 90, 95, angles=uni(90))
     assert 0 < p.symmetric_jobs <= 45
     assert ct.Plan(512, 720, 729, angles=uni(720)).symmetric_jobs == 181
-    assert ct.Plan(64, 45, 95, angles=uni(45)).symmetric_jobs == 0
+    assert ct.Plan(64, 45, 95, angles=uni(45)).symmetric_jobs == 23
     assert ct.Plan(64, 33, 95, angles=_angles(33, "random", 1)).symmetric_jobs == 0
     assert ct.Plan(64, 90, 95, angles=uni(90), dtype="f64").symmetric_jobs == 0
     assert ct.Plan(64, 90, 95, angles=uni(90), dtype="bf16").symmetric_jobs > 0
@@ -219,3 +220,27 @@ def test_staged_shape_refused_where_window_exceeds_shared_memory(ct):
     u = torch.ones((n, n), device="cuda")
     g = to_np(plan.rh_forward(u))
     assert np.all(np.isfinite(g)) and g.max() > 0
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("n,N,M", [(64, 91, 95), (130, 181, 185), (512, 721, 729)])
+def test_odd_view_count_symmetric_path(ct, n, N, M, dtype):
+    """Odd view counts take the symmetric path with pair jobs (channels {0, 1} or {2, 3}
+    only): both projectors match the oracle, and the operators stay exact transposes."""
+    import torch
+    th = np.arange(N) * (np.pi / N)
+    plan = ct.Plan(n, N, M, angles=th, dtype=dtype)
+    assert plan.symmetric_jobs == (N + 1) // 2
+    geo = oracle.Geometry(n, N, M, theta=th)
+    rng = np.random.default_rng(N)
+    u = rng.standard_normal((n, n))
+    g = rng.standard_normal((N, M))
+    if dtype == "bf16":                       # bfloat16-representable inputs: equal to FP32 up to rounding
+        u = torch.as_tensor(u, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+        g = torch.as_tensor(g, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    gf = to_np(plan.rh_forward(to_dev(u, torch.float32).to(plan.op_dtype)))
+    ub = to_np(plan.rh_adjoint(to_dev(g, torch.float32).to(plan.op_dtype)))
+    assert rel_l2(gf, oracle.rh_forward(u, geo)) < 1e-5
+    assert rel_l2(ub, oracle.rh_adjoint(g, geo)) < 1e-5
+    lhs, rhs = float(np.sum(gf * g)), float(np.sum(u * ub))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))

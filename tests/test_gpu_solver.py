@@ -158,3 +158,16 @@ def test_benchmark_configuration_properties(ct):
     assert d["objective"] < 0.05 * d0["objective"]
     assert d["violation"] < 0.2 * d0["violation"]
     assert d["rel_change"] < 1e-2
+
+
+@pytest.mark.parametrize("n,N,M", [(64, 91, 95), (96, 121, 137)])
+def test_odd_view_count_pair_jobs(ct, n, N, M):
+    """Odd view counts on [0, pi): every angle but 0 pairs only with its mirror pi - theta,
+    so the symmetric path runs (N + 1) / 2 pair jobs (two live channels each).  Iterates after
+    1 and 20 FP32 iterations equal the oracle's."""
+    res, plan, *_ = _run_both(ct, n, N, M, "f32", [1, 20])
+    assert plan.symmetric_jobs == (N + 1) // 2
+    for k, ref, got in res:
+        assert rel_l2(got["u"], ref.u) < 1e-5, (k, rel_l2(got["u"], ref.u))
+        assert rel_l2(got["Ru"], ref.Ru) < 1e-5
+        assert rel_l2(got["v1b"], ref.v1b) < 1e-5
