@@ -270,6 +270,7 @@ struct SliceDesc {
     int bp_tiles_x, bp_tiles_y;   // backprojection tiles
     int fwd_chunks;               // forward-projector CTAs per angle
     int rpc, cw;                  // FFT rows / columns per CTA
+    int packed, prp, pcw;         // real-input FFT form (row pairs, n/2 + 1 columns): rows / columns per CTA
     const AngleGeom *geom;
     const AngleMarch *march;
     float2 *cbuf;
@@ -496,6 +497,9 @@ size_t obp_smem_bytes(int wstride, int jobs_per_group);   // the symmetric backp
 void bp_tiles(int n, int &tx, int &ty);
 int fft_rows_per_cta(int n);
 bool wfft_supported(const ctr_plan *p);        // the warp-level preconditioner passes apply
+int fft_packed_rows_per_cta(const ctr_plan *p); // real-input form of the CTA-level passes: row pairs x 2 per CTA
+int fft_packed_cols_per_cta(const ctr_plan *p); // ... stored columns per CTA
+size_t fft_packed_smem(const ctr_plan *p, int which);   // ... dynamic shared memory (0 rows, 1 columns)
 size_t fft_rows_smem(int n, size_t esize);   // dynamic shared memory of the row passes
 size_t fft_cols_smem(int n, size_t esize);   // ... and of the column pass
 int fft_cols_per_cta(int n, size_t esize);
@@ -529,6 +533,7 @@ struct ctr_batch {
     // iteration form: 0 = one launch per stage (graph-captured), 1 = one persistent
     // cooperative launch per iteration (k_batch_iteration)
     int mode = 0;
+    int fft_packed = 1;                  // the stage tables use the real-input FFT form where slices allow it
     unsigned long long spin_limit = 1ull << 26;   // polls per grid barrier before giving up
     ctr::GridBarrier *d_gb = nullptr;
     int persist_grid = 0;                         // resident CTAs of the persistent kernel (0: unavailable)

@@ -1047,7 +1047,8 @@ k_fft_rows_fwd_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
         src.orbit = d.orbit;
         src.epi = d.bpe;
     }
-    fft_rows_fwd_body<float>(src, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
+    if (d.packed) fft_rows_fwd_packed_body<float>(src, d.cbuf, d.n, d.prp, d.fp, d.tw, blockIdx.x - prefix[s]);
+    else fft_rows_fwd_body<float>(src, d.cbuf, d.n, d.rpc, d.fp, d.tw, blockIdx.x - prefix[s]);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS)
@@ -1055,7 +1056,9 @@ k_fft_cols_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ prefi
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, blockIdx.x - prefix[s], d.twist);
+    if (d.packed) fft_cols_body<float>(d.cbuf, d.sym, d.n, d.pcw, d.fp, d.tw, blockIdx.x - prefix[s], 0, d.n / 2 + 1,
+                                       d.n / 2 + 1);
+    else fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, blockIdx.x - prefix[s], d.twist);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS)
@@ -1063,8 +1066,12 @@ k_fft_rows_inv_batch(const SliceDesc *__restrict__ sd, const int *__restrict__ p
 {
     const int s = find_slice_fft(prefix, ns, blockIdx.x);
     const SliceDesc &d = sd[s];
-    fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr, nullptr,
-                             nullptr, blockIdx.x - prefix[s]);
+    if (d.packed)
+        fft_rows_inv_packed_body<float>(d.cbuf, d.n, d.prp, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr,
+                                        nullptr, nullptr, blockIdx.x - prefix[s]);
+    else
+        fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr, nullptr,
+                                 nullptr, blockIdx.x - prefix[s]);
 }
 
 // Preconditioner symbols (Alg. 4, Sec. 4.3.1), with 1/n^2 of the inverse DFT:
@@ -1147,6 +1154,9 @@ size_t packed_cols_smem(const ctr_plan *p) { return (2 * (size_t)packed_cols_per
 }  // namespace
 
 bool wfft_supported(const ctr_plan *p) { return wfft_v(p) != 0; }
+int fft_packed_rows_per_cta(const ctr_plan *p) { return packed_rows_per_cta(p); }
+int fft_packed_cols_per_cta(const ctr_plan *p) { return packed_cols_per_cta(p); }
+size_t fft_packed_smem(const ctr_plan *p, int which) { return which == 0 ? packed_rows_smem(p) : packed_cols_smem(p); }
 
 size_t fft_smem_bytes(const ctr_plan *p, int which)
 {

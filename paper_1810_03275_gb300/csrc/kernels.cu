@@ -97,20 +97,26 @@ __device__ __forceinline__ void persist_stage_block(int stg, const SliceDesc *__
             src.orbit = d.orbit;
             src.epi = d.bpe;
         }
-        fft_rows_fwd_body<float>(src, d.cbuf, d.n, d.rpc, d.fp, d.tw, vb - pre[s]);
+        if (d.packed) fft_rows_fwd_packed_body<float>(src, d.cbuf, d.n, d.prp, d.fp, d.tw, vb - pre[s]);
+        else fft_rows_fwd_body<float>(src, d.cbuf, d.n, d.rpc, d.fp, d.tw, vb - pre[s]);
         return;
     }
     case BS_FFT_COLS: {
         const int s = find_slice_fft(pre, ns, vb);
         const SliceDesc &d = sd[s];
-        fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, vb - pre[s], d.twist);
+        if (d.packed) fft_cols_body<float>(d.cbuf, d.sym, d.n, d.pcw, d.fp, d.tw, vb - pre[s], 0, d.n / 2 + 1, d.n / 2 + 1);
+        else fft_cols_body<float>(d.cbuf, d.sym, d.n, d.cw, d.fp, d.tw, vb - pre[s], d.twist);
         return;
     }
     case BS_FFT_ROWS_INV: {
         const int s = find_slice_fft(pre, ns, vb);
         const SliceDesc &d = sd[s];
-        fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr, nullptr,
-                                 nullptr, vb - pre[s]);
+        if (d.packed)
+            fft_rows_inv_packed_body<float>(d.cbuf, d.n, d.prp, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr,
+                                            nullptr, nullptr, vb - pre[s]);
+        else
+            fft_rows_inv_body<float>(d.cbuf, d.n, d.rpc, d.fp, d.tw, d.u, 1, d.orbit ? nullptr : d.uT, nullptr, nullptr,
+                                     nullptr, vb - pre[s]);
         return;
     }
     case BS_ORBIT: {

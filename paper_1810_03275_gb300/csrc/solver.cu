@@ -1494,11 +1494,22 @@ ctr_status launch_batch_tv(const SliceDesc *sd, const int *prefix, int ns, int b
 // last iteration per slice so that each slice keeps the dual certificates for its
 // diagnostics.
 // ------------------------------------------------------------------------------
+bool batch_slice_packed(const ctr_batch *b, const ctr_plan *p);
+ctr_status batch_prepare(ctr_batch *b);
+
 ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const *mask, const double *alpha,
                        const double *delta, int iters, const ctr_params &prm, const double *betas, const double *cs,
                        float *const *u_out, ctr_diag *diags, cudaStream_t s)
 {
     const int ns = (int)b->plans.size();
+    // the circulant preconditioner's twisted column pass needs the complex form: the stage
+    // tables follow the kind of this solve
+    const int packed = prm.precond == 2 ? 0 : 1;
+    if (b->fft_packed != packed) {
+        b->fft_packed = packed;
+        ctr_status sp = batch_prepare(b);
+        if (sp != CTR_OK) return sp;
+    }
     std::vector<SliceDesc> hd(ns);
     std::vector<IterArgs<float>> args(ns);
     std::vector<double> beta(ns), c(ns);
@@ -1561,6 +1572,9 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
         d.fwd_chunks = fwd_grid_x(p->M);
         d.rpc = fft_rows_per_cta(p->n);
         d.cw = fft_cols_per_cta(p->n, 4);
+        d.packed = batch_slice_packed(b, p);
+        d.prp = fft_packed_rows_per_cta(p);
+        d.pcw = fft_packed_cols_per_cta(p);
         d.geom = p->d_geom;
         d.march = p->d_march;
         d.cbuf = (float2 *)p->cbuf;
@@ -1640,7 +1654,7 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
             return fail(CTR_ETIMEOUT, "persistent batched iteration: a grid barrier's bounded wait ran out");
     } else {
         const int blk = prm.graph_block;
-        std::vector<double> key = {6.0, (double)blk, (double)ns};
+        std::vector<double> key = {6.0, (double)blk, (double)ns, (double)b->fft_packed};
         for (int stg = 0; stg < BS_COUNT; ++stg) {
             key.push_back((double)b->blocks[stg]);
             key.push_back((double)b->smem[stg]);
@@ -1668,6 +1682,14 @@ ctr_status batch_solve(ctr_batch *b, const float *const *f, const uint8_t *const
     return CTR_OK;
 }
 
+// A slice's preconditioner stages take the real-input form when the batch's tables use it
+// and the first pass reads the backprojection's partial images (the symmetric path, or
+// several angle groups): a real input, never the complex buffer the form overwrites.
+bool batch_slice_packed(const ctr_batch *b, const ctr_plan *p)
+{
+    return b->fft_packed && (p->orbit || p->bp_groups > 1);
+}
+
 // Block tables and shared-memory sizes of the batched stages.
 ctr_status batch_prepare(ctr_batch *b)
 {
@@ -1679,13 +1701,15 @@ ctr_status batch_prepare(ctr_batch *b)
         int tx, ty;
         bp_tiles(p->n, tx, ty);
         const size_t nn = (size_t)p->n * p->n;
-        const int rpc = fft_rows_per_cta(p->n), cw = fft_cols_per_cta(p->n, 4);
+        const bool packed = batch_slice_packed(b, p);
+        const int rpc = packed ? fft_packed_rows_per_cta(p) : fft_rows_per_cta(p->n);
+        const int cw = fft_cols_per_cta(p->n, 4), pcw = fft_packed_cols_per_cta(p);
         int cnt[BS_COUNT];
         const int t32 = (p->n + 31) / 32;
         cnt[BS_BP] = p->orbit ? 0 : tx * ty * p->bp_groups;
         cnt[BS_BP_SYM] = p->orbit ? tx * ty * p->obp_groups : 0;
         cnt[BS_FFT_ROWS] = (p->n + rpc - 1) / rpc;
-        cnt[BS_FFT_COLS] = (p->n + cw - 1) / cw;
+        cnt[BS_FFT_COLS] = packed ? (p->n / 2 + 1 + pcw - 1) / pcw : (p->n + cw - 1) / cw;
         cnt[BS_FFT_ROWS_INV] = cnt[BS_FFT_ROWS];
         cnt[BS_ORBIT] = p->orbit ? t32 * t32 : 0;
         cnt[BS_FWD] = p->orbit ? 0 : fwd_grid_x(p->M) * fwd_grid_y(p->N);
@@ -1694,7 +1718,8 @@ ctr_status batch_prepare(ctr_batch *b)
         for (int stg = 0; stg < BS_COUNT; ++stg) pre[(size_t)stg * (ns + 1) + i + 1] = pre[(size_t)stg * (ns + 1) + i] + cnt[stg];
         const size_t smb = p->orbit ? 0 : bp_smem_bytes(p->wstride), smo = p->orbit ? obp_smem_bytes(p->wstride, (p->n_jobs + p->obp_groups - 1) / p->obp_groups) : 0;
         if (smo > b->smem[BS_BP_SYM]) b->smem[BS_BP_SYM] = smo;
-        const size_t smr = fft_rows_smem(p->n, sizeof(float)), smc = fft_cols_smem(p->n, sizeof(float));
+        const size_t smr = packed ? fft_packed_smem(p, 0) : fft_rows_smem(p->n, sizeof(float));
+        const size_t smc = packed ? fft_packed_smem(p, 1) : fft_cols_smem(p->n, sizeof(float));
         if (smb > b->smem[BS_BP]) b->smem[BS_BP] = smb;
         if (smr > b->smem[BS_FFT_ROWS]) b->smem[BS_FFT_ROWS] = smr;
         if (smr > b->smem[BS_FFT_ROWS_INV]) b->smem[BS_FFT_ROWS_INV] = smr;
