@@ -162,7 +162,9 @@ unsigned long long ctr_plan_launch_count(const ctr_plan *plan);
  * (-b, a) (e.g. theta, pi - theta, pi/2 - theta, pi/2 + theta) share one job, one ray
  * march and one staged detector coordinate per pixel.  FP32 and BF16 plans with
  * ds >= h take the path when every angle is such an image of its canonical pair and the jobs hold
- * two angles or more on average (uniform angles over [0, pi) with an even count).
+ * two angles or more on average, the unpaired angle 0 of an odd count aside (uniform angles
+ * over [0, pi): an even count in jobs of up to four angles, an odd count in (N + 1) / 2 jobs
+ * of theta and pi - theta, which the FP32 kernels run as two-channel "pair" jobs).
  * Results equal those of the per-angle path up to the order of FP32 summation. */
 int ctr_plan_symmetric_jobs(const ctr_plan *plan);
 
