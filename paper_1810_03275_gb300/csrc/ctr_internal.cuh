@@ -190,6 +190,11 @@ __device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int 
     return s;
 }
 
+// Row and column of the flat pixel index e of an n-wide image in 32-bit arithmetic (every
+// plan has n^2 < 2^32; a size_t division is a much longer instruction sequence).
+__device__ __forceinline__ int pix_i(size_t e, int n) { return (int)((unsigned)e / (unsigned)n); }
+__device__ __forceinline__ int pix_j(size_t e, int n) { return (int)((unsigned)e % (unsigned)n); }
+
 // grad_h u at pixel (i, j): forward differences with Neumann boundary (Sec. 3.1)
 template <typename T>
 __device__ __forceinline__ void grad_at(const T *__restrict__ u, int n, int i, int j, T inv_h, T &gx, T &gy)

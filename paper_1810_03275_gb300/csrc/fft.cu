@@ -1085,7 +1085,7 @@ __global__ void k_symbols(T *sym, T *symh, int n, double sigma, double tau, doub
     const double pi = 3.14159265358979323846;
     const double inv_n2 = 1.0 / ((double)n * (double)n);
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         const int ii = (2 * i < n) ? i : i - n;    // wrapped signed index (Nyquist sign irrelevant)
         const int jj = (2 * j < n) ? j : j - n;
         const double xi = 2.0 * pi * ii / n, xj = 2.0 * pi * jj / n;

@@ -132,7 +132,7 @@ __device__ __forceinline__ void persist_stage_block(int stg, const SliceDesc *__
         const TvDualJob<float> job{d.u, d.n, d.sigma, d.tau, d.lam, d.inv_h, d.v2b, d.y2, nullptr, d.ub};
         const size_t nn = (size_t)d.n * d.n, nb = (size_t)(pre[s + 1] - pre[s]);
         for (size_t e = (size_t)(vb - pre[s]) * blockDim.x + tid; e < nn; e += nb * blockDim.x)
-            tv_dual_at(job, (int)(e / d.n), (int)(e % d.n));
+            tv_dual_at(job, pix_i(e, d.n), pix_j(e, d.n));
         return;
     }
     case BS_FWD: {

@@ -78,6 +78,13 @@ constexpr int FWD_UNROLL = CTR_FWD_UNROLL;   // rows per unrolled step of the ra
 #endif
 constexpr int FWD_UNROLL_ORBIT = CTR_FWD_UNROLL_ORBIT;
 
+// x / d for x, d >= 0 with x d < 2^32 as the high word of x m, m = floor((2^32 - 1) / d) + 1
+// (then m - 2^32 / d < 1 and the error x (m - 2^32/d) / 2^32 stays below 1/d, so the floor is
+// exact).  The staging loops divide element indices by a row width once per copied element;
+// a runtime integer division costs an instruction sequence, this one multiply.
+__device__ __forceinline__ unsigned udiv_magic(unsigned d) { return d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int udiv_fast(int x, int d, unsigned m) { return d <= 1 ? x : (int)__umulhi((unsigned)x, m); }
+
 // 1 + frac(p) in [1, 2) from the low 32 bits of P (F = 32): the top 23 fraction
 // bits become the mantissa of a float, so the weight is exact and identical in
 // both projectors.
@@ -173,8 +180,9 @@ __device__ __forceinline__ void bp_body(const S *__restrict__ g, int n, int N, i
             sS[threadIdx.x] = ag.S;
         }
         body_sync<NAMED>();
+        const unsigned mw = udiv_magic((unsigned)wstride);
         for (int e = threadIdx.x; e < na * wstride; e += NT) {
-            const int a = e / wstride;
+            const int a = udiv_fast(e, wstride, mw);
             const int k = sK[a] + (e - a * wstride);
             const S *row = g + (size_t)(l0 + a) * M;
             const T g0 = (k >= 0 && k < M) ? (T)ldv(row + k) : T(0);
@@ -225,7 +233,7 @@ __device__ __forceinline__ void bp_reduce_body(const T *__restrict__ part, int g
     for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x) {
         T s = part[e];
         for (int z = 1; z < groups; ++z) s += part[(size_t)z * nn + e];
-        bp_epilogue(epi, n, (int)(e / n), (int)(e % n), s);
+        bp_epilogue(epi, n, pix_i(e, n), pix_j(e, n), s);
     }
 }
 
@@ -1267,9 +1275,10 @@ __device__ __forceinline__ void obp_body_async(const float *__restrict__ g, int 
         float *dst = reinterpret_cast<float *>(raw + (size_t)(ch & 1) * OBP_AJCH * WR);
         // four-channel jobs: slot w = the four channels at bin k + w; pair jobs: slot w = the two
         // live channels at bins k + w and k + w + 1 (lo and hi of one interpolation)
+        const unsigned mw = udiv_magic((unsigned)WR);
         for (int e = threadIdx.x; e < na * WR * 4; e += NT) {
             const int c = e & 3, rest = e >> 2;
-            const int a = rest / WR, w = rest - a * WR;
+            const int a = udiv_fast(rest, WR, mw), w = rest - a * WR;
             const unsigned pair = PAIRS ? sT[a0 + a].w : 0u;
             const int ch = pair ? 2 * (int)(pair - 1) + (c & 1) : c;
             const int k = sK[a0 + a] + w + (pair ? (c >> 1) : 0), l = sL[4 * (a0 + a) + ch];
@@ -1380,9 +1389,10 @@ __device__ __forceinline__ void obp_body(const S *__restrict__ g, int n, int M, 
         if (threadIdx.x < 4 * na) sL[threadIdx.x] = jobs[c0 + (threadIdx.x >> 2)].l[threadIdx.x & 3];
         __syncthreads();
         float *stf = reinterpret_cast<float *>(stage);
+        const unsigned mw = udiv_magic((unsigned)wstride);
         for (int e = threadIdx.x; e < na * wstride * 4; e += NT) {
             const int c = e & 3, rest = e >> 2;
-            const int a = rest / wstride, w = rest - a * wstride;
+            const int a = udiv_fast(rest, wstride, mw), w = rest - a * wstride;
             const int k = sK[a] + w, l = sL[4 * a + c];
             const S *row = g + (size_t)(l < 0 ? 0 : l) * M;
             const float g0 = (l >= 0 && k >= 0 && k < M) ? ldv(row + k) : 0.f;
@@ -1471,7 +1481,7 @@ k_bp_fold(const float *__restrict__ part, int groups, int n, BackprojEpi<float> 
     pdl_trigger();
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         bp_epilogue(epi, n, i, j, orbit_fold(part, groups, n, i, j));
     }
 }

@@ -77,7 +77,7 @@ __global__ void k_grad(const T *__restrict__ u, int n, T inv_h, T *px)
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         T gx, gy;
-        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        grad_at(u, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
         px[e] = gx;
         px[e + nn] = gy;
     }
@@ -89,7 +89,7 @@ __global__ void k_div(const T *__restrict__ px, int n, T inv_h, T *d)
     const size_t nn = (size_t)n * n;
     const T *py = px + nn;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         T d1 = T(0), d2 = T(0);
         if (n >= 2) {
             d1 = (i == 0) ? px[e] : (i == n - 1 ? -px[e - n] : px[e] - px[e - n]);
@@ -106,7 +106,7 @@ __global__ void k_init_y2(const T *__restrict__ u, const T *__restrict__ v2b, in
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         T gx, gy;
-        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        grad_at(u, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
         y2[e] = v2b[e] + st * gx;
         y2[e + nn] = v2b[e + nn] + st * gy;
     }
@@ -121,7 +121,7 @@ __device__ __forceinline__ void tv_dual_body(const T *__restrict__ u, int n, T s
     const size_t nn = (size_t)n * n;
     const TvDualJob<T> job{u, n, sigma, tau, lam, inv_h, v2b, y2, t2, ub};
     for (size_t e = b * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)nb * blockDim.x)
-        tv_dual_at(job, (int)(e / n), (int)(e % n));
+        tv_dual_at(job, pix_i(e, n), pix_j(e, n));
 }
 
 template <typename T>
@@ -153,7 +153,7 @@ k_cp_tv(const T *__restrict__ ub, int n, T tau, T lam, T inv_h, T *w)
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         T gx, gy;
-        grad_at(ub, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        grad_at(ub, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
         const T zx = w[e] + tau * gx, zy = w[e + nn] + tau * gy;
         T tx = T(0), ty = T(0);
         if (lam > T(0)) {
@@ -180,7 +180,7 @@ __global__ void k_kernel_sym(const T *__restrict__ y, int n, int c, int flat, T 
 {
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         if (flat) {
             const long long N = (long long)nn, t = i + (long long)n * j, pc = c + (long long)n * c;
             const long long ta = (t + pc) % N, tb = ((pc - t) % N + N) % N;
@@ -362,7 +362,7 @@ k_diag_img(const T *__restrict__ u, const T *__restrict__ du, const T *__restric
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; e < nn; e += (size_t)gridDim.x * RED_THREADS) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         const double c = u[e];
         const double gx = (i < n - 1) ? ((double)u[e + n] - c) * inv_h : 0.0;
         const double gy = (j < n - 1) ? ((double)u[e + 1] - c) * inv_h : 0.0;
@@ -877,7 +877,7 @@ __global__ void k_admm_resid(const T *__restrict__ w, const T *__restrict__ ew, 
         if (e < nm) y[e] = w[e] - ew[e] - Ru[e];
         if (e < nn) {
             T gx, gy;
-            grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+            grad_at(u, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
             q[e] = v[e] - ev[e] - gx;
             q[e + nn] = v[e + nn] - ev[e + nn] - gy;
         }
@@ -939,7 +939,7 @@ __global__ void k_admm_img(const T *__restrict__ u, int n, T inv_h, T thr, T *v,
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
         T gx, gy;
-        grad_at(u, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        grad_at(u, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
         const T ax = gx + ev[e], ay = gy + ev[e + nn];
         const T nrm = sqrt(ax * ax + ay * ay);
         const T fac = nrm > thr ? T(1) - thr / nrm : T(0);
@@ -1075,7 +1075,7 @@ __global__ void k_mark_dilate(const T *__restrict__ u, int n, double thr, int r,
 {
     const size_t nn = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
+        const int i = pix_i(e, n), j = pix_j(e, n);
         bool hit = false;
         for (int di = -r; di <= r && !hit; ++di) {
             const int ii = i + di;
@@ -1370,7 +1370,7 @@ k_vjp_tv(const T *__restrict__ u1, const T *__restrict__ v2b0, int n, T sigma, T
     double v[1] = {0.0};
     for (size_t e = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; e < nn; e += (size_t)gridDim.x * RED_THREADS) {
         T gx, gy;
-        grad_at(u1, n, (int)(e / n), (int)(e % n), inv_h, gx, gy);
+        grad_at(u1, n, pix_i(e, n), pix_j(e, n), inv_h, gx, gy);
         const T zx = v2b0[e] + T(2) * st * gx, zy = v2b0[e + nn] + T(2) * st * gy;
         const T ax = b2[e], ay = b2[e + nn];
         const T nz = sqrt(zx * zx + zy * zy);
