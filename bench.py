@@ -410,6 +410,30 @@ def run_ops(args):
     return 0
 
 
+def run_batch_step(args):
+    """The 64-slice batch of `forms.batched` (a profiler's target): per-slice set-up and a
+    warm-up solve outside, then one batched solve of `--batch-step` iterations inside the NVTX
+    range `batch_step`."""
+    import torch
+    from paper_1810_03275_gb300 import ctrecon as ct
+    from paper_1810_03275_gb300 import phantom
+    probs = phantom.config_batched(64, iters=30, n_ellipses=2, n_metal=1)
+    batch = ct.Batch([dict(n=p.n, n_angles=p.n_angles, n_bins=p.n_bins, angles=p.theta) for p in probs])
+    fs = [torch.as_tensor(p.f, dtype=torch.float32, device="cuda") for p in probs]
+    ms = [torch.as_tensor(p.mask, device="cuda") for p in probs]
+    al, de = [p.alpha for p in probs], [p.delta for p in probs]
+    betas = [pl.power_beta(10) for pl in batch.plans]
+    cs = [1.05 * pl.power_lambda(b, np.pi / pl.n, 10) for pl, b in zip(batch.plans, betas)]
+    prm = ct.default_params()
+    batch.solve(fs, ms, al, de, 3, params=prm, betas=betas, cs=cs, want_diag=False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("batch_step")
+    batch.solve(fs, ms, al, de, args.batch_step, params=prm, betas=betas, cs=cs, want_diag=False)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    return 0
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return 0
@@ -455,13 +479,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16-vs-FP32 2048^2 timing")
+    ap.add_argument("--batch-step", type=int, default=0, help="K: only run the 64-slice batched solve of K "
+                                                                 "iterations in an NVTX range (profiling)")
     ap.add_argument("--shape", default=None, help="G,J,S: backprojection groups and forward shape instead of the "
                                                   "tuner (for runs under a profiler)")
-    ap.add_argument("--ops", default=None, help="n,views,bins,dtype[,JxS]: only run R_h and R_h^* of that plan "
-                    "--steps times (for a profiler; JxS a forward shape), print nothing")
+    ap.add_argument("--ops", default=None, help="n,views,bins,dtype[,JxS]: only run R_h, R_h^* and the "
+                    "preconditioner of that plan --steps times (for a profiler; JxS a forward shape), print nothing")
     args = ap.parse_args()
     if args.ops:
         return run_ops(args)
+    if args.batch_step > 0:
+        return run_batch_step(args)
     if args.warmup < 3 and args.impl == "ours" and args.iters is None:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     rank, ws, local = dist_init()
