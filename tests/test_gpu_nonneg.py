@@ -132,3 +132,16 @@ def test_alg5_refused_where_not_covered(ct):
     with pytest.raises(Exception, match="nonneg"):
         batch.solve([torch.zeros((20, 47), device="cuda")], [None], [0.1], [-1.0], 2,
                     params=ct.default_params(nonneg=3))
+
+
+def test_alg5_at_a_warp_fft_size(ct):
+    """Alg. 5 on a 256 x 256 FP32 plan (symmetric path, warp-level preconditioner passes whose
+    first pass folds the partial planes with the u >= 0 epilogue): iterates after 1 and 10
+    iterations equal the oracle's."""
+    res, plan = _run(ct, 256, 90, 363, "uniform", "f32", [1, 10])
+    assert plan.symmetric_jobs > 0 and plan.fft_form == 0
+    for k, ref, got in res:
+        assert rel_l2(got["u"], ref.u) < 1e-5, (k, rel_l2(got["u"], ref.u))
+        if k > 1:
+            assert rel_l2(got["ub"], ref.ub) < 1e-5
+        assert rel_l2(got["v1b"], ref.v1b) < 1e-5

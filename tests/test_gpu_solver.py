@@ -160,7 +160,7 @@ def test_benchmark_configuration_properties(ct):
     assert d["rel_change"] < 1e-2
 
 
-@pytest.mark.parametrize("n,N,M", [(64, 91, 95), (96, 121, 137)])
+@pytest.mark.parametrize("n,N,M", [(64, 91, 95), (96, 121, 137), (256, 181, 363)])
 def test_odd_view_count_pair_jobs(ct, n, N, M):
     """Odd view counts on [0, pi): every angle but 0 pairs only with its mirror pi - theta,
     so the symmetric path runs (N + 1) / 2 pair jobs (two live channels each).  Iterates after
