@@ -77,3 +77,28 @@ def test_first_iterate_from_zero():
     st = oracle.pdrq_solve(geo, desc, 0.3, 1, sigma=sigma, tau=0.5, eps=0.2, beta=beta, c=1.0)
     assert np.all(st.u == 0)
     np.testing.assert_allclose(st.v1b, -sigma * (f / beta) / (1 + sigma), rtol=1e-14)
+
+
+def test_objective_converges_to_the_minimiser_value():
+    """The thesis's convergence record is the objective of (C_h) along the iterates: on a
+    small feasible problem it approaches the value at the Chambolle-Pock minimiser, with the
+    distance shrinking by orders of magnitude from 30 to 300 to 1500 iterations and the
+    iterates becoming feasible."""
+    geo, f, mask, desc = _feasible_problem(n=8, N=12, M=13, seed=3)
+    alpha, eps, tau = 0.5, np.pi / geo.n, 1 / np.sqrt(8)
+    beta = oracle.power_beta(geo, 60)
+    c = oracle.power_c(geo, beta, eps, 60)
+    u_cp = oracle.cp_solve(geo, desc, alpha, 20000, beta=beta)
+    ref = oracle.diagnostics(geo, desc, alpha, u_cp, beta=beta)["objective"]
+    errs, viol = [], []
+    st = None
+    done = 0
+    for k in (30, 300, 1500):
+        st = oracle.pdrq_solve(geo, desc, alpha, k - done, sigma=1.0, tau=tau, eps=eps, beta=beta, c=c, state=st)
+        done = k
+        d = oracle.diagnostics(geo, desc, alpha, st.u, beta=beta)
+        errs.append(abs(d["objective"] - ref) / ref)
+        viol.append(d["violation"])
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 1e-6 and errs[2] < 1e-3 * errs[0]
+    assert viol[2] < 1e-6
