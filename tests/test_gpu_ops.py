@@ -117,3 +117,17 @@ def test_fft_forms_agree(ct, n):
                                   params=p2)
             us.append(to_np(u))
         assert rel_l2(us[0], us[1]) < (2e-6 if dtype == "f32" else 2e-3), dtype
+
+
+def test_precond_apply_largest_image(ct):
+    """M^{-1} y at 4096 x 4096 (the CTA-level passes in real-input form) against numpy's FFT
+    on the oracle's symbol."""
+    import torch
+    n = 4096
+    plan = ct.Plan(n, 4, 5)
+    sigma, tau, c, eps = 1.3, 0.35, 0.7, np.pi / n
+    prm = ct.default_params(sigma=sigma, tau=tau, c=c, eps=eps)
+    y = np.random.default_rng(n).standard_normal((n, n))
+    got = to_np(plan.precond_apply(to_dev(y, torch.float32), prm))
+    ref = oracle.precond_apply(y, oracle.precond_symbol(n, sigma, tau, c, eps))
+    assert rel_l2(got, ref) < 2e-6
