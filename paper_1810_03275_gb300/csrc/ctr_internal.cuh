@@ -195,6 +195,27 @@ __device__ __forceinline__ float orbit_fold(const float *__restrict__ part, int 
 __device__ __forceinline__ int pix_i(size_t e, int n) { return (int)((unsigned)e / (unsigned)n); }
 __device__ __forceinline__ int pix_j(size_t e, int n) { return (int)((unsigned)e % (unsigned)n); }
 
+// The same fold for the four adjacent pixels (i, col .. col + 3) (col and n multiples of 4)
+// with 16-byte loads; each pixel's sum in the order of orbit_fold.
+__device__ __forceinline__ float4 orbit_fold4(const float *__restrict__ part, int groups, int n, int i, int col)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t e = (size_t)i * n + col, em = (size_t)(n - 1 - i) * n + col;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int z = 0; z < groups; ++z) {
+        const float *pz = part + (size_t)z * 4 * nn;
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(pz + e));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(pz + nn + em));
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(pz + 2 * nn + e));
+        const float4 d = __ldg(reinterpret_cast<const float4 *>(pz + 3 * nn + em));
+        s.x += a.x + b.x + c.x + d.x;
+        s.y += a.y + b.y + c.y + d.y;
+        s.z += a.z + b.z + c.z + d.z;
+        s.w += a.w + b.w + c.w + d.w;
+    }
+    return s;
+}
+
 // grad_h u at pixel (i, j): forward differences with Neumann boundary (Sec. 3.1)
 template <typename T>
 __device__ __forceinline__ void grad_at(const T *__restrict__ u, int n, int i, int j, T inv_h, T &gx, T &gy)

@@ -292,14 +292,41 @@ __device__ __forceinline__ void fft_rows_fwd_packed_body(const RowsInput<T> &src
     const int cc = (cnt + 1) / 2;
     const int H = n / 2 + 1;
     const unsigned mn = div_magic(n);
-    staged_copy(cc * n, [&](int e) {
-        const int c = fast_div(e, n, mn), j = e - c * n;
-        const int ra = r0 + 2 * c;
-        T2 v;
-        v.x = rows_input_value(src, n, ra, j);
-        v.y = ra + 1 < r0 + cnt ? rows_input_value(src, n, ra + 1, j) : T(0);
-        return v;
-    }, [&](int e, T2 v) { a[e] = v; });
+    bool folded = false;
+    if constexpr (sizeof(T) == 4) {
+        if (src.part && src.orbit && (n & 3) == 0) {
+            // the fold of the partial planes four columns at a time (16-byte loads), then
+            // the step-A epilogue per pixel
+            const int q = n / 4;
+            const unsigned mq = div_magic(q);
+            for (int e4 = threadIdx.x; e4 < cc * q; e4 += blockDim.x) {
+                const int c = fast_div(e4, q, mq), j = 4 * (e4 - c * q);
+                const int ra = r0 + 2 * c;
+                const bool two = ra + 1 < r0 + cnt;
+                const float4 fa = orbit_fold4(src.part, src.groups, n, ra, j);
+                const float4 fb = two ? orbit_fold4(src.part, src.groups, n, ra + 1, j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                T2 *dst = a + (size_t)c * n + j;
+                dst[0].x = bp_epilogue_value(src.epi, n, ra, j, fa.x);
+                dst[1].x = bp_epilogue_value(src.epi, n, ra, j + 1, fa.y);
+                dst[2].x = bp_epilogue_value(src.epi, n, ra, j + 2, fa.z);
+                dst[3].x = bp_epilogue_value(src.epi, n, ra, j + 3, fa.w);
+                dst[0].y = two ? bp_epilogue_value(src.epi, n, ra + 1, j, fb.x) : T(0);
+                dst[1].y = two ? bp_epilogue_value(src.epi, n, ra + 1, j + 1, fb.y) : T(0);
+                dst[2].y = two ? bp_epilogue_value(src.epi, n, ra + 1, j + 2, fb.z) : T(0);
+                dst[3].y = two ? bp_epilogue_value(src.epi, n, ra + 1, j + 3, fb.w) : T(0);
+            }
+            folded = true;
+        }
+    }
+    if (!folded)
+        staged_copy(cc * n, [&](int e) {
+            const int c = fast_div(e, n, mn), j = e - c * n;
+            const int ra = r0 + 2 * c;
+            T2 v;
+            v.x = rows_input_value(src, n, ra, j);
+            v.y = ra + 1 < r0 + cnt ? rows_input_value(src, n, ra + 1, j) : T(0);
+            return v;
+        }, [&](int e, T2 v) { a[e] = v; });
     __syncthreads();
     T2 *res = fft_smem<T>(a, b, n, cc, n, fp, -1, stw);
     const unsigned mh = div_magic(H);
@@ -860,22 +887,9 @@ k_wfft_rows_fwd_packed(RowsInput<float> src, float2 *cbuf, const float2 *__restr
     if (src.part && src.orbit) {
         // the fold of the partial planes four columns at a time (16-byte loads; each column's
         // sum in the order of orbit_fold), then the step-A epilogue per pixel
-        const size_t nn = (size_t)n * n;
         for (int e4 = threadIdx.x; e4 < n / 2; e4 += blockDim.x) {
             const int row = ra + (4 * e4 >= n ? 1 : 0), col = (4 * e4) & (n - 1);
-            const size_t e = (size_t)row * n + col, em = (size_t)(n - 1 - row) * n + col;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int z = 0; z < src.groups; ++z) {
-                const float *pz = src.part + (size_t)z * 4 * nn;
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(pz + e));
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(pz + nn + em));
-                const float4 c = __ldg(reinterpret_cast<const float4 *>(pz + 2 * nn + e));
-                const float4 d = __ldg(reinterpret_cast<const float4 *>(pz + 3 * nn + em));
-                acc.x += a.x + b.x + c.x + d.x;
-                acc.y += a.y + b.y + c.y + d.y;
-                acc.z += a.z + b.z + c.z + d.z;
-                acc.w += a.w + b.w + c.w + d.w;
-            }
+            const float4 acc = orbit_fold4(src.part, src.groups, n, row, col);
             float *dst = s_in + 4 * e4;
             dst[0] = bp_epilogue_value(src.epi, n, row, col, acc.x);
             dst[1] = bp_epilogue_value(src.epi, n, row, col + 1, acc.y);
